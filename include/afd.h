@@ -1,0 +1,195 @@
+/*
+ * afd.h -- C ABI of the assembly-free deflated finite element hot path of the
+ * augmented topological level-set method (Deng & Suresh, arXiv 2203.15115).
+ *
+ * The library solves K u = f (Eq. 1.1, Sec. 3.5) on a voxel mesh of nx*ny*nz
+ * trilinear hexahedra (Sec. 3.8 step 1) with one Young's modulus per element,
+ * without assembling K, by Jacobi-preconditioned conjugate gradients deflated
+ * with the rigid-body modes of agglomerated node groups (Sec. 3.5).  It then
+ * evaluates the compliance J = f^T u (Eqs. 1.3-1.4), per-element sensitivity
+ * fields (Eqs. 3.2, 3.3, 3.5 and the element-sensitivity fallback of Sec. 3.1),
+ * and extracts the next topology from the combined level-set (Eqs. 3.6, 3.17).
+ *
+ * Conventions (the paper is silent on them):
+ *   element (i,j,k), 0<=i<nx:  e = i + nx*(j + ny*k)
+ *   node    (i,j,k), 0<=i<=nx: n = i + (nx+1)*(j + (ny+1)*k)
+ *   DOF = 3*n + c, c in {0:x, 1:y, 2:z};  element edge h (option, default 1)
+ *   multi-RHS arrays are RHS-major: value (r, d) at r*ndof + d.
+ *
+ * Ownership: the library allocates and owns all device memory it uses; the
+ * caller owns every pointer it passes.  Host pointers are read/written only
+ * during the call.  Device pointers (flag *_on_device = 1) must point to
+ * memory of the mesh's device and stay valid until the call returns; the call
+ * is ordered on the mesh's CUDA stream and returns after that stream has
+ * finished the work unless stated otherwise.
+ *
+ * Errors: every int-returning call returns AFD_OK (0) or a negative AFD_ERR_*
+ * code; afd_last_error() returns a thread-local message for the last failure.
+ * No call aborts the process; device loops are iteration-capped and report a
+ * status word, so an unconverged or singular system is an error code, not a
+ * hang.
+ */
+#ifndef AFD_H_
+#define AFD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  AFD_OK = 0,
+  AFD_ERR_INVALID_ARG = -1,     /* bad size, null pointer, NaN/negative modulus ... */
+  AFD_ERR_OOM = -2,             /* device allocation failed, or a budget was exceeded */
+  AFD_ERR_NOT_CONVERGED = -3,   /* iteration cap reached; u still holds the best iterate */
+  AFD_ERR_COARSE_SINGULAR = -4, /* coarse Cholesky met a pivot <= 0 (e.g. no supports) */
+  AFD_ERR_NAN = -5,             /* a residual norm became NaN or Inf */
+  AFD_ERR_CUDA = -6,            /* a CUDA runtime call failed */
+  AFD_ERR_STATE = -7            /* call out of order (e.g. solve before set_loads_bcs) */
+};
+
+enum { AFD_FP64 = 0, AFD_MIXED = 1 };        /* solver precision */
+enum { AFD_F32 = 0, AFD_F64 = 1 };           /* arithmetic type of a stencil call */
+enum {
+  AFD_SENS_STRAIN_ENERGY = 0,  /* s_e = u_e^T (E_e K0) u_e; sums to J (Sec. 3.1 fallback) */
+  AFD_SENS_TJ = 1,             /* Eq. 3.2 at the element centroid, as printed */
+  AFD_SENS_VON_MISES = 2       /* von Mises stress at the element centroid (Eq. 3.3's measure) */
+};
+
+typedef struct afd_mesh afd_mesh;
+
+typedef struct {
+  int precision;      /* AFD_MIXED (FP32 inner DPCG in FP64 iterative refinement) or AFD_FP64 */
+  int group;          /* deflation agglomeration: elements per group edge (g); 0 = automatic */
+  double nu;          /* Poisson ratio (default 0.3, Sec. 4) */
+  double h;           /* element edge length (default 1) */
+  double e_void;      /* modulus given to removed elements by the level-set update (default 1e-3) */
+  int max_iter;       /* cap on inner DPCG iterations per solve (default 20000) */
+  int max_refine;     /* cap on FP64 refinement steps in AFD_MIXED (default 12) */
+  double inner_tol;   /* floor of the inner relative tolerance in AFD_MIXED (default 2e-5) */
+  int check_every;    /* DPCG iterations per captured CUDA graph between host checks (default 16) */
+  int autotune;       /* 1: time the stencil tile variants once per mesh and keep the fastest */
+} afd_options;
+
+typedef struct {
+  int iters;            /* inner DPCG iterations (summed over refinement steps) */
+  int refine_steps;     /* FP64 residual evaluations after the first (AFD_MIXED) */
+  double rel_residual;  /* final ||f - K u||_2 / ||f||_2 over free DOFs, FP64 */
+  double ms;            /* wall time of the solve call */
+  int status;           /* AFD_OK or AFD_ERR_NOT_CONVERGED / AFD_ERR_NAN for this RHS */
+} afd_stats;
+
+/* Fill *opt with the defaults listed above. */
+void afd_default_options(afd_options* opt);
+
+/* Create a mesh of nx*ny*nz hexahedra (Sec. 3.8 step 1).  cuda_stream is a
+ * cudaStream_t of the current device (NULL = the legacy default stream); every
+ * later call on the mesh is ordered on it.  opt may be NULL (defaults); it is
+ * copied.  nx, ny, nz >= 1 and the DOF count must fit in int32 indices. */
+int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_stream, afd_mesh** out);
+
+/* Per-element Young's modulus E_e (length nx*ny*nz, element order above),
+ * FP64, each finite and > 0.  Invalidates the coarse factor (rebuilt lazily
+ * by the next solve: E = W^T K W and its Cholesky factor, FP64). */
+int afd_set_element_moduli(afd_mesh* m, const double* E, int E_on_device);
+
+/* Loads and supports: n_rhs load cases f (n_rhs*ndof, FP64, RHS-major) and a
+ * fixed-DOF mask (ndof bytes, nonzero = displacement fixed to 0; shared by all
+ * load cases).  Loads on fixed DOFs are ignored.  Resets the warm start. */
+int afd_set_loads_bcs(afd_mesh* m, int n_rhs, const double* f, int f_on_device,
+                      const uint8_t* fixed_dof_mask, int mask_on_device);
+
+/* Solve K u = f for every load case to ||f - K u||_2 <= rel_tol ||f||_2 over
+ * the free DOFs (Eq. 1.1).  warm_start = 1 starts from the previous solution
+ * kept in the mesh (the level-set iterations of Sec. 3.2), 0 from u = 0.
+ * per_rhs (nullable) receives n_rhs stats; u_out (nullable) receives
+ * n_rhs*ndof FP64 displacements.  Returns AFD_ERR_NOT_CONVERGED if any load
+ * case missed the tolerance (u_out still written). */
+int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs,
+              double* u_out, int u_on_device);
+
+/* J_r = f_r^T u_r for every load case (Eqs. 1.3-1.4), FP64, host output. */
+int afd_compliance(afd_mesh* m, double* J_out);
+
+/* Per-element field of the given kind for every load case from the current
+ * solution: out has n_rhs*nelem floats, RHS-major. */
+int afd_sensitivity(afd_mesh* m, int kind, float* out, int out_on_device);
+
+/* p-norm of the element von Mises stresses, (sum_e sigma_vm,e^p)^(1/p), per
+ * load case (the stress measure of Eq. 3.3), FP64, host output. */
+int afd_pnorm_stress(afd_mesh* m, double p, double* out);
+
+/* Level-set update (Eqs. 3.6, 3.17-3.18): for every load case r compute the
+ * field of `kind`, divide it by its largest magnitude, add the fields with
+ * weights[r] (float32, fixed order), keep the k = round(v * nelem) elements
+ * with the largest value (ties keep the lower element index), set their
+ * modulus to 1 and the others to opt.e_void.  tau_out (nullable) receives the
+ * cut value, kept_out (nullable, host, nelem bytes) the kept mask. */
+int afd_levelset_update(afd_mesh* m, int kind, const double* weights, double volume_fraction,
+                        double* tau_out, uint8_t* kept_out);
+
+/* ---- lower-level entry points (the pieces of the path, used by the tests) ---- */
+
+/* y = K u on the free DOFs (rows and columns of fixed DOFs act as zero), in
+ * FP32 (arith = AFD_F32: u, y float) or FP64 (AFD_F64: double); n_rhs vectors
+ * of ndof values, RHS-major.  Device pointers only. */
+int afd_apply_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y);
+
+/* Deflation operators (Sec. 3.5): out = W^T v (n_rhs*6*N_g) and
+ * out = W y (n_rhs*ndof), FP64, device pointers.  Group G's 6 values are
+ * (T_x, T_y, T_z, R_x, R_y, R_z): force sums and moments about the group's
+ * node centroid. */
+int afd_deflation_wt(afd_mesh* m, int n_rhs, const double* v, double* out);
+int afd_deflation_w(afd_mesh* m, int n_rhs, const double* y, double* out);
+
+/* Number of coarse unknowns 6*N_g, and the dense coarse matrix W^T K W
+ * (n_c*n_c FP64, host) built from the current moduli and supports. */
+int afd_coarse_size(afd_mesh* m);
+int afd_coarse_matrix(afd_mesh* m, double* out_host);
+
+/* Keep the k largest of n float keys (device), ties toward the lower index:
+ * kept (device, n bytes) = 1/0, *tau_out = the k-th largest key (host).
+ * Runs on cuda_stream and returns after it finishes. */
+int afd_select_topk(const float* keys, int64_t n, int64_t k, uint8_t* kept, float* tau_out,
+                    void* cuda_stream);
+
+/* Time `launches` back-to-back stiffness applies y = K u (the solver's
+ * kernel and launch geometry, arith AFD_F32 or AFD_F64, n_rhs vectors, device
+ * pointers) on the mesh's stream with CUDA events recorded on that stream;
+ * *ms_out = mean device time per launch.  Measurement aid (Sec. 3.5 names
+ * memory access as the bottleneck of the assembly-free solve). */
+int afd_time_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y, int launches, double* ms_out);
+
+/* Number of CUDA kernels this mesh has launched so far (a CUDA-graph replay
+ * counts its kernel nodes). */
+int64_t afd_kernel_launches(const afd_mesh* m);
+
+/* Sizes of the mesh. */
+int64_t afd_ndof(const afd_mesh* m);
+int64_t afd_nelem(const afd_mesh* m);
+
+void afd_destroy(afd_mesh* m);
+const char* afd_last_error(void);
+
+/* ---- augmented-Lagrangian scalars (Eqs. 3.11, 3.12, 3.18), host only ---- */
+typedef struct {
+  double mu;     /* multiplier, starts at 100 (Sec. 3.8 step 1) */
+  double gamma;  /* penalty, starts at 10 (Sec. 3.8 step 1) */
+  double g;      /* last normalised constraint value, g = J/J_all - 1 */
+  int k;         /* update counter */
+} afd_al_state;
+
+void afd_al_init(afd_al_state* s);
+/* One update with the new constraint value: mu <- max(mu + gamma g, 0)
+ * (Eq. 3.11), then gamma kept if max(g,0) <= 0.25 max(g_prev,0) else
+ * gamma <- max(10 gamma, k^2) (Eq. 3.12). */
+void afd_al_update(afd_al_state* s, double g_new);
+/* Eq. 3.18 weight: mu + gamma g when positive, else 0. */
+double afd_al_weight(const afd_al_state* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFD_H_ */

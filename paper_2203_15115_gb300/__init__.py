@@ -1,0 +1,352 @@
+"""Python binding of the assembly-free deflated FE hot path (arXiv 2203.15115).
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of
+``lib/libafdcg.so`` behind the C ABI of ``include/afd.h``; the functions here
+carry the same names.  Host arrays are numpy arrays; device arrays are torch
+CUDA tensors (PyTorch supplies device memory and the current stream).  There
+is no CPU fallback: importing the binding without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libafdcg.so")
+
+AFD_OK = 0
+AFD_ERR_INVALID_ARG = -1
+AFD_ERR_OOM = -2
+AFD_ERR_NOT_CONVERGED = -3
+AFD_ERR_COARSE_SINGULAR = -4
+AFD_ERR_NAN = -5
+AFD_ERR_CUDA = -6
+AFD_ERR_STATE = -7
+AFD_FP64 = 0
+AFD_MIXED = 1
+AFD_F32 = 0
+AFD_F64 = 1
+AFD_SENS_STRAIN_ENERGY = 0
+AFD_SENS_TJ = 1
+AFD_SENS_VON_MISES = 2
+
+# every entry point of include/afd.h
+EXPORTS = [
+    "afd_default_options", "afd_create_mesh", "afd_set_element_moduli", "afd_set_loads_bcs", "afd_solve",
+    "afd_compliance", "afd_sensitivity", "afd_pnorm_stress", "afd_levelset_update", "afd_apply_stiffness",
+    "afd_deflation_wt", "afd_deflation_w", "afd_coarse_size", "afd_coarse_matrix", "afd_select_topk",
+    "afd_ndof", "afd_nelem", "afd_destroy", "afd_last_error", "afd_al_init", "afd_al_update", "afd_al_weight",
+    "afd_time_stiffness", "afd_kernel_launches",
+]
+
+
+class afd_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("group", ctypes.c_int), ("nu", ctypes.c_double),
+                ("h", ctypes.c_double), ("e_void", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
+
+
+class afd_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("refine_steps", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class afd_al_state(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("gamma", ctypes.c_double), ("g", ctypes.c_double), ("k", ctypes.c_int)]
+
+
+class AFDError(RuntimeError):
+    def __init__(self, code: int, msg: str, stats=None):
+        super().__init__(f"afd error {code}: {msg}")
+        self.code = code
+        self.stats = stats
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2203_15115_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+        sig = {
+            "afd_default_options": (None, [ctypes.POINTER(afd_options)]),
+            "afd_create_mesh": (i, [i, i, i, ctypes.POINTER(afd_options), vp, ctypes.POINTER(vp)]),
+            "afd_set_element_moduli": (i, [vp, vp, i]),
+            "afd_set_loads_bcs": (i, [vp, i, vp, i, vp, i]),
+            "afd_solve": (i, [vp, d, i, ctypes.POINTER(afd_stats), vp, i]),
+            "afd_compliance": (i, [vp, ctypes.POINTER(d)]),
+            "afd_sensitivity": (i, [vp, i, vp, i]),
+            "afd_pnorm_stress": (i, [vp, d, ctypes.POINTER(d)]),
+            "afd_levelset_update": (i, [vp, i, ctypes.POINTER(d), d, ctypes.POINTER(d), vp]),
+            "afd_apply_stiffness": (i, [vp, i, i, vp, vp]),
+            "afd_deflation_wt": (i, [vp, i, vp, vp]),
+            "afd_deflation_w": (i, [vp, i, vp, vp]),
+            "afd_coarse_size": (i, [vp]),
+            "afd_coarse_matrix": (i, [vp, vp]),
+            "afd_select_topk": (i, [vp, i64, i64, vp, ctypes.POINTER(ctypes.c_float), vp]),
+            "afd_ndof": (i64, [vp]),
+            "afd_nelem": (i64, [vp]),
+            "afd_destroy": (None, [vp]),
+            "afd_last_error": (ctypes.c_char_p, []),
+            "afd_al_init": (None, [ctypes.POINTER(afd_al_state)]),
+            "afd_al_update": (None, [ctypes.POINTER(afd_al_state), d]),
+            "afd_al_weight": (d, [ctypes.POINTER(afd_al_state)]),
+            "afd_time_stiffness": (i, [vp, i, i, vp, vp, i, ctypes.POINTER(d)]),
+            "afd_kernel_launches": (i64, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def afd_last_error() -> str:
+    return lib().afd_last_error().decode()
+
+
+def _check(rc: int, stats=None):
+    if rc != AFD_OK:
+        raise AFDError(rc, afd_last_error(), stats)
+
+
+def _arr(x, dtype):
+    """(pointer, on_device, keepalive) for a numpy array or a torch tensor."""
+    if hasattr(x, "data_ptr"):  # torch tensor
+        if x.dtype.itemsize != np.dtype(dtype).itemsize:
+            raise TypeError(f"expected a tensor of {np.dtype(dtype)}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return ctypes.c_void_p(a.ctypes.data), 0, a
+
+
+def current_stream():
+    """cudaStream_t of torch's current stream (None when torch/CUDA is absent)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+def afd_default_options() -> afd_options:
+    o = afd_options()
+    lib().afd_default_options(ctypes.byref(o))
+    return o
+
+
+def afd_create_mesh(nx: int, ny: int, nz: int, options: Optional[afd_options] = None, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    s = stream if stream is not None else current_stream()
+    _check(lib().afd_create_mesh(nx, ny, nz, ctypes.byref(options) if options is not None else None, s,
+                                 ctypes.byref(h)))
+    return h
+
+
+def afd_destroy(mesh) -> None:
+    if mesh:
+        lib().afd_destroy(mesh)
+
+
+def afd_ndof(mesh) -> int:
+    return int(lib().afd_ndof(mesh))
+
+
+def afd_nelem(mesh) -> int:
+    return int(lib().afd_nelem(mesh))
+
+
+def afd_set_element_moduli(mesh, E) -> None:
+    p, dev, _k = _arr(E, np.float64)
+    _check(lib().afd_set_element_moduli(mesh, p, dev))
+
+
+def afd_set_loads_bcs(mesh, f, fixed) -> None:
+    n_rhs = int(f.shape[0]) if len(f.shape) == 2 else 1
+    pf, df, _k1 = _arr(f, np.float64)
+    pm, dm, _k2 = _arr(fixed, np.uint8)
+    _check(lib().afd_set_loads_bcs(mesh, n_rhs, pf, df, pm, dm))
+
+
+def afd_solve(mesh, rel_tol: float, n_rhs: int, warm_start: bool = False, u_out=None, check: bool = True):
+    """Returns the per-RHS stats as dicts; raises AFDError unless check=False."""
+    st = (afd_stats * n_rhs)()
+    if u_out is not None:
+        pu, du, _k = _arr(u_out, np.float64)
+    else:
+        pu, du = None, 0
+    rc = lib().afd_solve(mesh, rel_tol, int(warm_start), st, pu, du)
+    stats = [s.as_dict() for s in st]
+    if check:
+        _check(rc, stats)
+    return stats if check else (rc, stats)
+
+
+def afd_compliance(mesh, n_rhs: int) -> np.ndarray:
+    J = (ctypes.c_double * n_rhs)()
+    _check(lib().afd_compliance(mesh, J))
+    return np.array(J[:])
+
+
+def afd_sensitivity(mesh, kind: int, out) -> None:
+    p, dev, _k = _arr(out, np.float32)
+    _check(lib().afd_sensitivity(mesh, kind, p, dev))
+
+
+def afd_pnorm_stress(mesh, p: float, n_rhs: int) -> np.ndarray:
+    out = (ctypes.c_double * n_rhs)()
+    _check(lib().afd_pnorm_stress(mesh, p, out))
+    return np.array(out[:])
+
+
+def afd_levelset_update(mesh, kind: int, weights, volume_fraction: float, kept_out: Optional[np.ndarray] = None) -> float:
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    tau = ctypes.c_double()
+    pk = None
+    if kept_out is not None:
+        assert kept_out.dtype == np.uint8 and kept_out.flags.c_contiguous
+        pk = ctypes.c_void_p(kept_out.ctypes.data)
+    _check(lib().afd_levelset_update(mesh, kind, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), volume_fraction,
+                                     ctypes.byref(tau), pk))
+    return tau.value
+
+
+def afd_apply_stiffness(mesh, arith: int, n_rhs: int, u, y) -> None:
+    dt = np.float64 if arith == AFD_F64 else np.float32
+    pu, _, _k1 = _arr(u, dt)
+    py, _, _k2 = _arr(y, dt)
+    _check(lib().afd_apply_stiffness(mesh, arith, n_rhs, pu, py))
+
+
+def afd_deflation_wt(mesh, n_rhs: int, v, out) -> None:
+    pv, _, _k1 = _arr(v, np.float64)
+    po, _, _k2 = _arr(out, np.float64)
+    _check(lib().afd_deflation_wt(mesh, n_rhs, pv, po))
+
+
+def afd_deflation_w(mesh, n_rhs: int, y, out) -> None:
+    py, _, _k1 = _arr(y, np.float64)
+    po, _, _k2 = _arr(out, np.float64)
+    _check(lib().afd_deflation_w(mesh, n_rhs, py, po))
+
+
+def afd_coarse_size(mesh) -> int:
+    return int(lib().afd_coarse_size(mesh))
+
+
+def afd_coarse_matrix(mesh) -> np.ndarray:
+    nc = afd_coarse_size(mesh)
+    out = np.zeros((nc, nc))
+    _check(lib().afd_coarse_matrix(mesh, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def afd_select_topk(keys, k: int, kept, stream=None) -> float:
+    pk, _, _k1 = _arr(keys, np.float32)
+    po, _, _k2 = _arr(kept, np.uint8)
+    tau = ctypes.c_float()
+    s = stream if stream is not None else current_stream()
+    _check(lib().afd_select_topk(pk, int(keys.numel() if hasattr(keys, "numel") else len(keys)), int(k), po,
+                                 ctypes.byref(tau), s))
+    return tau.value
+
+
+def afd_time_stiffness(mesh, arith: int, n_rhs: int, u, y, launches: int) -> float:
+    """Mean device ms per stiffness apply, timed with CUDA events on the mesh's stream."""
+    dt = np.float64 if arith == AFD_F64 else np.float32
+    pu, _, _k1 = _arr(u, dt)
+    py, _, _k2 = _arr(y, dt)
+    ms = ctypes.c_double()
+    _check(lib().afd_time_stiffness(mesh, arith, n_rhs, pu, py, launches, ctypes.byref(ms)))
+    return ms.value
+
+
+def afd_kernel_launches(mesh) -> int:
+    return int(lib().afd_kernel_launches(mesh))
+
+
+def afd_al_init() -> afd_al_state:
+    s = afd_al_state()
+    lib().afd_al_init(ctypes.byref(s))
+    return s
+
+
+def afd_al_update(s: afd_al_state, g_new: float) -> None:
+    lib().afd_al_update(ctypes.byref(s), g_new)
+
+
+def afd_al_weight(s: afd_al_state) -> float:
+    return float(lib().afd_al_weight(ctypes.byref(s)))
+
+
+class Mesh:
+    """Owning handle around one afd_mesh (same calls, managed lifetime)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, precision: int = AFD_MIXED, group: int = 0, nu: float = 0.3,
+                 e_void: float = 1e-3, **opts):
+        o = afd_default_options()
+        o.precision, o.group, o.nu, o.e_void = precision, group, nu, e_void
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.options = o
+        self.h = afd_create_mesh(nx, ny, nz, o)
+        self.n_rhs = 0
+
+    @property
+    def ndof(self) -> int:
+        return afd_ndof(self.h)
+
+    @property
+    def nelem(self) -> int:
+        return afd_nelem(self.h)
+
+    def set_element_moduli(self, E):
+        afd_set_element_moduli(self.h, E)
+
+    def set_loads_bcs(self, f, fixed):
+        self.n_rhs = int(f.shape[0]) if len(f.shape) == 2 else 1
+        afd_set_loads_bcs(self.h, f, fixed)
+
+    def solve(self, rel_tol: float, warm_start: bool = False, u_out=None, check: bool = True):
+        return afd_solve(self.h, rel_tol, self.n_rhs, warm_start, u_out, check)
+
+    def compliance(self) -> np.ndarray:
+        return afd_compliance(self.h, self.n_rhs)
+
+    def sensitivity(self, kind: int, out):
+        afd_sensitivity(self.h, kind, out)
+
+    def pnorm_stress(self, p: float) -> np.ndarray:
+        return afd_pnorm_stress(self.h, p, self.n_rhs)
+
+    def levelset_update(self, kind: int, weights, volume_fraction: float, kept_out=None) -> float:
+        return afd_levelset_update(self.h, kind, weights, volume_fraction, kept_out)
+
+    def close(self):
+        if self.h:
+            afd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

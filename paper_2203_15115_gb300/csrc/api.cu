@@ -1,0 +1,1000 @@
+// C ABI of the assembly-free deflated FE hot path (include/afd.h).
+//
+// Host driver: owns the device state of one mesh (moduli, supports, loads,
+// solution, Krylov vectors in FP32 and FP64, the coarse factor), runs the
+// deflated PCG either in FP64 or as FP32 inner solves inside FP64 iterative
+// refinement, with each chunk of `check_every` DPCG iterations captured once
+// into a CUDA graph and replayed, and convergence decided on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/afd.h"
+#include "afd_common.cuh"
+#include "coarse.cuh"
+#include "dpcg_kernels.cuh"
+#include "levelset.cuh"
+#include "sens.cuh"
+#include "stencil.cuh"
+
+using namespace afd;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(x)                                                                              \
+  do {                                                                                     \
+    cudaError_t e_ = (x);                                                                  \
+    if (e_ != cudaSuccess) return fail(AFD_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(x)              \
+  do {                      \
+    int rc_ = (x);          \
+    if (rc_ != AFD_OK) return rc_; \
+  } while (0)
+
+template <typename T>
+static int dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return AFD_OK;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(AFD_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", n * sizeof(T), cudaGetErrorString(e));
+  }
+  return AFD_OK;
+}
+
+template <typename T>
+static void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+// Krylov workspace of one arithmetic type.
+template <typename T>
+struct Work {
+  int cap = 0;  // RHS capacity
+  T *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *t = nullptr, *b = nullptr;
+  T* invdiag = nullptr;
+  T* E = nullptr;
+  ElemConsts<T> K;
+  cudaGraphExec_t graph = nullptr;
+  int graph_nrhs = 0;
+  int64_t graph_kernels = 0;
+};
+
+struct afd_mesh {
+  Grid gr;
+  Groups gp;
+  afd_options opt;
+  int device = 0;
+  cudaStream_t user = nullptr, s = nullptr;
+  cudaEvent_t ev = nullptr;
+  int kz = 8;
+  // state
+  double* E64 = nullptr;
+  uint8_t* fixed = nullptr;   // per node bits
+  int nrhs = 0, cap = 0;
+  double *f64 = nullptr, *u64 = nullptr, *r64 = nullptr;
+  std::vector<double> fnorm;
+  bool has_moduli = false, has_loads = false, has_solution = false;
+  // shared scratch
+  double* partials = nullptr;
+  size_t partials_cap = 0;
+  CGState* st = nullptr;
+  int* done = nullptr;
+  double *v = nullptr, *mu = nullptr, *wr = nullptr;
+  float* fbuf = nullptr;     // per-element float fields (R * nelem)
+  float* fkeys = nullptr;    // combined level-set keys
+  uint8_t* kept = nullptr;
+  void* sel = nullptr;       // SelectState
+  uint32_t* selcnt = nullptr;
+  float* fsmall = nullptr;   // small float scratch (partials of max, weights, maxima)
+  // coarse
+  int nc = 0;
+  double *Ec = nullptr, *Lw = nullptr, *Einv = nullptr, *dmax = nullptr;
+  int* dstatus = nullptr;
+  bool coarse_valid = false;
+  Work<float> w32;
+  Work<double> w64;
+  int64_t launches = 0;       // kernels launched (graph replays count their nodes)
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    int cur;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Order the mesh stream after the user's stream (device inputs made there).
+static int enter(afd_mesh* m) {
+  CK(cudaEventRecord(m->ev, m->user));
+  CK(cudaStreamWaitEvent(m->s, m->ev, 0));
+  return AFD_OK;
+}
+
+static int finish(afd_mesh* m) {
+  CK(cudaStreamSynchronize(m->s));
+  CK(cudaGetLastError());
+  return AFD_OK;
+}
+
+// layout of the small float scratch: [flag | per-RHS maxima | per-RHS weights | max partials]
+constexpr int MAX_RHS = 64;
+constexpr int FS_MAXV = 64;
+constexpr int FS_WEIGHTS = FS_MAXV + MAX_RHS;
+constexpr int FS_PARTS = FS_WEIGHTS + MAX_RHS;
+constexpr int FS_MAX_BLOCKS = RED_BLOCKS / 2;
+constexpr int FSMALL_SIZE = FS_PARTS + MAX_RHS * FS_MAX_BLOCKS;
+
+static int grid_blocks(size_t n, int threads = 256, int cap = RED_BLOCKS) {
+  size_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (int)std::min<size_t>(b, (size_t)cap);
+}
+
+// Captured DPCG graphs bake in buffer addresses: drop them whenever a buffer moves.
+static void invalidate_graphs(afd_mesh* m) {
+  if (m->w32.graph) { cudaGraphExecDestroy(m->w32.graph); m->w32.graph = nullptr; }
+  if (m->w64.graph) { cudaGraphExecDestroy(m->w64.graph); m->w64.graph = nullptr; }
+}
+
+static int ensure_partials(afd_mesh* m, size_t n) {
+  if (n <= m->partials_cap) return AFD_OK;
+  invalidate_graphs(m);
+  dfree(m->partials);
+  TRY(dalloc(&m->partials, n));
+  m->partials_cap = n;
+  return AFD_OK;
+}
+
+static void stencil_geom(const afd_mesh* m, bool f64, int& tiles_x, dim3& grid) {
+  if (f64)
+    StencilGeom<32, 4>::get(m->gr, m->kz, tiles_x, grid);
+  else
+    StencilGeom<32, 8>::get(m->gr, m->kz, tiles_x, grid);
+}
+
+static int stencil_blocks(const afd_mesh* m, bool f64) {
+  int tx;
+  dim3 g;
+  stencil_geom(m, f64, tx, g);
+  return (int)(g.x * g.y);
+}
+
+template <typename T, int MODE, typename TF>
+static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f, float* y32, double* partials,
+                          const int* done, int nrhs, const ElemConsts<T>& K) {
+  constexpr bool F64 = sizeof(T) == 8;
+  constexpr int TX = 32, TY = F64 ? 4 : 8;
+  StencilArgs<T, TF> a;
+  a.gr = m->gr;
+  a.u = u;
+  a.y = y;
+  a.E = E;
+  a.fixed = m->fixed;
+  a.K = K;
+  a.f = f;
+  a.y32 = y32;
+  a.partials = partials;
+  a.done = done;
+  a.kz = m->kz;
+  dim3 grid;
+  StencilGeom<TX, TY>::get(m->gr, m->kz, a.tiles_x, grid);
+  grid.z = nrhs;
+  stencil_kernel<T, TX, TY, MODE, TF><<<grid, TX * TY, 0, m->s>>>(a); m->launches++;
+  CK(cudaGetLastError());
+  return AFD_OK;
+}
+
+static int pick_group(int nx, int ny, int nz, int req) {
+  if (req > 0) return req;
+  for (int g = 4; g <= 1024; g *= 2) {
+    long ng = (long)std::max(nx / g, 1) * std::max(ny / g, 1) * std::max(nz / g, 1);
+    if (6 * ng <= 3072) return g;
+  }
+  return 1024;
+}
+
+template <typename T>
+static int ensure_work(afd_mesh* m, Work<T>& w, int nrhs) {
+  if (w.cap >= nrhs) return AFD_OK;
+  invalidate_graphs(m);
+  dfree(w.x); dfree(w.r); dfree(w.z); dfree(w.p); dfree(w.q); dfree(w.t); dfree(w.b);
+  if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
+  const size_t n = (size_t)nrhs * m->gr.ndof;
+  TRY(dalloc(&w.x, n)); TRY(dalloc(&w.r, n)); TRY(dalloc(&w.z, n)); TRY(dalloc(&w.p, n));
+  TRY(dalloc(&w.q, n)); TRY(dalloc(&w.t, n)); TRY(dalloc(&w.b, n));
+  w.cap = nrhs;
+  return AFD_OK;
+}
+
+static int ensure_rhs(afd_mesh* m, int nrhs) {
+  if (m->cap >= nrhs) return AFD_OK;
+  invalidate_graphs(m);
+  dfree(m->f64); dfree(m->u64); dfree(m->r64); dfree(m->st); dfree(m->done); dfree(m->v); dfree(m->mu); dfree(m->wr);
+  dfree(m->fbuf);
+  const size_t n = (size_t)nrhs * m->gr.ndof;
+  TRY(dalloc(&m->f64, n)); TRY(dalloc(&m->u64, n)); TRY(dalloc(&m->r64, n));
+  TRY(dalloc(&m->st, (size_t)nrhs)); TRY(dalloc(&m->done, (size_t)nrhs));
+  TRY(dalloc(&m->v, (size_t)nrhs * m->nc)); TRY(dalloc(&m->mu, (size_t)nrhs * m->nc));
+  TRY(dalloc(&m->wr, (size_t)nrhs * m->nc));
+  TRY(dalloc(&m->fbuf, (size_t)nrhs * m->gr.nelem));
+  m->cap = nrhs;
+  // graphs captured for a smaller RHS count stay valid; none need freeing here
+  return AFD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// coarse problem
+// ---------------------------------------------------------------------------
+static int build_coarse(afd_mesh* m) {
+  if (m->coarse_valid) return AFD_OK;
+  if (!m->has_moduli) return fail(AFD_ERR_STATE, "moduli not set");
+  const int nc = m->nc;
+  const size_t nn = (size_t)nc * nc;
+  if (!m->Ec) {
+    TRY(dalloc(&m->Ec, nn)); TRY(dalloc(&m->Lw, nn)); TRY(dalloc(&m->Einv, nn));
+    TRY(dalloc(&m->dmax, 1)); TRY(dalloc(&m->dstatus, 1));
+  }
+  CK(cudaMemsetAsync(m->Ec, 0, nn * sizeof(double), m->s));
+  k_coarse_assemble<<<m->gp.ng, COARSE_WARPS * 32, 0, m->s>>>(m->gr, m->gp, m->E64, m->fixed, m->w64.K, m->Ec); m->launches++;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(m->Lw, m->Ec, nn * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
+  CK(cudaMemsetAsync(m->dstatus, 0, sizeof(int), m->s));
+  k_max_diag<<<1, 256, 0, m->s>>>(m->Ec, nc, m->dmax); m->launches++;
+  for (int k0 = 0; k0 < nc; k0 += CH_NB) {
+    k_potrf_diag<<<1, 256, 0, m->s>>>(m->Lw, nc, k0, m->dmax, m->dstatus); m->launches++;
+    const int nb = std::min(CH_NB, nc - k0);
+    const int rows = nc - k0 - nb;
+    if (rows > 0) {
+      k_trsm_panel<<<(rows + 127) / 128, 128, 0, m->s>>>(m->Lw, nc, k0); m->launches++;
+      const int nt = (rows + 31) / 32;
+      k_syrk_update<<<nt * (nt + 1) / 2, 256, 0, m->s>>>(m->Lw, nc, k0); m->launches++;
+    }
+  }
+  CK(cudaGetLastError());
+  int status = 0;
+  CK(cudaMemcpyAsync(&status, m->dstatus, sizeof(int), cudaMemcpyDeviceToHost, m->s));
+  CK(cudaStreamSynchronize(m->s));
+  if (status != 0)
+    return fail(AFD_ERR_COARSE_SINGULAR, "coarse matrix W^T K W is singular (are there enough supports?)");
+  // U = L^T into Einv (scratch), Linv into Lw, then Einv = Linv^T Linv
+  {
+    dim3 tb(32, 8), tg((nc + 31) / 32, (nc + 31) / 32);
+    k_transpose<<<tg, tb, 0, m->s>>>(m->Lw, m->Einv, nc); m->launches++;
+    const size_t shm = (size_t)nc * sizeof(double);
+    if (shm > 48 * 1024) CK(cudaFuncSetAttribute(k_trtri_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_trtri_cols<<<nc, 256, shm, m->s>>>(m->Einv, m->Lw, nc); m->launches++;
+    dim3 gg((nc + 31) / 32, (nc + 31) / 32);
+    k_gram<<<gg, 1024, 0, m->s>>>(m->Lw, m->Einv, nc); m->launches++;
+    CK(cudaGetLastError());
+  }
+  m->coarse_valid = true;
+  return AFD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// deflated PCG (Sec. 3.5) in type T on K x = b; x holds the initial guess.
+// Per-RHS stop: r.r <= target2[r]; RHS with active[r] == 0 are skipped.
+// ---------------------------------------------------------------------------
+template <typename T, typename TB>
+static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std::vector<double>& target2,
+                const std::vector<int>& active, int max_iters, std::vector<CGState>& out) {
+  constexpr bool F64 = sizeof(T) == 8;
+  const Grid& gr = m->gr;
+  const int nsb = stencil_blocks(m, F64);
+  TRY(ensure_partials(m, (size_t)nrhs * std::max(nsb, 2 * RED_BLOCKS)));
+  // state init
+  std::vector<CGState> h(nrhs);
+  std::vector<int> hd(nrhs);
+  for (int r = 0; r < nrhs; ++r) {
+    memset(&h[r], 0, sizeof(CGState));
+    h[r].target2 = target2[r];
+    h[r].max_iters = max_iters;
+    h[r].done = active[r] ? 0 : 1;
+    hd[r] = h[r].done;
+  }
+  CK(cudaMemcpyAsync(m->st, h.data(), nrhs * sizeof(CGState), cudaMemcpyHostToDevice, m->s));
+  CK(cudaMemcpyAsync(m->done, hd.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, m->s));
+  const dim3 vg(RED_BLOCKS, nrhs);
+  const dim3 gg(m->gp.ng, nrhs);
+  const dim3 pg(grid_blocks(gr.nnodes, 256, 4 * RED_BLOCKS), nrhs);
+  const int capply_blocks = (m->nc * 32 + 255) / 256;
+  // r = b - K x ; x += W Einv W^T r ; r = b - K x  (deflated start)
+  TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, w.r, w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
+  k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, w.r, nullptr, m->fixed, m->v, nullptr, m->st); m->launches++;
+  k_coarse_apply<<<capply_blocks, 256, 0, m->s>>>(m->nc, nrhs, m->Einv, m->v, nullptr, m->mu, m->st); m->launches++;
+  k_prolong<T><<<pg, 256, 0, m->s>>>(2, gr, m->gp, x, nullptr, m->mu, m->fixed, m->st); m->launches++;
+  TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, w.r, w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
+  // two-level preconditioned residual y = z + W Einv W^T (r - K z), z = M^-1 r
+  // (the A-DEF2 form of deflation: the W^T r term keeps W^T r from drifting
+  // under rounding, which the plain projected recurrence does not)
+  k_precond_dot<T><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, w.r, w.invdiag, w.z, m->partials, m->st); m->launches++;
+  TRY((launch_stencil<T, ST_APPLY, TB>(m, w.z, w.t, w.E, nullptr, nullptr, nullptr, m->done, nrhs, w.K)));
+  k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, w.r, w.t, m->fixed, m->wr, m->v, m->st); m->launches++;
+  k_coarse_apply<<<capply_blocks, 256, 0, m->s>>>(m->nc, nrhs, m->Einv, m->wr, m->v, m->mu, m->st); m->launches++;
+  k_finalize<<<nrhs, 256, 0, m->s>>>(FIN_INIT, m->partials, RED_BLOCKS, m->st, m->done, m->wr, m->mu, m->nc); m->launches++;
+  k_prolong<T><<<pg, 256, 0, m->s>>>(3, gr, m->gp, w.p, w.z, m->mu, m->fixed, m->st); m->launches++;
+  CK(cudaGetLastError());
+
+  // one chunk of iterations, captured once into a graph
+  auto enqueue_chunk = [&]() -> int {
+    for (int it = 0; it < m->opt.check_every; ++it) {
+      TRY((launch_stencil<T, ST_APPLY_DOT, TB>(m, w.p, w.q, w.E, nullptr, nullptr, m->partials, m->done, nrhs, w.K)));
+      k_finalize<<<nrhs, 256, 0, m->s>>>(FIN_ALPHA, m->partials, nsb, m->st, m->done, nullptr, nullptr, 0); m->launches++;
+      k_cg_update<T><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, x, w.r, w.z, w.p, w.q, w.invdiag, m->partials, m->st); m->launches++;
+      TRY((launch_stencil<T, ST_APPLY, TB>(m, w.z, w.t, w.E, nullptr, nullptr, nullptr, m->done, nrhs, w.K)));
+      k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, w.r, w.t, m->fixed, m->wr, m->v, m->st); m->launches++;
+      k_coarse_apply<<<capply_blocks, 256, 0, m->s>>>(m->nc, nrhs, m->Einv, m->wr, m->v, m->mu, m->st); m->launches++;
+      k_finalize<<<nrhs, 256, 0, m->s>>>(FIN_BETA, m->partials, RED_BLOCKS, m->st, m->done, m->wr, m->mu, m->nc); m->launches++;
+      k_prolong<T><<<pg, 256, 0, m->s>>>(0, gr, m->gp, w.p, w.z, m->mu, m->fixed, m->st); m->launches++;
+    }
+    CK(cudaGetLastError());
+    return AFD_OK;
+  };
+  // the graph bakes in x and b; rebuild it when they or the RHS count change
+  static_assert(sizeof(void*) == 8, "64-bit");
+  cudaGraphExec_t& gexec = w.graph;
+  const bool reuse = gexec && w.graph_nrhs == nrhs;
+  if (!reuse) {
+    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+    cudaGraph_t graph;
+    const int64_t before = m->launches;
+    CK(cudaStreamBeginCapture(m->s, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_chunk();
+    w.graph_kernels = m->launches - before;  // captured, not run
+    m->launches = before;
+    cudaError_t e = cudaStreamEndCapture(m->s, &graph);
+    if (rc != AFD_OK) return rc;
+    if (e != cudaSuccess) return fail(AFD_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(AFD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    w.graph_nrhs = nrhs;
+  }
+  const int max_chunks = max_iters / std::max(1, m->opt.check_every) + 2;
+  std::vector<int> flags(nrhs);
+  for (int c = 0; c < max_chunks; ++c) {
+    CK(cudaMemcpyAsync(flags.data(), m->done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, m->s));
+    CK(cudaStreamSynchronize(m->s));
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) all &= flags[r] != 0;
+    if (all) break;
+    CK(cudaGraphLaunch(gexec, m->s));
+    m->launches += w.graph_kernels;
+  }
+  out.resize(nrhs);
+  CK(cudaMemcpyAsync(out.data(), m->st, nrhs * sizeof(CGState), cudaMemcpyDeviceToHost, m->s));
+  CK(cudaStreamSynchronize(m->s));
+  return AFD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI (C linkage from the declarations in afd.h)
+// ---------------------------------------------------------------------------
+
+void afd_default_options(afd_options* o) {
+  if (!o) return;
+  o->precision = AFD_MIXED;
+  o->group = 0;
+  o->nu = 0.3;
+  o->h = 1.0;
+  o->e_void = 1e-3;
+  o->max_iter = 20000;
+  o->max_refine = 12;
+  o->inner_tol = 2e-5;
+  o->check_every = 16;
+  o->autotune = 0;
+}
+
+const char* afd_last_error(void) { return g_err.c_str(); }
+
+int64_t afd_ndof(const afd_mesh* m) { return m ? m->gr.ndof : 0; }
+int64_t afd_nelem(const afd_mesh* m) { return m ? m->gr.nelem : 0; }
+
+int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_stream, afd_mesh** out) {
+  if (!out) return fail(AFD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(AFD_ERR_INVALID_ARG, "mesh sizes must be >= 1");
+  const double nn = (double)(nx + 1) * (ny + 1) * (nz + 1);
+  if (3.0 * nn >= 2147483647.0 || (double)nx * ny * nz >= 2147483647.0)
+    return fail(AFD_ERR_INVALID_ARG, "mesh too large for 32-bit DOF indices");
+  afd_options o;
+  afd_default_options(&o);
+  if (opt) o = *opt;
+  if (!(o.nu > -1.0 && o.nu < 0.5) || !(o.h > 0.0) || !(o.e_void > 0.0) || o.max_iter < 1 || o.max_refine < 0 ||
+      o.check_every < 1 || o.group < 0 || (o.precision != AFD_MIXED && o.precision != AFD_FP64))
+    return fail(AFD_ERR_INVALID_ARG, "invalid options");
+  afd_mesh* m = new afd_mesh();
+  m->opt = o;
+  CK(cudaGetDevice(&m->device));
+  m->user = (cudaStream_t)cuda_stream;
+  Grid& g = m->gr;
+  g.nx = nx; g.ny = ny; g.nz = nz;
+  g.nnx = nx + 1; g.nny = ny + 1; g.nnz = nz + 1;
+  g.nnodes = g.nnx * g.nny * g.nnz;
+  g.nelem = nx * ny * nz;
+  g.ndof = 3 * g.nnodes;
+  Groups& gp = m->gp;
+  gp.g = pick_group(nx, ny, nz, o.group);
+  gp.ngx = std::max(nx / gp.g, 1);
+  gp.ngy = std::max(ny / gp.g, 1);
+  gp.ngz = std::max(nz / gp.g, 1);
+  gp.ng = gp.ngx * gp.ngy * gp.ngz;
+  gp.h = o.h;
+  m->nc = 6 * gp.ng;
+  // z planes per CTA: enough CTAs to fill the GPU a few times
+  {
+    int tx;
+    dim3 gr;
+    StencilGeom<32, 8>::get(g, g.nnz, tx, gr);
+    const long tiles = gr.x;
+    long kz = (long)g.nnz * tiles / 2400;
+    m->kz = (int)std::max(4L, std::min<long>(kz, g.nnz));
+  }
+  m->w32.K = make_elem_consts<float>(o.nu, o.h);
+  m->w64.K = make_elem_consts<double>(o.nu, o.h);
+  int rc = AFD_OK;
+  if (cudaStreamCreateWithFlags(&m->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) != cudaSuccess) {
+    delete m;
+    return fail(AFD_ERR_CUDA, "stream creation failed");
+  }
+  if ((rc = dalloc(&m->E64, (size_t)g.nelem)) != AFD_OK || (rc = dalloc(&m->w32.E, (size_t)g.nelem)) != AFD_OK ||
+      (rc = dalloc(&m->w64.E, (size_t)g.nelem)) != AFD_OK || (rc = dalloc(&m->w32.invdiag, (size_t)g.nnodes)) != AFD_OK ||
+      (rc = dalloc(&m->w64.invdiag, (size_t)g.nnodes)) != AFD_OK || (rc = dalloc(&m->fixed, (size_t)g.nnodes)) != AFD_OK ||
+      (rc = dalloc(&m->fsmall, (size_t)FSMALL_SIZE)) != AFD_OK) {
+    afd_destroy(m);
+    return rc;
+  }
+  cudaMemsetAsync(m->fixed, 0, g.nnodes, m->s);
+  if (cudaStreamSynchronize(m->s) != cudaSuccess) {
+    afd_destroy(m);
+    return fail(AFD_ERR_CUDA, "init failed");
+  }
+  *out = m;
+  return AFD_OK;
+}
+
+void afd_destroy(afd_mesh* m) {
+  if (!m) return;
+  DeviceGuard dg(m->device);
+  if (m->s) cudaStreamSynchronize(m->s);
+  for (auto* wp : {&m->w32}) {
+    dfree(wp->x); dfree(wp->r); dfree(wp->z); dfree(wp->p); dfree(wp->q); dfree(wp->t); dfree(wp->b);
+    dfree(wp->invdiag); dfree(wp->E);
+    if (wp->graph) cudaGraphExecDestroy(wp->graph);
+  }
+  {
+    auto* wp = &m->w64;
+    dfree(wp->x); dfree(wp->r); dfree(wp->z); dfree(wp->p); dfree(wp->q); dfree(wp->t); dfree(wp->b);
+    dfree(wp->invdiag); dfree(wp->E);
+    if (wp->graph) cudaGraphExecDestroy(wp->graph);
+  }
+  dfree(m->E64); dfree(m->fixed); dfree(m->f64); dfree(m->u64); dfree(m->r64); dfree(m->partials);
+  dfree(m->st); dfree(m->done); dfree(m->v); dfree(m->mu); dfree(m->wr); dfree(m->fbuf); dfree(m->fkeys); dfree(m->kept);
+  if (m->sel) cudaFree(m->sel);
+  dfree(m->selcnt); dfree(m->fsmall);
+  dfree(m->Ec); dfree(m->Lw); dfree(m->Einv); dfree(m->dmax); dfree(m->dstatus);
+  if (m->ev) cudaEventDestroy(m->ev);
+  if (m->s) cudaStreamDestroy(m->s);
+  delete m;
+}
+
+template <typename T>
+__global__ void k_convert(size_t n, const double* __restrict__ a, T* __restrict__ b) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) b[i] = (T)a[i];
+}
+
+__global__ void k_check_moduli(size_t n, const double* __restrict__ E, int* bad) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    if (!(E[i] > 0.0) || !isfinite(E[i])) *bad = 1;
+}
+
+static int refresh_moduli(afd_mesh* m) {
+  const Grid& g = m->gr;
+  const size_t ne = g.nelem;
+  k_convert<float><<<grid_blocks(ne, 256, 4096), 256, 0, m->s>>>(ne, m->E64, m->w32.E); m->launches++;
+  k_convert<double><<<grid_blocks(ne, 256, 4096), 256, 0, m->s>>>(ne, m->E64, m->w64.E); m->launches++;
+  const double d0 = elem_diag(m->opt.nu, m->opt.h);
+  k_invdiag<float><<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->E64, d0, m->w32.invdiag); m->launches++;
+  k_invdiag<double><<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->E64, d0, m->w64.invdiag); m->launches++;
+  CK(cudaGetLastError());
+  m->coarse_valid = false;
+  m->has_moduli = true;
+  return AFD_OK;
+}
+
+int afd_set_element_moduli(afd_mesh* m, const double* E, int on_device) {
+  if (!m || !E) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const size_t ne = m->gr.nelem;
+  CK(cudaMemcpyAsync(m->E64, E, ne * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->s));
+  int* bad = (int*)m->fsmall;
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), m->s));
+  k_check_moduli<<<grid_blocks(ne, 256, 4096), 256, 0, m->s>>>(ne, m->E64, bad); m->launches++;
+  int hbad = 0;
+  CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, m->s));
+  CK(cudaStreamSynchronize(m->s));
+  if (hbad) {
+    m->has_moduli = false;
+    return fail(AFD_ERR_INVALID_ARG, "moduli must be finite and > 0");
+  }
+  TRY(refresh_moduli(m));
+  return finish(m);
+}
+
+__global__ void k_pack_fixed(int nnodes, const uint8_t* __restrict__ dof_mask, uint8_t* __restrict__ node_bits) {
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nnodes; n += gridDim.x * blockDim.x)
+    node_bits[n] = (dof_mask[3 * n] ? 1 : 0) | (dof_mask[3 * n + 1] ? 2 : 0) | (dof_mask[3 * n + 2] ? 4 : 0);
+}
+
+__global__ void k_zero_fixed(int nnodes, int nrhs, int ndof, const uint8_t* __restrict__ bits, double* __restrict__ f) {
+  const int rhs = blockIdx.y;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nnodes; n += gridDim.x * blockDim.x) {
+    const uint8_t b = bits[n];
+    for (int c = 0; c < 3; ++c)
+      if ((b >> c) & 1) f[(size_t)rhs * ndof + 3 * n + c] = 0.0;
+  }
+}
+
+static int reduce_partials_host(afd_mesh* m, int nrhs, int nparts, std::vector<double>& out) {
+  std::vector<double> h((size_t)nrhs * nparts);
+  CK(cudaMemcpyAsync(h.data(), m->partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+  CK(cudaStreamSynchronize(m->s));
+  out.assign(nrhs, 0.0);
+  for (int r = 0; r < nrhs; ++r)
+    for (int i = 0; i < nparts; ++i) out[r] += h[(size_t)r * nparts + i];
+  return AFD_OK;
+}
+
+int afd_set_loads_bcs(afd_mesh* m, int n_rhs, const double* f, int f_on_device, const uint8_t* mask, int mask_on_device) {
+  if (!m || !f || !mask) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (n_rhs < 1 || n_rhs > MAX_RHS) return fail(AFD_ERR_INVALID_ARG, "n_rhs must be in [1, %d]", MAX_RHS);
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  TRY(ensure_rhs(m, n_rhs));
+  const Grid& g = m->gr;
+  const size_t n = (size_t)n_rhs * g.ndof;
+  CK(cudaMemcpyAsync(m->f64, f, n * sizeof(double), f_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->s));
+  uint8_t* dmask = nullptr;
+  if (mask_on_device) {
+    dmask = (uint8_t*)mask;
+  } else {
+    TRY(dalloc(&dmask, (size_t)g.ndof));
+    CK(cudaMemcpyAsync(dmask, mask, g.ndof, cudaMemcpyHostToDevice, m->s));
+  }
+  k_pack_fixed<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g.nnodes, dmask, m->fixed); m->launches++;
+  k_zero_fixed<<<dim3(grid_blocks(g.nnodes, 256, 4096), n_rhs), 256, 0, m->s>>>(g.nnodes, n_rhs, g.ndof, m->fixed, m->f64); m->launches++;
+  CK(cudaMemsetAsync(m->u64, 0, n * sizeof(double), m->s));
+  CK(cudaGetLastError());
+  TRY(ensure_partials(m, (size_t)n_rhs * RED_BLOCKS));
+  k_dot<double, double><<<dim3(RED_BLOCKS, n_rhs), RED_THREADS, 0, m->s>>>(g.ndof, m->f64, m->f64, m->partials); m->launches++;
+  std::vector<double> ff;
+  TRY(reduce_partials_host(m, n_rhs, RED_BLOCKS, ff));
+  if (!mask_on_device) cudaFree(dmask);
+  m->fnorm.assign(n_rhs, 0.0);
+  for (int r = 0; r < n_rhs; ++r) {
+    if (!std::isfinite(ff[r])) return fail(AFD_ERR_INVALID_ARG, "load case %d is not finite", r);
+    m->fnorm[r] = std::sqrt(ff[r]);
+  }
+  m->nrhs = n_rhs;
+  m->has_loads = true;
+  m->has_solution = false;
+  m->coarse_valid = false;
+  return finish(m);
+}
+
+// r64 = f - K u64 (FP64), optional float copy into b32; returns ||r||/||f|| per RHS.
+static int true_residual(afd_mesh* m, float* b32, std::vector<double>& rel) {
+  const int nsb = stencil_blocks(m, true);
+  TRY(ensure_partials(m, (size_t)m->nrhs * std::max(nsb, 2 * RED_BLOCKS)));
+  TRY((launch_stencil<double, ST_RESIDUAL, double>(m, m->u64, m->r64, m->w64.E, m->f64, b32, m->partials, nullptr,
+                                                     m->nrhs, m->w64.K)));
+  std::vector<double> rr;
+  TRY(reduce_partials_host(m, m->nrhs, nsb, rr));
+  rel.resize(m->nrhs);
+  for (int r = 0; r < m->nrhs; ++r) rel[r] = m->fnorm[r] > 0 ? std::sqrt(rr[r]) / m->fnorm[r] : std::sqrt(rr[r]);
+  return AFD_OK;
+}
+
+int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, double* u_out, int u_on_device) {
+  if (!m) return fail(AFD_ERR_INVALID_ARG, "null mesh");
+  if (!(rel_tol > 0.0) || !std::isfinite(rel_tol)) return fail(AFD_ERR_INVALID_ARG, "rel_tol must be > 0");
+  if (!m->has_moduli || !m->has_loads) return fail(AFD_ERR_STATE, "set moduli and loads before solving");
+  DeviceGuard dg(m->device);
+  auto t0 = std::chrono::steady_clock::now();
+  TRY(enter(m));
+  const int R = m->nrhs;
+  const Grid& g = m->gr;
+  TRY(build_coarse(m));
+  if (!warm_start || !m->has_solution) CK(cudaMemsetAsync(m->u64, 0, (size_t)R * g.ndof * sizeof(double), m->s));
+  std::vector<int> iters(R, 0), status(R, AFD_OK), refine(R, 0);
+  std::vector<double> rel;
+  if (m->opt.precision == AFD_FP64) {
+    TRY(ensure_work(m, m->w64, R));
+    std::vector<double> t2(R);
+    std::vector<int> act(R, 1);
+      // the recursive residual drifts from the true one: aim 10% below the tolerance
+    for (int r = 0; r < R; ++r) t2[r] = (0.9 * rel_tol * m->fnorm[r]) * (0.9 * rel_tol * m->fnorm[r]);
+    std::vector<CGState> st;
+    TRY((dpcg<double, double>(m, m->w64, m->f64, m->u64, R, t2, act, m->opt.max_iter, st)));
+    for (int r = 0; r < R; ++r) {
+      iters[r] = st[r].iters;
+      status[r] = st[r].status;
+    }
+    TRY(true_residual(m, nullptr, rel));
+  } else {
+    TRY(ensure_work(m, m->w32, R));
+    float* b32 = m->w32.b;
+    TRY(true_residual(m, b32, rel));
+    for (int step = 0; step <= m->opt.max_refine; ++step) {
+      std::vector<int> act(R, 0);
+      std::vector<double> t2(R, 0.0);
+      bool any = false;
+      for (int r = 0; r < R; ++r) {
+        if (!std::isfinite(rel[r])) { status[r] = AFD_ERR_NAN; continue; }
+        if (rel[r] <= rel_tol || m->fnorm[r] == 0.0) continue;
+        if (step == m->opt.max_refine || iters[r] >= m->opt.max_iter) { status[r] = AFD_ERR_NOT_CONVERGED; continue; }
+        act[r] = 1;
+        any = true;
+        double eta = std::min(0.5, std::max(m->opt.inner_tol, 0.1 * rel_tol / rel[r]));
+        const double rn = rel[r] * (m->fnorm[r] > 0 ? m->fnorm[r] : 1.0);
+        t2[r] = (eta * rn) * (eta * rn);
+      }
+      if (!any) break;
+      CK(cudaMemsetAsync(m->w32.x, 0, (size_t)R * g.ndof * sizeof(float), m->s));
+      std::vector<CGState> st;
+      int budget = m->opt.max_iter;
+      for (int r = 0; r < R; ++r) if (act[r]) budget = std::min(budget, std::max(1, m->opt.max_iter - iters[r]));
+      TRY((dpcg<float, float>(m, m->w32, b32, m->w32.x, R, t2, act, budget, st)));
+      std::vector<int> skip(R);
+      for (int r = 0; r < R; ++r) {
+        skip[r] = !act[r];
+        if (act[r]) {
+          iters[r] += st[r].iters;
+          refine[r] += 1;
+          if (st[r].status == AFD_ERR_NAN) status[r] = AFD_ERR_NAN;
+        }
+      }
+      int* dskip = m->done;
+      CK(cudaMemcpyAsync(dskip, skip.data(), R * sizeof(int), cudaMemcpyHostToDevice, m->s));
+      k_accumulate<<<dim3(grid_blocks(g.ndof, 256, 2048), R), 256, 0, m->s>>>(g.ndof, R, m->u64, m->w32.x, dskip); m->launches++;
+      CK(cudaGetLastError());
+      TRY(true_residual(m, b32, rel));
+    }
+    for (int r = 0; r < R; ++r)
+      if (status[r] == AFD_OK && !(rel[r] <= rel_tol)) status[r] = AFD_ERR_NOT_CONVERGED;
+  }
+  m->has_solution = true;
+  if (u_out)
+    CK(cudaMemcpyAsync(u_out, m->u64, (size_t)R * g.ndof * sizeof(double),
+                       u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->s));
+  TRY(finish(m));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  int rc = AFD_OK;
+  for (int r = 0; r < R; ++r) {
+    if (m->opt.precision == AFD_FP64 && status[r] == AFD_OK && !(rel[r] <= rel_tol * 1.0000001)) status[r] = AFD_ERR_NOT_CONVERGED;
+    if (status[r] != AFD_OK && rc == AFD_OK) rc = status[r];
+    if (per_rhs) {
+      per_rhs[r].iters = iters[r];
+      per_rhs[r].refine_steps = refine[r];
+      per_rhs[r].rel_residual = rel[r];
+      per_rhs[r].ms = ms;
+      per_rhs[r].status = status[r];
+    }
+  }
+  if (rc != AFD_OK) fail(rc, "solve did not reach rel_tol %.3g for every load case", rel_tol);
+  return rc;
+}
+
+int afd_compliance(afd_mesh* m, double* J_out) {
+  if (!m || !J_out) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (!m->has_solution) return fail(AFD_ERR_STATE, "no solution");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  TRY(ensure_partials(m, (size_t)m->nrhs * RED_BLOCKS));
+  k_dot<double, double><<<dim3(RED_BLOCKS, m->nrhs), RED_THREADS, 0, m->s>>>(m->gr.ndof, m->f64, m->u64, m->partials); m->launches++;
+  CK(cudaGetLastError());
+  std::vector<double> J;
+  TRY(reduce_partials_host(m, m->nrhs, RED_BLOCKS, J));
+  for (int r = 0; r < m->nrhs; ++r) J_out[r] = J[r];
+  return finish(m);
+}
+
+static int fields_to(afd_mesh* m, int kind, float* out) {
+  FieldConsts F;
+  const double nu = m->opt.nu;
+  F.lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  F.mu = 1.0 / (2.0 * (1.0 + nu));
+  F.nu = nu;
+  F.inv4h = 1.0 / (4.0 * m->opt.h);
+  const dim3 grid(grid_blocks(m->gr.nelem, 256, 8 * RED_BLOCKS), m->nrhs);
+  if (m->opt.precision == AFD_FP64) {
+    k_element_fields<double><<<grid, 256, 0, m->s>>>(m->gr, m->u64, m->E64, m->w64.K, F, kind, out); m->launches++;
+  } else {
+    k_element_fields<float><<<grid, 256, 0, m->s>>>(m->gr, m->u64, m->E64, m->w32.K, F, kind, out); m->launches++;
+  }
+  CK(cudaGetLastError());
+  return AFD_OK;
+}
+
+int afd_sensitivity(afd_mesh* m, int kind, float* out, int out_on_device) {
+  if (!m || !out) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (kind < 0 || kind > 2) return fail(AFD_ERR_INVALID_ARG, "unknown sensitivity kind %d", kind);
+  if (!m->has_solution) return fail(AFD_ERR_STATE, "no solution");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  float* dst = out_on_device ? out : m->fbuf;
+  TRY(fields_to(m, kind, dst));
+  if (!out_on_device)
+    CK(cudaMemcpyAsync(out, m->fbuf, (size_t)m->nrhs * m->gr.nelem * sizeof(float), cudaMemcpyDeviceToHost, m->s));
+  return finish(m);
+}
+
+static int maxabs_per_rhs(afd_mesh* m, const float* x, int nrhs, float* dmax_out) {
+  float* part = m->fsmall + FS_PARTS;
+  const int nb = std::min(FS_MAX_BLOCKS, grid_blocks(m->gr.nelem));
+  k_maxabs_partial<<<dim3(nb, nrhs), 256, 0, m->s>>>(m->gr.nelem, x, part); m->launches++;
+  k_max_finalize<<<nrhs, 256, 0, m->s>>>(nb, part, dmax_out); m->launches++;
+  CK(cudaGetLastError());
+  return AFD_OK;
+}
+
+int afd_pnorm_stress(afd_mesh* m, double p, double* out) {
+  if (!m || !out) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (!(p >= 1.0) || !std::isfinite(p)) return fail(AFD_ERR_INVALID_ARG, "p must be >= 1");
+  if (!m->has_solution) return fail(AFD_ERR_STATE, "no solution");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const int R = m->nrhs;
+  TRY(fields_to(m, AFD_SENS_VON_MISES, m->fbuf));
+  float* dmaxv = m->fsmall + FS_MAXV;
+  TRY(maxabs_per_rhs(m, m->fbuf, R, dmaxv));
+  TRY(ensure_partials(m, (size_t)R * RED_BLOCKS));
+  k_pow_partial<<<dim3(RED_BLOCKS, R), 256, 0, m->s>>>(m->gr.nelem, m->fbuf, dmaxv, p, m->partials); m->launches++;
+  CK(cudaGetLastError());
+  std::vector<double> s;
+  TRY(reduce_partials_host(m, R, RED_BLOCKS, s));
+  std::vector<float> mx(R);
+  CK(cudaMemcpyAsync(mx.data(), dmaxv, R * sizeof(float), cudaMemcpyDeviceToHost, m->s));
+  CK(cudaStreamSynchronize(m->s));
+  for (int r = 0; r < R; ++r) out[r] = (double)mx[r] * std::pow(s[r], 1.0 / p);
+  return finish(m);
+}
+
+// Top-k selection on device keys (stream s); kept/E written on the device.
+static int select_topk_dev(cudaStream_t s, const float* keys, int64_t n, int64_t k, uint8_t* kept, SelectState* st,
+                           uint32_t* cnt, double* E64, float* E32, double e_void, float* tau, int64_t* nl) {
+  SelectState init;
+  memset(&init, 0, sizeof(init));
+  init.kk = (uint64_t)k;
+  CK(cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  const int hb = (int)std::min<int64_t>((n + 255) / 256, 4 * RED_BLOCKS);
+  if (k > 0) {
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 24 - 8 * pass;
+      k_select_hist<<<std::max(hb, 1), 256, 0, s>>>(n, keys, st, shift); if (nl) ++*nl;
+      k_select_pick<<<1, 32, 0, s>>>(st, shift); if (nl) ++*nl;
+    }
+  } else {
+    // keep nothing: a cut above every key
+    SelectState none = init;
+    none.prefix = 0xffffffffu;
+    none.kk = 0;
+    CK(cudaMemcpyAsync(st, &none, sizeof(none), cudaMemcpyHostToDevice, s));
+  }
+  const int nch = (int)((n + SEL_CHUNK - 1) / SEL_CHUNK);
+  if (nch > 0) {
+    k_count_eq<<<nch, 256, 0, s>>>(n, keys, st, cnt); if (nl) ++*nl;
+    k_scan_counts<<<1, 32, 0, s>>>(nch, cnt); if (nl) ++*nl;
+    k_mark<<<nch, 256, 0, s>>>(n, keys, st, cnt, kept, E64, E32, e_void); if (nl) ++*nl;
+  }
+  CK(cudaGetLastError());
+  SelectState fin;
+  CK(cudaMemcpyAsync(&fin, st, sizeof(fin), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (tau) {
+    if (k == 0) {
+      *tau = NAN;
+    } else {
+      uint32_t kk = fin.prefix;
+      uint32_t u = (kk & 0x80000000u) ? (kk & 0x7fffffffu) : ~kk;
+      float f;
+      memcpy(&f, &u, 4);
+      *tau = f;
+    }
+  }
+  return AFD_OK;
+}
+
+int afd_select_topk(const float* keys, int64_t n, int64_t k, uint8_t* kept, float* tau_out, void* cuda_stream) {
+  if (n < 0 || k < 0 || k > n) return fail(AFD_ERR_INVALID_ARG, "need 0 <= k <= n");
+  if (n > 0 && (!keys || !kept)) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (n == 0) {
+    if (tau_out) *tau_out = NAN;
+    return AFD_OK;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  SelectState* st = nullptr;
+  uint32_t* cnt = nullptr;
+  const int nch = (int)((n + SEL_CHUNK - 1) / SEL_CHUNK);
+  TRY(dalloc(&st, 1));
+  int rc = dalloc(&cnt, (size_t)nch);
+  if (rc == AFD_OK) rc = select_topk_dev(s, keys, n, k, kept, st, cnt, nullptr, nullptr, 0.0, tau_out, nullptr);
+  cudaFree(st);
+  if (cnt) cudaFree(cnt);
+  return rc;
+}
+
+int afd_levelset_update(afd_mesh* m, int kind, const double* weights, double volume_fraction, double* tau_out,
+                        uint8_t* kept_out) {
+  if (!m || !weights) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (kind < 0 || kind > 2) return fail(AFD_ERR_INVALID_ARG, "unknown field kind %d", kind);
+  if (!std::isfinite(volume_fraction)) return fail(AFD_ERR_INVALID_ARG, "volume fraction must be finite");
+  if (!m->has_solution) return fail(AFD_ERR_STATE, "no solution");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const int R = m->nrhs;
+  const int64_t n = m->gr.nelem;
+  if (!m->fkeys) {
+    TRY(dalloc(&m->fkeys, (size_t)n));
+    TRY(dalloc(&m->kept, (size_t)n));
+    SelectState* st;
+    TRY(dalloc(&st, 1));
+    m->sel = st;
+    TRY(dalloc(&m->selcnt, (size_t)((n + SEL_CHUNK - 1) / SEL_CHUNK)));
+  }
+  TRY(fields_to(m, kind, m->fbuf));
+  float* dmaxv = m->fsmall + FS_MAXV;
+  float* dw = m->fsmall + FS_WEIGHTS;
+  TRY(maxabs_per_rhs(m, m->fbuf, R, dmaxv));
+  std::vector<float> wf(R);
+  for (int r = 0; r < R; ++r) wf[r] = (float)weights[r];
+  CK(cudaMemcpyAsync(dw, wf.data(), R * sizeof(float), cudaMemcpyHostToDevice, m->s));
+  k_combine<<<grid_blocks(n, 256, 4096), 256, 0, m->s>>>((int)n, R, m->fbuf, dw, dmaxv, m->fkeys); m->launches++;
+  CK(cudaGetLastError());
+  const double kd = std::floor(volume_fraction * (double)n + 0.5);
+  const int64_t k = (int64_t)std::min<double>(std::max<double>(kd, 0.0), (double)n);
+  float tau;
+  TRY(select_topk_dev(m->s, m->fkeys, n, k, m->kept, (SelectState*)m->sel, m->selcnt, m->E64, nullptr, m->opt.e_void, &tau, &m->launches));
+  TRY(refresh_moduli(m));
+  if (kept_out) CK(cudaMemcpyAsync(kept_out, m->kept, (size_t)n, cudaMemcpyDeviceToHost, m->s));
+  if (tau_out) *tau_out = (double)tau;
+  return finish(m);
+}
+
+int afd_apply_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y) {
+  if (!m || !u || !y) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "n_rhs must be >= 1");
+  if (!m->has_moduli) return fail(AFD_ERR_STATE, "moduli not set");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  if (arith == AFD_F64)
+    TRY((launch_stencil<double, ST_APPLY, double>(m, (const double*)u, (double*)y, m->w64.E, nullptr, nullptr, nullptr,
+                                                    nullptr, n_rhs, m->w64.K)));
+  else if (arith == AFD_F32)
+    TRY((launch_stencil<float, ST_APPLY, float>(m, (const float*)u, (float*)y, m->w32.E, nullptr, nullptr, nullptr,
+                                                  nullptr, n_rhs, m->w32.K)));
+  else
+    return fail(AFD_ERR_INVALID_ARG, "arith must be AFD_F32 or AFD_F64");
+  return finish(m);
+}
+
+int afd_deflation_wt(afd_mesh* m, int n_rhs, const double* v, double* out) {
+  if (!m || !v || !out || n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "bad argument");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  k_restrict<double><<<dim3(m->gp.ng, n_rhs), 256, 0, m->s>>>(m->gr, m->gp, v, nullptr, m->fixed, out, nullptr, nullptr); m->launches++;
+  CK(cudaGetLastError());
+  return finish(m);
+}
+
+int afd_deflation_w(afd_mesh* m, int n_rhs, const double* y, double* out) {
+  if (!m || !y || !out || n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "bad argument");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  k_prolong<double><<<dim3(grid_blocks(m->gr.nnodes, 256, 4096), n_rhs), 256, 0, m->s>>>(1, m->gr, m->gp, out, nullptr, y,
+                                                                                          m->fixed, nullptr); m->launches++;
+  CK(cudaGetLastError());
+  return finish(m);
+}
+
+int afd_coarse_size(afd_mesh* m) { return m ? m->nc : 0; }
+
+int64_t afd_kernel_launches(const afd_mesh* m) { return m ? m->launches : 0; }
+
+int afd_time_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y, int launches, double* ms_out) {
+  if (!m || !u || !y || !ms_out || launches < 1 || n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "bad argument");
+  if (!m->has_moduli) return fail(AFD_ERR_STATE, "moduli not set");
+  if (arith != AFD_F32 && arith != AFD_F64) return fail(AFD_ERR_INVALID_ARG, "arith must be AFD_F32 or AFD_F64");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, m->s));
+  for (int i = 0; i < launches; ++i) {
+    if (arith == AFD_F64)
+      TRY((launch_stencil<double, ST_APPLY, double>(m, (const double*)u, (double*)y, m->w64.E, nullptr, nullptr, nullptr,
+                                                      nullptr, n_rhs, m->w64.K)));
+    else
+      TRY((launch_stencil<float, ST_APPLY, float>(m, (const float*)u, (float*)y, m->w32.E, nullptr, nullptr, nullptr,
+                                                    nullptr, n_rhs, m->w32.K)));
+  }
+  CK(cudaEventRecord(e1, m->s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = (double)ms / launches;
+  return finish(m);
+}
+
+int afd_coarse_matrix(afd_mesh* m, double* out_host) {
+  if (!m || !out_host) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  m->coarse_valid = false;
+  int rc = build_coarse(m);
+  if (rc != AFD_OK && rc != AFD_ERR_COARSE_SINGULAR) return rc;
+  CK(cudaMemcpyAsync(out_host, m->Ec, (size_t)m->nc * m->nc * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+  TRY(finish(m));
+  return rc;
+}
+
+// ---- augmented Lagrangian scalars (Eqs. 3.11, 3.12, 3.18) ----
+void afd_al_init(afd_al_state* s) {
+  if (!s) return;
+  s->mu = 100.0;
+  s->gamma = 10.0;
+  s->g = 0.0;
+  s->k = 0;
+}
+
+void afd_al_update(afd_al_state* s, double g_new) {
+  if (!s) return;
+  s->k += 1;
+  s->mu = std::max(s->mu + s->gamma * g_new, 0.0);
+  if (!(std::max(g_new, 0.0) <= 0.25 * std::max(s->g, 0.0))) s->gamma = std::max(10.0 * s->gamma, (double)s->k * s->k);
+  s->g = g_new;
+}
+
+double afd_al_weight(const afd_al_state* s) {
+  if (!s) return 0.0;
+  const double w = s->mu + s->gamma * s->g;
+  return w > 0.0 ? w : 0.0;
+}
+

@@ -1,0 +1,244 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Tolerances (written here, derived in the design doc): stencil FP64 1e-13 and FP32
+2e-6 relative (max-norm against max |y|); coarse matrix 1e-12; FP64 solve
+relative L2(u) <= 1e-9 and J <= 1e-10; mixed solve L2(u) <= 1e-5 and
+J <= 1e-6; sensitivities 1e-5 (mixed) and 2e-7 (FP64, float32 output);
+selection bit exact.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import paper_2203_15115_gb300 as afd  # noqa: E402
+from oracle import deflation, fe, levelset, sensitivity  # noqa: E402
+from synthetic import (clamp_face_x0, cantilever_24x12x12_solid, edge_load, small_cantilever,  # noqa: E402
+                       sphere_voids, top_point_loads)
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    afd.lib()
+
+
+def rand_fixed(nx, ny, nz, rng, p=0.1):
+    return (rng.random(3 * (nx + 1) * (ny + 1) * (nz + 1)) < p).astype(np.uint8)
+
+
+def oracle_masked_matvec(K, u, fixed):
+    uu = u.copy()
+    uu[fixed != 0] = 0.0
+    y = K @ uu
+    y[fixed != 0] = 0.0
+    return y
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (5, 3, 2), (33, 9, 5), (40, 17, 11), (3, 31, 8)])
+def test_stencil_matches_assembled_K(dims):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(sum(dims))
+    E = rng.uniform(1e-3, 1.0, nx * ny * nz)
+    fixed = rand_fixed(nx, ny, nz, rng)
+    K = fe.assemble(nx, ny, nz, E)
+    R = 3
+    u = rng.standard_normal((R, K.shape[0]))
+    m = afd.Mesh(nx, ny, nz)
+    m.set_element_moduli(E)
+    m.set_loads_bcs(np.zeros((1, K.shape[0])), fixed)
+    ref = np.stack([oracle_masked_matvec(K, u[r], fixed) for r in range(R)])
+    y64 = torch.zeros((R, K.shape[0]), dtype=torch.float64, device="cuda")
+    afd.afd_apply_stiffness(m.h, afd.AFD_F64, R, cuda(u), y64)
+    y64 = y64.cpu().numpy()
+    assert np.max(np.abs(y64 - ref)) <= 1e-13 * np.max(np.abs(ref))
+    y32 = torch.zeros((R, K.shape[0]), dtype=torch.float32, device="cuda")
+    afd.afd_apply_stiffness(m.h, afd.AFD_F32, R, cuda(u.astype(np.float32)), y32)
+    y32 = y32.cpu().numpy().astype(np.float64)
+    ref32 = np.stack([oracle_masked_matvec(K, u[r].astype(np.float32).astype(np.float64), fixed) for r in range(R)])
+    assert np.max(np.abs(y32 - ref32)) <= 2e-6 * np.max(np.abs(ref32))
+    m.close()
+
+
+@pytest.mark.parametrize("dims,g", [((4, 2, 2), 2), ((9, 5, 7), 3), ((12, 6, 6), 4)])
+def test_deflation_operators_and_coarse_matrix(dims, g):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(11)
+    E = np.where(rng.random(nx * ny * nz) < 0.3, 1e-3, 1.0)
+    fixed = clamp_face_x0(nx, ny, nz)
+    fixed[rng.random(fixed.size) < 0.05] = 1
+    m = afd.Mesh(nx, ny, nz, group=g)
+    m.set_element_moduli(E)
+    m.set_loads_bcs(edge_load(nx, ny, nz)[None], fixed)
+    W = deflation.deflation_matrix(nx, ny, nz, g, fixed)
+    nc = W.shape[1]
+    assert afd.afd_coarse_size(m.h) == nc
+    v = rng.standard_normal((2, W.shape[0]))
+    out = torch.zeros((2, nc), dtype=torch.float64, device="cuda")
+    afd.afd_deflation_wt(m.h, 2, cuda(v), out)
+    ref = v @ W
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
+    y = rng.standard_normal((2, nc))
+    out2 = torch.zeros((2, W.shape[0]), dtype=torch.float64, device="cuda")
+    afd.afd_deflation_w(m.h, 2, cuda(y), out2)
+    ref2 = y @ W.T
+    assert np.max(np.abs(out2.cpu().numpy() - ref2)) <= 1e-12 * np.max(np.abs(ref2))
+    Ec = afd.afd_coarse_matrix(m.h)
+    K = fe.assemble(nx, ny, nz, E)
+    Eref = deflation.coarse_matrix(K, W, fixed)
+    assert np.max(np.abs(Ec - Eref)) <= 1e-12 * np.max(np.abs(Eref))
+    m.close()
+
+
+def _solve(w, precision, tol, group=None):
+    m = afd.Mesh(w.nx, w.ny, w.nz, precision=precision, group=group or w.group)
+    m.set_element_moduli(w.E)
+    m.set_loads_bcs(w.f, w.fixed)
+    u = np.zeros_like(w.f)
+    stats = m.solve(tol, u_out=u)
+    return m, u, stats
+
+
+def test_fp64_solve_cantilever_24x12x12():
+    w = cantilever_24x12x12_solid()
+    m, u, stats = _solve(w, afd.AFD_FP64, 1e-10)
+    K = fe.assemble(w.nx, w.ny, w.nz, w.E)
+    uref = fe.solve_direct(K, w.f[0], w.fixed)
+    assert np.linalg.norm(u[0] - uref) <= 1e-9 * np.linalg.norm(uref)
+    assert fe.relative_residual(K, u[0], w.f[0], w.fixed) <= 1e-10
+    J = m.compliance()[0]
+    assert abs(J - fe.compliance(w.f[0], uref)) <= 1e-10 * abs(J)
+    assert stats[0]["rel_residual"] <= 1e-10
+    m.close()
+
+
+@pytest.mark.parametrize("case", ["solid", "voids"])
+def test_mixed_solve_matches_oracle(case):
+    if case == "solid":
+        w = cantilever_24x12x12_solid()
+    else:
+        w = small_cantilever(30, 14, 10, seed=3, n_spheres=6, rmin=1.5, rmax=4.0, group=4)
+    m, u, stats = _solve(w, afd.AFD_MIXED, 1e-8)
+    K = fe.assemble(w.nx, w.ny, w.nz, w.E)
+    uref = fe.solve_direct(K, w.f[0], w.fixed)
+    assert stats[0]["rel_residual"] <= 1e-8
+    assert fe.relative_residual(K, u[0], w.f[0], w.fixed) <= 1.0001e-8
+    assert np.linalg.norm(u[0] - uref) <= 1e-5 * np.linalg.norm(uref)
+    J = m.compliance()[0]
+    assert abs(J - fe.compliance(w.f[0], uref)) <= 1e-6 * abs(J)
+    m.close()
+
+
+def test_multi_rhs_batch_equals_single_solves():
+    nx, ny, nz = 20, 10, 8
+    E = sphere_voids(nx, ny, nz, 5, 1.5, 3.0, 4, 1e-3)
+    fixed = clamp_face_x0(nx, ny, nz)
+    f = np.concatenate([edge_load(nx, ny, nz)[None], top_point_loads(nx, ny, nz, 3, 9)])
+    m = afd.Mesh(nx, ny, nz, group=4)
+    m.set_element_moduli(E)
+    m.set_loads_bcs(f, fixed)
+    ub = np.zeros_like(f)
+    m.solve(1e-9, u_out=ub)
+    K = fe.assemble(nx, ny, nz, E)
+    for r in range(f.shape[0]):
+        ms = afd.Mesh(nx, ny, nz, group=4)
+        ms.set_element_moduli(E)
+        ms.set_loads_bcs(f[r:r + 1], fixed)
+        us = np.zeros((1, f.shape[1]))
+        ms.solve(1e-9, u_out=us)
+        uref = fe.solve_direct(K, f[r], fixed)
+        assert np.linalg.norm(ub[r] - uref) <= 1e-6 * np.linalg.norm(uref)
+        assert np.linalg.norm(ub[r] - us[0]) <= 1e-6 * np.linalg.norm(uref)
+        ms.close()
+    m.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(afd.AFD_MIXED, 1e-5), (afd.AFD_FP64, 2e-7)])
+def test_sensitivities_match_oracle(precision, tol):
+    w = small_cantilever(24, 12, 8, seed=7, n_spheres=5, rmin=1.5, rmax=3.5, group=4)
+    m, u, _ = _solve(w, precision, 1e-10 if precision == afd.AFD_FP64 else 1e-8)
+    K = fe.assemble(w.nx, w.ny, w.nz, w.E)
+    uref = fe.solve_direct(K, w.f[0], w.fixed)
+    refs = {
+        afd.AFD_SENS_STRAIN_ENERGY: sensitivity.strain_energy(w.nx, w.ny, w.nz, w.E, uref),
+        afd.AFD_SENS_TJ: sensitivity.topological_compliance(w.nx, w.ny, w.nz, w.E, uref),
+        afd.AFD_SENS_VON_MISES: sensitivity.element_von_mises(w.nx, w.ny, w.nz, w.E, uref),
+    }
+    for kind, ref in refs.items():
+        out = np.zeros((1, m.nelem), np.float32)
+        m.sensitivity(kind, out)
+        assert np.linalg.norm(out[0] - ref) <= tol * np.linalg.norm(ref), kind
+    p = 8.0
+    pn = m.pnorm_stress(p)[0]
+    assert abs(pn - sensitivity.pnorm(refs[afd.AFD_SENS_VON_MISES], p)) <= 10 * tol * pn
+    s = np.zeros((1, m.nelem), np.float32)
+    m.sensitivity(afd.AFD_SENS_STRAIN_ENERGY, s)
+    assert abs(s.astype(np.float64).sum() - m.compliance()[0]) <= 1e-5 * m.compliance()[0]
+    m.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 1000, 4096, 4097, 100003])
+def test_select_topk_bit_exact(n):
+    rng = np.random.default_rng(n)
+    keys = np.concatenate([rng.integers(-3, 4, n // 2).astype(np.float32),
+                           rng.standard_normal(n - n // 2).astype(np.float32)])
+    rng.shuffle(keys)
+    if n > 3:
+        keys[:3] = [0.0, -0.0, 0.0]
+    dk = cuda(keys)
+    for frac in (0.0, 0.01, 0.37, 0.5, 0.999, 1.0):
+        k = levelset.keep_count(frac, n)
+        kept = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        tau = afd.afd_select_topk(dk, k, kept)
+        ref, tref = levelset.select_top(keys, k)
+        assert np.array_equal(kept.cpu().numpy(), ref), (n, frac)
+        if k:
+            assert tau == np.float32(tref)
+
+
+def test_levelset_update_keeps_the_oracle_set_up_to_rounding_ties():
+    w = small_cantilever(24, 12, 8, seed=8, n_spheres=4, rmin=1.5, rmax=3.5, group=4, n_rhs=2)
+    m, u, _ = _solve(w, afd.AFD_MIXED, 1e-9)
+    K = fe.assemble(w.nx, w.ny, w.nz, w.E)
+    fields = []
+    for r in range(2):
+        uref = fe.solve_direct(K, w.f[r], w.fixed)
+        fields.append(sensitivity.strain_energy(w.nx, w.ny, w.nz, w.E, uref).astype(np.float32))
+    weights = [1.0, 0.5]
+    keys = levelset.combine(fields, weights)
+    v = 0.8
+    kref, tref = levelset.select_top(keys, levelset.keep_count(v, keys.size))
+    kept = np.zeros(m.nelem, np.uint8)
+    tau = m.levelset_update(afd.AFD_SENS_STRAIN_ENERGY, weights, v, kept)
+    assert kept.sum() == kref.sum()
+    diff = np.flatnonzero(kept != kref)
+    # disagreements only where the oracle key sits within rounding of the cut
+    assert np.all(np.abs(keys[diff] - tref) <= 1e-4 * abs(tref) + 1e-30)
+    assert abs(tau - tref) <= 1e-4 * abs(tref)
+    m.close()
+
+
+def test_error_paths():
+    nx, ny, nz = 6, 3, 3
+    m = afd.Mesh(nx, ny, nz, group=2)
+    with pytest.raises(afd.AFDError) as e:
+        m.solve(1e-6)
+    assert e.value.code == afd.AFD_ERR_STATE
+    bad = np.ones(nx * ny * nz)
+    bad[3] = np.nan
+    with pytest.raises(afd.AFDError) as e:
+        m.set_element_moduli(bad)
+    assert e.value.code == afd.AFD_ERR_INVALID_ARG
+    m.set_element_moduli(np.ones(nx * ny * nz))
+    # no supports: the rigid motions of the whole body are in the coarse space
+    m.set_loads_bcs(edge_load(nx, ny, nz)[None], np.zeros(3 * 7 * 4 * 4, np.uint8))
+    with pytest.raises(afd.AFDError) as e:
+        m.solve(1e-6)
+    assert e.value.code == afd.AFD_ERR_COARSE_SINGULAR
+    m.close()
