@@ -74,6 +74,9 @@ template <typename T>
 struct Work {
   int cap = 0;  // RHS capacity
   T *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *t = nullptr, *b = nullptr;
+  T* r2 = nullptr;       // second residual buffer (r is double-buffered across iterations)
+  T* AW = nullptr;       // K W on the node shells of the groups (see k_build_aw)
+  size_t aw_cap = 0;
   T* invdiag = nullptr;
   T* E = nullptr;
   ElemConsts<T> K;
@@ -111,8 +114,20 @@ struct afd_mesh {
   float* fsmall = nullptr;   // small float scratch (partials of max, weights, maxima)
   // coarse
   int nc = 0;
-  double *Ec = nullptr, *Lw = nullptr, *Einv = nullptr, *dmax = nullptr;
+  int nsplit = 1;              // slabs per group in the coarse right-hand side
+  double* Ec = nullptr;        // W^T K W, FP64 sums
+  double* Einv64 = nullptr;    // its inverse, FP64 path
+  float* Einv32 = nullptr;     // its inverse, mixed path
+  double *gjP = nullptr, *gjB = nullptr, *gjR = nullptr;  // Gauss-Jordan scratch
+  double* cpart = nullptr;     // coarse right-hand side partials [rhs][G][split][12]
+  unsigned int* counters = nullptr;  // last-block counters: [rhs] stencil, [MAX_RHS] coarse
+  double* dmax = nullptr;
   int* dstatus = nullptr;
+  uint8_t* gfix = nullptr;     // [N_g] group holds a fixed DOF
+  std::vector<uint8_t> gfix_h;  // host copy
+  long long* aw_off = nullptr; // [N_g] offset of group G's block in AW
+  size_t aw_total = 0;         // elements of AW
+  int nsplit_aw = 1;
   bool coarse_valid = false;
   Work<float> w32;
   Work<double> w64;
@@ -177,11 +192,13 @@ static int ensure_partials(afd_mesh* m, size_t n) {
   return AFD_OK;
 }
 
+constexpr int TY32 = 16, TY64 = 8;  // warps per stencil CTA for FP32 / FP64
+
 static void stencil_geom(const afd_mesh* m, bool f64, int& tiles_x, dim3& grid) {
   if (f64)
-    StencilGeom<32, 4>::get(m->gr, m->kz, tiles_x, grid);
+    StencilGeom<TY64>::get(m->gr, m->kz, tiles_x, grid);
   else
-    StencilGeom<32, 8>::get(m->gr, m->kz, tiles_x, grid);
+    StencilGeom<TY32>::get(m->gr, m->kz, tiles_x, grid);
 }
 
 static int stencil_blocks(const afd_mesh* m, bool f64) {
@@ -193,9 +210,11 @@ static int stencil_blocks(const afd_mesh* m, bool f64) {
 
 template <typename T, int MODE, typename TF>
 static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f, float* y32, double* partials,
-                          const int* done, int nrhs, const ElemConsts<T>& K) {
+                          const int* done, int nrhs, const ElemConsts<T>& K, CGState* st = nullptr,
+                          unsigned int* counter = nullptr, const T* z = nullptr, const double* mu = nullptr,
+                          T* pout = nullptr) {
   constexpr bool F64 = sizeof(T) == 8;
-  constexpr int TX = 32, TY = F64 ? 4 : 8;
+  constexpr int TY = F64 ? TY64 : TY32;
   StencilArgs<T, TF> a;
   a.gr = m->gr;
   a.u = u;
@@ -208,10 +227,16 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
   a.partials = partials;
   a.done = done;
   a.kz = m->kz;
+  a.st = st;
+  a.counter = counter;
+  a.z = z;
+  a.mu = mu;
+  a.pout = pout;
+  a.gp = m->gp;
   dim3 grid;
-  StencilGeom<TX, TY>::get(m->gr, m->kz, a.tiles_x, grid);
+  StencilGeom<TY>::get(m->gr, m->kz, a.tiles_x, grid);
   grid.z = nrhs;
-  stencil_kernel<T, TX, TY, MODE, TF><<<grid, TX * TY, 0, m->s>>>(a); m->launches++;
+  stencil_kernel<T, TY, MODE, TF><<<grid, ST_TX * TY, 0, m->s>>>(a); m->launches++;
   CK(cudaGetLastError());
   return AFD_OK;
 }
@@ -229,11 +254,11 @@ template <typename T>
 static int ensure_work(afd_mesh* m, Work<T>& w, int nrhs) {
   if (w.cap >= nrhs) return AFD_OK;
   invalidate_graphs(m);
-  dfree(w.x); dfree(w.r); dfree(w.z); dfree(w.p); dfree(w.q); dfree(w.t); dfree(w.b);
+  dfree(w.x); dfree(w.r); dfree(w.z); dfree(w.p); dfree(w.q); dfree(w.t); dfree(w.b); dfree(w.r2);
   if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
   const size_t n = (size_t)nrhs * m->gr.ndof;
   TRY(dalloc(&w.x, n)); TRY(dalloc(&w.r, n)); TRY(dalloc(&w.z, n)); TRY(dalloc(&w.p, n));
-  TRY(dalloc(&w.q, n)); TRY(dalloc(&w.t, n)); TRY(dalloc(&w.b, n));
+  TRY(dalloc(&w.q, n)); TRY(dalloc(&w.t, n)); TRY(dalloc(&w.b, n)); TRY(dalloc(&w.r2, n));
   w.cap = nrhs;
   return AFD_OK;
 }
@@ -248,6 +273,8 @@ static int ensure_rhs(afd_mesh* m, int nrhs) {
   TRY(dalloc(&m->st, (size_t)nrhs)); TRY(dalloc(&m->done, (size_t)nrhs));
   TRY(dalloc(&m->v, (size_t)nrhs * m->nc)); TRY(dalloc(&m->mu, (size_t)nrhs * m->nc));
   TRY(dalloc(&m->wr, (size_t)nrhs * m->nc));
+  dfree(m->cpart);
+  TRY(dalloc(&m->cpart, (size_t)nrhs * m->gp.ng * m->nsplit * 14));
   TRY(dalloc(&m->fbuf, (size_t)nrhs * m->gr.nelem));
   m->cap = nrhs;
   // graphs captured for a smaller RHS count stay valid; none need freeing here
@@ -257,30 +284,22 @@ static int ensure_rhs(afd_mesh* m, int nrhs) {
 // ---------------------------------------------------------------------------
 // coarse problem
 // ---------------------------------------------------------------------------
-static int build_coarse(afd_mesh* m) {
-  if (m->coarse_valid) return AFD_OK;
-  if (!m->has_moduli) return fail(AFD_ERR_STATE, "moduli not set");
+// In-place inverse of the SPD coarse matrix A (nc x nc, type T) by blocked
+// Gauss-Jordan sweeps; a relative pivot below `rel` means W^T K W is singular.
+template <typename T>
+static int invert_coarse(afd_mesh* m, T* A, double rel) {
   const int nc = m->nc;
-  const size_t nn = (size_t)nc * nc;
-  if (!m->Ec) {
-    TRY(dalloc(&m->Ec, nn)); TRY(dalloc(&m->Lw, nn)); TRY(dalloc(&m->Einv, nn));
-    TRY(dalloc(&m->dmax, 1)); TRY(dalloc(&m->dstatus, 1));
-  }
-  CK(cudaMemsetAsync(m->Ec, 0, nn * sizeof(double), m->s));
-  k_coarse_assemble<<<m->gp.ng, COARSE_WARPS * 32, 0, m->s>>>(m->gr, m->gp, m->E64, m->fixed, m->w64.K, m->Ec); m->launches++;
-  CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(m->Lw, m->Ec, nn * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
-  CK(cudaMemsetAsync(m->dstatus, 0, sizeof(int), m->s));
   k_max_diag<<<1, 256, 0, m->s>>>(m->Ec, nc, m->dmax); m->launches++;
-  for (int k0 = 0; k0 < nc; k0 += CH_NB) {
-    k_potrf_diag<<<1, 256, 0, m->s>>>(m->Lw, nc, k0, m->dmax, m->dstatus); m->launches++;
-    const int nb = std::min(CH_NB, nc - k0);
-    const int rows = nc - k0 - nb;
-    if (rows > 0) {
-      k_trsm_panel<<<(rows + 127) / 128, 128, 0, m->s>>>(m->Lw, nc, k0); m->launches++;
-      const int nt = (rows + 31) / 32;
-      k_syrk_update<<<nt * (nt + 1) / 2, 256, 0, m->s>>>(m->Lw, nc, k0); m->launches++;
-    }
+  CK(cudaMemsetAsync(m->dstatus, 0, sizeof(int), m->s));
+  T* P = (T*)m->gjP;
+  T* B = (T*)m->gjB;
+  T* R = (T*)m->gjR;
+  const dim3 ug((nc + 31) / 32, (nc + 31) / 32);
+  for (int k0 = 0; k0 < nc; k0 += GJ_NB) {
+    const int nb = std::min(GJ_NB, nc - k0);
+    k_gj_pivot<T><<<1, 256, 0, m->s>>>(A, nc, k0, P, m->dmax, rel, m->dstatus); m->launches++;
+    k_gj_panel<T><<<(nc * nb + 255) / 256, 256, 0, m->s>>>(A, nc, k0, P, B, R); m->launches++;
+    k_gj_update<T><<<ug, 256, 0, m->s>>>(A, nc, k0, P, B, R, k0 + GJ_NB >= nc ? 1 : 0); m->launches++;
   }
   CK(cudaGetLastError());
   int status = 0;
@@ -288,16 +307,63 @@ static int build_coarse(afd_mesh* m) {
   CK(cudaStreamSynchronize(m->s));
   if (status != 0)
     return fail(AFD_ERR_COARSE_SINGULAR, "coarse matrix W^T K W is singular (are there enough supports?)");
-  // U = L^T into Einv (scratch), Linv into Lw, then Einv = Linv^T Linv
-  {
-    dim3 tb(32, 8), tg((nc + 31) / 32, (nc + 31) / 32);
-    k_transpose<<<tg, tb, 0, m->s>>>(m->Lw, m->Einv, nc); m->launches++;
-    const size_t shm = (size_t)nc * sizeof(double);
-    if (shm > 48 * 1024) CK(cudaFuncSetAttribute(k_trtri_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_trtri_cols<<<nc, 256, shm, m->s>>>(m->Einv, m->Lw, nc); m->launches++;
-    dim3 gg((nc + 31) / 32, (nc + 31) / 32);
-    k_gram<<<gg, 1024, 0, m->s>>>(m->Lw, m->Einv, nc); m->launches++;
-    CK(cudaGetLastError());
+  return AFD_OK;
+}
+
+// E = W^T K W into m->Ec (FP64 sums; element math in FP32 on the mixed path).
+static int assemble_coarse(afd_mesh* m) {
+  if (!m->has_moduli) return fail(AFD_ERR_STATE, "moduli not set");
+  const int nc = m->nc;
+  const size_t nn = (size_t)nc * nc;
+  if (!m->Ec) {
+    TRY(dalloc(&m->Ec, nn));
+    TRY(dalloc(&m->gjP, (size_t)GJ_NB * GJ_NB));
+    TRY(dalloc(&m->gjB, (size_t)nc * GJ_NB));
+    TRY(dalloc(&m->gjR, (size_t)nc * GJ_NB));
+    TRY(dalloc(&m->dmax, 1));
+    TRY(dalloc(&m->dstatus, 1));
+  }
+  CK(cudaMemsetAsync(m->Ec, 0, nn * sizeof(double), m->s));
+  const dim3 grid(m->gp.ng, 27);
+  if (m->opt.precision == AFD_FP64) {
+    k_coarse_block<double><<<grid, COARSE_THREADS, 0, m->s>>>(m->gr, m->gp, m->E64, m->fixed, m->w64.K, m->Ec); m->launches++;
+  } else {
+    k_coarse_block<float><<<grid, COARSE_THREADS, 0, m->s>>>(m->gr, m->gp, m->E64, m->fixed, m->w32.K, m->Ec); m->launches++;
+  }
+  CK(cudaGetLastError());
+  return AFD_OK;
+}
+
+// K W on the groups' node shells for the work type of the solve.
+template <typename T>
+static int build_aw(afd_mesh* m, Work<T>& w) {
+  if (!m->has_loads) return fail(AFD_ERR_STATE, "supports not set");
+  if (w.aw_cap < m->aw_total) {
+    invalidate_graphs(m);
+    dfree(w.AW);
+    TRY(dalloc(&w.AW, m->aw_total));
+    w.aw_cap = m->aw_total;
+  }
+  const dim3 grid(m->gp.ng, m->nsplit_aw);
+  k_build_aw<T><<<grid, 128, 0, m->s>>>(m->gr, m->gp, m->nsplit_aw, m->E64, m->fixed, m->gfix, m->aw_off, w.K, w.AW); m->launches++;
+  CK(cudaGetLastError());
+  return AFD_OK;
+}
+
+static int build_coarse(afd_mesh* m) {
+  if (m->coarse_valid) return AFD_OK;
+  TRY(assemble_coarse(m));
+  if (m->opt.precision == AFD_FP64) TRY(build_aw<double>(m, m->w64));
+  else TRY(build_aw<float>(m, m->w32));
+  const size_t nn = (size_t)m->nc * m->nc;
+  if (m->opt.precision == AFD_FP64) {
+    if (!m->Einv64) TRY(dalloc(&m->Einv64, nn));
+    CK(cudaMemcpyAsync(m->Einv64, m->Ec, nn * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
+    TRY(invert_coarse<double>(m, m->Einv64, 1e-12));
+  } else {
+    if (!m->Einv32) TRY(dalloc(&m->Einv32, nn));
+    k_convert_dense<float><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(nn, m->Ec, m->Einv32); m->launches++;
+    TRY(invert_coarse<float>(m, m->Einv32, 1e-5));
   }
   m->coarse_valid = true;
   return AFD_OK;
@@ -326,38 +392,49 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
   }
   CK(cudaMemcpyAsync(m->st, h.data(), nrhs * sizeof(CGState), cudaMemcpyHostToDevice, m->s));
   CK(cudaMemcpyAsync(m->done, hd.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, m->s));
-  const dim3 vg(RED_BLOCKS, nrhs);
   const dim3 gg(m->gp.ng, nrhs);
+  const dim3 ug(m->gp.ng, m->nsplit, nrhs);
   const dim3 pg(grid_blocks(gr.nnodes, 256, 4 * RED_BLOCKS), nrhs);
-  const int capply_blocks = (m->nc * 32 + 255) / 256;
+  const int crows = (m->nc * 32 + 255) / 256;
+  const size_t csmem = (size_t)m->nc * sizeof(double);
+  const T* Einv = F64 ? (const T*)m->Einv64 : (const T*)m->Einv32;
+  unsigned int* cnt_st = m->counters;            // [rhs]
+  unsigned int* cnt_co = m->counters + MAX_RHS;  // coarse step
+  T* R[2] = {w.r, w.r2};
+  T* P[2] = {w.p, w.t};
   // r = b - K x ; x += W Einv W^T r ; r = b - K x  (deflated start)
-  TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, w.r, w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
-  k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, w.r, nullptr, m->fixed, m->v, nullptr, m->st); m->launches++;
-  k_coarse_apply<<<capply_blocks, 256, 0, m->s>>>(m->nc, nrhs, m->Einv, m->v, nullptr, m->mu, m->st); m->launches++;
+  TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, R[0], w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
+  k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, R[0], nullptr, m->fixed, m->v, nullptr, m->st); m->launches++;
+  k_coarse_solve<T><<<crows, 256, 0, m->s>>>(m->nc, nrhs, Einv, m->v, m->mu, m->st); m->launches++;
   k_prolong<T><<<pg, 256, 0, m->s>>>(2, gr, m->gp, x, nullptr, m->mu, m->fixed, m->st); m->launches++;
-  TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, w.r, w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
-  // two-level preconditioned residual y = z + W Einv W^T (r - K z), z = M^-1 r
+  TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, R[0], w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
+  // Two-level preconditioned residual y = z + W Einv W^T (r - K z), z = M^-1 r
   // (the A-DEF2 form of deflation: the W^T r term keeps W^T r from drifting
-  // under rounding, which the plain projected recurrence does not)
-  k_precond_dot<T><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, w.r, w.invdiag, w.z, m->partials, m->st); m->launches++;
-  TRY((launch_stencil<T, ST_APPLY, TB>(m, w.z, w.t, w.E, nullptr, nullptr, nullptr, m->done, nrhs, w.K)));
-  k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, w.r, w.t, m->fixed, m->wr, m->v, m->st); m->launches++;
-  k_coarse_apply<<<capply_blocks, 256, 0, m->s>>>(m->nc, nrhs, m->Einv, m->wr, m->v, m->mu, m->st); m->launches++;
-  k_finalize<<<nrhs, 256, 0, m->s>>>(FIN_INIT, m->partials, RED_BLOCKS, m->st, m->done, m->wr, m->mu, m->nc); m->launches++;
-  k_prolong<T><<<pg, 256, 0, m->s>>>(3, gr, m->gp, w.p, w.z, m->mu, m->fixed, m->st); m->launches++;
+  // under rounding, which the plain projected recurrence does not).  The
+  // initial step runs the merged update with alpha = 0 (p = q = 0).
+  CK(cudaMemsetAsync(P[0], 0, (size_t)nrhs * gr.ndof * sizeof(T), m->s));
+  CK(cudaMemsetAsync(w.q, 0, (size_t)nrhs * gr.ndof * sizeof(T), m->s));
+  k_update_coarse<T><<<ug, 256, 0, m->s>>>(gr, m->gp, m->nsplit, x, R[0], R[1], w.z, P[0], w.q, w.invdiag, m->fixed,
+                                          m->gfix, m->aw_off, w.AW, m->cpart, m->st); m->launches++;
+  k_coarse_step<T><<<crows, 256, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->nsplit, m->cpart, m->wr, 2, m->done,
+                                               cnt_co); m->launches++;
   CK(cudaGetLastError());
 
-  // one chunk of iterations, captured once into a graph
+  // One chunk of iterations (even length), captured once into a graph.  Per
+  // iteration: the stencil forms p = y + beta p_old while applying K to it
+  // (and takes alpha), the merged update/coarse kernel, the coarse step (beta).
   auto enqueue_chunk = [&]() -> int {
     for (int it = 0; it < m->opt.check_every; ++it) {
-      TRY((launch_stencil<T, ST_APPLY_DOT, TB>(m, w.p, w.q, w.E, nullptr, nullptr, m->partials, m->done, nrhs, w.K)));
-      k_finalize<<<nrhs, 256, 0, m->s>>>(FIN_ALPHA, m->partials, nsb, m->st, m->done, nullptr, nullptr, 0); m->launches++;
-      k_cg_update<T><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, x, w.r, w.z, w.p, w.q, w.invdiag, m->partials, m->st); m->launches++;
-      TRY((launch_stencil<T, ST_APPLY, TB>(m, w.z, w.t, w.E, nullptr, nullptr, nullptr, m->done, nrhs, w.K)));
-      k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, w.r, w.t, m->fixed, m->wr, m->v, m->st); m->launches++;
-      k_coarse_apply<<<capply_blocks, 256, 0, m->s>>>(m->nc, nrhs, m->Einv, m->wr, m->v, m->mu, m->st); m->launches++;
-      k_finalize<<<nrhs, 256, 0, m->s>>>(FIN_BETA, m->partials, RED_BLOCKS, m->st, m->done, m->wr, m->mu, m->nc); m->launches++;
-      k_prolong<T><<<pg, 256, 0, m->s>>>(0, gr, m->gp, w.p, w.z, m->mu, m->fixed, m->st); m->launches++;
+      T* pold = P[it & 1];
+      T* pnew = P[(it + 1) & 1];
+      T* rold = R[(it + 1) & 1];
+      T* rnew = R[it & 1];
+      TRY((launch_stencil<T, ST_APPLY_DOT, TB>(m, pold, w.q, w.E, nullptr, nullptr, m->partials, m->done, nrhs, w.K,
+                                                m->st, cnt_st, w.z, m->mu, pnew)));
+      k_update_coarse<T><<<ug, 256, 0, m->s>>>(gr, m->gp, m->nsplit, x, rold, rnew, w.z, pnew, w.q, w.invdiag, m->fixed,
+                                              m->gfix, m->aw_off, w.AW, m->cpart, m->st); m->launches++;
+      k_coarse_step<T><<<crows, 256, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->nsplit, m->cpart, m->wr, 1,
+                                                   m->done, cnt_co); m->launches++;
     }
     CK(cudaGetLastError());
     return AFD_OK;
@@ -432,6 +509,7 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
   afd_options o;
   afd_default_options(&o);
   if (opt) o = *opt;
+  o.check_every += o.check_every & 1;  // p is double-buffered: chunks of even length
   if (!(o.nu > -1.0 && o.nu < 0.5) || !(o.h > 0.0) || !(o.e_void > 0.0) || o.max_iter < 1 || o.max_refine < 0 ||
       o.check_every < 1 || o.group < 0 || (o.precision != AFD_MIXED && o.precision != AFD_FP64))
     return fail(AFD_ERR_INVALID_ARG, "invalid options");
@@ -453,13 +531,22 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
   gp.ng = gp.ngx * gp.ngy * gp.ngz;
   gp.h = o.h;
   m->nc = 6 * gp.ng;
+  // shares per group of the merged update / coarse right-hand side kernel
+  // (about 600 blocks) and of the K W build (about 2400 blocks of 128 threads)
+  m->nsplit = std::max(1, std::min(4 * gp.g, (600 + gp.ng - 1) / gp.ng));
+  m->nsplit_aw = std::max(1, std::min(16 * gp.g, (2400 + gp.ng - 1) / gp.ng));
+  if (m->nc > 8192) {
+    delete m;
+    return fail(AFD_ERR_INVALID_ARG, "coarse space too large (%d unknowns > 8192): use a larger group", 6 * gp.ng);
+  }
   // z planes per CTA: enough CTAs to fill the GPU a few times
   {
     int tx;
     dim3 gr;
-    StencilGeom<32, 8>::get(g, g.nnz, tx, gr);
+    StencilGeom<TY32>::get(g, g.nnz, tx, gr);
     const long tiles = gr.x;
-    long kz = (long)g.nnz * tiles / 2400;
+    // about two waves of 512-thread CTAs (2 resident per SM), at least 4 planes per CTA
+    long kz = (long)g.nnz * tiles / 608;
     m->kz = (int)std::max(4L, std::min<long>(kz, g.nnz));
   }
   m->w32.K = make_elem_consts<float>(o.nu, o.h);
@@ -473,11 +560,15 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
   if ((rc = dalloc(&m->E64, (size_t)g.nelem)) != AFD_OK || (rc = dalloc(&m->w32.E, (size_t)g.nelem)) != AFD_OK ||
       (rc = dalloc(&m->w64.E, (size_t)g.nelem)) != AFD_OK || (rc = dalloc(&m->w32.invdiag, (size_t)g.nnodes)) != AFD_OK ||
       (rc = dalloc(&m->w64.invdiag, (size_t)g.nnodes)) != AFD_OK || (rc = dalloc(&m->fixed, (size_t)g.nnodes)) != AFD_OK ||
-      (rc = dalloc(&m->fsmall, (size_t)FSMALL_SIZE)) != AFD_OK) {
+      (rc = dalloc(&m->fsmall, (size_t)FSMALL_SIZE)) != AFD_OK ||
+      (rc = dalloc(&m->counters, (size_t)MAX_RHS + 1)) != AFD_OK ||
+      (rc = dalloc(&m->gfix, (size_t)gp.ng)) != AFD_OK ||
+      (rc = dalloc(&m->aw_off, (size_t)gp.ng)) != AFD_OK) {
     afd_destroy(m);
     return rc;
   }
   cudaMemsetAsync(m->fixed, 0, g.nnodes, m->s);
+  cudaMemsetAsync(m->counters, 0, (MAX_RHS + 1) * sizeof(unsigned int), m->s);
   if (cudaStreamSynchronize(m->s) != cudaSuccess) {
     afd_destroy(m);
     return fail(AFD_ERR_CUDA, "init failed");
@@ -492,20 +583,23 @@ void afd_destroy(afd_mesh* m) {
   if (m->s) cudaStreamSynchronize(m->s);
   for (auto* wp : {&m->w32}) {
     dfree(wp->x); dfree(wp->r); dfree(wp->z); dfree(wp->p); dfree(wp->q); dfree(wp->t); dfree(wp->b);
+    dfree(wp->r2); dfree(wp->AW);
     dfree(wp->invdiag); dfree(wp->E);
     if (wp->graph) cudaGraphExecDestroy(wp->graph);
   }
   {
     auto* wp = &m->w64;
     dfree(wp->x); dfree(wp->r); dfree(wp->z); dfree(wp->p); dfree(wp->q); dfree(wp->t); dfree(wp->b);
+    dfree(wp->r2); dfree(wp->AW);
     dfree(wp->invdiag); dfree(wp->E);
     if (wp->graph) cudaGraphExecDestroy(wp->graph);
   }
   dfree(m->E64); dfree(m->fixed); dfree(m->f64); dfree(m->u64); dfree(m->r64); dfree(m->partials);
-  dfree(m->st); dfree(m->done); dfree(m->v); dfree(m->mu); dfree(m->wr); dfree(m->fbuf); dfree(m->fkeys); dfree(m->kept);
+  dfree(m->st); dfree(m->done); dfree(m->v); dfree(m->mu); dfree(m->wr); dfree(m->cpart); dfree(m->fbuf); dfree(m->fkeys); dfree(m->kept);
   if (m->sel) cudaFree(m->sel);
   dfree(m->selcnt); dfree(m->fsmall);
-  dfree(m->Ec); dfree(m->Lw); dfree(m->Einv); dfree(m->dmax); dfree(m->dstatus);
+  dfree(m->Ec); dfree(m->Einv64); dfree(m->Einv32); dfree(m->gjP); dfree(m->gjB); dfree(m->gjR);
+  dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gfix); dfree(m->aw_off);
   if (m->ev) cudaEventDestroy(m->ev);
   if (m->s) cudaStreamDestroy(m->s);
   delete m;
@@ -596,6 +690,21 @@ int afd_set_loads_bcs(afd_mesh* m, int n_rhs, const double* f, int f_on_device, 
     CK(cudaMemcpyAsync(dmask, mask, g.ndof, cudaMemcpyHostToDevice, m->s));
   }
   k_pack_fixed<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g.nnodes, dmask, m->fixed); m->launches++;
+  CK(cudaMemsetAsync(m->gfix, 0, m->gp.ng, m->s));
+  k_group_fixed<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->gp, m->fixed, m->gfix); m->launches++;
+  m->gfix_h.assign(m->gp.ng, 0);
+  CK(cudaMemcpyAsync(m->gfix_h.data(), m->gfix, m->gp.ng, cudaMemcpyDeviceToHost, m->s));
+  CK(cudaStreamSynchronize(m->s));
+  {
+    std::vector<long long> off(m->gp.ng);
+    size_t tot = 0;
+    for (int G = 0; G < m->gp.ng; ++G) {
+      off[G] = (long long)tot;
+      tot += 18 * (size_t)node_shell_count(g, m->gp, G, m->gfix_h[G] != 0);
+    }
+    m->aw_total = tot;
+    CK(cudaMemcpyAsync(m->aw_off, off.data(), m->gp.ng * sizeof(long long), cudaMemcpyHostToDevice, m->s));
+  }
   k_zero_fixed<<<dim3(grid_blocks(g.nnodes, 256, 4096), n_rhs), 256, 0, m->s>>>(g.nnodes, n_rhs, g.ndof, m->fixed, m->f64); m->launches++;
   CK(cudaMemsetAsync(m->u64, 0, n * sizeof(double), m->s));
   CK(cudaGetLastError());
@@ -968,11 +1077,9 @@ int afd_coarse_matrix(afd_mesh* m, double* out_host) {
   DeviceGuard dg(m->device);
   TRY(enter(m));
   m->coarse_valid = false;
-  int rc = build_coarse(m);
-  if (rc != AFD_OK && rc != AFD_ERR_COARSE_SINGULAR) return rc;
+  TRY(assemble_coarse(m));
   CK(cudaMemcpyAsync(out_host, m->Ec, (size_t)m->nc * m->nc * sizeof(double), cudaMemcpyDeviceToHost, m->s));
-  TRY(finish(m));
-  return rc;
+  return finish(m);
 }
 
 // ---- augmented Lagrangian scalars (Eqs. 3.11, 3.12, 3.18) ----

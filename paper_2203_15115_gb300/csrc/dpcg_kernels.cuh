@@ -25,148 +25,47 @@ struct CGState {
   int status;       // 0 ok, AFD_ERR_NOT_CONVERGED, AFD_ERR_NAN
 };
 
-// z = r * invdiag (zero on fixed DOFs), partial sums of r.z and r.r
-template <typename T>
-__global__ void __launch_bounds__(RED_THREADS)
-k_precond_dot(int ndof, const T* __restrict__ r, const T* __restrict__ invdiag, T* __restrict__ z,
-              double* partials, const CGState* st) {
-  __shared__ double red[64];
-  const int rhs = blockIdx.y;
-  if (st && st[rhs].done) return;
-  const size_t off = (size_t)rhs * ndof;
-  T s[2] = {T(0), T(0)};
-  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
-    const T rv = r[off + d];
-    const T zv = rv * invdiag[d / 3];
-    z[off + d] = zv;
-    s[0] += rv * zv;
-    s[1] += rv * rv;
-  }
-  double o[2];
-  block_sum_to_f64<2>(s, red, o);
-  if (threadIdx.x == 0) {
-    partials[((size_t)rhs * gridDim.x + blockIdx.x) * 2 + 0] = o[0];
-    partials[((size_t)rhs * gridDim.x + blockIdx.x) * 2 + 1] = o[1];
-  }
-}
-
-// x += alpha p; r -= alpha q; z = r * invdiag; partial sums of r.z, r.r
-template <typename T>
-__global__ void __launch_bounds__(RED_THREADS)
-k_cg_update(int ndof, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
-            const T* __restrict__ q, const T* __restrict__ invdiag, double* partials, const CGState* st) {
-  __shared__ double red[64];
-  const int rhs = blockIdx.y;
-  if (st[rhs].done) return;
-  const T alpha = (T)st[rhs].alpha;
-  const size_t off = (size_t)rhs * ndof;
-  T s[2] = {T(0), T(0)};
-  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
-    const size_t i = off + d;
-    x[i] = fma(alpha, p[i], x[i]);
-    const T rv = fma(-alpha, q[i], r[i]);
-    r[i] = rv;
-    const T zv = rv * invdiag[d / 3];
-    z[i] = zv;
-    s[0] += rv * zv;
-    s[1] += rv * rv;
-  }
-  double o[2];
-  block_sum_to_f64<2>(s, red, o);
-  if (threadIdx.x == 0) {
-    partials[((size_t)rhs * gridDim.x + blockIdx.x) * 2 + 0] = o[0];
-    partials[((size_t)rhs * gridDim.x + blockIdx.x) * 2 + 1] = o[1];
-  }
-}
-
-// Sum nparts partials (stride `stride`, component `comp`) of one RHS in a fixed order.
-__device__ inline double sum_partials(const double* p, int nparts, int stride, int comp) {
-  __shared__ double sh[256];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += p[(size_t)i * stride + comp];
-  sh[threadIdx.x] = s;
+// Block-wide sum in a fixed order (per-thread strided sums, warp tree, then
+// warps in order); any blockDim.x that is a multiple of 32, up to 1024.  The
+// result is returned to every thread.
+__device__ inline double block_sum_bcast(double s) {
+  __shared__ double sh[33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  s = warp_sum(s);
+  if (lane == 0) sh[warp] = s;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    sh[32] = t;
   }
-  double out = sh[0];
+  __syncthreads();
+  const double out = sh[32];
   __syncthreads();
   return out;
 }
 
-enum FinMode { FIN_INIT = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
-
-// One block per RHS (256 threads).
-//  FIN_ALPHA: alpha = rho / (p.Ap).
-//  FIN_INIT / FIN_BETA: rho = r.z + (W^T r).mu (the preconditioned residual
-//  y = z + W mu of the two-level operator), r.r, beta = rho_new / rho_old,
-//  convergence test on r.r and the iteration cap.
-__global__ void k_finalize(int mode, const double* partials, int nparts, CGState* st, int* done_flags,
-                           const double* wr, const double* mu, int nc) {
-  const int rhs = blockIdx.x;
-  CGState& s = st[rhs];
-  if (s.done) return;
-  const double* p = partials + (size_t)rhs * nparts * (mode == FIN_ALPHA ? 1 : 2);
-  if (mode == FIN_ALPHA) {
-    const double pap = sum_partials(p, nparts, 1, 0);
-    if (threadIdx.x == 0) {
-      if (!(pap > 0.0) || !isfinite(pap)) {
-        s.status = isfinite(pap) ? -3 : -5;
-        s.done = 1;
-        if (done_flags) done_flags[rhs] = 1;
-      } else {
-        s.alpha = s.rz / pap;
-      }
-    }
-    return;
-  }
-  const double rz = sum_partials(p, nparts, 2, 0);
-  const double rr = sum_partials(p, nparts, 2, 1);
-  // coarse part of rho, fixed order
-  __shared__ double sh[256];
-  double c = 0.0;
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) c += wr[(size_t)rhs * nc + i] * mu[(size_t)rhs * nc + i];
-  sh[threadIdx.x] = c;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double rho = rz + sh[0];
-    if (!isfinite(rr) || !isfinite(rho)) {
-      s.status = -5;
-      s.done = 1;
-    } else {
-      if (mode == FIN_BETA) {
-        s.beta = rho / s.rz;
-        s.iters += 1;
-      } else {
-        s.beta = 0.0;
-      }
-      s.rz = rho;
-      s.rr = rr;
-      if (rr <= s.target2) {
-        s.done = 1;
-        s.status = 0;
-      } else if (s.iters >= s.max_iters) {
-        s.done = 1;
-        s.status = -3;
-      }
-    }
-    if (done_flags) done_flags[rhs] = s.done;
-  }
+// Sum nparts partials (stride `stride`, component `comp`) of one RHS in a fixed order.
+__device__ inline double sum_partials(const double* p, int nparts, int stride, int comp) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += p[(size_t)i * stride + comp];
+  return block_sum_bcast(s);
 }
 
 // ---------------------------------------------------------------------------
 // Deflation (Sec. 3.5; coarse space = rigid-body modes of agglomerated groups)
 // ---------------------------------------------------------------------------
 
-// W^T of one or two vectors (Sec. 3.5 deflation space): for each group G the
-// sums over its free DOFs of (v, r x v), r = x_node - c_G, i.e. force and
-// moment about the group centroid.  out_a[rhs][6G+q] = (W^T a)_G,
-// out_b = W^T b when b is given.  One block per (group, rhs); FP64 output.
+// Node-plane range [lo, hi] of group X along an axis with n elements.
+__device__ __forceinline__ void group_range(int X, int g, int ng, int n, int& lo, int& hi) {
+  lo = g * X;
+  hi = (X == ng - 1) ? n : g * X + g - 1;
+}
+
+// W^T of one or two vectors: for each group G the sums over its free DOFs of
+// (v, r x v), r = x_node - c_G (force and moment about the group centroid).
+// out_a[rhs][6G+q] = (W^T a)_G, out_b = W^T b when b is given.  One block per
+// (group, rhs); FP64 output.  (Used by the deflated start and the tests.)
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_restrict(Grid gr, Groups gp, const T* __restrict__ a, const T* __restrict__ b, const uint8_t* __restrict__ fixed,
@@ -175,10 +74,11 @@ k_restrict(Grid gr, Groups gp, const T* __restrict__ a, const T* __restrict__ b,
   const int G = blockIdx.x, rhs = blockIdx.y;
   if (st && st[rhs].done) return;
   const int Gx = G % gp.ngx, Gy = (G / gp.ngx) % gp.ngy, Gz = G / (gp.ngx * gp.ngy);
-  const int ilo = gp.g * Gx, ihi = (Gx == gp.ngx - 1) ? gr.nx : gp.g * Gx + gp.g - 1;
-  const int jlo = gp.g * Gy, jhi = (Gy == gp.ngy - 1) ? gr.ny : gp.g * Gy + gp.g - 1;
-  const int klo = gp.g * Gz, khi = (Gz == gp.ngz - 1) ? gr.nz : gp.g * Gz + gp.g - 1;
-  const T cx = (T)(0.5 * gp.h * (ilo + ihi)), cy = (T)(0.5 * gp.h * (jlo + jhi)), cz = (T)(0.5 * gp.h * (klo + khi));
+  int ilo, ihi, jlo, jhi, klo, khi;
+  group_range(Gx, gp.g, gp.ngx, gr.nx, ilo, ihi);
+  group_range(Gy, gp.g, gp.ngy, gr.ny, jlo, jhi);
+  group_range(Gz, gp.g, gp.ngz, gr.nz, klo, khi);
+  const T hh = (T)(0.5 * gp.h);
   const int lx = ihi - ilo + 1, ly = jhi - jlo + 1, lz = khi - klo + 1;
   const int cnt = lx * ly * lz;
   const size_t off = (size_t)rhs * gr.ndof;
@@ -189,7 +89,7 @@ k_restrict(Grid gr, Groups gp, const T* __restrict__ a, const T* __restrict__ b,
     const int i = ilo + q % lx, j = jlo + (q / lx) % ly, k = klo + q / (lx * ly);
     const int n = i + gr.nnx * (j + gr.nny * k);
     const uint8_t fb = fixed ? fixed[n] : 0;
-    const T rx = (T)(gp.h * i) - cx, ry = (T)(gp.h * j) - cy, rz = (T)(gp.h * k) - cz;
+    const T rx = hh * (T)(2 * i - ilo - ihi), ry = hh * (T)(2 * j - jlo - jhi), rz = hh * (T)(2 * k - klo - khi);
 #pragma unroll
     for (int which = 0; which < 2; ++which) {
       const T* v = which == 0 ? a : b;
@@ -218,16 +118,299 @@ k_restrict(Grid gr, Groups gp, const T* __restrict__ a, const T* __restrict__ b,
   }
 }
 
-// W mu at node n of group G: t + omega x r (zero on fixed DOFs).
+// Elements of a box [X0,X1]x[Y0,Y1]x[Z0,Z1] minus an inner box [x0,x1]x[y0,y1]x[z0,z1]
+// (the shell), enumerated in z-layer, row, column order.
+struct Shell {
+  int X0, Y0, Z0, LX, LY, LZ;   // outer box origin and extent
+  int x0, y0, z0, IX, IY, IZ;   // inner box origin and extent (all > 0, or none)
+  int A, Rg, nlo, nmid;          // layer area, ring area, full layers below, ring layers
+  int count;
+  __device__ void init(int X0_, int X1, int Y0_, int Y1, int Z0_, int Z1, int x0_, int x1, int y0_, int y1, int z0_,
+                       int z1, bool full) {
+    X0 = X0_; Y0 = Y0_; Z0 = Z0_;
+    LX = X1 - X0 + 1; LY = Y1 - Y0 + 1; LZ = Z1 - Z0 + 1;
+    x0 = x0_; y0 = y0_; z0 = z0_;
+    IX = max(x1 - x0 + 1, 0); IY = max(y1 - y0 + 1, 0); IZ = max(z1 - z0 + 1, 0);
+    if (full || IX == 0 || IY == 0 || IZ == 0) { IX = IY = IZ = 0; x0 = X0; y0 = Y0; z0 = Z0; }
+    A = LX * LY;
+    Rg = A - IX * IY;
+    nlo = IZ ? (z0 - Z0) : LZ;
+    nmid = IZ;
+    count = (LX > 0 && LY > 0 && LZ > 0) ? (LZ - IZ) * A + IZ * Rg : 0;
+  }
+  __device__ void at(int q, int& x, int& y, int& z) const {
+    if (q < nlo * A) {
+      z = Z0 + q / A;
+      const int t = q % A;
+      x = X0 + t % LX;
+      y = Y0 + t / LX;
+      return;
+    }
+    q -= nlo * A;
+    if (q < nmid * Rg) {
+      z = z0 + q / Rg;
+      int u = q % Rg;
+      const int nb = (y0 - Y0) * LX;
+      if (u < nb) {
+        y = Y0 + u / LX;
+        x = X0 + u % LX;
+        return;
+      }
+      u -= nb;
+      const int side = LX - IX;
+      if (u < IY * side) {
+        y = y0 + u / side;
+        const int c = u % side, left = x0 - X0;
+        x = c < left ? X0 + c : x0 + IX + (c - left);
+        return;
+      }
+      u -= IY * side;
+      y = y0 + IY + u / LX;
+      x = X0 + u % LX;
+      return;
+    }
+    q -= nmid * Rg;
+    z = z0 + IZ + q / A;
+    const int t = q % A;
+    x = X0 + t % LX;
+    y = Y0 + t / LX;
+  }
+};
+
+// Node shell of group G: the nodes of elements that can carry energy for a
+// rigid motion of G, i.e. the box [lo-1, hi+1]^3 (clipped to the grid) minus
+// the nodes whose eight elements all lie inside G ([lo+1, hi-1]^3); the
+// whole box when the group holds a fixed DOF.
+__host__ __device__ inline void node_shell_bounds(const Grid& gr, const Groups& gp, int G, int (&b)[12]) {
+  const int Gx = G % gp.ngx, Gy = (G / gp.ngx) % gp.ngy, Gz = G / (gp.ngx * gp.ngy);
+  const int X[3] = {Gx, Gy, Gz}, NG[3] = {gp.ngx, gp.ngy, gp.ngz}, N[3] = {gr.nx, gr.ny, gr.nz};
+  for (int d = 0; d < 3; ++d) {
+    const int lo = gp.g * X[d], hi = (X[d] == NG[d] - 1) ? N[d] : gp.g * X[d] + gp.g - 1;
+    b[2 * d] = lo > 0 ? lo - 1 : 0;          // outer box
+    b[2 * d + 1] = hi < N[d] ? hi + 1 : N[d];
+    b[6 + 2 * d] = lo + 1;                   // inner box
+    b[6 + 2 * d + 1] = hi - 1;
+  }
+}
+
+__host__ __device__ inline int node_shell_count(const Grid& gr, const Groups& gp, int G, bool full) {
+  int b[12];
+  node_shell_bounds(gr, gp, G, b);
+  const int LX = b[1] - b[0] + 1, LY = b[3] - b[2] + 1, LZ = b[5] - b[4] + 1;
+  int IX = b[7] - b[6] + 1, IY = b[9] - b[8] + 1, IZ = b[11] - b[10] + 1;
+  if (full || IX <= 0 || IY <= 0 || IZ <= 0) IX = IY = IZ = 0;
+  return LX * LY * LZ - IX * IY * IZ;
+}
+
+// K W_G on the node shell of every group, stored per group as 18 arrays
+// (mode m, component c) over the shell slots: AW[off_G + (6c + m) * n_G + q]
+// = (K W_G)_{(node q, c), m}.  Gathered per slot from its (up to) eight
+// elements in a fixed order (deterministic); element math in TC.  Elements
+// whose nodes all lie in G with no fixed DOF contribute nothing.  One block
+// per (group, split).
+template <typename TC>
+__global__ void __launch_bounds__(128)
+k_build_aw(Grid gr, Groups gp, int nsplit, const double* __restrict__ Emod, const uint8_t* __restrict__ fixed,
+           const uint8_t* __restrict__ gfix, const long long* __restrict__ aw_off, ElemConsts<TC> K, TC* __restrict__ AW) {
+  const int G = blockIdx.x, sp = blockIdx.y;
+  int b[12];
+  node_shell_bounds(gr, gp, G, b);
+  const bool full = gfix && gfix[G];
+  Shell sh;
+  sh.init(b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], b[8], b[9], b[10], b[11], full);
+  const int Gx = G % gp.ngx, Gy = (G / gp.ngx) % gp.ngy, Gz = G / (gp.ngx * gp.ngy);
+  int ilo, ihi, jlo, jhi, klo, khi;
+  group_range(Gx, gp.g, gp.ngx, gr.nx, ilo, ihi);
+  group_range(Gy, gp.g, gp.ngy, gr.ny, jlo, jhi);
+  group_range(Gz, gp.g, gp.ngz, gr.nz, klo, khi);
+  const TC hh = (TC)(0.5 * gp.h);
+  const int nG = sh.count;
+  TC* out = AW + aw_off[G];
+  const int per = (nG + nsplit - 1) / nsplit;
+  const int qb = sp * per, qe = min(qb + per, nG);
+  for (int q = qb + threadIdx.x; q < qe; q += blockDim.x) {
+    int ni, nj, nk;
+    sh.at(q, ni, nj, nk);
+    TC acc[18];
+#pragma unroll
+    for (int t = 0; t < 18; ++t) acc[t] = TC(0);
+    const uint8_t fbn = fixed ? fixed[ni + gr.nnx * (nj + gr.nny * nk)] : 0;
+#pragma unroll 1
+    for (int d = 0; d < 8; ++d) {
+      const int ei = ni - 1 + (d & 1), ej = nj - 1 + ((d >> 1) & 1), ek = nk - 1 + ((d >> 2) & 1);
+      if (ei < 0 || ei >= gr.nx || ej < 0 || ej >= gr.ny || ek < 0 || ek >= gr.nz) continue;
+      const int la = (1 - (d & 1)) + 2 * (1 - ((d >> 1) & 1)) + 4 * (1 - ((d >> 2) & 1));  // node q in e
+      bool inG[8];
+      uint8_t fb[8];
+      bool anyG = false, leaves = false, anyfix = false;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int i = ei + (a & 1), j = ej + ((a >> 1) & 1), k = ek + ((a >> 2) & 1);
+        inG[a] = i >= ilo && i <= ihi && j >= jlo && j <= jhi && k >= klo && k <= khi;
+        fb[a] = fixed ? fixed[i + gr.nnx * (j + gr.nny * k)] : 0;
+        anyG |= inG[a];
+        leaves |= !inG[a];
+        anyfix |= fb[a] != 0;
+      }
+      if (!anyG || (!leaves && !anyfix)) continue;
+      const TC Ee = (TC)Emod[ei + gr.nx * (ej + gr.ny * ek)];
+#pragma unroll 1
+      for (int col = 0; col < 6; ++col) {
+        TC v[3][8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const int i = ei + (a & 1), j = ej + ((a >> 1) & 1), k = ek + ((a >> 2) & 1);
+          const TC rx = hh * (TC)(2 * i - ilo - ihi), ry = hh * (TC)(2 * j - jlo - jhi), rz = hh * (TC)(2 * k - klo - khi);
+          TC w0 = 0, w1 = 0, w2 = 0;
+          if (col == 0) w0 = 1;
+          else if (col == 1) w1 = 1;
+          else if (col == 2) w2 = 1;
+          else if (col == 3) { w1 = -rz; w2 = ry; }
+          else if (col == 4) { w0 = rz; w2 = -rx; }
+          else { w0 = -ry; w1 = rx; }
+          v[0][a] = (inG[a] && !(fb[a] & 1)) ? w0 : TC(0);
+          v[1][a] = (inG[a] && !(fb[a] & 2)) ? w1 : TC(0);
+          v[2][a] = (inG[a] && !(fb[a] & 4)) ? w2 : TC(0);
+        }
+        hex8_apply(v, Ee, K);
+        // row of node q (local index la), masked at its fixed DOFs
+        TC y0 = TC(0), y1 = TC(0), y2 = TC(0);
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          if (a == la) { y0 = v[0][a]; y1 = v[1][a]; y2 = v[2][a]; }
+        acc[0 * 6 + col] += (fbn & 1) ? TC(0) : y0;
+        acc[1 * 6 + col] += (fbn & 2) ? TC(0) : y1;
+        acc[2 * 6 + col] += (fbn & 4) ? TC(0) : y2;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 18; ++t) out[(size_t)t * nG + q] = acc[t];
+  }
+}
+
+// One DPCG vector step merged with the coarse right-hand side, per (group,
+// split, rhs): over the group's nodes x += alpha p, r_new = r_old - alpha q,
+// z = M^-1 r_new (written), partial r.z, r.r and W_G^T r_new; over the group's
+// node shell (W_G^T K z) = (K W_G)^T z from the stored AW, with z recomputed
+// from r_old (r is double-buffered, so no block sees another's new values).
+// Writes part[rhs][G][split][0..13] = (r.z, r.r, W^T r (6), W^T r - W^T K z (6)).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_update_coarse(Grid gr, Groups gp, int nsplit, T* __restrict__ x, const T* __restrict__ r_old, T* __restrict__ r_new,
+                T* __restrict__ z, const T* __restrict__ p, const T* __restrict__ q, const T* __restrict__ invdiag,
+                const uint8_t* __restrict__ fixed, const uint8_t* __restrict__ gfix, const long long* __restrict__ aw_off,
+                const T* __restrict__ AW, double* __restrict__ part, const CGState* st) {
+  __shared__ double red[32 * 14];
+  const int G = blockIdx.x, sp = blockIdx.y, rhs = blockIdx.z;
+  if (st[rhs].done) return;
+  const T alpha = (T)st[rhs].alpha;
+  const int Gx = G % gp.ngx, Gy = (G / gp.ngx) % gp.ngy, Gz = G / (gp.ngx * gp.ngy);
+  int ilo, ihi, jlo, jhi, klo, khi;
+  group_range(Gx, gp.g, gp.ngx, gr.nx, ilo, ihi);
+  group_range(Gy, gp.g, gp.ngy, gr.ny, jlo, jhi);
+  group_range(Gz, gp.g, gp.ngz, gr.nz, klo, khi);
+  const T hh = (T)(0.5 * gp.h);
+  const size_t off = (size_t)rhs * gr.ndof;
+  T s[14];
+#pragma unroll
+  for (int t = 0; t < 14; ++t) s[t] = T(0);
+  {
+    const int lx = ihi - ilo + 1, ly = jhi - jlo + 1, lz = khi - klo + 1;
+    const int cnt = lx * ly * lz;
+    const int per = (cnt + nsplit - 1) / nsplit;
+    const int qb = sp * per, qe = min(qb + per, cnt);
+    for (int t = qb + threadIdx.x; t < qe; t += blockDim.x) {
+      const int i = ilo + t % lx, j = jlo + (t / lx) % ly, k = klo + t / (lx * ly);
+      const int n = i + gr.nnx * (j + gr.nny * k);
+      const T dinv = invdiag[n];
+      const size_t d = off + 3 * (size_t)n;
+      T rn[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        x[d + c] = fma(alpha, p[d + c], x[d + c]);
+        rn[c] = fma(-alpha, q[d + c], r_old[d + c]);
+        r_new[d + c] = rn[c];
+        const T zv = rn[c] * dinv;
+        z[d + c] = zv;
+        s[0] += rn[c] * zv;
+        s[1] += rn[c] * rn[c];
+      }
+      const T rx = hh * (T)(2 * i - ilo - ihi), ry = hh * (T)(2 * j - jlo - jhi), rz = hh * (T)(2 * k - klo - khi);
+      s[2] += rn[0];
+      s[3] += rn[1];
+      s[4] += rn[2];
+      s[5] += ry * rn[2] - rz * rn[1];
+      s[6] += rz * rn[0] - rx * rn[2];
+      s[7] += rx * rn[1] - ry * rn[0];
+    }
+  }
+  {
+    int b[12];
+    node_shell_bounds(gr, gp, G, b);
+    Shell sh;
+    sh.init(b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], b[8], b[9], b[10], b[11], gfix && gfix[G]);
+    const int nG = sh.count;
+    const T* aw = AW + aw_off[G];
+    const int per = (nG + nsplit - 1) / nsplit;
+    const int qb = sp * per, qe = min(qb + per, nG);
+    for (int t = qb + threadIdx.x; t < qe; t += blockDim.x) {
+      int i, j, k;
+      sh.at(t, i, j, k);
+      const int n = i + gr.nnx * (j + gr.nny * k);
+      const uint8_t fb = fixed ? fixed[n] : 0;
+      const T dinv = invdiag[n];
+      const size_t d = off + 3 * (size_t)n;
+      T zc[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) zc[c] = ((fb >> c) & 1) ? T(0) : fma(-alpha, q[d + c], r_old[d + c]) * dinv;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        T acc = T(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc = fma(aw[(size_t)(6 * c + m) * nG + t], zc[c], acc);
+        s[8 + m] += acc;
+      }
+    }
+  }
+  double o[14];
+  block_sum_to_f64<14>(s, red, o);
+  if (threadIdx.x == 0) {
+    double* pp = part + (((size_t)rhs * gp.ng + G) * nsplit + sp) * 14;
+    pp[0] = o[0];
+    pp[1] = o[1];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      pp[2 + m] = o[2 + m];
+      pp[8 + m] = o[2 + m] - o[8 + m];
+    }
+  }
+}
+
+// gfix[G] = 1 when a node of group G has a fixed DOF.
+__global__ void k_group_fixed(Grid gr, Groups gp, const uint8_t* __restrict__ fixed, uint8_t* __restrict__ gfix) {
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gr.nnodes; n += gridDim.x * blockDim.x) {
+    if (!fixed[n]) continue;
+    const int i = n % gr.nnx, j = (n / gr.nnx) % gr.nny, k = n / (gr.nnx * gr.nny);
+    const int G = group_of_axis(i, gp.g, gp.ngx) + gp.ngx * (group_of_axis(j, gp.g, gp.ngy) + gp.ngy * group_of_axis(k, gp.g, gp.ngz));
+    gfix[G] = 1;
+  }
+}
+
+// W mu at node (i, j, k): t + omega x r of the node's group (zero on fixed DOFs).
 template <typename T>
 __device__ __forceinline__ void prolong_node(const Grid& gr, const Groups& gp, const double* mu, int i, int j, int k,
                                              T (&w)[3]) {
   const int Gx = group_of_axis(i, gp.g, gp.ngx), Gy = group_of_axis(j, gp.g, gp.ngy), Gz = group_of_axis(k, gp.g, gp.ngz);
   const int G = Gx + gp.ngx * (Gy + gp.ngy * Gz);
   const double* m = mu + 6 * G;
-  const T rx = (T)(gp.h * i - group_centroid_axis(Gx, gp.g, gp.ngx, gr.nnx, gp.h));
-  const T ry = (T)(gp.h * j - group_centroid_axis(Gy, gp.g, gp.ngy, gr.nny, gp.h));
-  const T rz = (T)(gp.h * k - group_centroid_axis(Gz, gp.g, gp.ngz, gr.nnz, gp.h));
+  int lo, hi;
+  const T hh = (T)(0.5 * gp.h);
+  group_range(Gx, gp.g, gp.ngx, gr.nx, lo, hi);
+  const T rx = hh * (T)(2 * i - lo - hi);
+  group_range(Gy, gp.g, gp.ngy, gr.ny, lo, hi);
+  const T ry = hh * (T)(2 * j - lo - hi);
+  group_range(Gz, gp.g, gp.ngz, gr.nz, lo, hi);
+  const T rz = hh * (T)(2 * k - lo - hi);
   const T tx = (T)m[0], ty = (T)m[1], tz = (T)m[2], ox = (T)m[3], oy = (T)m[4], oz = (T)m[5];
   w[0] = tx + (oy * rz - oz * ry);
   w[1] = ty + (oz * rx - ox * rz);
@@ -264,23 +447,105 @@ k_prolong(int mode, Grid gr, Groups gp, T* __restrict__ p, const T* __restrict__
   }
 }
 
-// mu[rhs] = Einv (va[rhs] - vb[rhs]) (vb nullable); one warp per row, all RHS
-// at once (Einv symmetric, row-major).
+// Coarse solve mu[rhs] = Einv v[rhs] (Einv symmetric, row-major, type TE);
+// one warp per row, all RHS (used by the deflated start).
+template <typename TE>
 __global__ void __launch_bounds__(256)
-k_coarse_apply(int nc, int nrhs, const double* __restrict__ Einv, const double* __restrict__ va,
-               const double* __restrict__ vb, double* __restrict__ mu, const CGState* st) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= nc) return;
-  const double* row = Einv + (size_t)warp * nc;
+k_coarse_solve(int nc, int nrhs, const TE* __restrict__ Einv, const double* __restrict__ v, double* __restrict__ mu,
+               const CGState* st) {
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= nc) return;
+  const TE* er = Einv + (size_t)row * nc;
   for (int r = 0; r < nrhs; ++r) {
     if (st && st[r].done) continue;
-    const double* ar = va + (size_t)r * nc;
-    const double* br = vb ? vb + (size_t)r * nc : nullptr;
-    double s = 0.0;
-    for (int c = lane; c < nc; c += 32) s = fma(row[c], br ? ar[c] - br[c] : ar[c], s);
+    const double* vr = v + (size_t)r * nc;
+    TE s = TE(0);
+    for (int c = lane; c < nc; c += 32) s = fma(er[c], (TE)vr[c], s);
     s = warp_sum(s);
-    if (lane == 0) mu[(size_t)r * nc + warp] = s;
+    if (lane == 0) mu[(size_t)r * nc + row] = (double)s;
   }
+}
+
+// Coarse step of one DPCG iteration: v_G and (W^T r)_G are summed from the
+// k_update_coarse records of their nsplit shares, mu = Einv v (one warp per
+// row, all RHS), and the last block to finish takes the beta step for every
+// RHS: rho = r.z + (W^T r).mu (the preconditioned residual y = z + W mu of
+// the two-level operator), r.r, beta = rho / rho_old, the convergence test
+// and the iteration count.  fin == 2 marks the initial step (beta = 0).
+template <typename TE>
+__global__ void __launch_bounds__(256)
+k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict__ mu, CGState* st, int nsplit,
+              const double* __restrict__ part, double* __restrict__ wr_out, int fin, int* done_flags,
+              unsigned int* counter) {
+  extern __shared__ double vs[];   // nc values of v for the current RHS
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int ng = nc / 6;
+  for (int r = 0; r < nrhs; ++r) {
+    if (st[r].done) continue;
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      const int G = q / 6, c = q % 6;
+      const double* pp = part + (((size_t)r * ng + G) * nsplit) * 14;
+      double sv = 0.0, sw = 0.0;
+      for (int s2 = 0; s2 < nsplit; ++s2) {
+        sw += pp[s2 * 14 + 2 + c];
+        sv += pp[s2 * 14 + 8 + c];
+      }
+      vs[q] = sv;
+      if (blockIdx.x == 0) wr_out[(size_t)r * nc + q] = sw;
+    }
+    __syncthreads();
+    if (row < nc) {
+      const TE* er = Einv + (size_t)row * nc;
+      TE s = TE(0);
+      for (int c = lane; c < nc; c += 32) s = fma(er[c], (TE)vs[c], s);
+      s = warp_sum(s);
+      if (lane == 0) mu[(size_t)r * nc + row] = (double)s;
+    }
+    __syncthreads();
+  }
+  // last block: beta step for every RHS
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nrec = ng * nsplit;
+  for (int r = 0; r < nrhs; ++r) {
+    CGState& S = st[r];
+    if (S.done) continue;
+    const double* pp = part + (size_t)r * nrec * 14;
+    const double rz = sum_partials(pp, nrec, 14, 0);
+    const double rr = sum_partials(pp, nrec, 14, 1);
+    double c = 0.0;
+    for (int i = threadIdx.x; i < nc; i += blockDim.x) c += wr_out[(size_t)r * nc + i] * mu[(size_t)r * nc + i];
+    const double cdot = block_sum_bcast(c);
+    if (threadIdx.x == 0) {
+      const double rho = rz + cdot;
+      if (!isfinite(rr) || !isfinite(rho)) {
+        S.status = -5;
+        S.done = 1;
+      } else {
+        S.beta = fin == 2 ? 0.0 : rho / S.rz;
+        if (fin != 2) S.iters += 1;
+        S.rz = rho;
+        S.rr = rr;
+        if (rr <= S.target2) {
+          S.done = 1;
+          S.status = 0;
+        } else if (S.iters >= S.max_iters) {
+          S.done = 1;
+          S.status = -3;
+        }
+      }
+      if (done_flags) done_flags[r] = S.done;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *counter = 0u;
 }
 
 // ---------------------------------------------------------------------------

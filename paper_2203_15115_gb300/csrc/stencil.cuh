@@ -1,18 +1,23 @@
 // Matrix-free stiffness apply y = K u on the voxel hex8 mesh (Sec. 3.5: the
 // system is solved without assembling K; the cost is memory traffic).
 //
-// Design (sm_103a): a CTA owns a TX x TY column of elements in (x, y) and marches
-// through a range of z node planes.  Per element layer it stages the next node
-// plane of u (3 components, masked at fixed DOFs) in shared memory, every
-// thread applies E_e * K0 to one element in the Walsh-Hadamard modal form
-// (afd_common.cuh), writes the 24 element forces to shared memory (SoA, bank
-// conflict free), and each node thread gathers the 4 bottom-face forces of the
-// layer above and the 4 top-face forces of the layer below.  Neighbouring CTAs
-// overlap by one element column so that every node is finished by exactly one
-// CTA: no atomics, deterministic sums.
+// Design (sm_103a).  Every thread owns one node column (i, j) and marches
+// along z; a CTA is 32 lanes (x) by TY warps (y).  The element operator is
+// applied in the Walsh-Hadamard modal form of afd_common.cuh, with the three
+// butterfly stages factorised across the grid instead of per element:
+//   x stage: sum/difference of the node and its +x neighbour (warp shuffle),
+//   y stage: sum/difference of two x-edges (one shared-memory exchange),
+//   z stage: sum/difference of the face values of two planes (registers),
+// so every x-edge and face is transformed once, not once per element.  The
+// transposed stages run in reverse order on the element forces: the two
+// elements sharing a face are added before the face is split into edges, and
+// the two faces sharing an edge before it is split into nodes.  Nothing goes
+// through global atomics; CTAs overlap by one column in x and one row in y so
+// every node is finished by exactly one thread.
 #pragma once
 
 #include "afd_common.cuh"
+#include "dpcg_kernels.cuh"
 
 namespace afd {
 
@@ -36,144 +41,305 @@ struct StencilArgs {
   const int* done;        // [rhs] skip the work when nonzero (nullable)
   int kz;                 // node planes per CTA
   int tiles_x;            // CTAs along x
+  // ST_APPLY_DOT inside the solver: the last CTA of each RHS turns the u.y
+  // partials into the CG step length alpha = rho / (p.Ap) (nullable)
+  CGState* st;
+  unsigned int* counter;  // [rhs], zero between launches
+  // Fused search-direction update (nullable z): the applied vector is
+  // p = z + W mu + beta p_old, formed as each node is loaded (u holds p_old,
+  // beta comes from st), and written back to pout at the nodes this CTA owns.
+  const T* z;
+  const double* mu;       // [rhs][6 N_g]
+  T* pout;
+  Groups gp;
 };
 
-template <typename T, int TX, int TY, int MODE, typename TF>
-__global__ void __launch_bounds__(TX * TY)
-stencil_kernel(const StencilArgs<T, TF> a) {
-  constexpr int NT = TX * TY;
-  constexpr int PX = TX + 1, PY = TY + 1;     // node plane tile
-  __shared__ T us[2][3][PY][PX];
-  __shared__ T eo[24][TY][TX];
-  __shared__ double red[32 * 1];
+constexpr int ST_TX = 32;  // lanes per warp; lanes 1..30 finish nodes, lane 31 is a halo column
 
-  const int rhs = blockIdx.z;
-  if (a.done && a.done[rhs]) return;
-  const Grid gr = a.gr;
-  const int tile_x = blockIdx.x % a.tiles_x;
-  const int tile_y = blockIdx.x / a.tiles_x;
-  const int ex0 = tile_x * (TX - 1) - 1;
-  const int ey0 = tile_y * (TY - 1) - 1;
-  const int k0 = blockIdx.y * a.kz;
-  const int k1 = min(k0 + a.kz, gr.nnz);
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const size_t voff = (size_t)rhs * gr.ndof;
-  const T* __restrict__ u = a.u + voff;
-  T* __restrict__ y = a.y + voff;
-
-  auto load_plane = [&](int kn, int slot) {
-    // nodes [ex0, ex0+TX] x [ey0, ey0+TY] of plane kn, AoS rows of 3*PX values
-    for (int q = threadIdx.x; q < 3 * PX * PY; q += NT) {
-      const int row = q / (3 * PX);
-      const int w = q - row * 3 * PX;
-      const int nxl = w / 3;
-      const int c = w - nxl * 3;
-      const int i = ex0 + nxl, j = ey0 + row;
-      T val = T(0);
-      if (kn >= 0 && kn < gr.nnz && i >= 0 && i < gr.nnx && j >= 0 && j < gr.nny) {
-        const int n = i + gr.nnx * (j + gr.nny * kn);
-        const bool fx = a.fixed ? ((a.fixed[n] >> c) & 1) : false;
-        val = fx ? T(0) : u[3 * (size_t)n + c];
-      }
-      us[slot][c][row][nxl] = val;
-    }
-  };
-
-  // node owned by this thread (interior of the element tile)
-  const int ni = ex0 + tx, nj = ey0 + ty;
-  const bool node_thread = tx >= 1 && ty >= 1 && ni <= gr.nx && nj <= gr.ny;
-  T acc[3] = {T(0), T(0), T(0)};
-  T part = T(0);
-  const int ei = ex0 + tx, ej = ey0 + ty;
-  const bool elem_xy = ei >= 0 && ei < gr.nx && ej >= 0 && ej < gr.ny;
-
-  load_plane(k0 - 1, (k0 - 1) & 1);
-  for (int l = k0 - 1; l < k1; ++l) {
-    load_plane(l + 1, (l + 1) & 1);
-    __syncthreads();
-    // ---- element (ei, ej, l) ----
-    {
-      T E = T(0);
-      if (elem_xy && l >= 0 && l < gr.nz) E = a.E[ei + gr.nx * (ej + gr.ny * l)];
-      T v[3][8];
-      if (E != T(0)) {
-#pragma unroll
-        for (int az = 0; az < 2; ++az) {
-          const int s = (l + az) & 1;
-#pragma unroll
-          for (int ay = 0; ay < 2; ++ay)
-#pragma unroll
-            for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-              for (int c = 0; c < 3; ++c) v[c][ax + 2 * ay + 4 * az] = us[s][c][ty + ay][tx + ax];
-        }
-        hex8_apply(v, E, a.K);
-      } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int q = 0; q < 8; ++q) v[c][q] = T(0);
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) eo[3 * q + c][ty][tx] = v[c][q];
-    }
-    __syncthreads();
-    // ---- nodes of plane l (bottom faces of layer l + top faces of layer l-1) ----
-    if (node_thread) {
-      T top[3] = {T(0), T(0), T(0)};
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          const int la = (1 - dx) + 2 * (1 - dy);  // our local index in element (tx-1+dx, ty-1+dy)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            acc[c] += eo[3 * la + c][ty - 1 + dy][tx - 1 + dx];
-            top[c] += eo[3 * (la + 4) + c][ty - 1 + dy][tx - 1 + dx];
-          }
-        }
-      if (l >= k0) {
-        const int n = ni + gr.nnx * (nj + gr.nny * l);
-        const uint8_t fb = a.fixed ? a.fixed[n] : 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const bool fx = (fb >> c) & 1;
-          T out;
-          if (MODE == ST_RESIDUAL) {
-            out = fx ? T(0) : (T)a.f[voff + 3 * (size_t)n + c] - acc[c];
-            part += out * out;
-            if (a.y32) a.y32[voff + 3 * (size_t)n + c] = (float)out;
-          } else {
-            out = fx ? T(0) : acc[c];
-            if (MODE == ST_APPLY_DOT) part += us[l & 1][c][ty][tx] * out;
-          }
-          y[3 * (size_t)n + c] = out;
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc[c] = top[c];
-    }
-    __syncthreads();
-  }
-  if (MODE != ST_APPLY) {
-    T pv[1] = {part};
-    double out[1];
-    block_sum_to_f64<1>(pv, red, out);
-    if (threadIdx.x == 0) a.partials[(size_t)rhs * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = out[0];
-  }
-}
-
-// Launch geometry of the stencil for a grid.
-template <int TX, int TY>
+// Launch geometry: a CTA of TY warps finishes (ST_TX-2) x (TY-2) node columns
+// over kz planes (TY-1 element rows; the last warp only supplies x-edges).
+template <int TY>
 struct StencilGeom {
   static void get(const Grid& gr, int kz, int& tiles_x, dim3& grid) {
-    tiles_x = (gr.nnx + (TX - 2)) / (TX - 1);
-    const int tiles_y = (gr.nny + (TY - 2)) / (TY - 1);
+    tiles_x = (gr.nnx + (ST_TX - 3)) / (ST_TX - 2);
+    const int tiles_y = (gr.nny + (TY - 3)) / (TY - 2);
     const int zch = (gr.nnz + kz - 1) / kz;
     grid = dim3(tiles_x * tiles_y, zch, 1);
   }
 };
+
+template <typename T, int TY, int MODE, typename TF>
+__global__ void __launch_bounds__(ST_TX * TY)
+stencil_kernel(const StencilArgs<T, TF> a) {
+  // TY warps: warps 0..TY-2 own element rows, the last warp only supplies the
+  // x-edges of the row above the tile.  Exchange buffers: each is written,
+  // then read after a barrier; the other exchange's barrier separates that
+  // read from the next write.
+  __shared__ T xe[6][TY][ST_TX];   // x-edge (S, D) x 3 components
+  __shared__ T ye[6][TY][ST_TX];   // edge contributions sent to the row above
+  __shared__ double red[32];
+
+  const int rhs = blockIdx.z;
+  if (a.done && a.done[rhs]) return;
+  const Grid gr = a.gr;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tile_x = blockIdx.x % a.tiles_x;
+  const int tile_y = blockIdx.x / a.tiles_x;
+  const int i = tile_x * (ST_TX - 2) - 1 + lane;   // node / element column
+  const int j = tile_y * (TY - 2) - 1 + w;
+  const int k0 = blockIdx.y * a.kz;
+  const int k1 = min(k0 + a.kz, gr.nnz);
+  const size_t voff = (size_t)rhs * gr.ndof;
+  const T* __restrict__ u = a.u + voff;
+
+  const bool col_ok = i >= 0 && i < gr.nnx && j >= 0 && j < gr.nny;
+  const bool elem_xy = lane < ST_TX - 1 && i >= 0 && i < gr.nx && j >= 0 && j < gr.ny && w < TY - 1;
+  const bool out_xy = lane >= 1 && lane < ST_TX - 1 && w >= 1 && w < TY - 1 && i <= gr.nx && j <= gr.ny;
+
+  // Fused search direction p = z + W mu + beta p_old.  For this thread's
+  // column the rigid motion of group G is W mu = A_G + r_z B_G with
+  // A_G = t + omega x (r_x, r_y, 0), B_G = (omega_y, -omega_x, 0); A, B are
+  // refreshed when the plane index enters the next group along z.
+  const bool formp = a.z != nullptr;
+  const T beta = formp ? (T)a.st[rhs].beta : T(0);
+  const Groups gp = a.gp;
+  const T hh = (T)(0.5 * gp.h);
+  T rx = T(0), ry = T(0);
+  int gxy = 0;            // Gx + ngx * Gy
+  int gz = -1, gz_next = 0, zlo = 0, zhi = 0;
+  T A0 = T(0), A1 = T(0), A2 = T(0), B0 = T(0), B1 = T(0);
+  const double* murhs = formp ? a.mu + (size_t)rhs * 6 * gp.ng : nullptr;
+  if (formp && col_ok) {
+    int lo, hi;
+    const int Gx = group_of_axis(i, gp.g, gp.ngx), Gy = group_of_axis(j, gp.g, gp.ngy);
+    group_range(Gx, gp.g, gp.ngx, gr.nx, lo, hi);
+    rx = hh * (T)(2 * i - lo - hi);
+    group_range(Gy, gp.g, gp.ngy, gr.ny, lo, hi);
+    ry = hh * (T)(2 * j - lo - hi);
+    gxy = Gx + gp.ngx * Gy;
+  }
+  auto refresh_group = [&](int k) {
+    gz = group_of_axis(k, gp.g, gp.ngz);
+    group_range(gz, gp.g, gp.ngz, gr.nz, zlo, zhi);
+    gz_next = (gz == gp.ngz - 1) ? (1 << 30) : zhi + 1;
+    const double* m6 = murhs + 6 * (gxy + gp.ngx * gp.ngy * gz);
+    const T tx = (T)m6[0], ty = (T)m6[1], tz = (T)m6[2], ox = (T)m6[3], oy = (T)m6[4], oz = (T)m6[5];
+    A0 = tx - oz * ry;
+    A1 = ty + oz * rx;
+    A2 = tz + (ox * ry - oy * rx);
+    B0 = oy;
+    B1 = -ox;
+  };
+
+  auto load_node = [&](int k, T (&v)[3]) {
+    if (col_ok && k >= 0 && k < gr.nnz) {
+      const int n = i + gr.nnx * (j + gr.nny * k);
+      const uint8_t fb = a.fixed ? a.fixed[n] : 0;
+      const T* p = u + 3 * (size_t)n;
+      if (formp) {
+        if (k >= gz_next || gz < 0) refresh_group(k);
+        const T* zz = a.z + voff + 3 * (size_t)n;
+        const T rz = hh * (T)(2 * k - zlo - zhi);
+        v[0] = (fb & 1) ? T(0) : fma(beta, p[0], zz[0] + fma(rz, B0, A0));
+        v[1] = (fb & 2) ? T(0) : fma(beta, p[1], zz[1] + fma(rz, B1, A1));
+        v[2] = (fb & 4) ? T(0) : fma(beta, p[2], zz[2] + A2);
+      } else {
+        v[0] = (fb & 1) ? T(0) : p[0];
+        v[1] = (fb & 2) ? T(0) : p[1];
+        v[2] = (fb & 4) ? T(0) : p[2];
+      }
+    } else {
+      v[0] = v[1] = v[2] = T(0);
+    }
+  };
+
+  // face values (x-edge stage then y stage) of a node plane for element column (i, j):
+  // F[c][q], q = mx + 2 my (mx: x-difference, my: y-difference)
+  auto face_values = [&](const T (&un)[3], T (&F)[3][4]) {
+    T S[3], D[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T right = __shfl_down_sync(0xffffffffu, un[c], 1);  // lane 31: unused
+      S[c] = right + un[c];
+      D[c] = right - un[c];
+      xe[c][w][lane] = S[c];
+      xe[3 + c][w][lane] = D[c];
+    }
+    __syncthreads();
+    if (w < TY - 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T S1 = xe[c][w + 1][lane], D1 = xe[3 + c][w + 1][lane];
+        F[c][0] = S1 + S[c];
+        F[c][1] = D1 + D[c];
+        F[c][2] = S1 - S[c];
+        F[c][3] = D1 - D[c];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F[c][0] = F[c][1] = F[c][2] = F[c][3] = T(0);
+    }
+  };
+
+  T Fb[3][4];      // face values of the plane below the current element layer
+  T Tprev[3][4];   // top-face forces of the element layer below the current plane
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Fb[c][q] = Tprev[c][q] = T(0);
+
+  {
+    T un0[3];
+    load_node(k0 - 1, un0);
+    face_values(un0, Fb);
+    __syncthreads();  // the loop's first x-edge write follows this read
+  }
+  T ucur[3] = {T(0), T(0), T(0)};   // (formed) u at (i, j, l) for the dot epilogue and p write
+  T part = T(0);
+  T un[3];
+  load_node(k0, un);   // prefetch of the next plane
+
+  for (int l = k0 - 1; l < k1; ++l) {
+    // element layer l lies between node planes l and l+1; finish plane l
+    T Ft[3][4];
+    face_values(un, Ft);
+    const T u_l1[3] = {un[0], un[1], un[2]};  // plane l+1
+    T E = T(0);
+    if (elem_xy && l >= 0 && l < gr.nz) E = a.E[i + gr.nx * (j + gr.ny * l)];
+    if (l + 2 <= k1) load_node(l + 2, un);  // prefetch plane l+2
+    T Bf[3][4];  // bottom-face forces of element layer l (plane l)
+    if (E != T(0)) {
+      T h[3][8];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          h[c][q] = Ft[c][q] + Fb[c][q];
+          h[c][q + 4] = Ft[c][q] - Fb[c][q];
+        }
+      modal_forces(h, E, a.K);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const T g0 = h[c][q], g1 = h[c][q + 4];
+          Bf[c][q] = g0 - g1;
+          const T tf = g0 + g1;
+          h[c][q] = tf;   // keep the top-face force
+        }
+      // plane l total face force: this layer's bottom + the layer below's top
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          Bf[c][q] += Tprev[c][q];
+          Tprev[c][q] = h[c][q];
+        }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          Bf[c][q] = Tprev[c][q];
+          Tprev[c][q] = T(0);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Fb[c][q] = Ft[c][q];
+
+    // transposed y stage: face (i, j) -> x-edges of rows j and j+1
+    T e0[3][2], e1[3][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int mx = 0; mx < 2; ++mx) {
+        e0[c][mx] = Bf[c][mx] - Bf[c][mx + 2];
+        e1[c][mx] = Bf[c][mx] + Bf[c][mx + 2];
+      }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ye[2 * c][w][lane] = e1[c][0];
+      ye[2 * c + 1][w][lane] = e1[c][1];
+    }
+    __syncthreads();
+    if (w >= 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        e0[c][0] += ye[2 * c][w - 1][lane];
+        e0[c][1] += ye[2 * c + 1][w - 1][lane];
+      }
+    }
+    // transposed x stage: edge (i, i+1) -> node i gets s - d, node i+1 gets s + d
+    T yv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T sp = e0[c][0] + e0[c][1];
+      const T from_left = __shfl_up_sync(0xffffffffu, sp, 1);
+      yv[c] = (e0[c][0] - e0[c][1]) + (lane >= 1 ? from_left : T(0));
+    }
+    if (l >= k0 && out_xy) {
+      const int n = i + gr.nnx * (j + gr.nny * l);
+      const uint8_t fb = a.fixed ? a.fixed[n] : 0;
+      T* yp = a.y + voff + 3 * (size_t)n;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const bool fx = (fb >> c) & 1;
+        T out;
+        if (MODE == ST_RESIDUAL) {
+          out = fx ? T(0) : (T)a.f[voff + 3 * (size_t)n + c] - yv[c];
+          part += out * out;
+          if (a.y32) a.y32[voff + 3 * (size_t)n + c] = (float)out;
+        } else {
+          out = fx ? T(0) : yv[c];
+          if (MODE == ST_APPLY_DOT) part += ucur[c] * out;
+        }
+        yp[c] = out;
+      }
+      if (formp) {
+        T* pp = a.pout + voff + 3 * (size_t)n;
+        pp[0] = ucur[0];
+        pp[1] = ucur[1];
+        pp[2] = ucur[2];
+      }
+    }
+    if (MODE == ST_APPLY_DOT) {
+      ucur[0] = u_l1[0];
+      ucur[1] = u_l1[1];
+      ucur[2] = u_l1[2];
+    }
+  }
+  if (MODE != ST_APPLY) {
+    T pv[1] = {out_xy ? part : T(0)};
+    double o[1];
+    block_sum_to_f64<1>(pv, red, o);
+    const int nparts = gridDim.x * gridDim.y;
+    double* parts = a.partials + (size_t)rhs * nparts;
+    if (threadIdx.x == 0) parts[blockIdx.y * gridDim.x + blockIdx.x] = o[0];
+    if (MODE == ST_APPLY_DOT && a.st) {
+      __shared__ bool s_last;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_last = atomicAdd(&a.counter[rhs], 1u) == (unsigned)nparts - 1u;
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        const double pap = sum_partials(parts, nparts, 1, 0);
+        if (threadIdx.x == 0) {
+          CGState& S = a.st[rhs];
+          if (!(pap > 0.0) || !isfinite(pap)) {
+            S.status = isfinite(pap) ? -3 : -5;
+            S.done = 1;
+            const_cast<int*>(a.done)[rhs] = 1;
+          } else {
+            S.alpha = S.rz / pap;
+          }
+          a.counter[rhs] = 0u;
+        }
+      }
+    }
+  }
+}
 
 }  // namespace afd
