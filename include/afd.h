@@ -155,6 +155,23 @@ int afd_coarse_matrix(afd_mesh* m, double* out_host);
 int afd_select_topk(const float* keys, int64_t n, int64_t k, uint8_t* kept, float* tau_out,
                     void* cuda_stream);
 
+/* The same selection as afd_select_topk without allocating device memory.
+ * The paper has no counterpart: this is for callers that cannot call
+ * cudaMalloc -- code whose device memory belongs to another allocator (a
+ * framework's caching allocator that already holds the memory) and
+ * latency-sensitive loops where cudaMalloc/cudaFree would synchronise the
+ * device.  The scratch (about 17 KB: the selection state and one counter per
+ * 4096 keys) is a file-scope device array that every device loading this
+ * library keeps until the process exits.  Limit: n <= 16,777,216 keys; larger
+ * n returns AFD_ERR_INVALID_ARG without touching the device.  The first call
+ * on a device looks up the array's device address (once, with that device
+ * current); make that first call before any stream capture.  Every call
+ * shares the one array and re-initialises it; calls that overlap on the GPU
+ * (e.g. on two streams at once) race and give undefined results.  Returns
+ * after cuda_stream has finished, like afd_select_topk. */
+int afd_select_topk_noalloc(const float* keys, int64_t n, int64_t k, uint8_t* kept, float* tau_out,
+                            void* cuda_stream);
+
 /* Time `launches` back-to-back stiffness applies y = K u (the solver's
  * kernel and launch geometry, arith AFD_F32 or AFD_F64, n_rhs vectors, device
  * pointers) on the mesh's stream with CUDA events recorded on that stream;

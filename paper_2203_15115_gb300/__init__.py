@@ -39,7 +39,7 @@ EXPORTS = [
     "afd_compliance", "afd_sensitivity", "afd_pnorm_stress", "afd_levelset_update", "afd_apply_stiffness",
     "afd_deflation_wt", "afd_deflation_w", "afd_coarse_size", "afd_coarse_matrix", "afd_select_topk",
     "afd_ndof", "afd_nelem", "afd_destroy", "afd_last_error", "afd_al_init", "afd_al_update", "afd_al_weight",
-    "afd_time_stiffness", "afd_kernel_launches",
+    "afd_time_stiffness", "afd_kernel_launches", "afd_select_topk_noalloc",
 ]
 
 
@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
             "afd_al_weight": (d, [ctypes.POINTER(afd_al_state)]),
             "afd_time_stiffness": (i, [vp, i, i, vp, vp, i, ctypes.POINTER(d)]),
             "afd_kernel_launches": (i64, [vp]),
+            "afd_select_topk_noalloc": (i, [vp, i64, i64, vp, ctypes.POINTER(ctypes.c_float), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -280,6 +281,18 @@ def afd_time_stiffness(mesh, arith: int, n_rhs: int, u, y, launches: int) -> flo
 
 def afd_kernel_launches(mesh) -> int:
     return int(lib().afd_kernel_launches(mesh))
+
+
+def afd_select_topk_noalloc(keys, k: int, kept, stream=None, n: Optional[int] = None) -> float:
+    """afd_select_topk without device allocation (file-scope device scratch,
+    at most 16,777,216 keys; see include/afd.h)."""
+    pk, _, _k1 = _arr(keys, np.float32)
+    po, _, _k2 = _arr(kept, np.uint8)
+    tau = ctypes.c_float()
+    s = stream if stream is not None else current_stream()
+    count = n if n is not None else int(keys.numel() if hasattr(keys, "numel") else len(keys))
+    _check(lib().afd_select_topk_noalloc(pk, count, int(k), po, ctypes.byref(tau), s))
+    return tau.value
 
 
 def afd_al_init() -> afd_al_state:

@@ -13,6 +13,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -965,6 +966,54 @@ int afd_select_topk(const float* keys, int64_t n, int64_t k, uint8_t* kept, floa
   cudaFree(st);
   if (cnt) cudaFree(cnt);
   return rc;
+}
+
+// ---- afd_select_topk_noalloc: the top-k selection without device allocation ----
+// Its scratch (the radix-select state, then one count per chunk of SEL_CHUNK
+// keys) is a file-scope device array: every device that loads this library
+// holds it until the process exits, and every call shares it.
+constexpr int64_t NOALLOC_MAX_CHUNKS = 4096;
+constexpr int64_t NOALLOC_MAX_KEYS = NOALLOC_MAX_CHUNKS * SEL_CHUNK;  // 16,777,216 keys
+constexpr size_t NOALLOC_STATE_BYTES = (sizeof(SelectState) + 255) / 256 * 256;
+constexpr size_t NOALLOC_BYTES = NOALLOC_STATE_BYTES + NOALLOC_MAX_CHUNKS * sizeof(uint32_t);
+static __device__ __align__(256) unsigned char g_topk_scratch[NOALLOC_BYTES];
+
+// Device address of g_topk_scratch on the current device.  Host code only
+// holds a host-side stand-in for the symbol, so the address is looked up once
+// per device (with that device current) and cached.
+static int noalloc_scratch(void** out) {
+  static std::mutex mu;
+  static void* addr[128] = {nullptr};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return fail(AFD_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_topk_scratch);
+    if (e != cudaSuccess) return fail(AFD_ERR_CUDA, "cudaGetSymbolAddress(g_topk_scratch): %s", cudaGetErrorString(e));
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return AFD_OK;
+}
+
+int afd_select_topk_noalloc(const float* keys, int64_t n, int64_t k, uint8_t* kept, float* tau_out,
+                            void* cuda_stream) {
+  if (n < 0 || k < 0 || k > n) return fail(AFD_ERR_INVALID_ARG, "need 0 <= k <= n");
+  if (n > NOALLOC_MAX_KEYS)
+    return fail(AFD_ERR_INVALID_ARG, "afd_select_topk_noalloc takes at most %lld keys (got %lld)",
+                (long long)NOALLOC_MAX_KEYS, (long long)n);
+  if (n > 0 && (!keys || !kept)) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (n == 0) {
+    if (tau_out) *tau_out = NAN;
+    return AFD_OK;
+  }
+  void* base = nullptr;
+  TRY(noalloc_scratch(&base));
+  SelectState* st = (SelectState*)base;
+  uint32_t* cnt = (uint32_t*)((unsigned char*)base + NOALLOC_STATE_BYTES);
+  return select_topk_dev((cudaStream_t)cuda_stream, keys, n, k, kept, st, cnt, nullptr, nullptr, 0.0, tau_out, nullptr);
 }
 
 int afd_levelset_update(afd_mesh* m, int kind, const double* weights, double volume_fraction, double* tau_out,
