@@ -174,8 +174,9 @@ int afd_select_topk_noalloc(const float* keys, int64_t n, int64_t k, uint8_t* ke
 
 /* Time `launches` back-to-back stiffness applies y = K u (the solver's
  * kernel and launch geometry, arith AFD_F32 or AFD_F64, n_rhs vectors, device
- * pointers) on the mesh's stream with CUDA events recorded on that stream;
- * *ms_out = mean device time per launch.  Measurement aid (Sec. 3.5 names
+ * pointers, one launch per vector) on the mesh's stream with CUDA events
+ * recorded on that stream; *ms_out = mean device time per round of n_rhs
+ * launches.  Measurement aid (Sec. 3.5 names
  * memory access as the bottleneck of the assembly-free solve). */
 int afd_time_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y, int launches, double* ms_out);
 

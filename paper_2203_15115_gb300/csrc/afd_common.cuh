@@ -17,6 +17,7 @@ struct Grid {
   int nnodes;         // nnx*nny*nnz
   int nelem;          // nx*ny*nz
   int ndof;           // 3*nnodes
+  int vs;             // per-RHS stride of the device vectors: ndof rounded up to a multiple of 4
 };
 
 // Deflation groups: node (i,j,k) -> (min(i/g, ngx-1), ...).
@@ -195,6 +196,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // Block-wide sum of NV values per thread into FP64; result valid in thread 0.
 // `scratch` must hold 32*NV doubles.  blockDim.x must be a multiple of 32.
+// Warp trees in the working type, then thread q adds value q over the warps
+// in order (deterministic).
 template <int NV, typename T>
 __device__ __forceinline__ void block_sum_to_f64(T (&v)[NV], double* scratch, double (&out)[NV]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -205,13 +208,15 @@ __device__ __forceinline__ void block_sum_to_f64(T (&v)[NV], double* scratch, do
     if (lane == 0) scratch[q * 32 + warp] = (double)w;
   }
   __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < nwarps; ++w) s += scratch[threadIdx.x * 32 + w];
+    scratch[threadIdx.x * 32] = s;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double s = 0.0;
-      for (int w = 0; w < nwarps; ++w) s += scratch[q * 32 + w];
-      out[q] = s;
-    }
+    for (int q = 0; q < NV; ++q) out[q] = scratch[q * 32];
   }
   __syncthreads();
 }

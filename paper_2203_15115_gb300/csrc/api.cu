@@ -78,7 +78,8 @@ struct Work {
   T* r2 = nullptr;       // second residual buffer (r is double-buffered across iterations)
   T* AW = nullptr;       // K W on the node shells of the groups (see k_build_aw)
   size_t aw_cap = 0;
-  T* invdiag = nullptr;
+  T* invdiag = nullptr;  // per node
+  T* invd = nullptr;     // per DOF (the flat update's Jacobi factors)
   T* E = nullptr;
   ElemConsts<T> K;
   cudaGraphExec_t graph = nullptr;
@@ -126,7 +127,11 @@ struct afd_mesh {
   int* dstatus = nullptr;
   uint8_t* gfix = nullptr;     // [N_g] group holds a fixed DOF
   std::vector<uint8_t> gfix_h;  // host copy
-  long long* aw_off = nullptr; // [N_g] offset of group G's block in AW
+  long long* aw_off = nullptr; // [N_g + 1] offset of group G's block in AW (last: total)
+  int* aw_node = nullptr;      // [aw_total / 18] node index of every shell slot
+  double* grec = nullptr;      // [rhs][N_g][12] per-group records of the coarse right-hand side
+  double* upart = nullptr;     // [rhs][RED_BLOCKS][2] partials of the vector update
+  unsigned int* gcount = nullptr;  // [rhs][N_g] split counters
   size_t aw_total = 0;         // elements of AW
   int nsplit_aw = 1;
   bool coarse_valid = false;
@@ -257,7 +262,7 @@ static int ensure_work(afd_mesh* m, Work<T>& w, int nrhs) {
   invalidate_graphs(m);
   dfree(w.x); dfree(w.r); dfree(w.z); dfree(w.p); dfree(w.q); dfree(w.t); dfree(w.b); dfree(w.r2);
   if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
-  const size_t n = (size_t)nrhs * m->gr.ndof;
+  const size_t n = (size_t)nrhs * m->gr.vs;
   TRY(dalloc(&w.x, n)); TRY(dalloc(&w.r, n)); TRY(dalloc(&w.z, n)); TRY(dalloc(&w.p, n));
   TRY(dalloc(&w.q, n)); TRY(dalloc(&w.t, n)); TRY(dalloc(&w.b, n)); TRY(dalloc(&w.r2, n));
   w.cap = nrhs;
@@ -269,13 +274,17 @@ static int ensure_rhs(afd_mesh* m, int nrhs) {
   invalidate_graphs(m);
   dfree(m->f64); dfree(m->u64); dfree(m->r64); dfree(m->st); dfree(m->done); dfree(m->v); dfree(m->mu); dfree(m->wr);
   dfree(m->fbuf);
-  const size_t n = (size_t)nrhs * m->gr.ndof;
+  const size_t n = (size_t)nrhs * m->gr.vs;
   TRY(dalloc(&m->f64, n)); TRY(dalloc(&m->u64, n)); TRY(dalloc(&m->r64, n));
   TRY(dalloc(&m->st, (size_t)nrhs)); TRY(dalloc(&m->done, (size_t)nrhs));
   TRY(dalloc(&m->v, (size_t)nrhs * m->nc)); TRY(dalloc(&m->mu, (size_t)nrhs * m->nc));
   TRY(dalloc(&m->wr, (size_t)nrhs * m->nc));
-  dfree(m->cpart);
-  TRY(dalloc(&m->cpart, (size_t)nrhs * m->gp.ng * m->nsplit * 14));
+  dfree(m->cpart); dfree(m->grec); dfree(m->gcount); dfree(m->upart);
+  TRY(dalloc(&m->cpart, (size_t)nrhs * m->gp.ng * m->nsplit * 12));
+  TRY(dalloc(&m->grec, (size_t)nrhs * m->gp.ng * 12));
+  TRY(dalloc(&m->upart, (size_t)nrhs * RED_BLOCKS * 2));
+  TRY(dalloc(&m->gcount, (size_t)nrhs * m->gp.ng));
+  CK(cudaMemsetAsync(m->gcount, 0, (size_t)nrhs * m->gp.ng * sizeof(unsigned int), m->s));
   TRY(dalloc(&m->fbuf, (size_t)nrhs * m->gr.nelem));
   m->cap = nrhs;
   // graphs captured for a smaller RHS count stay valid; none need freeing here
@@ -346,7 +355,8 @@ static int build_aw(afd_mesh* m, Work<T>& w) {
     w.aw_cap = m->aw_total;
   }
   const dim3 grid(m->gp.ng, m->nsplit_aw);
-  k_build_aw<T><<<grid, 128, 0, m->s>>>(m->gr, m->gp, m->nsplit_aw, m->E64, m->fixed, m->gfix, m->aw_off, w.K, w.AW); m->launches++;
+  k_build_aw<T><<<grid, 128, 0, m->s>>>(m->gr, m->gp, m->nsplit_aw, m->E64, m->fixed, m->gfix, m->aw_off, w.K, w.AW,
+                                         m->aw_node); m->launches++;
   CK(cudaGetLastError());
   return AFD_OK;
 }
@@ -401,41 +411,42 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
   const T* Einv = F64 ? (const T*)m->Einv64 : (const T*)m->Einv32;
   unsigned int* cnt_st = m->counters;            // [rhs]
   unsigned int* cnt_co = m->counters + MAX_RHS;  // coarse step
-  T* R[2] = {w.r, w.r2};
   T* P[2] = {w.p, w.t};
+  const dim3 vg(RED_BLOCKS, nrhs);
   // r = b - K x ; x += W Einv W^T r ; r = b - K x  (deflated start)
-  TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, R[0], w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
-  k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, R[0], nullptr, m->fixed, m->v, nullptr, m->st); m->launches++;
+  TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, w.r, w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
+  k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, w.r, nullptr, m->fixed, m->v, nullptr, m->st); m->launches++;
   k_coarse_solve<T><<<crows, 256, 0, m->s>>>(m->nc, nrhs, Einv, m->v, m->mu, m->st); m->launches++;
   k_prolong<T><<<pg, 256, 0, m->s>>>(2, gr, m->gp, x, nullptr, m->mu, m->fixed, m->st); m->launches++;
-  TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, R[0], w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
+  TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, w.r, w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
   // Two-level preconditioned residual y = z + W Einv W^T (r - K z), z = M^-1 r
   // (the A-DEF2 form of deflation: the W^T r term keeps W^T r from drifting
   // under rounding, which the plain projected recurrence does not).  The
-  // initial step runs the merged update with alpha = 0 (p = q = 0).
-  CK(cudaMemsetAsync(P[0], 0, (size_t)nrhs * gr.ndof * sizeof(T), m->s));
-  CK(cudaMemsetAsync(w.q, 0, (size_t)nrhs * gr.ndof * sizeof(T), m->s));
-  k_update_coarse<T><<<ug, 256, 0, m->s>>>(gr, m->gp, m->nsplit, x, R[0], R[1], w.z, P[0], w.q, w.invdiag, m->fixed,
-                                          m->gfix, m->aw_off, w.AW, m->cpart, m->st); m->launches++;
-  k_coarse_step<T><<<crows, 256, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->nsplit, m->cpart, m->wr, 2, m->done,
-                                               cnt_co); m->launches++;
+  // initial step runs the vector update with alpha = 0 (p = q = 0).
+  CK(cudaMemsetAsync(P[0], 0, (size_t)nrhs * gr.vs * sizeof(T), m->s));
+  CK(cudaMemsetAsync(w.q, 0, (size_t)nrhs * gr.vs * sizeof(T), m->s));
+  k_update<T><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, x, w.r, w.z, P[0], w.q, w.invd, m->upart, m->st); m->launches++;
+  k_coarse_rhs<T><<<ug, 256, 0, m->s>>>(gr, m->gp, m->nsplit, w.r, w.z, m->aw_off, m->aw_node, w.AW, m->cpart, m->grec,
+                                       m->gcount, m->st); m->launches++;
+  k_coarse_step<T><<<crows, 256, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->grec, m->wr, 2, m->done, cnt_co,
+                                               m->upart, RED_BLOCKS); m->launches++;
   CK(cudaGetLastError());
 
   // One chunk of iterations (even length), captured once into a graph.  Per
   // iteration: the stencil forms p = y + beta p_old while applying K to it
-  // (and takes alpha), the merged update/coarse kernel, the coarse step (beta).
+  // (and takes alpha), the vector update (x, r, z, r.z, r.r), the coarse
+  // right-hand side, the coarse step (mu, beta).
   auto enqueue_chunk = [&]() -> int {
     for (int it = 0; it < m->opt.check_every; ++it) {
       T* pold = P[it & 1];
       T* pnew = P[(it + 1) & 1];
-      T* rold = R[(it + 1) & 1];
-      T* rnew = R[it & 1];
       TRY((launch_stencil<T, ST_APPLY_DOT, TB>(m, pold, w.q, w.E, nullptr, nullptr, m->partials, m->done, nrhs, w.K,
                                                 m->st, cnt_st, w.z, m->mu, pnew)));
-      k_update_coarse<T><<<ug, 256, 0, m->s>>>(gr, m->gp, m->nsplit, x, rold, rnew, w.z, pnew, w.q, w.invdiag, m->fixed,
-                                              m->gfix, m->aw_off, w.AW, m->cpart, m->st); m->launches++;
-      k_coarse_step<T><<<crows, 256, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->nsplit, m->cpart, m->wr, 1,
-                                                   m->done, cnt_co); m->launches++;
+      k_update<T><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, x, w.r, w.z, pnew, w.q, w.invd, m->upart, m->st); m->launches++;
+      k_coarse_rhs<T><<<ug, 256, 0, m->s>>>(gr, m->gp, m->nsplit, w.r, w.z, m->aw_off, m->aw_node, w.AW, m->cpart,
+                                           m->grec, m->gcount, m->st); m->launches++;
+      k_coarse_step<T><<<crows, 256, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->grec, m->wr, 1, m->done, cnt_co,
+                                                   m->upart, RED_BLOCKS); m->launches++;
     }
     CK(cudaGetLastError());
     return AFD_OK;
@@ -524,6 +535,7 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
   g.nnodes = g.nnx * g.nny * g.nnz;
   g.nelem = nx * ny * nz;
   g.ndof = 3 * g.nnodes;
+  g.vs = (g.ndof + 3) / 4 * 4;
   Groups& gp = m->gp;
   gp.g = pick_group(nx, ny, nz, o.group);
   gp.ngx = std::max(nx / gp.g, 1);
@@ -534,7 +546,7 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
   m->nc = 6 * gp.ng;
   // shares per group of the merged update / coarse right-hand side kernel
   // (about 600 blocks) and of the K W build (about 2400 blocks of 128 threads)
-  m->nsplit = std::max(1, std::min(4 * gp.g, (600 + gp.ng - 1) / gp.ng));
+  m->nsplit = std::max(1, std::min(gp.g, (1200 + gp.ng - 1) / gp.ng));
   m->nsplit_aw = std::max(1, std::min(16 * gp.g, (2400 + gp.ng - 1) / gp.ng));
   if (m->nc > 8192) {
     delete m;
@@ -561,10 +573,11 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
   if ((rc = dalloc(&m->E64, (size_t)g.nelem)) != AFD_OK || (rc = dalloc(&m->w32.E, (size_t)g.nelem)) != AFD_OK ||
       (rc = dalloc(&m->w64.E, (size_t)g.nelem)) != AFD_OK || (rc = dalloc(&m->w32.invdiag, (size_t)g.nnodes)) != AFD_OK ||
       (rc = dalloc(&m->w64.invdiag, (size_t)g.nnodes)) != AFD_OK || (rc = dalloc(&m->fixed, (size_t)g.nnodes)) != AFD_OK ||
+      (rc = dalloc(&m->w32.invd, (size_t)g.vs)) != AFD_OK || (rc = dalloc(&m->w64.invd, (size_t)g.vs)) != AFD_OK ||
       (rc = dalloc(&m->fsmall, (size_t)FSMALL_SIZE)) != AFD_OK ||
       (rc = dalloc(&m->counters, (size_t)MAX_RHS + 1)) != AFD_OK ||
       (rc = dalloc(&m->gfix, (size_t)gp.ng)) != AFD_OK ||
-      (rc = dalloc(&m->aw_off, (size_t)gp.ng)) != AFD_OK) {
+      (rc = dalloc(&m->aw_off, (size_t)gp.ng + 1)) != AFD_OK) {
     afd_destroy(m);
     return rc;
   }
@@ -584,14 +597,14 @@ void afd_destroy(afd_mesh* m) {
   if (m->s) cudaStreamSynchronize(m->s);
   for (auto* wp : {&m->w32}) {
     dfree(wp->x); dfree(wp->r); dfree(wp->z); dfree(wp->p); dfree(wp->q); dfree(wp->t); dfree(wp->b);
-    dfree(wp->r2); dfree(wp->AW);
+    dfree(wp->r2); dfree(wp->AW); dfree(wp->invd);
     dfree(wp->invdiag); dfree(wp->E);
     if (wp->graph) cudaGraphExecDestroy(wp->graph);
   }
   {
     auto* wp = &m->w64;
     dfree(wp->x); dfree(wp->r); dfree(wp->z); dfree(wp->p); dfree(wp->q); dfree(wp->t); dfree(wp->b);
-    dfree(wp->r2); dfree(wp->AW);
+    dfree(wp->r2); dfree(wp->AW); dfree(wp->invd);
     dfree(wp->invdiag); dfree(wp->E);
     if (wp->graph) cudaGraphExecDestroy(wp->graph);
   }
@@ -600,7 +613,8 @@ void afd_destroy(afd_mesh* m) {
   if (m->sel) cudaFree(m->sel);
   dfree(m->selcnt); dfree(m->fsmall);
   dfree(m->Ec); dfree(m->Einv64); dfree(m->Einv32); dfree(m->gjP); dfree(m->gjB); dfree(m->gjR);
-  dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gfix); dfree(m->aw_off);
+  dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gfix); dfree(m->aw_off); dfree(m->aw_node);
+  dfree(m->grec); dfree(m->gcount); dfree(m->upart);
   if (m->ev) cudaEventDestroy(m->ev);
   if (m->s) cudaStreamDestroy(m->s);
   delete m;
@@ -609,6 +623,12 @@ void afd_destroy(afd_mesh* m) {
 template <typename T>
 __global__ void k_convert(size_t n, const double* __restrict__ a, T* __restrict__ b) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) b[i] = (T)a[i];
+}
+
+// b[d] = a[d / 3]: per-node values repeated for the node's three DOFs.
+template <typename T>
+__global__ void k_expand3(int ndof, const T* __restrict__ a, T* __restrict__ b) {
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) b[d] = a[d / 3];
 }
 
 __global__ void k_check_moduli(size_t n, const double* __restrict__ E, int* bad) {
@@ -624,6 +644,8 @@ static int refresh_moduli(afd_mesh* m) {
   const double d0 = elem_diag(m->opt.nu, m->opt.h);
   k_invdiag<float><<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->E64, d0, m->w32.invdiag); m->launches++;
   k_invdiag<double><<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->E64, d0, m->w64.invdiag); m->launches++;
+  k_expand3<float><<<grid_blocks(g.ndof, 256, 4096), 256, 0, m->s>>>(g.ndof, m->w32.invdiag, m->w32.invd); m->launches++;
+  k_expand3<double><<<grid_blocks(g.ndof, 256, 4096), 256, 0, m->s>>>(g.ndof, m->w64.invdiag, m->w64.invd); m->launches++;
   CK(cudaGetLastError());
   m->coarse_valid = false;
   m->has_moduli = true;
@@ -655,12 +677,12 @@ __global__ void k_pack_fixed(int nnodes, const uint8_t* __restrict__ dof_mask, u
     node_bits[n] = (dof_mask[3 * n] ? 1 : 0) | (dof_mask[3 * n + 1] ? 2 : 0) | (dof_mask[3 * n + 2] ? 4 : 0);
 }
 
-__global__ void k_zero_fixed(int nnodes, int nrhs, int ndof, const uint8_t* __restrict__ bits, double* __restrict__ f) {
+__global__ void k_zero_fixed(int nnodes, int nrhs, int vs, const uint8_t* __restrict__ bits, double* __restrict__ f) {
   const int rhs = blockIdx.y;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nnodes; n += gridDim.x * blockDim.x) {
     const uint8_t b = bits[n];
     for (int c = 0; c < 3; ++c)
-      if ((b >> c) & 1) f[(size_t)rhs * ndof + 3 * n + c] = 0.0;
+      if ((b >> c) & 1) f[(size_t)rhs * vs + 3 * n + c] = 0.0;
   }
 }
 
@@ -681,8 +703,11 @@ int afd_set_loads_bcs(afd_mesh* m, int n_rhs, const double* f, int f_on_device, 
   TRY(enter(m));
   TRY(ensure_rhs(m, n_rhs));
   const Grid& g = m->gr;
-  const size_t n = (size_t)n_rhs * g.ndof;
-  CK(cudaMemcpyAsync(m->f64, f, n * sizeof(double), f_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->s));
+  const size_t n = (size_t)n_rhs * g.vs;
+  CK(cudaMemsetAsync(m->f64, 0, n * sizeof(double), m->s));
+  CK(cudaMemcpy2DAsync(m->f64, (size_t)g.vs * sizeof(double), f, (size_t)g.ndof * sizeof(double),
+                       (size_t)g.ndof * sizeof(double), n_rhs,
+                       f_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->s));
   uint8_t* dmask = nullptr;
   if (mask_on_device) {
     dmask = (uint8_t*)mask;
@@ -697,20 +722,26 @@ int afd_set_loads_bcs(afd_mesh* m, int n_rhs, const double* f, int f_on_device, 
   CK(cudaMemcpyAsync(m->gfix_h.data(), m->gfix, m->gp.ng, cudaMemcpyDeviceToHost, m->s));
   CK(cudaStreamSynchronize(m->s));
   {
-    std::vector<long long> off(m->gp.ng);
+    std::vector<long long> off(m->gp.ng + 1);
     size_t tot = 0;
     for (int G = 0; G < m->gp.ng; ++G) {
       off[G] = (long long)tot;
       tot += 18 * (size_t)node_shell_count(g, m->gp, G, m->gfix_h[G] != 0);
     }
+    off[m->gp.ng] = (long long)tot;
+    if (tot > m->aw_total || !m->aw_node) {
+      invalidate_graphs(m);
+      dfree(m->aw_node);
+      TRY(dalloc(&m->aw_node, tot / 18 + 1));
+    }
     m->aw_total = tot;
-    CK(cudaMemcpyAsync(m->aw_off, off.data(), m->gp.ng * sizeof(long long), cudaMemcpyHostToDevice, m->s));
+    CK(cudaMemcpyAsync(m->aw_off, off.data(), (m->gp.ng + 1) * sizeof(long long), cudaMemcpyHostToDevice, m->s));
   }
-  k_zero_fixed<<<dim3(grid_blocks(g.nnodes, 256, 4096), n_rhs), 256, 0, m->s>>>(g.nnodes, n_rhs, g.ndof, m->fixed, m->f64); m->launches++;
+  k_zero_fixed<<<dim3(grid_blocks(g.nnodes, 256, 4096), n_rhs), 256, 0, m->s>>>(g.nnodes, n_rhs, g.vs, m->fixed, m->f64); m->launches++;
   CK(cudaMemsetAsync(m->u64, 0, n * sizeof(double), m->s));
   CK(cudaGetLastError());
   TRY(ensure_partials(m, (size_t)n_rhs * RED_BLOCKS));
-  k_dot<double, double><<<dim3(RED_BLOCKS, n_rhs), RED_THREADS, 0, m->s>>>(g.ndof, m->f64, m->f64, m->partials); m->launches++;
+  k_dot<double, double><<<dim3(RED_BLOCKS, n_rhs), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->f64, m->f64, m->partials); m->launches++;
   std::vector<double> ff;
   TRY(reduce_partials_host(m, n_rhs, RED_BLOCKS, ff));
   if (!mask_on_device) cudaFree(dmask);
@@ -749,7 +780,7 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
   const int R = m->nrhs;
   const Grid& g = m->gr;
   TRY(build_coarse(m));
-  if (!warm_start || !m->has_solution) CK(cudaMemsetAsync(m->u64, 0, (size_t)R * g.ndof * sizeof(double), m->s));
+  if (!warm_start || !m->has_solution) CK(cudaMemsetAsync(m->u64, 0, (size_t)R * g.vs * sizeof(double), m->s));
   std::vector<int> iters(R, 0), status(R, AFD_OK), refine(R, 0);
   std::vector<double> rel;
   if (m->opt.precision == AFD_FP64) {
@@ -784,7 +815,7 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
         t2[r] = (eta * rn) * (eta * rn);
       }
       if (!any) break;
-      CK(cudaMemsetAsync(m->w32.x, 0, (size_t)R * g.ndof * sizeof(float), m->s));
+      CK(cudaMemsetAsync(m->w32.x, 0, (size_t)R * g.vs * sizeof(float), m->s));
       std::vector<CGState> st;
       int budget = m->opt.max_iter;
       for (int r = 0; r < R; ++r) if (act[r]) budget = std::min(budget, std::max(1, m->opt.max_iter - iters[r]));
@@ -800,7 +831,7 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
       }
       int* dskip = m->done;
       CK(cudaMemcpyAsync(dskip, skip.data(), R * sizeof(int), cudaMemcpyHostToDevice, m->s));
-      k_accumulate<<<dim3(grid_blocks(g.ndof, 256, 2048), R), 256, 0, m->s>>>(g.ndof, R, m->u64, m->w32.x, dskip); m->launches++;
+      k_accumulate<<<dim3(grid_blocks(g.ndof, 256, 2048), R), 256, 0, m->s>>>(g.ndof, g.vs, m->u64, m->w32.x, dskip); m->launches++;
       CK(cudaGetLastError());
       TRY(true_residual(m, b32, rel));
     }
@@ -809,8 +840,9 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
   }
   m->has_solution = true;
   if (u_out)
-    CK(cudaMemcpyAsync(u_out, m->u64, (size_t)R * g.ndof * sizeof(double),
-                       u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->s));
+    CK(cudaMemcpy2DAsync(u_out, (size_t)g.ndof * sizeof(double), m->u64, (size_t)g.vs * sizeof(double),
+                         (size_t)g.ndof * sizeof(double), R,
+                         u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->s));
   TRY(finish(m));
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   int rc = AFD_OK;
@@ -835,7 +867,7 @@ int afd_compliance(afd_mesh* m, double* J_out) {
   DeviceGuard dg(m->device);
   TRY(enter(m));
   TRY(ensure_partials(m, (size_t)m->nrhs * RED_BLOCKS));
-  k_dot<double, double><<<dim3(RED_BLOCKS, m->nrhs), RED_THREADS, 0, m->s>>>(m->gr.ndof, m->f64, m->u64, m->partials); m->launches++;
+  k_dot<double, double><<<dim3(RED_BLOCKS, m->nrhs), RED_THREADS, 0, m->s>>>(m->gr.ndof, m->gr.vs, m->f64, m->u64, m->partials); m->launches++;
   CK(cudaGetLastError());
   std::vector<double> J;
   TRY(reduce_partials_host(m, m->nrhs, RED_BLOCKS, J));
@@ -1059,14 +1091,17 @@ int afd_apply_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* 
   if (!m->has_moduli) return fail(AFD_ERR_STATE, "moduli not set");
   DeviceGuard dg(m->device);
   TRY(enter(m));
-  if (arith == AFD_F64)
-    TRY((launch_stencil<double, ST_APPLY, double>(m, (const double*)u, (double*)y, m->w64.E, nullptr, nullptr, nullptr,
-                                                    nullptr, n_rhs, m->w64.K)));
-  else if (arith == AFD_F32)
-    TRY((launch_stencil<float, ST_APPLY, float>(m, (const float*)u, (float*)y, m->w32.E, nullptr, nullptr, nullptr,
-                                                  nullptr, n_rhs, m->w32.K)));
-  else
-    return fail(AFD_ERR_INVALID_ARG, "arith must be AFD_F32 or AFD_F64");
+  if (arith != AFD_F32 && arith != AFD_F64) return fail(AFD_ERR_INVALID_ARG, "arith must be AFD_F32 or AFD_F64");
+  // caller arrays are RHS-major with stride ndof: one launch per RHS
+  const size_t nd = (size_t)m->gr.ndof;
+  for (int r = 0; r < n_rhs; ++r) {
+    if (arith == AFD_F64)
+      TRY((launch_stencil<double, ST_APPLY, double>(m, (const double*)u + r * nd, (double*)y + r * nd, m->w64.E, nullptr,
+                                                      nullptr, nullptr, nullptr, 1, m->w64.K)));
+    else
+      TRY((launch_stencil<float, ST_APPLY, float>(m, (const float*)u + r * nd, (float*)y + r * nd, m->w32.E, nullptr,
+                                                    nullptr, nullptr, nullptr, 1, m->w32.K)));
+  }
   return finish(m);
 }
 
@@ -1074,7 +1109,10 @@ int afd_deflation_wt(afd_mesh* m, int n_rhs, const double* v, double* out) {
   if (!m || !v || !out || n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "bad argument");
   DeviceGuard dg(m->device);
   TRY(enter(m));
-  k_restrict<double><<<dim3(m->gp.ng, n_rhs), 256, 0, m->s>>>(m->gr, m->gp, v, nullptr, m->fixed, out, nullptr, nullptr); m->launches++;
+  for (int r = 0; r < n_rhs; ++r) {
+    k_restrict<double><<<dim3(m->gp.ng, 1), 256, 0, m->s>>>(m->gr, m->gp, v + (size_t)r * m->gr.ndof, nullptr, m->fixed,
+                                                            out + (size_t)r * m->nc, nullptr, nullptr); m->launches++;
+  }
   CK(cudaGetLastError());
   return finish(m);
 }
@@ -1083,8 +1121,10 @@ int afd_deflation_w(afd_mesh* m, int n_rhs, const double* y, double* out) {
   if (!m || !y || !out || n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "bad argument");
   DeviceGuard dg(m->device);
   TRY(enter(m));
-  k_prolong<double><<<dim3(grid_blocks(m->gr.nnodes, 256, 4096), n_rhs), 256, 0, m->s>>>(1, m->gr, m->gp, out, nullptr, y,
-                                                                                          m->fixed, nullptr); m->launches++;
+  for (int r = 0; r < n_rhs; ++r) {
+    k_prolong<double><<<dim3(grid_blocks(m->gr.nnodes, 256, 4096), 1), 256, 0, m->s>>>(
+        1, m->gr, m->gp, out + (size_t)r * m->gr.ndof, nullptr, y + (size_t)r * m->nc, m->fixed, nullptr); m->launches++;
+  }
   CK(cudaGetLastError());
   return finish(m);
 }
@@ -1103,13 +1143,16 @@ int afd_time_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, m->s));
+  const size_t nd = (size_t)m->gr.ndof;
   for (int i = 0; i < launches; ++i) {
-    if (arith == AFD_F64)
-      TRY((launch_stencil<double, ST_APPLY, double>(m, (const double*)u, (double*)y, m->w64.E, nullptr, nullptr, nullptr,
-                                                      nullptr, n_rhs, m->w64.K)));
-    else
-      TRY((launch_stencil<float, ST_APPLY, float>(m, (const float*)u, (float*)y, m->w32.E, nullptr, nullptr, nullptr,
-                                                    nullptr, n_rhs, m->w32.K)));
+    for (int r = 0; r < n_rhs; ++r) {
+      if (arith == AFD_F64)
+        TRY((launch_stencil<double, ST_APPLY, double>(m, (const double*)u + r * nd, (double*)y + r * nd, m->w64.E,
+                                                        nullptr, nullptr, nullptr, nullptr, 1, m->w64.K)));
+      else
+        TRY((launch_stencil<float, ST_APPLY, float>(m, (const float*)u + r * nd, (float*)y + r * nd, m->w32.E, nullptr,
+                                                      nullptr, nullptr, nullptr, 1, m->w32.K)));
+    }
   }
   CK(cudaEventRecord(e1, m->s));
   CK(cudaEventSynchronize(e1));

@@ -81,7 +81,7 @@ k_restrict(Grid gr, Groups gp, const T* __restrict__ a, const T* __restrict__ b,
   const T hh = (T)(0.5 * gp.h);
   const int lx = ihi - ilo + 1, ly = jhi - jlo + 1, lz = khi - klo + 1;
   const int cnt = lx * ly * lz;
-  const size_t off = (size_t)rhs * gr.ndof;
+  const size_t off = (size_t)rhs * gr.vs;
   T s[12];
 #pragma unroll
   for (int q = 0; q < 12; ++q) s[q] = T(0);
@@ -211,7 +211,8 @@ __host__ __device__ inline int node_shell_count(const Grid& gr, const Groups& gp
 template <typename TC>
 __global__ void __launch_bounds__(128)
 k_build_aw(Grid gr, Groups gp, int nsplit, const double* __restrict__ Emod, const uint8_t* __restrict__ fixed,
-           const uint8_t* __restrict__ gfix, const long long* __restrict__ aw_off, ElemConsts<TC> K, TC* __restrict__ AW) {
+           const uint8_t* __restrict__ gfix, const long long* __restrict__ aw_off, ElemConsts<TC> K, TC* __restrict__ AW,
+           int* __restrict__ aw_node) {
   const int G = blockIdx.x, sp = blockIdx.y;
   int b[12];
   node_shell_bounds(gr, gp, G, b);
@@ -285,35 +286,103 @@ k_build_aw(Grid gr, Groups gp, int nsplit, const double* __restrict__ Emod, cons
     }
 #pragma unroll
     for (int t = 0; t < 18; ++t) out[(size_t)t * nG + q] = acc[t];
+    aw_node[aw_off[G] / 18 + q] = ni + gr.nnx * (nj + gr.nny * nk);
   }
 }
 
-// One DPCG vector step merged with the coarse right-hand side, per (group,
-// split, rhs): over the group's nodes x += alpha p, r_new = r_old - alpha q,
-// z = M^-1 r_new (written), partial r.z, r.r and W_G^T r_new; over the group's
-// node shell (W_G^T K z) = (K W_G)^T z from the stored AW, with z recomputed
-// from r_old (r is double-buffered, so no block sees another's new values).
-// Writes part[rhs][G][split][0..13] = (r.z, r.r, W^T r (6), W^T r - W^T K z (6)).
+// Vector width of the flat update: 16-byte loads.
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
+
+// x += alpha p; r -= alpha q; z = r * invd (invd per DOF, zero on fixed DOFs);
+// partial sums of r.z and r.r per block.  Flat over the DOFs of each RHS with
+// 16-byte vector accesses (the RHS stride vs keeps every RHS aligned).
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_update_coarse(Grid gr, Groups gp, int nsplit, T* __restrict__ x, const T* __restrict__ r_old, T* __restrict__ r_new,
-                T* __restrict__ z, const T* __restrict__ p, const T* __restrict__ q, const T* __restrict__ invdiag,
-                const uint8_t* __restrict__ fixed, const uint8_t* __restrict__ gfix, const long long* __restrict__ aw_off,
-                const T* __restrict__ AW, double* __restrict__ part, const CGState* st) {
-  __shared__ double red[32 * 14];
-  const int G = blockIdx.x, sp = blockIdx.y, rhs = blockIdx.z;
+__global__ void __launch_bounds__(RED_THREADS)
+k_update(int ndof, int vs, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
+         const T* __restrict__ q, const T* __restrict__ invd, double* partials, const CGState* st) {
+  using V = typename Vec<T>::type;
+  constexpr int NV = Vec<T>::n;
+  __shared__ double red[64];
+  const int rhs = blockIdx.y;
   if (st[rhs].done) return;
   const T alpha = (T)st[rhs].alpha;
+  const size_t off = (size_t)rhs * vs;
+  T s[2] = {T(0), T(0)};
+  const int nvec = ndof / NV;
+  V* xv = (V*)(x + off);
+  V* rv = (V*)(r + off);
+  V* zv = (V*)(z + off);
+  const V* pv = (const V*)(p + off);
+  const V* qv = (const V*)(q + off);
+  const V* dv = (const V*)invd;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvec; t += gridDim.x * blockDim.x) {
+    V xx = xv[t], rr = rv[t];
+    const V pp = pv[t], qq = qv[t], dd = dv[t];
+    T* xs = (T*)&xx;
+    T* rs = (T*)&rr;
+    const T* ps = (const T*)&pp;
+    const T* qs = (const T*)&qq;
+    const T* ds = (const T*)&dd;
+    V zz;
+    T* zs = (T*)&zz;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      xs[c] = fma(alpha, ps[c], xs[c]);
+      rs[c] = fma(-alpha, qs[c], rs[c]);
+      zs[c] = rs[c] * ds[c];
+      s[0] += rs[c] * zs[c];
+      s[1] += rs[c] * rs[c];
+    }
+    xv[t] = xx;
+    rv[t] = rr;
+    zv[t] = zz;
+  }
+  // tail DOFs
+  for (int d = nvec * NV + blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
+    const size_t i = off + d;
+    x[i] = fma(alpha, p[i], x[i]);
+    const T rn = fma(-alpha, q[i], r[i]);
+    r[i] = rn;
+    const T zn = rn * invd[d];
+    z[i] = zn;
+    s[0] += rn * zn;
+    s[1] += rn * rn;
+  }
+  double o[2];
+  block_sum_to_f64<2>(s, red, o);
+  if (threadIdx.x == 0) {
+    partials[((size_t)rhs * gridDim.x + blockIdx.x) * 2 + 0] = o[0];
+    partials[((size_t)rhs * gridDim.x + blockIdx.x) * 2 + 1] = o[1];
+  }
+}
+
+// Right-hand side of the coarse solve of the two-level preconditioner,
+//   v_G = (W^T r)_G - (W^T K z)_G,   (W^T K z)_G = (K W_G)^T z,
+// per (group, split, rhs): W^T r over the group's nodes, (K W_G)^T z over
+// its node shell from the stored AW (slot -> node index in aw_node).  r and z
+// are zero on fixed DOFs.  The group's last split block adds the nsplit
+// records in order into rec[rhs][G][0..11] = (W^T r (6), v (6)).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_coarse_rhs(Grid gr, Groups gp, int nsplit, const T* __restrict__ r, const T* __restrict__ z,
+             const long long* __restrict__ aw_off, const int* __restrict__ aw_node, const T* __restrict__ AW,
+             double* __restrict__ part, double* __restrict__ rec, unsigned int* __restrict__ gcount, const CGState* st) {
+  __shared__ double red[32 * 12];
+  __shared__ bool s_last;
+  const int G = blockIdx.x, sp = blockIdx.y, rhs = blockIdx.z;
+  if (st[rhs].done) return;
   const int Gx = G % gp.ngx, Gy = (G / gp.ngx) % gp.ngy, Gz = G / (gp.ngx * gp.ngy);
   int ilo, ihi, jlo, jhi, klo, khi;
   group_range(Gx, gp.g, gp.ngx, gr.nx, ilo, ihi);
   group_range(Gy, gp.g, gp.ngy, gr.ny, jlo, jhi);
   group_range(Gz, gp.g, gp.ngz, gr.nz, klo, khi);
   const T hh = (T)(0.5 * gp.h);
-  const size_t off = (size_t)rhs * gr.ndof;
-  T s[14];
+  const size_t off = (size_t)rhs * gr.vs;
+  T s[12];
 #pragma unroll
-  for (int t = 0; t < 14; ++t) s[t] = T(0);
+  for (int t = 0; t < 12; ++t) s[t] = T(0);
   {
     const int lx = ihi - ilo + 1, ly = jhi - jlo + 1, lz = khi - klo + 1;
     const int cnt = lx * ly * lz;
@@ -321,69 +390,54 @@ k_update_coarse(Grid gr, Groups gp, int nsplit, T* __restrict__ x, const T* __re
     const int qb = sp * per, qe = min(qb + per, cnt);
     for (int t = qb + threadIdx.x; t < qe; t += blockDim.x) {
       const int i = ilo + t % lx, j = jlo + (t / lx) % ly, k = klo + t / (lx * ly);
-      const int n = i + gr.nnx * (j + gr.nny * k);
-      const T dinv = invdiag[n];
-      const size_t d = off + 3 * (size_t)n;
-      T rn[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        x[d + c] = fma(alpha, p[d + c], x[d + c]);
-        rn[c] = fma(-alpha, q[d + c], r_old[d + c]);
-        r_new[d + c] = rn[c];
-        const T zv = rn[c] * dinv;
-        z[d + c] = zv;
-        s[0] += rn[c] * zv;
-        s[1] += rn[c] * rn[c];
-      }
+      const size_t d = off + 3 * (size_t)(i + gr.nnx * (j + gr.nny * k));
+      const T r0 = r[d], r1 = r[d + 1], r2 = r[d + 2];
       const T rx = hh * (T)(2 * i - ilo - ihi), ry = hh * (T)(2 * j - jlo - jhi), rz = hh * (T)(2 * k - klo - khi);
-      s[2] += rn[0];
-      s[3] += rn[1];
-      s[4] += rn[2];
-      s[5] += ry * rn[2] - rz * rn[1];
-      s[6] += rz * rn[0] - rx * rn[2];
-      s[7] += rx * rn[1] - ry * rn[0];
+      s[0] += r0;
+      s[1] += r1;
+      s[2] += r2;
+      s[3] += ry * r2 - rz * r1;
+      s[4] += rz * r0 - rx * r2;
+      s[5] += rx * r1 - ry * r0;
     }
   }
   {
-    int b[12];
-    node_shell_bounds(gr, gp, G, b);
-    Shell sh;
-    sh.init(b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], b[8], b[9], b[10], b[11], gfix && gfix[G]);
-    const int nG = sh.count;
-    const T* aw = AW + aw_off[G];
+    const long long base = aw_off[G];
+    const int nG = (int)((aw_off[G + 1] - base) / 18);
+    const T* aw = AW + base;
+    const int* nodes = aw_node + base / 18;
     const int per = (nG + nsplit - 1) / nsplit;
     const int qb = sp * per, qe = min(qb + per, nG);
     for (int t = qb + threadIdx.x; t < qe; t += blockDim.x) {
-      int i, j, k;
-      sh.at(t, i, j, k);
-      const int n = i + gr.nnx * (j + gr.nny * k);
-      const uint8_t fb = fixed ? fixed[n] : 0;
-      const T dinv = invdiag[n];
-      const size_t d = off + 3 * (size_t)n;
-      T zc[3];
+      const size_t d = off + 3 * (size_t)nodes[t];
+      const T z0 = z[d], z1 = z[d + 1], z2 = z[d + 2];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) zc[c] = ((fb >> c) & 1) ? T(0) : fma(-alpha, q[d + c], r_old[d + c]) * dinv;
-#pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        T acc = T(0);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc = fma(aw[(size_t)(6 * c + m) * nG + t], zc[c], acc);
-        s[8 + m] += acc;
-      }
+      for (int m = 0; m < 6; ++m)
+        s[6 + m] += aw[(size_t)m * nG + t] * z0 + aw[(size_t)(6 + m) * nG + t] * z1 + aw[(size_t)(12 + m) * nG + t] * z2;
     }
   }
-  double o[14];
-  block_sum_to_f64<14>(s, red, o);
+  double o[12];
+  block_sum_to_f64<12>(s, red, o);
+  double* mine = part + (((size_t)rhs * gp.ng + G) * nsplit + sp) * 12;
   if (threadIdx.x == 0) {
-    double* pp = part + (((size_t)rhs * gp.ng + G) * nsplit + sp) * 14;
-    pp[0] = o[0];
-    pp[1] = o[1];
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
-      pp[2 + m] = o[2 + m];
-      pp[8 + m] = o[2 + m] - o[8 + m];
+      mine[m] = o[m];
+      mine[6 + m] = o[m] - o[6 + m];
     }
+    __threadfence();
+    s_last = atomicAdd(&gcount[(size_t)rhs * gp.ng + G], 1u) == (unsigned)nsplit - 1u;
   }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 12) {
+    const double* pp = part + (((size_t)rhs * gp.ng + G) * nsplit) * 12;
+    double v = 0.0;
+    for (int s2 = 0; s2 < nsplit; ++s2) v += pp[s2 * 12 + threadIdx.x];
+    rec[((size_t)rhs * gp.ng + G) * 12 + threadIdx.x] = v;
+  }
+  if (threadIdx.x == 0) gcount[(size_t)rhs * gp.ng + G] = 0u;
 }
 
 // gfix[G] = 1 when a node of group G has a fixed DOF.
@@ -428,7 +482,7 @@ k_prolong(int mode, Grid gr, Groups gp, T* __restrict__ p, const T* __restrict__
   const int rhs = blockIdx.y;
   if (st && st[rhs].done) return;
   const T beta = (mode == 0 && st) ? (T)st[rhs].beta : T(0);
-  const size_t off = (size_t)rhs * gr.ndof;
+  const size_t off = (size_t)rhs * gr.vs;
   const double* m = mu + (size_t)rhs * 6 * gp.ng;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gr.nnodes; n += gridDim.x * blockDim.x) {
     const int i = n % gr.nnx, j = (n / gr.nnx) % gr.nny, k = n / (gr.nnx * gr.nny);
@@ -467,17 +521,17 @@ k_coarse_solve(int nc, int nrhs, const TE* __restrict__ Einv, const double* __re
   }
 }
 
-// Coarse step of one DPCG iteration: v_G and (W^T r)_G are summed from the
-// k_update_coarse records of their nsplit shares, mu = Einv v (one warp per
+// Coarse step of one DPCG iteration: v_G and (W^T r)_G are read from the
+// per-group k_coarse_rhs records, mu = Einv v (one warp per
 // row, all RHS), and the last block to finish takes the beta step for every
-// RHS: rho = r.z + (W^T r).mu (the preconditioned residual y = z + W mu of
+// RHS from the k_update partials: rho = r.z + (W^T r).mu (the preconditioned residual y = z + W mu of
 // the two-level operator), r.r, beta = rho / rho_old, the convergence test
 // and the iteration count.  fin == 2 marks the initial step (beta = 0).
 template <typename TE>
 __global__ void __launch_bounds__(256)
-k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict__ mu, CGState* st, int nsplit,
-              const double* __restrict__ part, double* __restrict__ wr_out, int fin, int* done_flags,
-              unsigned int* counter) {
+k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict__ mu, CGState* st,
+              const double* __restrict__ rec, double* __restrict__ wr_out, int fin, int* done_flags,
+              unsigned int* counter, const double* __restrict__ upd_partials, int upd_nparts) {
   extern __shared__ double vs[];   // nc values of v for the current RHS
   __shared__ bool s_last;
   const int lane = threadIdx.x & 31;
@@ -487,14 +541,9 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
     if (st[r].done) continue;
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
       const int G = q / 6, c = q % 6;
-      const double* pp = part + (((size_t)r * ng + G) * nsplit) * 14;
-      double sv = 0.0, sw = 0.0;
-      for (int s2 = 0; s2 < nsplit; ++s2) {
-        sw += pp[s2 * 14 + 2 + c];
-        sv += pp[s2 * 14 + 8 + c];
-      }
-      vs[q] = sv;
-      if (blockIdx.x == 0) wr_out[(size_t)r * nc + q] = sw;
+      const double* pp = rec + ((size_t)r * ng + G) * 12;
+      vs[q] = pp[6 + c];
+      if (blockIdx.x == 0) wr_out[(size_t)r * nc + q] = pp[c];
     }
     __syncthreads();
     if (row < nc) {
@@ -513,13 +562,12 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const int nrec = ng * nsplit;
   for (int r = 0; r < nrhs; ++r) {
     CGState& S = st[r];
     if (S.done) continue;
-    const double* pp = part + (size_t)r * nrec * 14;
-    const double rz = sum_partials(pp, nrec, 14, 0);
-    const double rr = sum_partials(pp, nrec, 14, 1);
+    const double* pp = upd_partials + (size_t)r * upd_nparts * 2;
+    const double rz = sum_partials(pp, upd_nparts, 2, 0);
+    const double rr = sum_partials(pp, upd_nparts, 2, 1);
     double c = 0.0;
     for (int i = threadIdx.x; i < nc; i += blockDim.x) c += wr_out[(size_t)r * nc + i] * mu[(size_t)r * nc + i];
     const double cdot = block_sum_bcast(c);
@@ -553,10 +601,10 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
 // ---------------------------------------------------------------------------
 
 // u64 += (double) d32  (per RHS; skip RHS whose outer loop has converged)
-__global__ void k_accumulate(int ndof, int nrhs, double* __restrict__ u, const float* __restrict__ d, const int* skip) {
+__global__ void k_accumulate(int ndof, int vs, double* __restrict__ u, const float* __restrict__ d, const int* skip) {
   const int rhs = blockIdx.y;
   if (skip && skip[rhs]) return;
-  const size_t off = (size_t)rhs * ndof;
+  const size_t off = (size_t)rhs * vs;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += gridDim.x * blockDim.x)
     u[off + i] += (double)d[off + i];
 }
@@ -566,13 +614,13 @@ __global__ void k_fill(size_t n, T* __restrict__ x, T v) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) x[i] = v;
 }
 
-// Partial sums of x.y (FP64) per block, per RHS; x, y in type T.
+// Partial sums of x.y (FP64) per block, per RHS (n values, RHS stride vs).
 template <typename T, typename U>
 __global__ void __launch_bounds__(RED_THREADS)
-k_dot(int n, const T* __restrict__ x, const U* __restrict__ y, double* partials) {
+k_dot(int n, int vs, const T* __restrict__ x, const U* __restrict__ y, double* partials) {
   __shared__ double red[32];
   const int rhs = blockIdx.y;
-  const size_t off = (size_t)rhs * n;
+  const size_t off = (size_t)rhs * vs;
   double s[1] = {0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     s[0] = fma((double)x[off + i], (double)y[off + i], s[0]);

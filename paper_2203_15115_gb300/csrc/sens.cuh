@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256)
 k_element_fields(Grid gr, const double* __restrict__ u, const double* __restrict__ Emod, ElemConsts<TC> K,
                  FieldConsts F, int kind, float* __restrict__ out) {
   const int rhs = blockIdx.y;
-  const double* ur = u + (size_t)rhs * gr.ndof;
+  const double* ur = u + (size_t)rhs * gr.vs;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < gr.nelem; e += gridDim.x * blockDim.x) {
     const int i = e % gr.nx, j = (e / gr.nx) % gr.ny, k = e / (gr.nx * gr.ny);
     double uu[3][8];

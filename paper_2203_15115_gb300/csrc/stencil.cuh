@@ -89,7 +89,7 @@ stencil_kernel(const StencilArgs<T, TF> a) {
   const int j = tile_y * (TY - 2) - 1 + w;
   const int k0 = blockIdx.y * a.kz;
   const int k1 = min(k0 + a.kz, gr.nnz);
-  const size_t voff = (size_t)rhs * gr.ndof;
+  const size_t voff = (size_t)rhs * gr.vs;
   const T* __restrict__ u = a.u + voff;
 
   const bool col_ok = i >= 0 && i < gr.nnx && j >= 0 && j < gr.nny;
