@@ -70,7 +70,7 @@ typedef struct {
   int max_refine;     /* cap on FP64 refinement steps in AFD_MIXED (default 12) */
   double inner_tol;   /* floor of the inner relative tolerance in AFD_MIXED (default 2e-5) */
   int check_every;    /* DPCG iterations per captured CUDA graph between host checks (default 16) */
-  int autotune;       /* 1: time the stencil tile variants once per mesh and keep the fastest */
+  int autotune;       /* 1 (default): at the first solve, time the stencil's z depth per CTA and keep the fastest */
 } afd_options;
 
 typedef struct {
@@ -183,6 +183,10 @@ int afd_time_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y
 /* Number of CUDA kernels this mesh has launched so far (a CUDA-graph replay
  * counts its kernel nodes). */
 int64_t afd_kernel_launches(const afd_mesh* m);
+
+/* Node planes per CTA of the stiffness kernel (chosen by the autotuner at the
+ * first solve when opt.autotune is set, else by a size heuristic). */
+int afd_stencil_depth(const afd_mesh* m);
 
 /* Sizes of the mesh. */
 int64_t afd_ndof(const afd_mesh* m);

@@ -39,7 +39,7 @@ EXPORTS = [
     "afd_compliance", "afd_sensitivity", "afd_pnorm_stress", "afd_levelset_update", "afd_apply_stiffness",
     "afd_deflation_wt", "afd_deflation_w", "afd_coarse_size", "afd_coarse_matrix", "afd_select_topk",
     "afd_ndof", "afd_nelem", "afd_destroy", "afd_last_error", "afd_al_init", "afd_al_update", "afd_al_weight",
-    "afd_time_stiffness", "afd_kernel_launches", "afd_select_topk_noalloc",
+    "afd_time_stiffness", "afd_kernel_launches", "afd_select_topk_noalloc", "afd_stencil_depth",
 ]
 
 
@@ -106,6 +106,7 @@ def lib() -> ctypes.CDLL:
             "afd_time_stiffness": (i, [vp, i, i, vp, vp, i, ctypes.POINTER(d)]),
             "afd_kernel_launches": (i64, [vp]),
             "afd_select_topk_noalloc": (i, [vp, i64, i64, vp, ctypes.POINTER(ctypes.c_float), vp]),
+            "afd_stencil_depth": (i, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -277,6 +278,10 @@ def afd_time_stiffness(mesh, arith: int, n_rhs: int, u, y, launches: int) -> flo
     ms = ctypes.c_double()
     _check(lib().afd_time_stiffness(mesh, arith, n_rhs, pu, py, launches, ctypes.byref(ms)))
     return ms.value
+
+
+def afd_stencil_depth(mesh) -> int:
+    return int(lib().afd_stencil_depth(mesh))
 
 
 def afd_kernel_launches(mesh) -> int:

@@ -95,6 +95,7 @@ struct afd_mesh {
   cudaStream_t user = nullptr, s = nullptr;
   cudaEvent_t ev = nullptr;
   int kz = 8;
+  bool tuned = false;          // autotuner has chosen kz for this mesh
   // state
   double* E64 = nullptr;
   uint8_t* fixed = nullptr;   // per node bits
@@ -380,6 +381,58 @@ static int build_coarse(afd_mesh* m) {
   return AFD_OK;
 }
 
+// Stencil autotuner: the z depth of the column-marching CTAs trades
+// redundant element layers ((kz+1)/kz) against the number of CTAs (waves over
+// the SMs).  Each candidate is timed on the solver's FP32 kernel and stream
+// with CUDA events (3 launches after one warm-up); the fastest is kept for
+// the mesh.
+static int autotune_stencil(afd_mesh* m) {
+  TRY(ensure_work(m, m->w32, 1));
+  const Grid& g = m->gr;
+  static const int cand[] = {2, 3, 4, 5, 6, 8, 12, 16, 24, 32};
+  size_t maxp = 0;
+  for (int kz : cand) {
+    if (kz > g.nnz && kz != cand[0]) continue;
+    int tx;
+    dim3 gr;
+    StencilGeom<TY32>::get(g, kz, tx, gr);
+    maxp = std::max(maxp, (size_t)gr.x * gr.y);
+    StencilGeom<TY64>::get(g, kz, tx, gr);
+    maxp = std::max(maxp, (size_t)gr.x * gr.y);
+  }
+  TRY(ensure_partials(m, (size_t)std::max(m->cap, 1) * std::max(maxp, (size_t)2 * RED_BLOCKS)));
+  CK(cudaMemsetAsync(m->w32.p, 0, (size_t)g.vs * sizeof(float), m->s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_kz = m->kz;
+  for (int kz : cand) {
+    if (kz > g.nnz && kz != cand[0]) continue;
+    m->kz = kz;
+    TRY((launch_stencil<float, ST_APPLY, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr, nullptr, nullptr, 1,
+                                                  m->w32.K)));
+    CK(cudaEventRecord(e0, m->s));
+    for (int rep = 0; rep < 3; ++rep)
+      TRY((launch_stencil<float, ST_APPLY, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr, nullptr, nullptr,
+                                                    1, m->w32.K)));
+    CK(cudaEventRecord(e1, m->s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_kz = kz;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->kz = best_kz;
+  m->tuned = true;
+  invalidate_graphs(m);  // captured launches bake in the grid
+  return AFD_OK;
+}
+
 // ---------------------------------------------------------------------------
 // deflated PCG (Sec. 3.5) in type T on K x = b; x holds the initial guess.
 // Per-RHS stop: r.r <= target2[r]; RHS with active[r] == 0 are skipped.
@@ -503,7 +556,7 @@ void afd_default_options(afd_options* o) {
   o->max_refine = 12;
   o->inner_tol = 2e-5;
   o->check_every = 16;
-  o->autotune = 0;
+  o->autotune = 1;
 }
 
 const char* afd_last_error(void) { return g_err.c_str(); }
@@ -780,6 +833,7 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
   const int R = m->nrhs;
   const Grid& g = m->gr;
   TRY(build_coarse(m));
+  if (m->opt.autotune && !m->tuned && m->opt.precision == AFD_MIXED) TRY(autotune_stencil(m));
   if (!warm_start || !m->has_solution) CK(cudaMemsetAsync(m->u64, 0, (size_t)R * g.vs * sizeof(double), m->s));
   std::vector<int> iters(R, 0), status(R, AFD_OK), refine(R, 0);
   std::vector<double> rel;
@@ -1132,6 +1186,8 @@ int afd_deflation_w(afd_mesh* m, int n_rhs, const double* y, double* out) {
 int afd_coarse_size(afd_mesh* m) { return m ? m->nc : 0; }
 
 int64_t afd_kernel_launches(const afd_mesh* m) { return m ? m->launches : 0; }
+
+int afd_stencil_depth(const afd_mesh* m) { return m ? m->kz : 0; }
 
 int afd_time_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y, int launches, double* ms_out) {
   if (!m || !u || !y || !ms_out || launches < 1 || n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "bad argument");
