@@ -195,6 +195,44 @@ int64_t afd_nelem(const afd_mesh* m);
 void afd_destroy(afd_mesh* m);
 const char* afd_last_error(void);
 
+/* ---- serving: solve requests of different mesh sizes concurrently ---- */
+
+/* Upper bound of the device bytes a mesh of this size holds after a solve
+ * with n_rhs load cases (host only; used for admission). */
+size_t afd_mesh_bytes(int nx, int ny, int nz, int n_rhs, const afd_options* opt);
+
+typedef struct afd_server afd_server;
+
+typedef struct {
+  int max_slots;         /* requests in flight at once (worker threads, one CUDA stream each) */
+  double budget_bytes;   /* device memory the in-flight and cached meshes may hold */
+  afd_options opt;       /* options of every mesh the server creates */
+} afd_server_config;
+
+/* Start a server on the current device.  Requests are admitted in arrival
+ * order as slots and budget free up (continuous batching: a request that
+ * arrives while others are on the GPU starts as soon as one of them finishes
+ * and leaves room); their kernels overlap on the device through the slots'
+ * streams.  Each slot keeps its last mesh (moduli, vectors, coarse inverse)
+ * and reuses it for a request of the same size. */
+int afd_server_create(const afd_server_config* cfg, afd_server** out);
+
+/* Queue one solve of K u = f (one load case) on an nx*ny*nz mesh: E
+ * (nelem), f (ndof) and the fixed-DOF mask (ndof) are host arrays copied by
+ * the call.  *id_out identifies the request.  AFD_ERR_OOM if the mesh alone
+ * exceeds the budget. */
+int afd_server_submit(afd_server* s, int nx, int ny, int nz, const double* E, const double* f,
+                      const uint8_t* fixed_dof_mask, double rel_tol, int64_t* id_out);
+
+/* Wait for request id and collect its result: stats, compliance J = f^T u,
+ * latency from submit to completion (ms), and the displacement (u_out,
+ * nullable host array of ndof).  Returns the solve's status code. */
+int afd_server_wait(afd_server* s, int64_t id, afd_stats* stats, double* J_out, double* latency_ms,
+                    double* u_out);
+
+/* Stop the workers after the queued requests and free every mesh. */
+void afd_server_destroy(afd_server* s);
+
 /* ---- augmented-Lagrangian scalars (Eqs. 3.11, 3.12, 3.18), host only ---- */
 typedef struct {
   double mu;     /* multiplier, starts at 100 (Sec. 3.8 step 1) */

@@ -40,6 +40,7 @@ EXPORTS = [
     "afd_deflation_wt", "afd_deflation_w", "afd_coarse_size", "afd_coarse_matrix", "afd_select_topk",
     "afd_ndof", "afd_nelem", "afd_destroy", "afd_last_error", "afd_al_init", "afd_al_update", "afd_al_weight",
     "afd_time_stiffness", "afd_kernel_launches", "afd_select_topk_noalloc", "afd_stencil_depth",
+    "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
 ]
 
 
@@ -56,6 +57,10 @@ class afd_stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class afd_server_config(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("budget_bytes", ctypes.c_double), ("opt", afd_options)]
 
 
 class afd_al_state(ctypes.Structure):
@@ -107,6 +112,11 @@ def lib() -> ctypes.CDLL:
             "afd_kernel_launches": (i64, [vp]),
             "afd_select_topk_noalloc": (i, [vp, i64, i64, vp, ctypes.POINTER(ctypes.c_float), vp]),
             "afd_stencil_depth": (i, [vp]),
+            "afd_mesh_bytes": (ctypes.c_size_t, [i, i, i, i, ctypes.POINTER(afd_options)]),
+            "afd_server_create": (i, [ctypes.POINTER(afd_server_config), ctypes.POINTER(vp)]),
+            "afd_server_submit": (i, [vp, i, i, i, vp, vp, vp, d, ctypes.POINTER(i64)]),
+            "afd_server_wait": (i, [vp, i64, ctypes.POINTER(afd_stats), ctypes.POINTER(d), ctypes.POINTER(d), vp]),
+            "afd_server_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -298,6 +308,59 @@ def afd_select_topk_noalloc(keys, k: int, kept, stream=None, n: Optional[int] = 
     count = n if n is not None else int(keys.numel() if hasattr(keys, "numel") else len(keys))
     _check(lib().afd_select_topk_noalloc(pk, count, int(k), po, ctypes.byref(tau), s))
     return tau.value
+
+
+def afd_mesh_bytes(nx: int, ny: int, nz: int, n_rhs: int = 1, options: Optional[afd_options] = None) -> int:
+    return int(lib().afd_mesh_bytes(nx, ny, nz, n_rhs, ctypes.byref(options) if options is not None else None))
+
+
+class Server:
+    """Serving loop (afd_server_*): requests of different mesh sizes admitted
+    continuously under a device-memory budget, solved concurrently in
+    max_slots slots.  submit() copies the host inputs; wait() returns
+    (status, stats, J, latency_ms, u)."""
+
+    def __init__(self, max_slots: int = 4, budget_bytes: float = 60e9, precision: int = AFD_MIXED, **opts):
+        cfg = afd_server_config()
+        cfg.max_slots, cfg.budget_bytes = max_slots, float(budget_bytes)
+        cfg.opt = afd_default_options()
+        cfg.opt.precision = precision
+        for k, v in opts.items():
+            setattr(cfg.opt, k, v)
+        self.cfg = cfg
+        self.h = ctypes.c_void_p()
+        _check(lib().afd_server_create(ctypes.byref(cfg), ctypes.byref(self.h)))
+        self.sizes = {}
+
+    def submit(self, nx: int, ny: int, nz: int, E, f, fixed, rel_tol: float) -> int:
+        pE, _, k1 = _arr(E, np.float64)
+        pf, _, k2 = _arr(np.asarray(f).reshape(-1), np.float64)
+        pm, _, k3 = _arr(fixed, np.uint8)
+        rid = ctypes.c_int64()
+        _check(lib().afd_server_submit(self.h, nx, ny, nz, pE, pf, pm, rel_tol, ctypes.byref(rid)))
+        self.sizes[rid.value] = 3 * (nx + 1) * (ny + 1) * (nz + 1)
+        return rid.value
+
+    def wait(self, rid: int, want_u: bool = True):
+        st = afd_stats()
+        J = ctypes.c_double()
+        lat = ctypes.c_double()
+        n = self.sizes.pop(rid)
+        u = np.zeros(n) if want_u else None
+        rc = lib().afd_server_wait(self.h, rid, ctypes.byref(st), ctypes.byref(J), ctypes.byref(lat),
+                                   ctypes.c_void_p(u.ctypes.data) if want_u else None)
+        return rc, st.as_dict(), J.value, lat.value, u
+
+    def close(self):
+        if self.h:
+            lib().afd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def afd_al_init() -> afd_al_state:

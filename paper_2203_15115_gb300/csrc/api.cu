@@ -1189,6 +1189,30 @@ int64_t afd_kernel_launches(const afd_mesh* m) { return m ? m->launches : 0; }
 
 int afd_stencil_depth(const afd_mesh* m) { return m ? m->kz : 0; }
 
+size_t afd_mesh_bytes(int nx, int ny, int nz, int n_rhs, const afd_options* opt) {
+  afd_options o;
+  afd_default_options(&o);
+  if (opt) o = *opt;
+  if (nx < 1 || ny < 1 || nz < 1 || n_rhs < 1) return 0;
+  const size_t ne = (size_t)nx * ny * nz;
+  const size_t nn = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+  const size_t vs = (3 * nn + 3) / 4 * 4;
+  const int g = pick_group(nx, ny, nz, o.group);
+  const size_t ng = (size_t)std::max(nx / g, 1) * std::max(ny / g, 1) * std::max(nz / g, 1);
+  const size_t nc = 6 * ng;
+  const bool f64 = o.precision == AFD_FP64;
+  const size_t tsz = f64 ? 8 : 4;
+  size_t b = 0;
+  b += ne * (8 + 4 + 8) + ne * (4 * (size_t)n_rhs + 4 + 1);        // moduli, fields, keys, kept
+  b += nn * (1 + 4 + 8) + vs * (4 + 8);                             // mask, Jacobi factors
+  b += (size_t)n_rhs * vs * (3 * 8 + 8 * tsz);                      // f, u, r (FP64) + Krylov work
+  b += nc * nc * (8 + tsz) + nc * GJ_NB * 2 * 8 + GJ_NB * GJ_NB * 8; // coarse matrix, inverse, sweep scratch
+  const size_t box = (size_t)(g + 3) * (g + 3) * (g + 3);
+  b += ng * box * (18 * tsz + 4);                                   // K W on group shells (upper bound)
+  b += (size_t)n_rhs * (nc * 4 * 8 + ng * 64 * 12 * 8) + 64 * 1024 * 1024 / 8;  // coarse vectors, partials
+  return b + b / 10;
+}
+
 int afd_time_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y, int launches, double* ms_out) {
   if (!m || !u || !y || !ms_out || launches < 1 || n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "bad argument");
   if (!m->has_moduli) return fail(AFD_ERR_STATE, "moduli not set");

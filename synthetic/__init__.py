@@ -92,17 +92,28 @@ def void_fraction_spheres(nx: int, ny: int, nz: int, target: float, rng: np.rand
                           rmin: float = 4.0, rmax: float = 10.0, e_void: float = 1e-3,
                           e_solid: float = 1.0, max_spheres: int = 10000) -> np.ndarray:
     """Add radius-U[rmin,rmax] spheres at uniform centres until the void volume
-    fraction reaches ``target``."""
-    cx, cy, cz = _centroids(nx, ny, nz)
-    void = np.zeros(cx.shape, dtype=bool)
+    fraction reaches ``target`` (each sphere marks the elements whose centroid
+    lies inside it; only its bounding box is visited)."""
+    void = np.zeros((nz, ny, nx), dtype=bool)
     n = void.size
+    count = 0
     for _ in range(max_spheres):
-        if void.sum() >= target * n:
+        if count >= target * n:
             break
         x0, y0, z0 = rng.uniform([0, 0, 0], [nx, ny, nz])
         r = rng.uniform(rmin, rmax)
-        void |= (cx - x0) ** 2 + (cy - y0) ** 2 + (cz - z0) ** 2 < r * r
-    return np.where(void, e_void, e_solid).astype(np.float64)
+        i0, i1 = max(int(np.floor(x0 - r)), 0), min(int(np.ceil(x0 + r)) + 1, nx)
+        j0, j1 = max(int(np.floor(y0 - r)), 0), min(int(np.ceil(y0 + r)) + 1, ny)
+        k0, k1 = max(int(np.floor(z0 - r)), 0), min(int(np.ceil(z0 + r)) + 1, nz)
+        if i0 >= i1 or j0 >= j1 or k0 >= k1:
+            continue
+        cz, cy, cx = np.meshgrid(np.arange(k0, k1) + 0.5, np.arange(j0, j1) + 0.5, np.arange(i0, i1) + 0.5,
+                                 indexing="ij")
+        inside = (cx - x0) ** 2 + (cy - y0) ** 2 + (cz - z0) ** 2 < r * r
+        box = void[k0:k1, j0:j1, i0:i1]
+        count += int(np.count_nonzero(inside & ~box))
+        box |= inside
+    return np.where(void.reshape(-1), e_void, e_solid).astype(np.float64)
 
 
 def top_point_loads(nx: int, ny: int, nz: int, n_rhs: int, seed: int) -> np.ndarray:

@@ -54,3 +54,13 @@ def test_al_scalars_match_oracle(afd):
         g_old = g
         assert s.mu == mu and s.gamma == gamma and s.k == k
         assert afd.afd_al_weight(s) == levelset.al_weight(mu, gamma, g)
+
+
+def test_mesh_bytes_estimate_grows_with_the_mesh(afd):
+    a = afd.afd_mesh_bytes(32, 16, 16)
+    b = afd.afd_mesh_bytes(64, 32, 32)
+    c = afd.afd_mesh_bytes(64, 32, 32, 8)
+    ndof = 3 * 65 * 33 * 33
+    assert 0 < a < b < c
+    assert b > ndof * (3 * 8 + 8 * 4)       # at least the FP64 and FP32 vectors
+    assert afd.afd_mesh_bytes(0, 1, 1) == 0
