@@ -16,10 +16,19 @@ finished), an L2 flush (write of 512 MB) between timed steps, max over ranks.
 (host-to-device copies of the moduli and loads, device-to-host copies of u,
 J and the field inside the timed region).
 
+Two more legs run at N = 1 after the timed steps: "batched" (the 96x48x48
+mesh with 8 load cases in one multi-RHS solve, against one case at a time and
+against the FP64 path) and "serve" (256 requests of mixed mesh sizes through
+the serving loop under a 60 GB budget: saturated solves/s, and p50/p99 latency
+at 0.8 x that rate).  `cpu_baseline` times the CPU oracle on a bounded sample.
+
     python bench.py [--steps K] [--warmup W] [--impl ours|reference]
+                    [--no-serve] [--no-batched] [--no-cpu-baseline]
 
 Under torchrun (N > 1) every rank solves its own replica (independent
-problems, no collective on the data path): weak scaling.
+problems, no collective on the data path): weak scaling.  `ms_per_step` is
+the slowest rank's time per step; `value` is the whole job's time per step,
+that time divided by N.
 """
 from __future__ import annotations
 
@@ -38,6 +47,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "dCG solve ms & GDOF/s matvec at rel-res 1e-6, mixed vs FP64 on GB300; serve p50/p99"
 VOLUME_FRACTION = 0.9
+UNIT = "ms per topology step (dCG solve to rel-res 1e-6 + coarse setup + J + sensitivity + level-set)"
 
 
 def rank_info():
@@ -157,11 +167,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = (afd.afd_kernel_launches(mesh.h) - l0) // max(1, args.steps)
     clk = clocks.stop()
-    ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(times)), world, dev)
+    value = whole_job_ms_per_step(ms, world)
 
     # stencil roofline: FP32 matvec on the solver's stream, same launch geometry
     u32 = torch.randn((1, mesh.ndof), dtype=torch.float32, device=dev)
@@ -226,8 +233,8 @@ def run_ours(args):
 
     out = {
         "metric": METRIC,
-        "value": round(ms, 4),
-        "unit": "ms per topology step (mixed dCG solve to rel-res 1e-6 + coarse setup + J + sensitivity + level-set)",
+        "value": round(value, 4),
+        "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
@@ -239,6 +246,7 @@ def run_ours(args):
         "data": "synthetic (seeded spherical voids)",
         "config": {"workload": w.name, "elements": ne, "dofs": 3 * nn, "group": mesh.options.group or "auto",
                    "stencil_planes_per_cta": afd.afd_stencil_depth(mesh.h),
+                   "stencil_warps_per_cta": afd.afd_stencil_warps(mesh.h),
                    "tol": w.tol, "volume_fraction": VOLUME_FRACTION, "l2": "flushed (512 MB write) between timed steps",
                    "parallelism": f"replicas x{world}"},
         "solve": {"mixed_ms": round(float(np.median(solve_ms)), 3), "fp64_ms": round(float(np.median(fp64)), 3),
@@ -248,7 +256,7 @@ def run_ours(args):
                   "speedup_mixed_vs_fp64": round(float(np.median(fp64)) / float(np.median(solve_ms)), 3)},
         "matvec": {"f32_ms": round(mv_ms, 5), "f32_gdofs": round(3 * nn / (mv_ms * 1e-3) / 1e9, 3),
                    "f64_ms": round(mv64_ms, 5), "f64_gdofs": round(3 * nn / (mv64_ms * 1e-3) / 1e9, 3)},
-        "roofline": {"kernel": "stencil_kernel<float,32,8> (K u, FP32)", "bound": "hbm",
+        "roofline": {"kernel": "stencil2_kernel<TY,ST_APPLY> (K u, FP32, packed float2)", "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "peak_source": peak_kind, "bytes_per_launch": bytes32},
@@ -258,81 +266,261 @@ def run_ours(args):
         "clocks": clk,
         "last_step": {k: v for k, v in last.items() if k != "stats"},
     }
-    if rank == 0 and args.cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w)
     mesh.close()
+    if world == 1 and args.batched:
+        out["batched"] = batched_leg(afd, torch, dev, flush)
+    if world == 1 and args.serve:
+        del flush
+        torch.cuda.empty_cache()
+        out["serve"] = serve_leg(afd)
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w)
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def cpu_baseline(w, budget_s: float = 15.0):
-    """The oracle as it stands on the host cores, on a bounded sample: CSR
-    assembly plus as many plain Jacobi-PCG iterations as fit in the budget;
-    scaled to a full solve by the oracle's own iteration count for this
-    workload (oracle/reference_iterations.json)."""
-    from oracle import fe
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value over all ranks: a job's step time is its slowest
+    rank's.  Works on any process group (NCCL with a device, gloo on CPU)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
 
-    cores = len(os.sched_getaffinity(0))
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_ms_per_step(ms_max: float, world: int) -> float:
+    """Replicas: every rank completes one step per ms_max, so the whole job
+    completes `world` steps in that time."""
+    return ms_max / max(world, 1)
+
+
+def percentile(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def serve_leg(afd, n_requests: int = 256, slots: int = 8, budget: float = 60e9, tol: float = 1e-6):
+    """The serving stream (meshes nx x nx/2 x nx/2, nx in {32,...,160}, 10-40 %
+    seeded voids, cantilever loads) through the library's serving loop under a
+    60 GB device budget.  A burst (all requests at t = 0) gives the saturated
+    solves/s; the stream's Poisson arrivals, rescaled to 0.8 x that rate, give
+    the latency percentiles.  Latency = submit to completion, measured by the
+    server.  Inputs are generated before the timed region."""
+    from synthetic import serving_request_inputs, serving_stream
+
+    reqs = serving_stream(n_requests, rate_per_s=50.0)
+    inputs = [serving_request_inputs(r) for r in reqs]
+    srv = afd.Server(max_slots=slots, budget_bytes=budget)
+    first = {}
+    for r, x in zip(reqs, inputs):
+        first.setdefault(r["nx"], (r, x))
+    warm = [srv.submit(r["nx"], r["ny"], r["nz"], x[0], x[1], x[2], tol) for r, x in first.values()]
+    for rid in warm:
+        srv.wait(rid, want_u=False)
+
+    def run(scale):
+        t0 = time.perf_counter()
+        ids = []
+        for r, (E, f, fx) in zip(reqs, inputs):
+            if scale is not None:
+                dt = t0 + r["arrival_s"] * scale - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            ids.append(srv.submit(r["nx"], r["ny"], r["nz"], E, f, fx, tol))
+        lat, failed, worst = [], 0, 0.0
+        for rid in ids:
+            rc, st, J, l, _ = srv.wait(rid, want_u=False)
+            if rc != afd.AFD_OK or not (st["rel_residual"] <= tol):
+                failed += 1
+            worst = max(worst, st["rel_residual"])
+            lat.append(l)
+        wall = time.perf_counter() - t0
+        return {"requests": len(ids), "wall_s": round(wall, 3), "solves_per_s": round(len(ids) / wall, 2),
+                "p50_ms": round(percentile(lat, 50), 2), "p99_ms": round(percentile(lat, 99), 2),
+                "failed": failed, "max_rel_residual": worst}
+
+    burst = run(None)
+    rate = 0.8 * burst["solves_per_s"]
+    poisson = run(50.0 / rate)
+    poisson["offered_rate_per_s"] = round(rate, 2)
+    srv.close()
+    dofs = [3 * (r["nx"] + 1) * (r["ny"] + 1) * (r["nz"] + 1) for r in reqs]
+    return {"slots": slots, "budget_gb": budget / 1e9, "tol": tol, "mean_dofs": int(np.mean(dofs)),
+            "burst": burst, "poisson_0.8x": poisson}
+
+
+def batched_leg(afd, torch, dev, flush, reps: int = 3):
+    """The 96x48x48 multi-load workload: 8 load cases in one multi-RHS solve
+    (coarse set-up, mixed dCG to 1e-6, compliance, von Mises and topological
+    compliance fields for all 8) against 8 one-RHS solves and against the
+    pure-FP64 batched solve."""
+    from synthetic import multiload_96x48x48_voids
+
+    w = multiload_96x48x48_voids()
+    ne = w.nx * w.ny * w.nz
+    E_d = torch.from_numpy(w.E).to(dev)
+    f_d = torch.from_numpy(w.f).to(dev)
+    m_d = torch.from_numpy(w.fixed).to(dev)
+    s_d = torch.empty((w.n_rhs, ne), dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        fn()
+        out = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            out.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(out)), r
+
+    res = {}
+    for name, prec in (("mixed", afd.AFD_MIXED), ("fp64", afd.AFD_FP64)):
+        m = afd.Mesh(w.nx, w.ny, w.nz, precision=prec, group=w.group)
+        m.set_loads_bcs(f_d, m_d)
+
+        def step():
+            m.set_element_moduli(E_d)
+            st = m.solve(w.tol)
+            m.compliance()
+            m.sensitivity(afd.AFD_SENS_VON_MISES, s_d)
+            m.sensitivity(afd.AFD_SENS_TJ, s_d)
+            return st
+
+        ms, st = timed(step)
+        res[name] = {"ms": round(ms, 3), "max_iters": max(x["iters"] for x in st),
+                     "max_rel_residual": max(x["rel_residual"] for x in st)}
+        m.close()
+    m1 = afd.Mesh(w.nx, w.ny, w.nz, precision=afd.AFD_MIXED, group=w.group)
+
+    def one_by_one():
+        for r in range(w.n_rhs):
+            m1.set_loads_bcs(f_d[r:r + 1], m_d)
+            m1.set_element_moduli(E_d)
+            m1.solve(w.tol)
+            m1.compliance()
+            m1.sensitivity(afd.AFD_SENS_VON_MISES, s_d[r:r + 1])
+            m1.sensitivity(afd.AFD_SENS_TJ, s_d[r:r + 1])
+
+    ms1, _ = timed(one_by_one)
+    m1.close()
+    res["mixed_one_rhs_at_a_time"] = {"ms": round(ms1, 3)}
+    res["batched_speedup_vs_one_at_a_time"] = round(ms1 / res["mixed"]["ms"], 3)
+    res["mixed_speedup_vs_fp64"] = round(res["fp64"]["ms"] / res["mixed"]["ms"], 3)
+    return {"workload": w.name, "n_rhs": w.n_rhs, "elements": ne, **res}
+
+
+def oracle_step_sample(w, budget_s: float = 8.0):
+    """One topology step of the oracle as it stands, on a bounded sample of the
+    workload: CSR assembly, the set-up and a bounded number of iterations of
+    its plain Jacobi-PCG (``fe.solve_pcg`` at two iteration caps gives the
+    set-up and per-iteration cost), compliance, the strain-energy field and
+    the level-set selection.  The solve is scaled to a full one by the
+    oracle's own iteration count for this workload
+    (oracle/reference_iterations.json).  Returns (ms per step or None, note)."""
+    from oracle import fe, levelset, sensitivity
+
     t0 = time.perf_counter()
     K = fe.assemble(w.nx, w.ny, w.nz, w.E)
     t_asm = time.perf_counter() - t0
-    fr = fe.free_dofs(w.fixed)
-    A = K[fr][:, fr].tocsr()
-    b = w.f[0][fr]
-    dinv = 1.0 / A.diagonal()
-    x = np.zeros_like(b)
-    r = b.copy()
-    z = dinv * r
-    p = z.copy()
-    rz = r @ z
-    t1 = time.perf_counter()
-    it = 0
-    while time.perf_counter() - t1 < budget_s:
-        q = A @ p
-        a = rz / (p @ q)
-        x += a * p
-        r -= a * q
-        z = dinv * r
-        rzn = r @ z
-        p = z + (rzn / rz) * p
-        rz = rzn
-        it += 1
-    per_it = (time.perf_counter() - t1) / max(it, 1)
+    f = w.f[0]
+    m1 = 4
+    t0 = time.perf_counter()
+    fe.solve_pcg(K, f, w.fixed, rtol=w.tol, maxiter=m1)
+    t1 = time.perf_counter() - t0
+    # second cap sized from a rough per-iteration guess so the sample stays within budget_s
+    guess = max(t1 / (m1 + 4), 1e-4)
+    m2 = m1 + max(8, int(0.8 * budget_s / guess))
+    t0 = time.perf_counter()
+    u, _ = fe.solve_pcg(K, f, w.fixed, rtol=w.tol, maxiter=m2)
+    t2 = time.perf_counter() - t0
+    per_it = max(t2 - t1, 1e-9) / (m2 - m1)
+    setup = max(t1 - m1 * per_it, 0.0)
+    t0 = time.perf_counter()
+    fe.compliance(f, u)
+    s = sensitivity.strain_energy(w.nx, w.ny, w.nz, w.E, u)
+    kept, _ = levelset.select_top(s, levelset.keep_count(VOLUME_FRACTION, s.size))
+    levelset.apply_topology(kept, w.e_void)
+    t_post = time.perf_counter() - t0
     ref = os.path.join(ROOT, "oracle", "reference_iterations.json")
-    n_it = None
-    if os.path.exists(ref):
-        n_it = json.load(open(ref)).get(w.name, {}).get("iterations")
+    n_it = json.load(open(ref)).get(w.name, {}).get("iterations") if os.path.exists(ref) else None
+    note = (f"{w.name}: CSR assembly {t_asm:.1f} s, PCG set-up {setup:.1f} s, {m2} Jacobi-PCG iterations "
+            f"({per_it * 1e3:.1f} ms each), J + strain energy + selection {t_post:.1f} s")
     if n_it is None:
-        return {"value": None, "unit": "ms", "cores": cores, "kind": "oracle",
-                "sample": f"assembly {t_asm:.1f} s + {it} PCG iterations at {per_it*1e3:.1f} ms; no stored count"}
-    total_ms = (t_asm + per_it * n_it) * 1e3
-    return {"value": round(total_ms, 1), "unit": "ms per solve (oracle FP64 Jacobi-PCG to 1e-6)", "cores": cores,
-            "kind": "oracle",
-            "sample": f"{w.name}: CSR assembly {t_asm:.1f} s + {it} Jacobi-PCG iterations in {budget_s:.0f} s "
-                      f"({per_it*1e3:.1f} ms each), scaled to the oracle's {n_it} iterations to 1e-6"}
+        return None, note + "; no stored iteration count"
+    return (t_asm + setup + per_it * n_it + t_post) * 1e3, note + f"; solve scaled to the oracle's {n_it} iterations to {w.tol:g}"
+
+
+def cpu_baseline(w, budget_s: float = 8.0):
+    """The oracle timed on the host cores on a bounded sample (rank 0, N = 1)."""
+    cores = len(os.sched_getaffinity(0))
+    v, note = oracle_step_sample(w, budget_s)
+    return {"value": None if v is None else round(v, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": note}
 
 
 def run_reference(args):
-    """The reference arm: the CPU oracle as it stands, one bounded sample per step."""
+    """The reference arm: the CPU oracle as it stands, one bounded sample of the
+    workload per step, on rank 0 only."""
     rank, world, _ = rank_info()
     if rank != 0:
         return
     from synthetic import cantilever_128x64x64_voids
 
     w = cantilever_128x64x64_voids()
-    vals = []
+    vals, note = [], ""
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(w, budget_s=10.0)
-        if i >= args.warmup:
-            vals.append(cb["value"])
-    v = float(np.median([x for x in vals if x is not None])) if any(x is not None for x in vals) else None
-    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": cb["unit"], "n_gpus": world,
+        v, note = oracle_step_sample(w, budget_s=4.0)
+        if i >= args.warmup and v is not None:
+            vals.append(v)
+    v = round(float(np.median(vals)), 1) if vals else None
+    cores = len(os.sched_getaffinity(0))
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
-                      "config": {"workload": w.name}, "cpu_baseline": cb,
-                      "e2e": {"value": v, "unit": cb["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded spherical voids)",
+                      "config": {"workload": w.name},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": note},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
           flush=True)
+
+
+def launch_summary(path: str):
+    """Per-kernel launches, total time and share from an ncu launch list
+    (``--metrics gpu__time_duration.sum --csv``) of ``bench.py --steps 1``:
+    the launches of the one timed step, i.e. those after the first L2-flush
+    fill (torch's fill kernel) up to the next torch kernel."""
+    import csv
+
+    rows = []
+    with open(path) as fh:
+        lines = [ln for ln in fh if ln.startswith('"')]
+    for d in csv.DictReader(lines):
+        if d.get("Metric Name") != "gpu__time_duration.sum":
+            continue
+        v = float(d["Metric Value"].replace(",", ""))
+        unit = d.get("Metric Unit", "ns")
+        scale = {"ns": 1e-3, "usecond": 1.0, "us": 1.0, "msecond": 1e3, "ms": 1e3, "nsecond": 1e-3}.get(unit, 1e-3)
+        rows.append((d["Kernel Name"], v * scale))
+    torch_k = lambda n: "at::" in n or "elementwise" in n or "FillFunctor" in n
+    start = next((i for i, (n, _) in enumerate(rows) if torch_k(n)), -1)
+    end = next((i for i in range(start + 1, len(rows)) if torch_k(rows[i][0])), len(rows))
+    step = rows[start + 1:end]
+    agg = {}
+    for n, us in step:
+        short = n.split("(")[0].replace("void ", "")
+        c, t = agg.get(short, (0, 0.0))
+        agg[short] = (c + 1, t + us)
+    total = sum(t for _, t in agg.values())
+    print(f"launches in the timed step: {len(step)}, total device time {total:.1f} us (serialised, cold)")
+    print(f"{'kernel':60s} {'launches':>8s} {'total us':>10s} {'share':>7s}")
+    for k, (c, t) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        print(f"{k[:60]:60s} {c:8d} {t:10.1f} {t / total:7.1%}")
 
 
 def profile_stencil(n: int, launches: int):
@@ -361,10 +549,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-serve", dest="serve", action="store_false", help="skip the serving-stream leg")
+    ap.add_argument("--no-batched", dest="batched", action="store_false", help="skip the 8-load-case leg")
     ap.add_argument("--profile-stencil", type=int, default=0, metavar="NX",
                     help="only time the FP32 stencil on an NX x NX/2 x NX/2 mesh (for ncu)")
+    ap.add_argument("--launch-summary", metavar="CSV", help="summarise an ncu launch list of one timed step")
     args = ap.parse_args()
-    if args.profile_stencil:
+    if args.launch_summary:
+        launch_summary(args.launch_summary)
+    elif args.profile_stencil:
         profile_stencil(args.profile_stencil, max(1, args.steps))
     elif args.impl == "reference":
         run_reference(args)
