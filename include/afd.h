@@ -184,9 +184,13 @@ int afd_time_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y
  * counts its kernel nodes). */
 int64_t afd_kernel_launches(const afd_mesh* m);
 
-/* Node planes per CTA of the stiffness kernel (chosen by the autotuner at the
- * first solve when opt.autotune is set, else by a size heuristic). */
+/* Node planes per CTA of the FP32 stiffness kernel (chosen by the autotuner at
+ * the first mixed solve when opt.autotune is set, else by a size heuristic). */
 int afd_stencil_depth(const afd_mesh* m);
+
+/* Warps per CTA of the FP32 stiffness kernel (8 or 16; each warp owns two node
+ * rows, a CTA finishes 2 * warps - 2 of them); chosen with the depth. */
+int afd_stencil_warps(const afd_mesh* m);
 
 /* Sizes of the mesh. */
 int64_t afd_ndof(const afd_mesh* m);

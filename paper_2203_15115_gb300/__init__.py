@@ -40,6 +40,7 @@ EXPORTS = [
     "afd_deflation_wt", "afd_deflation_w", "afd_coarse_size", "afd_coarse_matrix", "afd_select_topk",
     "afd_ndof", "afd_nelem", "afd_destroy", "afd_last_error", "afd_al_init", "afd_al_update", "afd_al_weight",
     "afd_time_stiffness", "afd_kernel_launches", "afd_select_topk_noalloc", "afd_stencil_depth",
+    "afd_stencil_warps",
     "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
 ]
 
@@ -112,6 +113,7 @@ def lib() -> ctypes.CDLL:
             "afd_kernel_launches": (i64, [vp]),
             "afd_select_topk_noalloc": (i, [vp, i64, i64, vp, ctypes.POINTER(ctypes.c_float), vp]),
             "afd_stencil_depth": (i, [vp]),
+            "afd_stencil_warps": (i, [vp]),
             "afd_mesh_bytes": (ctypes.c_size_t, [i, i, i, i, ctypes.POINTER(afd_options)]),
             "afd_server_create": (i, [ctypes.POINTER(afd_server_config), ctypes.POINTER(vp)]),
             "afd_server_submit": (i, [vp, i, i, i, vp, vp, vp, d, ctypes.POINTER(i64)]),
@@ -292,6 +294,10 @@ def afd_time_stiffness(mesh, arith: int, n_rhs: int, u, y, launches: int) -> flo
 
 def afd_stencil_depth(mesh) -> int:
     return int(lib().afd_stencil_depth(mesh))
+
+
+def afd_stencil_warps(mesh) -> int:
+    return int(lib().afd_stencil_warps(mesh))
 
 
 def afd_kernel_launches(mesh) -> int:

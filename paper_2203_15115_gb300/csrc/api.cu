@@ -15,6 +15,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/afd.h"
@@ -24,6 +25,7 @@
 #include "levelset.cuh"
 #include "sens.cuh"
 #include "stencil.cuh"
+#include "stencil2.cuh"
 
 using namespace afd;
 
@@ -94,8 +96,9 @@ struct afd_mesh {
   int device = 0;
   cudaStream_t user = nullptr, s = nullptr;
   cudaEvent_t ev = nullptr;
-  int kz = 8;
-  bool tuned = false;          // autotuner has chosen kz for this mesh
+  int kz = 8;                  // node planes per CTA of the FP64 stencil
+  int kz32 = 8, ty32 = 16;     // planes per CTA and warps per CTA of the FP32 stencil
+  bool tuned = false;          // autotuner has chosen kz32 / ty32 for this mesh
   // state
   double* E64 = nullptr;
   uint8_t* fixed = nullptr;   // per node bits
@@ -199,13 +202,20 @@ static int ensure_partials(afd_mesh* m, size_t n) {
   return AFD_OK;
 }
 
-constexpr int TY32 = 16, TY64 = 8;  // warps per stencil CTA for FP32 / FP64
+constexpr int TY64 = 8;  // warps per FP64 stencil CTA; the FP32 stencil takes m->ty32 (8 or 16)
+
+static void geom32(const Grid& g, int ty, int kz, int& tiles_x, dim3& grid) {
+  if (ty == 8)
+    StencilGeom2<8>::get(g, kz, tiles_x, grid);
+  else
+    StencilGeom2<16>::get(g, kz, tiles_x, grid);
+}
 
 static void stencil_geom(const afd_mesh* m, bool f64, int& tiles_x, dim3& grid) {
   if (f64)
     StencilGeom<TY64>::get(m->gr, m->kz, tiles_x, grid);
   else
-    StencilGeom<TY32>::get(m->gr, m->kz, tiles_x, grid);
+    geom32(m->gr, m->ty32, m->kz32, tiles_x, grid);
 }
 
 static int stencil_blocks(const afd_mesh* m, bool f64) {
@@ -221,7 +231,6 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
                           unsigned int* counter = nullptr, const T* z = nullptr, const double* mu = nullptr,
                           T* pout = nullptr) {
   constexpr bool F64 = sizeof(T) == 8;
-  constexpr int TY = F64 ? TY64 : TY32;
   StencilArgs<T, TF> a;
   a.gr = m->gr;
   a.u = u;
@@ -233,7 +242,7 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
   a.y32 = y32;
   a.partials = partials;
   a.done = done;
-  a.kz = m->kz;
+  a.kz = F64 ? m->kz : m->kz32;
   a.st = st;
   a.counter = counter;
   a.z = z;
@@ -241,9 +250,20 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
   a.pout = pout;
   a.gp = m->gp;
   dim3 grid;
-  StencilGeom<TY>::get(m->gr, m->kz, a.tiles_x, grid);
+  stencil_geom(m, F64, a.tiles_x, grid);
   grid.z = nrhs;
-  stencil_kernel<T, TY, MODE, TF><<<grid, ST_TX * TY, 0, m->s>>>(a); m->launches++;
+  if constexpr (F64) {
+    stencil_kernel<T, TY64, MODE, TF><<<grid, ST_TX * TY64, 0, m->s>>>(a);
+  } else {
+    static_assert(std::is_same<TF, float>::value, "the FP32 stencil takes FP32 right-hand sides");
+    // the packed FP32 kernel forms p in ST_APPLY_DOT only, and always there
+    if ((MODE == ST_APPLY_DOT) != (z != nullptr)) return fail(AFD_ERR_INVALID_ARG, "stencil mode / z mismatch");
+    if (m->ty32 == 8)
+      stencil2_kernel<8, MODE><<<grid, ST_TX * 8, 0, m->s>>>(a);
+    else
+      stencil2_kernel<16, MODE><<<grid, ST_TX * 16, 0, m->s>>>(a);
+  }
+  m->launches++;
   CK(cudaGetLastError());
   return AFD_OK;
 }
@@ -381,53 +401,56 @@ static int build_coarse(afd_mesh* m) {
   return AFD_OK;
 }
 
-// Stencil autotuner: the z depth of the column-marching CTAs trades
-// redundant element layers ((kz+1)/kz) against the number of CTAs (waves over
-// the SMs).  Each candidate is timed on the solver's FP32 kernel and stream
-// with CUDA events (3 launches after one warm-up); the fastest is kept for
-// the mesh.
+// Stencil autotuner: the FP32 stencil's CTA shape (8 or 16 warps, i.e. 14 or
+// 30 finished node rows) and z depth trade redundant halo rows and element
+// layers against the number of CTAs (waves over the SMs).  Each candidate is
+// timed on the solver's FP32 kernel and stream with CUDA events (3 launches
+// after one warm-up); the fastest is kept for the mesh.
 static int autotune_stencil(afd_mesh* m) {
   TRY(ensure_work(m, m->w32, 1));
   const Grid& g = m->gr;
-  static const int cand[] = {2, 3, 4, 5, 6, 8, 12, 16, 24, 32};
+  static const int cand_kz[] = {2, 3, 4, 5, 6, 8, 12, 16, 24, 32};
+  static const int cand_ty[] = {8, 16};
   size_t maxp = 0;
-  for (int kz : cand) {
-    if (kz > g.nnz && kz != cand[0]) continue;
-    int tx;
-    dim3 gr;
-    StencilGeom<TY32>::get(g, kz, tx, gr);
-    maxp = std::max(maxp, (size_t)gr.x * gr.y);
-    StencilGeom<TY64>::get(g, kz, tx, gr);
-    maxp = std::max(maxp, (size_t)gr.x * gr.y);
-  }
+  for (int ty : cand_ty)
+    for (int kz : cand_kz) {
+      int tx;
+      dim3 gr;
+      geom32(g, ty, kz, tx, gr);
+      maxp = std::max(maxp, (size_t)gr.x * gr.y);
+    }
   TRY(ensure_partials(m, (size_t)std::max(m->cap, 1) * std::max(maxp, (size_t)2 * RED_BLOCKS)));
   CK(cudaMemsetAsync(m->w32.p, 0, (size_t)g.vs * sizeof(float), m->s));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_kz = m->kz;
-  for (int kz : cand) {
-    if (kz > g.nnz && kz != cand[0]) continue;
-    m->kz = kz;
-    TRY((launch_stencil<float, ST_APPLY, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr, nullptr, nullptr, 1,
-                                                  m->w32.K)));
-    CK(cudaEventRecord(e0, m->s));
-    for (int rep = 0; rep < 3; ++rep)
+  int best_kz = m->kz32, best_ty = m->ty32;
+  for (int ty : cand_ty)
+    for (int kz : cand_kz) {
+      if (kz > g.nnz && kz != cand_kz[0]) continue;
+      m->ty32 = ty;
+      m->kz32 = kz;
       TRY((launch_stencil<float, ST_APPLY, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr, nullptr, nullptr,
                                                     1, m->w32.K)));
-    CK(cudaEventRecord(e1, m->s));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) {
-      best = ms;
-      best_kz = kz;
+      CK(cudaEventRecord(e0, m->s));
+      for (int rep = 0; rep < 3; ++rep)
+        TRY((launch_stencil<float, ST_APPLY, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr, nullptr,
+                                                      nullptr, 1, m->w32.K)));
+      CK(cudaEventRecord(e1, m->s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_kz = kz;
+        best_ty = ty;
+      }
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  m->kz = best_kz;
+  m->kz32 = best_kz;
+  m->ty32 = best_ty;
   m->tuned = true;
   invalidate_graphs(m);  // captured launches bake in the grid
   return AFD_OK;
@@ -605,15 +628,18 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
     delete m;
     return fail(AFD_ERR_INVALID_ARG, "coarse space too large (%d unknowns > 8192): use a larger group", 6 * gp.ng);
   }
-  // z planes per CTA: enough CTAs to fill the GPU a few times
+  // z planes per CTA before tuning: enough CTAs to fill the GPU a few times
   {
     int tx;
     dim3 gr;
-    StencilGeom<TY32>::get(g, g.nnz, tx, gr);
-    const long tiles = gr.x;
-    // about two waves of 512-thread CTAs (2 resident per SM), at least 4 planes per CTA
-    long kz = (long)g.nnz * tiles / 608;
+    StencilGeom<TY64>::get(g, g.nnz, tx, gr);
+    // about four waves of the FP64 CTAs, at least 4 planes per CTA
+    long kz = (long)g.nnz * gr.x / 1216;
     m->kz = (int)std::max(4L, std::min<long>(kz, g.nnz));
+    geom32(g, 16, g.nnz, tx, gr);
+    // about two waves of 512-thread FP32 CTAs (1 resident per SM)
+    kz = (long)g.nnz * gr.x / 304;
+    m->kz32 = (int)std::max(4L, std::min<long>(kz, g.nnz));
   }
   m->w32.K = make_elem_consts<float>(o.nu, o.h);
   m->w64.K = make_elem_consts<double>(o.nu, o.h);
@@ -1187,7 +1213,9 @@ int afd_coarse_size(afd_mesh* m) { return m ? m->nc : 0; }
 
 int64_t afd_kernel_launches(const afd_mesh* m) { return m ? m->launches : 0; }
 
-int afd_stencil_depth(const afd_mesh* m) { return m ? m->kz : 0; }
+int afd_stencil_depth(const afd_mesh* m) { return m ? m->kz32 : 0; }
+
+int afd_stencil_warps(const afd_mesh* m) { return m ? m->ty32 : 0; }
 
 size_t afd_mesh_bytes(int nx, int ny, int nz, int n_rhs, const afd_options* opt) {
   afd_options o;

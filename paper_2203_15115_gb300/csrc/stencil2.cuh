@@ -1,0 +1,385 @@
+// FP32 matrix-free stiffness apply y = K u, two node rows per thread with the
+// two element rows packed into the lanes of one float2 (Sec. 3.5: K is never
+// assembled; the cost of an iteration is the operator apply).
+//
+// Design (sm_103a).  The modal hex8 operator and the column march are those
+// of stencil.cuh: every thread owns node columns and marches along z, the x
+// butterflies go through warp shuffles, the y butterflies through shared
+// memory, the z butterflies stay in registers.  Here a thread owns the two
+// node rows jb = base + 2w and jb + 1 of its column and computes the two
+// element rows A (between jb and jb+1) and B (between jb+1 and jb+2) at once:
+// every value of the element pipeline is a float2 (A in .x, B in .y), so each
+// butterfly, each modal-force product and each transposed butterfly is one
+// packed FP32 instruction (FADD2/FFMA2/FMUL2 of sm_100+) for two elements.
+// Only row jb+2 comes from the next warp (shared memory), so a CTA of TY
+// warps covers 2 TY node rows and finishes 2 TY - 2 of them, with one barrier
+// per exchange for two nodes per thread.  The arithmetic of each element is
+// the same sequence of correctly rounded operations as in stencil.cuh.
+#pragma once
+
+#include "afd_common.cuh"
+#include "dpcg_kernels.cuh"
+#include "stencil.cuh"
+
+namespace afd {
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b, rounded once (b * -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Modal forces of two elements (modal_forces in afd_common.cuh, lane-wise),
+// h[c][0] (the rigid translation) is neither read nor written.
+__device__ __forceinline__ void modal_forces2(float2 (&h)[3][8], float2 E, const ElemConsts<float>& K) {
+  const float2 l16 = mul2(bc2(K.l16), E), m16 = mul2(bc2(K.m16), E), m8 = mul2(bc2(K.m8), E);
+  const float2 l48 = mul2(bc2(K.l48), E), m48 = mul2(bc2(K.m48), E), m3 = mul2(bc2(K.m3_48), E);
+  const float2 t144 = mul2(bc2(K.t144), E);
+  {
+    const float2 Axx = h[0][1], Ayy = h[1][2], Azz = h[2][4];
+    const float2 tr = mul2(l16, add2(add2(Axx, Ayy), Azz));
+    const float2 sxy = mul2(m16, add2(h[0][2], h[1][1]));
+    const float2 syz = mul2(m16, add2(h[1][4], h[2][2]));
+    const float2 szx = mul2(m16, add2(h[2][1], h[0][4]));
+    h[0][1] = fma2(m8, Axx, tr);
+    h[1][2] = fma2(m8, Ayy, tr);
+    h[2][4] = fma2(m8, Azz, tr);
+    h[0][2] = sxy; h[1][1] = sxy;
+    h[1][4] = syz; h[2][2] = syz;
+    h[2][1] = szx; h[0][4] = szx;
+  }
+  {
+    const float2 Px = h[0][3], Py = h[1][3], Pz = h[2][3];
+    const float2 Qx = h[0][6], Qy = h[1][6], Qz = h[2][6];
+    const float2 Rx = h[0][5], Ry = h[1][5], Rz = h[2][5];
+    const float2 s1 = mul2(l48, add2(Px, Qz));
+    const float2 s2 = mul2(l48, add2(Py, Rz));
+    const float2 s3 = mul2(l48, add2(Rx, Qy));
+    const float2 s = add2(add2(Pz, Qx), Ry);
+    h[0][3] = fma2(m3, Px, s1);
+    h[2][6] = fma2(m3, Qz, s1);
+    h[1][3] = fma2(m3, Py, s2);
+    h[2][5] = fma2(m3, Rz, s2);
+    h[0][5] = fma2(m3, Rx, s3);
+    h[1][6] = fma2(m3, Qy, s3);
+    h[2][3] = mul2(m48, add2(Pz, s));
+    h[0][6] = mul2(m48, add2(Qx, s));
+    h[1][5] = mul2(m48, add2(Ry, s));
+  }
+  h[0][7] = mul2(h[0][7], t144);
+  h[1][7] = mul2(h[1][7], t144);
+  h[2][7] = mul2(h[2][7], t144);
+}
+
+// Launch geometry: a CTA of TY warps covers 2 TY node rows, finishes rows
+// base+1 .. base+2TY-2 (2 TY - 2 of them), and (ST_TX - 2) columns over kz planes.
+template <int TY>
+struct StencilGeom2 {
+  static constexpr int ROWS = 2 * TY - 2;
+  static void get(const Grid& gr, int kz, int& tiles_x, dim3& grid) {
+    tiles_x = (gr.nnx + (ST_TX - 3)) / (ST_TX - 2);
+    const int tiles_y = (gr.nny + ROWS - 1) / ROWS;
+    const int zch = (gr.nnz + kz - 1) / kz;
+    grid = dim3(tiles_x * tiles_y, zch, 1);
+  }
+};
+
+template <int TY, int MODE>
+__global__ void __launch_bounds__(ST_TX * TY, 16 / TY)
+stencil2_kernel(const StencilArgs<float, float> a) {
+  // Exchange buffers (each written, then read after a barrier; the other
+  // exchange's barrier separates that read from the next write):
+  //   xe: (S, D) x-edge values of row jb for the warp below, per component
+  //   ye: (mx = 0, 1) forces of element B on row jb + 2, for the warp above
+  __shared__ float2 xe[3][TY][ST_TX];
+  __shared__ float2 ye[3][TY][ST_TX];
+  __shared__ double red[32];
+
+  const int rhs = blockIdx.z;
+  if (a.done && a.done[rhs]) return;
+  const Grid gr = a.gr;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tile_x = blockIdx.x % a.tiles_x;
+  const int tile_y = blockIdx.x / a.tiles_x;
+  const int i = tile_x * (ST_TX - 2) - 1 + lane;
+  const int jb = tile_y * StencilGeom2<TY>::ROWS - 1 + 2 * w;   // row a = 0; row a = 1 is jb + 1
+  const int k0 = blockIdx.y * a.kz;
+  const int k1 = min(k0 + a.kz, gr.nnz);
+  const size_t voff = (size_t)rhs * gr.vs;
+  const float* __restrict__ u = a.u + voff;
+
+  const bool ci = i >= 0 && i < gr.nnx;
+  const bool col0 = ci && jb >= 0 && jb < gr.nny;
+  const bool col1 = ci && jb + 1 >= 0 && jb + 1 < gr.nny;
+  const bool ei = lane < ST_TX - 1 && i >= 0 && i < gr.nx;
+  const bool elA = ei && jb >= 0 && jb < gr.ny;
+  const bool elB = ei && w < TY - 1 && jb + 1 >= 0 && jb + 1 < gr.ny;
+  const bool oi = lane >= 1 && lane < ST_TX - 1 && i <= gr.nx;
+  const bool out0 = oi && w >= 1 && jb <= gr.ny;
+  const bool out1 = oi && w <= TY - 2 && jb + 1 <= gr.ny;
+
+  // Fused search direction p = z + W mu + beta p_old (as in stencil.cuh; in
+  // ST_APPLY_DOT, which the solver always launches with z); the two rows may
+  // lie in different groups along y, so A and B are per row.
+  constexpr bool formp = MODE == ST_APPLY_DOT;
+  const float beta = formp ? (float)a.st[rhs].beta : 0.f;
+  const Groups gp = a.gp;
+  const float hh = (float)(0.5 * gp.h);
+  float rx = 0.f, ry0 = 0.f, ry1 = 0.f;
+  int gxy0 = 0, gxy1 = 0;
+  int gz = -1, gz_next = 0, zlo = 0, zhi = 0;
+  float2 A0 = bc2(0.f), A1 = bc2(0.f), A2 = bc2(0.f), B0 = bc2(0.f), B1 = bc2(0.f);
+  const double* murhs = formp ? a.mu + (size_t)rhs * 6 * gp.ng : nullptr;
+  if (formp && ci) {
+    int lo, hi;
+    const int Gx = group_of_axis(i, gp.g, gp.ngx);
+    group_range(Gx, gp.g, gp.ngx, gr.nx, lo, hi);
+    rx = hh * (float)(2 * i - lo - hi);
+    const int j0 = max(jb, 0), j1 = min(jb + 1, gr.nny - 1);
+    const int Gy0 = group_of_axis(j0, gp.g, gp.ngy), Gy1 = group_of_axis(j1, gp.g, gp.ngy);
+    group_range(Gy0, gp.g, gp.ngy, gr.ny, lo, hi);
+    ry0 = hh * (float)(2 * j0 - lo - hi);
+    group_range(Gy1, gp.g, gp.ngy, gr.ny, lo, hi);
+    ry1 = hh * (float)(2 * j1 - lo - hi);
+    gxy0 = Gx + gp.ngx * Gy0;
+    gxy1 = Gx + gp.ngx * Gy1;
+  }
+  auto refresh_group = [&](int k) {
+    gz = group_of_axis(k, gp.g, gp.ngz);
+    group_range(gz, gp.g, gp.ngz, gr.nz, zlo, zhi);
+    gz_next = (gz == gp.ngz - 1) ? (1 << 30) : zhi + 1;
+    const int gzo = gp.ngx * gp.ngy * gz;
+    const double* m0 = murhs + 6 * (gxy0 + gzo);
+    const double* m1 = murhs + 6 * (gxy1 + gzo);
+    const float tx0 = (float)m0[0], ty0 = (float)m0[1], tz0 = (float)m0[2];
+    const float ox0 = (float)m0[3], oy0 = (float)m0[4], oz0 = (float)m0[5];
+    const float tx1 = (float)m1[0], ty1 = (float)m1[1], tz1 = (float)m1[2];
+    const float ox1 = (float)m1[3], oy1 = (float)m1[4], oz1 = (float)m1[5];
+    A0 = make_float2(tx0 - oz0 * ry0, tx1 - oz1 * ry1);
+    A1 = make_float2(ty0 + oz0 * rx, ty1 + oz1 * rx);
+    A2 = make_float2(tz0 + (ox0 * ry0 - oy0 * rx), tz1 + (ox1 * ry1 - oy1 * rx));
+    B0 = make_float2(oy0, oy1);
+    B1 = make_float2(-ox0, -ox1);
+  };
+
+  // (u or the formed p) of both rows at plane k; fixed bits of both rows in fbits
+  auto load_node = [&](int k, float2 (&v)[3], unsigned& fbits) {
+    v[0] = v[1] = v[2] = bc2(0.f);
+    fbits = 0u;
+    if (k < 0 || k >= gr.nnz) return;
+    const int n0 = i + gr.nnx * (jb + gr.nny * k);
+    const int n1 = n0 + gr.nnx;
+    const unsigned f0 = (col0 && a.fixed) ? a.fixed[n0] : 0u;
+    const unsigned f1 = (col1 && a.fixed) ? a.fixed[n1] : 0u;
+    fbits = f0 | (f1 << 8);
+    float p0[3] = {0.f, 0.f, 0.f}, p1[3] = {0.f, 0.f, 0.f};
+    if (col0) {
+      const float* q = u + 3 * (size_t)n0;
+      p0[0] = q[0]; p0[1] = q[1]; p0[2] = q[2];
+    }
+    if (col1) {
+      const float* q = u + 3 * (size_t)n1;
+      p1[0] = q[0]; p1[1] = q[1]; p1[2] = q[2];
+    }
+    if constexpr (formp) {
+      if (k >= gz_next || gz < 0) refresh_group(k);
+      float z0[3] = {0.f, 0.f, 0.f}, z1[3] = {0.f, 0.f, 0.f};
+      if (col0) {
+        const float* q = a.z + voff + 3 * (size_t)n0;
+        z0[0] = q[0]; z0[1] = q[1]; z0[2] = q[2];
+      }
+      if (col1) {
+        const float* q = a.z + voff + 3 * (size_t)n1;
+        z1[0] = q[0]; z1[1] = q[1]; z1[2] = q[2];
+      }
+      const float2 rz = bc2(hh * (float)(2 * k - zlo - zhi)), bt = bc2(beta);
+      v[0] = fma2(bt, make_float2(p0[0], p1[0]), add2(make_float2(z0[0], z1[0]), fma2(rz, B0, A0)));
+      v[1] = fma2(bt, make_float2(p0[1], p1[1]), add2(make_float2(z0[1], z1[1]), fma2(rz, B1, A1)));
+      v[2] = fma2(bt, make_float2(p0[2], p1[2]), add2(make_float2(z0[2], z1[2]), A2));
+    } else {
+      v[0] = make_float2(p0[0], p1[0]);
+      v[1] = make_float2(p0[1], p1[1]);
+      v[2] = make_float2(p0[2], p1[2]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (!col0 || ((f0 >> c) & 1u)) v[c].x = 0.f;
+      if (!col1 || ((f1 >> c) & 1u)) v[c].y = 0.f;
+    }
+  };
+
+  // Face values of elements A and B on one node plane: F[c][q], q = mx + 2 my.
+  auto face_values = [&](const float2 (&un)[3], float2 (&F)[3][4]) {
+    float2 S[3], D[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 right = make_float2(__shfl_down_sync(0xffffffffu, un[c].x, 1),
+                                       __shfl_down_sync(0xffffffffu, un[c].y, 1));  // lane 31: unused
+      S[c] = add2(right, un[c]);
+      D[c] = sub2(right, un[c]);
+      xe[c][w][lane] = make_float2(S[c].x, D[c].x);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 up = (w < TY - 1) ? xe[c][w + 1][lane] : bc2(0.f);   // (S, D) of row jb + 2
+      const float2 St = make_float2(S[c].y, up.x), Dt = make_float2(D[c].y, up.y);
+      F[c][0] = add2(St, S[c]);
+      F[c][1] = add2(Dt, D[c]);
+      F[c][2] = sub2(St, S[c]);
+      F[c][3] = sub2(Dt, D[c]);
+    }
+  };
+
+  float2 Fb[3][4], Tprev[3][4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Fb[c][q] = Tprev[c][q] = bc2(0.f);
+
+  {
+    float2 un0[3];
+    unsigned fdummy;
+    load_node(k0 - 1, un0, fdummy);
+    face_values(un0, Fb);
+    __syncthreads();  // the loop's first x-edge write follows this read
+  }
+  float2 ucur[3] = {bc2(0.f), bc2(0.f), bc2(0.f)};   // formed u at plane l (dot and p write)
+  unsigned fcur = 0u, fnext;
+  float part = 0.f;
+  float2 un[3];
+  load_node(k0, un, fnext);
+
+  for (int l = k0 - 1; l < k1; ++l) {
+    float2 Ft[3][4];
+    face_values(un, Ft);
+    const float2 u_l1[3] = {un[0], un[1], un[2]};
+    const unsigned f_l1 = fnext;
+    float2 E = bc2(0.f);
+    if (l >= 0 && l < gr.nz) {
+      const int e0 = i + gr.nx * (jb + gr.ny * l);
+      if (elA) E.x = a.E[e0];
+      if (elB) E.y = a.E[e0 + gr.nx];
+    }
+    if (l + 2 <= k1) load_node(l + 2, un, fnext);
+
+    float2 h[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int q = 1; q < 4; ++q) h[c][q] = add2(Ft[c][q], Fb[c][q]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) h[c][q + 4] = sub2(Ft[c][q], Fb[c][q]);
+    }
+    modal_forces2(h, E, a.K);
+    float2 Bf[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      // q = 0: the rigid-translation force is zero
+      Bf[c][0] = sub2(Tprev[c][0], h[c][4]);
+      Tprev[c][0] = h[c][4];
+#pragma unroll
+      for (int q = 1; q < 4; ++q) {
+        Bf[c][q] = add2(sub2(h[c][q], h[c][q + 4]), Tprev[c][q]);
+        Tprev[c][q] = add2(h[c][q], h[c][q + 4]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Fb[c][q] = Ft[c][q];
+    }
+
+    // transposed y stage: e0 -> (row jb from A, row jb+1 from B), e1 -> (row jb+1 from A, row jb+2 from B)
+    float2 e0[3][2], e1[3][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int mx = 0; mx < 2; ++mx) {
+        e0[c][mx] = sub2(Bf[c][mx], Bf[c][mx + 2]);
+        e1[c][mx] = add2(Bf[c][mx], Bf[c][mx + 2]);
+      }
+      ye[c][w][lane] = make_float2(e1[c][0].y, e1[c][1].y);
+    }
+    __syncthreads();
+    float2 yv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 below = (w >= 1) ? ye[c][w - 1][lane] : bc2(0.f);   // element row jb-1 on row jb
+      const float2 t0 = add2(e0[c][0], make_float2(below.x, e1[c][0].x));
+      const float2 t1 = add2(e0[c][1], make_float2(below.y, e1[c][1].x));
+      // transposed x stage: edge (i, i+1) -> node i gets s - d, node i+1 gets s + d
+      const float2 sp = add2(t0, t1);
+      const float2 fl = make_float2(__shfl_up_sync(0xffffffffu, sp.x, 1), __shfl_up_sync(0xffffffffu, sp.y, 1));
+      yv[c] = add2(sub2(t0, t1), lane >= 1 ? fl : bc2(0.f));
+    }
+
+    if (l >= k0) {
+      const int n0 = i + gr.nnx * (jb + gr.nny * l);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const bool ok = r == 0 ? out0 : out1;
+        if (!ok) continue;
+        const int n = n0 + r * gr.nnx;
+        const unsigned fb = (fcur >> (8 * r)) & 0xffu;
+        float* yp = a.y + voff + 3 * (size_t)n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float yc = r == 0 ? yv[c].x : yv[c].y;
+          const float uc = r == 0 ? ucur[c].x : ucur[c].y;
+          const bool fx = (fb >> c) & 1u;
+          float out;
+          if (MODE == ST_RESIDUAL) {
+            out = fx ? 0.f : a.f[voff + 3 * (size_t)n + c] - yc;
+            part += out * out;
+            if (a.y32) a.y32[voff + 3 * (size_t)n + c] = out;
+          } else {
+            out = fx ? 0.f : yc;
+            if (MODE == ST_APPLY_DOT) part += uc * out;
+          }
+          yp[c] = out;
+        }
+        if constexpr (formp) {
+          float* pp = a.pout + voff + 3 * (size_t)n;
+          pp[0] = r == 0 ? ucur[0].x : ucur[0].y;
+          pp[1] = r == 0 ? ucur[1].x : ucur[1].y;
+          pp[2] = r == 0 ? ucur[2].x : ucur[2].y;
+        }
+      }
+    }
+    ucur[0] = u_l1[0];
+    ucur[1] = u_l1[1];
+    ucur[2] = u_l1[2];
+    fcur = f_l1;
+  }
+  if (MODE != ST_APPLY) {
+    float pv[1] = {part};
+    double o[1];
+    block_sum_to_f64<1>(pv, red, o);
+    const int nparts = gridDim.x * gridDim.y;
+    double* parts = a.partials + (size_t)rhs * nparts;
+    if (threadIdx.x == 0) parts[blockIdx.y * gridDim.x + blockIdx.x] = o[0];
+    if (MODE == ST_APPLY_DOT && a.st) {
+      __shared__ bool s_last;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_last = atomicAdd(&a.counter[rhs], 1u) == (unsigned)nparts - 1u;
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        const double pap = sum_partials(parts, nparts, 1, 0);
+        if (threadIdx.x == 0) {
+          CGState& S = a.st[rhs];
+          if (!(pap > 0.0) || !isfinite(pap)) {
+            S.status = isfinite(pap) ? -3 : -5;
+            S.done = 1;
+            const_cast<int*>(a.done)[rhs] = 1;
+          } else {
+            S.alpha = S.rz / pap;
+          }
+          a.counter[rhs] = 0u;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace afd
