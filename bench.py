@@ -247,6 +247,7 @@ def run_ours(args):
         "config": {"workload": w.name, "elements": ne, "dofs": 3 * nn, "group": mesh.options.group or "auto",
                    "stencil_planes_per_cta": afd.afd_stencil_depth(mesh.h),
                    "stencil_warps_per_cta": afd.afd_stencil_warps(mesh.h),
+                   "inner_solver": "persistent cooperative kernel" if mesh.options.persistent else "CUDA-graph chunks",
                    "tol": w.tol, "volume_fraction": VOLUME_FRACTION, "l2": "flushed (512 MB write) between timed steps",
                    "parallelism": f"replicas x{world}"},
         "solve": {"mixed_ms": round(float(np.median(solve_ms)), 3), "fp64_ms": round(float(np.median(fp64)), 3),

@@ -71,6 +71,9 @@ typedef struct {
   double inner_tol;   /* floor of the inner relative tolerance in AFD_MIXED (default 2e-5) */
   int check_every;    /* DPCG iterations per captured CUDA graph between host checks (default 16) */
   int autotune;       /* 1 (default): at the first solve, time the stencil's z depth per CTA and keep the fastest */
+  int persistent;     /* AFD_MIXED inner solves: 0 (default) CUDA-graph chunks of check_every iterations,
+                         one kernel per phase; 1 one cooperatively launched persistent kernel per inner
+                         solve with grid-wide barriers between its phases (afd_solver_phase_times) */
 } afd_options;
 
 typedef struct {
@@ -191,6 +194,15 @@ int afd_stencil_depth(const afd_mesh* m);
 /* Warps per CTA of the FP32 stiffness kernel (8 or 16; each warp owns two node
  * rows, a CTA finishes 2 * warps - 2 of them); chosen with the depth. */
 int afd_stencil_warps(const afd_mesh* m);
+
+/* Measurement aid for the persistent inner solver (opt.persistent), as seen
+ * by its CTA 0 and summed over all iterations since the last reset, in ms:
+ * out10[0..4] wall time of the phases between grid barriers -- stencil with
+ * the fused search direction, vector update, coarse right-hand side, coarse
+ * apply, scalar recurrences; out10[5] the iterations counted; out10[6..9]
+ * the part of phases 0..3 that CTA 0 spent waiting in the barrier.  reset = 1
+ * zeroes the counters after reading.  Host output. */
+int afd_solver_phase_times(afd_mesh* m, double* out10, int reset);
 
 /* Sizes of the mesh. */
 int64_t afd_ndof(const afd_mesh* m);

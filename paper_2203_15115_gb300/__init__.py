@@ -40,7 +40,7 @@ EXPORTS = [
     "afd_deflation_wt", "afd_deflation_w", "afd_coarse_size", "afd_coarse_matrix", "afd_select_topk",
     "afd_ndof", "afd_nelem", "afd_destroy", "afd_last_error", "afd_al_init", "afd_al_update", "afd_al_weight",
     "afd_time_stiffness", "afd_kernel_launches", "afd_select_topk_noalloc", "afd_stencil_depth",
-    "afd_stencil_warps",
+    "afd_stencil_warps", "afd_solver_phase_times",
     "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
 ]
 
@@ -49,7 +49,7 @@ class afd_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("group", ctypes.c_int), ("nu", ctypes.c_double),
                 ("h", ctypes.c_double), ("e_void", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("persistent", ctypes.c_int)]
 
 
 class afd_stats(ctypes.Structure):
@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
             "afd_select_topk_noalloc": (i, [vp, i64, i64, vp, ctypes.POINTER(ctypes.c_float), vp]),
             "afd_stencil_depth": (i, [vp]),
             "afd_stencil_warps": (i, [vp]),
+            "afd_solver_phase_times": (i, [vp, ctypes.POINTER(ctypes.c_double), i]),
             "afd_mesh_bytes": (ctypes.c_size_t, [i, i, i, i, ctypes.POINTER(afd_options)]),
             "afd_server_create": (i, [ctypes.POINTER(afd_server_config), ctypes.POINTER(vp)]),
             "afd_server_submit": (i, [vp, i, i, i, vp, vp, vp, d, ctypes.POINTER(i64)]),
@@ -298,6 +299,14 @@ def afd_stencil_depth(mesh) -> int:
 
 def afd_stencil_warps(mesh) -> int:
     return int(lib().afd_stencil_warps(mesh))
+
+
+def afd_solver_phase_times(mesh, reset: bool = True) -> dict:
+    out = (ctypes.c_double * 10)()
+    _check(lib().afd_solver_phase_times(mesh, out, int(reset)))
+    names = ["stencil_ms", "update_ms", "coarse_rhs_ms", "coarse_apply_ms", "scalars_ms", "iterations",
+             "stencil_wait_ms", "update_wait_ms", "coarse_rhs_wait_ms", "coarse_apply_wait_ms"]
+    return {k: out[q] for q, k in enumerate(names)}
 
 
 def afd_kernel_launches(mesh) -> int:

@@ -26,6 +26,7 @@
 #include "sens.cuh"
 #include "stencil.cuh"
 #include "stencil2.cuh"
+#include "dpcg_persistent.cuh"
 
 using namespace afd;
 
@@ -129,14 +130,21 @@ struct afd_mesh {
   unsigned int* counters = nullptr;  // last-block counters: [rhs] stencil, [MAX_RHS] coarse
   double* dmax = nullptr;
   int* dstatus = nullptr;
-  uint8_t* gfix = nullptr;     // [N_g] group holds a fixed DOF
-  std::vector<uint8_t> gfix_h;  // host copy
+  int* gbox = nullptr;         // [N_g][6] bounding box of the group's fixed nodes (max < min: none)
+  std::vector<int> gbox_h;     // host copy
   long long* aw_off = nullptr; // [N_g + 1] offset of group G's block in AW (last: total)
   int* aw_node = nullptr;      // [aw_total / 18] node index of every shell slot
   double* grec = nullptr;      // [rhs][N_g][12] per-group records of the coarse right-hand side
   double* upart = nullptr;     // [rhs][RED_BLOCKS][2] partials of the vector update
   unsigned int* gcount = nullptr;  // [rhs][N_g] split counters
   size_t aw_total = 0;         // elements of AW
+  // persistent inner solver: per-CTA partials, coarse records, grid barrier
+  double* ppart = nullptr;
+  size_t ppart_cap = 0;
+  double* prec = nullptr;
+  size_t prec_cap = 0;
+  GridBarrier* gbar = nullptr;
+  unsigned long long* ptime = nullptr;   // [10] phase times of the persistent solver (ns), iterations, barrier waits
   int nsplit_aw = 1;
   bool coarse_valid = false;
   Work<float> w32;
@@ -376,7 +384,7 @@ static int build_aw(afd_mesh* m, Work<T>& w) {
     w.aw_cap = m->aw_total;
   }
   const dim3 grid(m->gp.ng, m->nsplit_aw);
-  k_build_aw<T><<<grid, 128, 0, m->s>>>(m->gr, m->gp, m->nsplit_aw, m->E64, m->fixed, m->gfix, m->aw_off, w.K, w.AW,
+  k_build_aw<T><<<grid, 128, 0, m->s>>>(m->gr, m->gp, m->nsplit_aw, m->E64, m->fixed, m->gbox, m->aw_off, w.K, w.AW,
                                          m->aw_node); m->launches++;
   CK(cudaGetLastError());
   return AFD_OK;
@@ -457,6 +465,89 @@ static int autotune_stencil(afd_mesh* m) {
 }
 
 // ---------------------------------------------------------------------------
+// FP32 inner DPCG iterations as one cooperative persistent kernel
+// (dpcg_persistent.cuh).  Launched after the deflated start; returns with
+// *launched = 0 (and nothing enqueued) when the device cannot co-schedule the
+// grid, in which case the caller runs the CUDA-graph path.
+// ---------------------------------------------------------------------------
+template <int TY>
+static int launch_persistent(afd_mesh* m, Work<float>& w, float* x, int nrhs, int& launched) {
+  launched = 0;
+  const Grid& gr = m->gr;
+  int nsm = 0, coop = 0;
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+  CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, m->device));
+  if (!coop || nrhs > PERSIST_MAX_RHS) return AFD_OK;
+  const size_t smem = (size_t)m->nc * sizeof(double);
+  if (smem > 48 * 1024)
+    CK(cudaFuncSetAttribute(k_dpcg_persistent<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dpcg_persistent<TY>, ST_TX * TY, smem));
+  if (per_sm < 1) return AFD_OK;
+  const int nb = per_sm * nsm;
+  PersistArgs pa;
+  memset(&pa, 0, sizeof(pa));
+  pa.sa.gr = gr;
+  pa.sa.E = w.E;
+  pa.sa.fixed = m->fixed;
+  pa.sa.K = w.K;
+  pa.sa.kz = m->kz32;
+  pa.sa.gp = m->gp;
+  dim3 sg;
+  StencilGeom2<TY>::get(gr, m->kz32, pa.sa.tiles_x, sg);
+  pa.ntiles = (int)(sg.x * sg.y);
+  pa.nrhs = nrhs;
+  pa.x = x;
+  pa.r = w.r;
+  pa.z = w.z;
+  pa.q = w.q;
+  pa.P0 = w.p;
+  pa.P1 = w.t;
+  pa.invd = w.invd;
+  pa.nc = m->nc;
+  pa.nsplit = std::max(1, std::min(m->gp.g, nb / std::max(1, m->gp.ng)));
+  pa.aw_off = m->aw_off;
+  pa.aw_node = m->aw_node;
+  pa.AW = w.AW;
+  pa.Einv = m->Einv32;
+  pa.mu = m->mu;
+  // tile partials, then the per-CTA records (4 doubles each, 32-byte aligned for the vector loads)
+  const size_t st_len = ((size_t)nrhs * pa.ntiles + 3) / 4 * 4;
+  const size_t need = st_len + (size_t)nrhs * 4 * (size_t)nb;
+  if (need > m->ppart_cap) {
+    dfree(m->ppart);
+    m->ppart_cap = 0;
+    TRY(dalloc(&m->ppart, need));
+    m->ppart_cap = need;
+  }
+  const size_t needr = (size_t)nrhs * m->gp.ng * pa.nsplit * 12;
+  if (needr > m->prec_cap) {
+    dfree(m->prec);
+    m->prec_cap = 0;
+    TRY(dalloc(&m->prec, needr));
+    m->prec_cap = needr;
+  }
+  if (!m->gbar) TRY(dalloc(&m->gbar, 1));
+  if (!m->ptime) {
+    TRY(dalloc(&m->ptime, 10));
+    CK(cudaMemsetAsync(m->ptime, 0, 10 * sizeof(unsigned long long), m->s));
+  }
+  pa.ptime = m->ptime;
+  pa.rec = m->prec;
+  pa.part_st = m->ppart;
+  pa.part_up = m->ppart + st_len;
+  pa.st = m->st;
+  pa.done = m->done;
+  pa.bar = m->gbar;
+  CK(cudaMemsetAsync(m->gbar, 0, sizeof(GridBarrier), m->s));
+  void* args[] = {&pa};
+  CK(cudaLaunchCooperativeKernel((const void*)k_dpcg_persistent<TY>, dim3(nb), dim3(ST_TX * TY), args, smem, m->s));
+  m->launches++;
+  launched = 1;
+  return AFD_OK;
+}
+
+// ---------------------------------------------------------------------------
 // deflated PCG (Sec. 3.5) in type T on K x = b; x holds the initial guess.
 // Per-RHS stop: r.r <= target2[r]; RHS with active[r] == 0 are skipped.
 // ---------------------------------------------------------------------------
@@ -507,6 +598,24 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
   k_coarse_step<T><<<crows, 256, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->grec, m->wr, 2, m->done, cnt_co,
                                                m->upart, RED_BLOCKS); m->launches++;
   CK(cudaGetLastError());
+
+  if constexpr (!F64) {
+    if (m->opt.persistent) {
+      int launched = 0;
+      if (m->ty32 == 8)
+        TRY(launch_persistent<8>(m, w, x, nrhs, launched));
+      else
+        TRY(launch_persistent<16>(m, w, x, nrhs, launched));
+      if (launched) {
+        out.resize(nrhs);
+        CK(cudaMemcpyAsync(out.data(), m->st, nrhs * sizeof(CGState), cudaMemcpyDeviceToHost, m->s));
+        CK(cudaStreamSynchronize(m->s));
+        for (int r = 0; r < nrhs; ++r)
+          if (out[r].status == AFD_ERR_CUDA) return fail(AFD_ERR_CUDA, "persistent solver: a grid-barrier wait ran out");
+        return AFD_OK;
+      }
+    }
+  }
 
   // One chunk of iterations (even length), captured once into a graph.  Per
   // iteration: the stencil forms p = y + beta p_old while applying K to it
@@ -580,6 +689,7 @@ void afd_default_options(afd_options* o) {
   o->inner_tol = 2e-5;
   o->check_every = 16;
   o->autotune = 1;
+  o->persistent = 0;
 }
 
 const char* afd_last_error(void) { return g_err.c_str(); }
@@ -655,7 +765,7 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
       (rc = dalloc(&m->w32.invd, (size_t)g.vs)) != AFD_OK || (rc = dalloc(&m->w64.invd, (size_t)g.vs)) != AFD_OK ||
       (rc = dalloc(&m->fsmall, (size_t)FSMALL_SIZE)) != AFD_OK ||
       (rc = dalloc(&m->counters, (size_t)MAX_RHS + 1)) != AFD_OK ||
-      (rc = dalloc(&m->gfix, (size_t)gp.ng)) != AFD_OK ||
+      (rc = dalloc(&m->gbox, (size_t)gp.ng * 6)) != AFD_OK ||
       (rc = dalloc(&m->aw_off, (size_t)gp.ng + 1)) != AFD_OK) {
     afd_destroy(m);
     return rc;
@@ -692,8 +802,9 @@ void afd_destroy(afd_mesh* m) {
   if (m->sel) cudaFree(m->sel);
   dfree(m->selcnt); dfree(m->fsmall);
   dfree(m->Ec); dfree(m->Einv64); dfree(m->Einv32); dfree(m->gjP); dfree(m->gjB); dfree(m->gjR);
-  dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gfix); dfree(m->aw_off); dfree(m->aw_node);
+  dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gbox); dfree(m->aw_off); dfree(m->aw_node);
   dfree(m->grec); dfree(m->gcount); dfree(m->upart);
+  dfree(m->ppart); dfree(m->prec); dfree(m->gbar); dfree(m->ptime);
   if (m->ev) cudaEventDestroy(m->ev);
   if (m->s) cudaStreamDestroy(m->s);
   delete m;
@@ -795,17 +906,17 @@ int afd_set_loads_bcs(afd_mesh* m, int n_rhs, const double* f, int f_on_device, 
     CK(cudaMemcpyAsync(dmask, mask, g.ndof, cudaMemcpyHostToDevice, m->s));
   }
   k_pack_fixed<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g.nnodes, dmask, m->fixed); m->launches++;
-  CK(cudaMemsetAsync(m->gfix, 0, m->gp.ng, m->s));
-  k_group_fixed<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->gp, m->fixed, m->gfix); m->launches++;
-  m->gfix_h.assign(m->gp.ng, 0);
-  CK(cudaMemcpyAsync(m->gfix_h.data(), m->gfix, m->gp.ng, cudaMemcpyDeviceToHost, m->s));
+  k_group_box_init<<<grid_blocks((size_t)6 * m->gp.ng, 256, 256), 256, 0, m->s>>>(m->gp.ng, m->gbox); m->launches++;
+  k_group_fixed<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->gp, m->fixed, m->gbox); m->launches++;
+  m->gbox_h.assign((size_t)6 * m->gp.ng, 0);
+  CK(cudaMemcpyAsync(m->gbox_h.data(), m->gbox, (size_t)6 * m->gp.ng * sizeof(int), cudaMemcpyDeviceToHost, m->s));
   CK(cudaStreamSynchronize(m->s));
   {
     std::vector<long long> off(m->gp.ng + 1);
     size_t tot = 0;
     for (int G = 0; G < m->gp.ng; ++G) {
       off[G] = (long long)tot;
-      tot += 18 * (size_t)node_shell_count(g, m->gp, G, m->gfix_h[G] != 0);
+      tot += 18 * (size_t)node_shell_count(g, m->gp, G, m->gbox_h.data() + 6 * G);
     }
     off[m->gp.ng] = (long long)tot;
     if (tot > m->aw_total || !m->aw_node) {
@@ -1216,6 +1327,19 @@ int64_t afd_kernel_launches(const afd_mesh* m) { return m ? m->launches : 0; }
 int afd_stencil_depth(const afd_mesh* m) { return m ? m->kz32 : 0; }
 
 int afd_stencil_warps(const afd_mesh* m) { return m ? m->ty32 : 0; }
+
+int afd_solver_phase_times(afd_mesh* m, double* out10, int reset) {
+  if (!m || !out10) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  DeviceGuard dg(m->device);
+  unsigned long long h[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (m->ptime) {
+    CK(cudaMemcpyAsync(h, m->ptime, sizeof(h), cudaMemcpyDeviceToHost, m->s));
+    if (reset) CK(cudaMemsetAsync(m->ptime, 0, sizeof(h), m->s));
+    CK(cudaStreamSynchronize(m->s));
+  }
+  for (int q = 0; q < 10; ++q) out10[q] = q == 5 ? (double)h[q] : (double)h[q] * 1e-6;
+  return AFD_OK;
+}
 
 size_t afd_mesh_bytes(int nx, int ny, int nz, int n_rhs, const afd_options* opt) {
   afd_options o;

@@ -177,11 +177,18 @@ struct Shell {
   }
 };
 
-// Node shell of group G: the nodes of elements that can carry energy for a
-// rigid motion of G, i.e. the box [lo-1, hi+1]^3 (clipped to the grid) minus
-// the nodes whose eight elements all lie inside G ([lo+1, hi-1]^3); the
-// whole box when the group holds a fixed DOF.
-__host__ __device__ inline void node_shell_bounds(const Grid& gr, const Groups& gp, int G, int (&b)[12]) {
+// Node shell of group G: the nodes where (K W_G) can be nonzero.  K W_G
+// vanishes at a node all of whose elements lie inside G and hold no fixed
+// DOF (the rigid motions are in the null space of the element stiffness), so
+// the shell is the box [lo-1, hi+1]^3 (clipped to the grid) minus an inner
+// box inside [lo+1, hi-1]^3.  When G holds fixed nodes (bounding box fb =
+// {imin, imax, jmin, jmax, kmin, kmax}, or fb[1] < fb[0] for none), every
+// element touching one lies within fb dilated by one node, so the inner box
+// is cut back on the one side (axis and direction) that keeps it largest
+// while clear of that dilated box; an empty inner box leaves the whole box.
+// b[0..5] outer box, b[6..11] inner box (empty when an extent is < 1).
+__host__ __device__ inline void node_shell_bounds(const Grid& gr, const Groups& gp, int G, const int* fb,
+                                                  int (&b)[12]) {
   const int Gx = G % gp.ngx, Gy = (G / gp.ngx) % gp.ngy, Gz = G / (gp.ngx * gp.ngy);
   const int X[3] = {Gx, Gy, Gz}, NG[3] = {gp.ngx, gp.ngy, gp.ngz}, N[3] = {gr.nx, gr.ny, gr.nz};
   for (int d = 0; d < 3; ++d) {
@@ -191,14 +198,52 @@ __host__ __device__ inline void node_shell_bounds(const Grid& gr, const Groups& 
     b[6 + 2 * d] = lo + 1;                   // inner box
     b[6 + 2 * d + 1] = hi - 1;
   }
+  if (!fb || fb[1] < fb[0]) return;
+  int D[6];
+  bool inter = true;
+  for (int d = 0; d < 3; ++d) {
+    D[2 * d] = fb[2 * d] - 1;
+    D[2 * d + 1] = fb[2 * d + 1] + 1;
+    inter = inter && D[2 * d] <= b[6 + 2 * d + 1] && D[2 * d + 1] >= b[6 + 2 * d];
+  }
+  if (!inter) return;
+  long long best = 0;
+  int blo = 0, bhi = -1, bd = 0;
+  for (int d = 0; d < 3; ++d) {
+    for (int side = 0; side < 2; ++side) {
+      int lo = b[6 + 2 * d], hi = b[6 + 2 * d + 1];
+      if (side == 0)
+        lo = lo > D[2 * d + 1] + 1 ? lo : D[2 * d + 1] + 1;
+      else
+        hi = hi < D[2 * d] - 1 ? hi : D[2 * d] - 1;
+      long long vol = hi >= lo ? (long long)(hi - lo + 1) : 0;
+      for (int e = 0; e < 3; ++e)
+        if (e != d) {
+          const int ext = b[6 + 2 * e + 1] - b[6 + 2 * e] + 1;
+          vol *= ext > 0 ? ext : 0;
+        }
+      if (vol > best) {
+        best = vol;
+        blo = lo;
+        bhi = hi;
+        bd = d;
+      }
+    }
+  }
+  if (best > 0) {
+    b[6 + 2 * bd] = blo;
+    b[6 + 2 * bd + 1] = bhi;
+  } else {
+    b[7] = b[6] - 1;   // no inner box: the whole box
+  }
 }
 
-__host__ __device__ inline int node_shell_count(const Grid& gr, const Groups& gp, int G, bool full) {
+__host__ __device__ inline int node_shell_count(const Grid& gr, const Groups& gp, int G, const int* fb) {
   int b[12];
-  node_shell_bounds(gr, gp, G, b);
+  node_shell_bounds(gr, gp, G, fb, b);
   const int LX = b[1] - b[0] + 1, LY = b[3] - b[2] + 1, LZ = b[5] - b[4] + 1;
   int IX = b[7] - b[6] + 1, IY = b[9] - b[8] + 1, IZ = b[11] - b[10] + 1;
-  if (full || IX <= 0 || IY <= 0 || IZ <= 0) IX = IY = IZ = 0;
+  if (IX <= 0 || IY <= 0 || IZ <= 0) IX = IY = IZ = 0;
   return LX * LY * LZ - IX * IY * IZ;
 }
 
@@ -211,14 +256,13 @@ __host__ __device__ inline int node_shell_count(const Grid& gr, const Groups& gp
 template <typename TC>
 __global__ void __launch_bounds__(128)
 k_build_aw(Grid gr, Groups gp, int nsplit, const double* __restrict__ Emod, const uint8_t* __restrict__ fixed,
-           const uint8_t* __restrict__ gfix, const long long* __restrict__ aw_off, ElemConsts<TC> K, TC* __restrict__ AW,
+           const int* __restrict__ gbox, const long long* __restrict__ aw_off, ElemConsts<TC> K, TC* __restrict__ AW,
            int* __restrict__ aw_node) {
   const int G = blockIdx.x, sp = blockIdx.y;
   int b[12];
-  node_shell_bounds(gr, gp, G, b);
-  const bool full = gfix && gfix[G];
+  node_shell_bounds(gr, gp, G, gbox ? gbox + 6 * G : nullptr, b);
   Shell sh;
-  sh.init(b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], b[8], b[9], b[10], b[11], full);
+  sh.init(b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], b[8], b[9], b[10], b[11], false);
   const int Gx = G % gp.ngx, Gy = (G / gp.ngx) % gp.ngy, Gz = G / (gp.ngx * gp.ngy);
   int ilo, ihi, jlo, jhi, klo, khi;
   group_range(Gx, gp.g, gp.ngx, gr.nx, ilo, ihi);
@@ -358,6 +402,37 @@ k_update(int ndof, int vs, T* __restrict__ x, T* __restrict__ r, T* __restrict__
   }
 }
 
+// (W^T r) sums of the nodes of group G in the node planes [kb, ke): each
+// thread takes node columns (i, j) of a 16-wide layout and marches along z, so
+// the node index advances by a plane stride and no division is needed.
+// Adds (sum r, sum (x - c) x r) into s[0..5]; r is zero on fixed DOFs.
+template <typename T, typename LDF>
+__device__ __forceinline__ void group_wtr_planes(const Grid& gr, const T* r, size_t off, int ilo, int ihi, int jlo,
+                                                 int jhi, int klo, int khi, int kb, int ke, T hh, T (&s)[12],
+                                                 LDF ld) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4, nty = blockDim.x >> 4;
+  const size_t plane = (size_t)gr.nnx * gr.nny;
+  for (int j = jlo + ty; j <= jhi; j += nty) {
+    const T ry = hh * (T)(2 * j - jlo - jhi);
+    for (int i = ilo + tx; i <= ihi; i += 16) {
+      const T rx = hh * (T)(2 * i - ilo - ihi);
+      const T* rp = r + off + 3 * ((size_t)i + (size_t)gr.nnx * j + plane * kb);
+      T rz = hh * (T)(2 * kb - klo - khi);
+      const T dz = hh * T(2);
+#pragma unroll 4
+      for (int k = kb; k < ke; ++k, rp += 3 * plane, rz += dz) {
+        const T r0 = ld(rp), r1 = ld(rp + 1), r2 = ld(rp + 2);
+        s[0] += r0;
+        s[1] += r1;
+        s[2] += r2;
+        s[3] += ry * r2 - rz * r1;
+        s[4] += rz * r0 - rx * r2;
+        s[5] += rx * r1 - ry * r0;
+      }
+    }
+  }
+}
+
 // Right-hand side of the coarse solve of the two-level preconditioner,
 //   v_G = (W^T r)_G - (W^T K z)_G,   (W^T K z)_G = (K W_G)^T z,
 // per (group, split, rhs): W^T r over the group's nodes, (K W_G)^T z over
@@ -384,22 +459,10 @@ k_coarse_rhs(Grid gr, Groups gp, int nsplit, const T* __restrict__ r, const T* _
 #pragma unroll
   for (int t = 0; t < 12; ++t) s[t] = T(0);
   {
-    const int lx = ihi - ilo + 1, ly = jhi - jlo + 1, lz = khi - klo + 1;
-    const int cnt = lx * ly * lz;
-    const int per = (cnt + nsplit - 1) / nsplit;
-    const int qb = sp * per, qe = min(qb + per, cnt);
-    for (int t = qb + threadIdx.x; t < qe; t += blockDim.x) {
-      const int i = ilo + t % lx, j = jlo + (t / lx) % ly, k = klo + t / (lx * ly);
-      const size_t d = off + 3 * (size_t)(i + gr.nnx * (j + gr.nny * k));
-      const T r0 = r[d], r1 = r[d + 1], r2 = r[d + 2];
-      const T rx = hh * (T)(2 * i - ilo - ihi), ry = hh * (T)(2 * j - jlo - jhi), rz = hh * (T)(2 * k - klo - khi);
-      s[0] += r0;
-      s[1] += r1;
-      s[2] += r2;
-      s[3] += ry * r2 - rz * r1;
-      s[4] += rz * r0 - rx * r2;
-      s[5] += rx * r1 - ry * r0;
-    }
+    const int lz = khi - klo + 1;
+    const int kper = (lz + nsplit - 1) / nsplit;
+    const int kb = klo + sp * kper, ke = min(kb + kper, khi + 1);
+    group_wtr_planes(gr, r, off, ilo, ihi, jlo, jhi, klo, khi, kb, ke, hh, s, [](const T* p) { return __ldg(p); });
   }
   {
     const long long base = aw_off[G];
@@ -440,14 +503,24 @@ k_coarse_rhs(Grid gr, Groups gp, int nsplit, const T* __restrict__ r, const T* _
   if (threadIdx.x == 0) gcount[(size_t)rhs * gp.ng + G] = 0u;
 }
 
-// gfix[G] = 1 when a node of group G has a fixed DOF.
-__global__ void k_group_fixed(Grid gr, Groups gp, const uint8_t* __restrict__ fixed, uint8_t* __restrict__ gfix) {
+// gbox[6G..6G+5] = bounding box (imin, imax, jmin, jmax, kmin, kmax) of the
+// nodes of group G with a fixed DOF; initialised to (INT_MAX, -1, ...) so that
+// an empty box has max < min.
+__global__ void k_group_fixed(Grid gr, Groups gp, const uint8_t* __restrict__ fixed, int* __restrict__ gbox) {
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gr.nnodes; n += gridDim.x * blockDim.x) {
     if (!fixed[n]) continue;
     const int i = n % gr.nnx, j = (n / gr.nnx) % gr.nny, k = n / (gr.nnx * gr.nny);
     const int G = group_of_axis(i, gp.g, gp.ngx) + gp.ngx * (group_of_axis(j, gp.g, gp.ngy) + gp.ngy * group_of_axis(k, gp.g, gp.ngz));
-    gfix[G] = 1;
+    int* bx = gbox + 6 * G;
+    atomicMin(bx + 0, i); atomicMax(bx + 1, i);
+    atomicMin(bx + 2, j); atomicMax(bx + 3, j);
+    atomicMin(bx + 4, k); atomicMax(bx + 5, k);
   }
+}
+
+__global__ void k_group_box_init(int ng, int* __restrict__ gbox) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 6 * ng; t += gridDim.x * blockDim.x)
+    gbox[t] = (t & 1) ? -1 : 0x7fffffff;
 }
 
 // W mu at node (i, j, k): t + omega x r of the node's group (zero on fixed DOFs).

@@ -85,29 +85,49 @@ struct StencilGeom2 {
   }
 };
 
-template <int TY, int MODE>
-__global__ void __launch_bounds__(ST_TX * TY, 16 / TY)
-stencil2_kernel(const StencilArgs<float, float> a) {
+// Load policies for the vectors the stencil reads: LoadRO for data that no
+// CTA of the running kernel writes (read-only cache path), LoadCG for data
+// written by other CTAs of the same (persistent) kernel, read from L2.
+struct LoadRO {
+  template <typename X>
+  __device__ __forceinline__ static X ld(const X* p) { return __ldg(p); }
+};
+struct LoadCG {
+  template <typename X>
+  __device__ __forceinline__ static X ld(const X* p) { return __ldcg(p); }
+};
+// Weak load cached in L1 (ld.global.ca): for data written by other CTAs
+// before a grid-wide barrier whose acquire fence orders it (never the
+// non-coherent path).
+struct LoadCA {
+  template <typename X>
+  __device__ __forceinline__ static X ld(const X* p) { return __ldca(p); }
+};
+
+// One CTA tile (tile = tile_x + tiles_x * tile_y, z chunk zc) of one RHS.
+// Returns this thread's partial sum (ST_RESIDUAL: y.y, ST_APPLY_DOT: p.Ap,
+// else 0) over the nodes it finishes.  beta: ST_APPLY_DOT's search-direction
+// coefficient.  Called by every thread of the CTA.
+template <int TY, int MODE, typename LD>
+__device__ __forceinline__ float stencil2_tile(const StencilArgs<float, float>& a, float beta, int tile, int zc,
+                                               int rhs) {
   // Exchange buffers (each written, then read after a barrier; the other
   // exchange's barrier separates that read from the next write):
   //   xe: (S, D) x-edge values of row jb for the warp below, per component
   //   ye: (mx = 0, 1) forces of element B on row jb + 2, for the warp above
   __shared__ float2 xe[3][TY][ST_TX];
   __shared__ float2 ye[3][TY][ST_TX];
-  __shared__ double red[32];
 
-  const int rhs = blockIdx.z;
-  if (a.done && a.done[rhs]) return;
   const Grid gr = a.gr;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int tile_x = blockIdx.x % a.tiles_x;
-  const int tile_y = blockIdx.x / a.tiles_x;
+  const int tile_x = tile % a.tiles_x;
+  const int tile_y = tile / a.tiles_x;
   const int i = tile_x * (ST_TX - 2) - 1 + lane;
   const int jb = tile_y * StencilGeom2<TY>::ROWS - 1 + 2 * w;   // row a = 0; row a = 1 is jb + 1
-  const int k0 = blockIdx.y * a.kz;
+  const int k0 = zc * a.kz;
   const int k1 = min(k0 + a.kz, gr.nnz);
   const size_t voff = (size_t)rhs * gr.vs;
-  const float* __restrict__ u = a.u + voff;
+  const float* u = a.u + voff;
 
   const bool ci = i >= 0 && i < gr.nnx;
   const bool col0 = ci && jb >= 0 && jb < gr.nny;
@@ -123,7 +143,6 @@ stencil2_kernel(const StencilArgs<float, float> a) {
   // ST_APPLY_DOT, which the solver always launches with z); the two rows may
   // lie in different groups along y, so A and B are per row.
   constexpr bool formp = MODE == ST_APPLY_DOT;
-  const float beta = formp ? (float)a.st[rhs].beta : 0.f;
   const Groups gp = a.gp;
   const float hh = (float)(0.5 * gp.h);
   float rx = 0.f, ry0 = 0.f, ry1 = 0.f;
@@ -152,10 +171,10 @@ stencil2_kernel(const StencilArgs<float, float> a) {
     const int gzo = gp.ngx * gp.ngy * gz;
     const double* m0 = murhs + 6 * (gxy0 + gzo);
     const double* m1 = murhs + 6 * (gxy1 + gzo);
-    const float tx0 = (float)m0[0], ty0 = (float)m0[1], tz0 = (float)m0[2];
-    const float ox0 = (float)m0[3], oy0 = (float)m0[4], oz0 = (float)m0[5];
-    const float tx1 = (float)m1[0], ty1 = (float)m1[1], tz1 = (float)m1[2];
-    const float ox1 = (float)m1[3], oy1 = (float)m1[4], oz1 = (float)m1[5];
+    const float tx0 = (float)LD::ld(m0), ty0 = (float)LD::ld(m0 + 1), tz0 = (float)LD::ld(m0 + 2);
+    const float ox0 = (float)LD::ld(m0 + 3), oy0 = (float)LD::ld(m0 + 4), oz0 = (float)LD::ld(m0 + 5);
+    const float tx1 = (float)LD::ld(m1), ty1 = (float)LD::ld(m1 + 1), tz1 = (float)LD::ld(m1 + 2);
+    const float ox1 = (float)LD::ld(m1 + 3), oy1 = (float)LD::ld(m1 + 4), oz1 = (float)LD::ld(m1 + 5);
     A0 = make_float2(tx0 - oz0 * ry0, tx1 - oz1 * ry1);
     A1 = make_float2(ty0 + oz0 * rx, ty1 + oz1 * rx);
     A2 = make_float2(tz0 + (ox0 * ry0 - oy0 * rx), tz1 + (ox1 * ry1 - oy1 * rx));
@@ -170,28 +189,28 @@ stencil2_kernel(const StencilArgs<float, float> a) {
     if (k < 0 || k >= gr.nnz) return;
     const int n0 = i + gr.nnx * (jb + gr.nny * k);
     const int n1 = n0 + gr.nnx;
-    const unsigned f0 = (col0 && a.fixed) ? a.fixed[n0] : 0u;
-    const unsigned f1 = (col1 && a.fixed) ? a.fixed[n1] : 0u;
+    const unsigned f0 = (col0 && a.fixed) ? __ldg(a.fixed + n0) : 0u;
+    const unsigned f1 = (col1 && a.fixed) ? __ldg(a.fixed + n1) : 0u;
     fbits = f0 | (f1 << 8);
     float p0[3] = {0.f, 0.f, 0.f}, p1[3] = {0.f, 0.f, 0.f};
     if (col0) {
       const float* q = u + 3 * (size_t)n0;
-      p0[0] = q[0]; p0[1] = q[1]; p0[2] = q[2];
+      p0[0] = LD::ld(q); p0[1] = LD::ld(q + 1); p0[2] = LD::ld(q + 2);
     }
     if (col1) {
       const float* q = u + 3 * (size_t)n1;
-      p1[0] = q[0]; p1[1] = q[1]; p1[2] = q[2];
+      p1[0] = LD::ld(q); p1[1] = LD::ld(q + 1); p1[2] = LD::ld(q + 2);
     }
     if constexpr (formp) {
       if (k >= gz_next || gz < 0) refresh_group(k);
       float z0[3] = {0.f, 0.f, 0.f}, z1[3] = {0.f, 0.f, 0.f};
       if (col0) {
         const float* q = a.z + voff + 3 * (size_t)n0;
-        z0[0] = q[0]; z0[1] = q[1]; z0[2] = q[2];
+        z0[0] = LD::ld(q); z0[1] = LD::ld(q + 1); z0[2] = LD::ld(q + 2);
       }
       if (col1) {
         const float* q = a.z + voff + 3 * (size_t)n1;
-        z1[0] = q[0]; z1[1] = q[1]; z1[2] = q[2];
+        z1[0] = LD::ld(q); z1[1] = LD::ld(q + 1); z1[2] = LD::ld(q + 2);
       }
       const float2 rz = bc2(hh * (float)(2 * k - zlo - zhi)), bt = bc2(beta);
       v[0] = fma2(bt, make_float2(p0[0], p1[0]), add2(make_float2(z0[0], z1[0]), fma2(rz, B0, A0)));
@@ -259,8 +278,8 @@ stencil2_kernel(const StencilArgs<float, float> a) {
     float2 E = bc2(0.f);
     if (l >= 0 && l < gr.nz) {
       const int e0 = i + gr.nx * (jb + gr.ny * l);
-      if (elA) E.x = a.E[e0];
-      if (elB) E.y = a.E[e0 + gr.nx];
+      if (elA) E.x = __ldg(a.E + e0);
+      if (elB) E.y = __ldg(a.E + e0 + gr.nx);
     }
     if (l + 2 <= k1) load_node(l + 2, un, fnext);
 
@@ -328,7 +347,7 @@ stencil2_kernel(const StencilArgs<float, float> a) {
           const bool fx = (fb >> c) & 1u;
           float out;
           if (MODE == ST_RESIDUAL) {
-            out = fx ? 0.f : a.f[voff + 3 * (size_t)n + c] - yc;
+            out = fx ? 0.f : __ldg(a.f + voff + 3 * (size_t)n + c) - yc;
             part += out * out;
             if (a.y32) a.y32[voff + 3 * (size_t)n + c] = out;
           } else {
@@ -350,6 +369,17 @@ stencil2_kernel(const StencilArgs<float, float> a) {
     ucur[2] = u_l1[2];
     fcur = f_l1;
   }
+  return MODE == ST_APPLY ? 0.f : part;
+}
+
+template <int TY, int MODE>
+__global__ void __launch_bounds__(ST_TX * TY, 16 / TY)
+stencil2_kernel(const StencilArgs<float, float> a) {
+  __shared__ double red[32];
+  const int rhs = blockIdx.z;
+  if (a.done && a.done[rhs]) return;
+  const float beta = MODE == ST_APPLY_DOT ? (float)a.st[rhs].beta : 0.f;
+  const float part = stencil2_tile<TY, MODE, LoadRO>(a, beta, blockIdx.x, blockIdx.y, rhs);
   if (MODE != ST_APPLY) {
     float pv[1] = {part};
     double o[1];

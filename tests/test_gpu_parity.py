@@ -139,6 +139,32 @@ def test_mixed_solve_matches_oracle(case):
     m.close()
 
 
+@pytest.mark.parametrize("n_rhs", [1, 3])
+def test_persistent_and_graph_inner_solvers_agree(n_rhs):
+    """The cooperative persistent inner DPCG and the CUDA-graph chunks run the
+    same iteration (Sec. 3.5): both reach the tolerance, agree with the direct
+    solve, and take nearly the same number of iterations."""
+    w = small_cantilever(40, 20, 12, seed=5, n_spheres=8, rmin=1.5, rmax=4.0, group=4, n_rhs=n_rhs)
+    K = fe.assemble(w.nx, w.ny, w.nz, w.E)
+    out = {}
+    for pers in (1, 0):
+        m = afd.Mesh(w.nx, w.ny, w.nz, group=w.group, persistent=pers)
+        m.set_element_moduli(w.E)
+        m.set_loads_bcs(w.f, w.fixed)
+        u = np.zeros_like(w.f)
+        st = m.solve(1e-9, u_out=u)
+        out[pers] = (u, st)
+        m.close()
+    for r in range(n_rhs):
+        uref = fe.solve_direct(K, w.f[r], w.fixed)
+        for pers in (1, 0):
+            u, st = out[pers]
+            assert st[r]["rel_residual"] <= 1e-9
+            assert np.linalg.norm(u[r] - uref) <= 1e-6 * np.linalg.norm(uref)
+        i1, i0 = out[1][1][r]["iters"], out[0][1][r]["iters"]
+        assert abs(i1 - i0) <= max(2, i0 // 50), (i1, i0)
+
+
 def test_multi_rhs_batch_equals_single_solves():
     nx, ny, nz = 20, 10, 8
     E = sphere_voids(nx, ny, nz, 5, 1.5, 3.0, 4, 1e-3)
