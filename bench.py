@@ -524,22 +524,45 @@ def launch_summary(path: str):
         print(f"{k[:60]:60s} {c:8d} {t:10.1f} {t / total:7.1%}")
 
 
-def profile_stencil(n: int, launches: int):
+def profile_stencil(n: int, launches: int, warps: int = 0, planes: int = 0):
     """Apply K u on an n x n/2 x n/2 all-solid mesh (FP32, one RHS) `launches`
-    times: a case larger than L2 for ncu captures of the stencil kernel."""
+    times, in the CTA shape given (0 = the size heuristic): a case for ncu
+    captures of the stencil kernel (n >= 320 is larger than L2)."""
     import torch
 
     import paper_2203_15115_gb300 as afd
 
     nx, ny, nz = n, n // 2, n // 2
-    mesh = afd.Mesh(nx, ny, nz)
+    mesh = afd.Mesh(nx, ny, nz, stencil_warps=warps, stencil_planes=planes)
     mesh.set_element_moduli(np.ones(nx * ny * nz))
     u = torch.randn((1, mesh.ndof), dtype=torch.float32, device="cuda")
     y = torch.empty_like(u)
     ms = afd.afd_time_stiffness(mesh.h, afd.AFD_F32, 1, u, y, launches)
     nn = (nx + 1) * (ny + 1) * (nz + 1)
     b = 2 * 3 * nn * 4 + 4 * nx * ny * nz + nn
-    print(json.dumps({"mesh": [nx, ny, nz], "ms": ms, "GB/s": b / (ms * 1e-3) / 1e9, "bytes": b}))
+    print(json.dumps({"mesh": [nx, ny, nz], "ms": ms, "GB/s": b / (ms * 1e-3) / 1e9, "bytes": b,
+                      "warps": afd.afd_stencil_warps(mesh.h), "planes": afd.afd_stencil_depth(mesh.h)}))
+    mesh.close()
+
+
+def profile_solve(warps: int, planes: int, solves: int):
+    """`solves` mixed solves of the 128x64x64 voided cantilever with the FP32
+    stencil in a pinned CTA shape (no autotuning): the solver's kernels in
+    their solve-time configuration, for ncu captures."""
+    import torch
+
+    import paper_2203_15115_gb300 as afd
+    from synthetic import cantilever_128x64x64_voids
+
+    w = cantilever_128x64x64_voids()
+    mesh = afd.Mesh(w.nx, w.ny, w.nz, group=w.group, stencil_warps=warps or 8, stencil_planes=planes or 6)
+    mesh.set_loads_bcs(w.f, w.fixed)
+    for _ in range(solves):
+        mesh.set_element_moduli(w.E)
+        st = mesh.solve(w.tol)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": w.name, "iters": st[0]["iters"], "rel_residual": st[0]["rel_residual"],
+                      "warps": afd.afd_stencil_warps(mesh.h), "planes": afd.afd_stencil_depth(mesh.h)}))
     mesh.close()
 
 
@@ -555,11 +578,17 @@ def main():
     ap.add_argument("--profile-stencil", type=int, default=0, metavar="NX",
                     help="only time the FP32 stencil on an NX x NX/2 x NX/2 mesh (for ncu)")
     ap.add_argument("--launch-summary", metavar="CSV", help="summarise an ncu launch list of one timed step")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="only run --steps mixed solves of the 128x64x64 workload in a pinned stencil shape (for ncu)")
+    ap.add_argument("--stencil-warps", type=int, default=0, help="pinned FP32 stencil warps per CTA (profile modes)")
+    ap.add_argument("--stencil-planes", type=int, default=0, help="pinned FP32 stencil planes per CTA (profile modes)")
     args = ap.parse_args()
     if args.launch_summary:
         launch_summary(args.launch_summary)
     elif args.profile_stencil:
-        profile_stencil(args.profile_stencil, max(1, args.steps))
+        profile_stencil(args.profile_stencil, max(1, args.steps), args.stencil_warps, args.stencil_planes)
+    elif args.profile_solve:
+        profile_solve(args.stencil_warps, args.stencil_planes, max(1, args.steps))
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -74,6 +74,12 @@ typedef struct {
   int persistent;     /* AFD_MIXED inner solves: 0 (default) CUDA-graph chunks of check_every iterations,
                          one kernel per phase; 1 one cooperatively launched persistent kernel per inner
                          solve with grid-wide barriers between its phases (afd_solver_phase_times) */
+  int stencil_warps;  /* FP32 stencil CTA: 8 or 16 warps; 0 (default) = chosen by the autotuner/heuristic */
+  int stencil_planes; /* FP32 stencil: node planes per CTA (>= 1); 0 (default) = autotuner/heuristic.
+                         When both are set the autotuner does not run. */
+  int pdl;            /* 1: the kernels of a captured DPCG iteration chunk use programmatic dependent launch
+                         (each may be scheduled while its predecessor finishes its reductions); 0 (default):
+                         plain stream order, measured faster on the 128x64x64 workload */
 } afd_options;
 
 typedef struct {
@@ -194,6 +200,18 @@ int afd_stencil_depth(const afd_mesh* m);
 /* Warps per CTA of the FP32 stiffness kernel (8 or 16; each warp owns two node
  * rows, a CTA finishes 2 * warps - 2 of them); chosen with the depth. */
 int afd_stencil_warps(const afd_mesh* m);
+
+/* Measurement aid for the CUDA-graph inner solver: continues the last FP32
+ * inner DPCG iteration of a completed AFD_MIXED solve for `iters` iterations
+ * (no stopping test; the solution u is not touched), launching its kernels
+ * one by one with CUDA events between them on the mesh's stream.  us_out5 =
+ * mean microseconds per iteration of the stencil, the vector update, the
+ * coarse right-hand side, the coarse step, and (variant 1) the separate
+ * search-direction kernel.  variant 0: the stencil forms p = z + W mu +
+ * beta p_old as it loads it; variant 1: k_prolong forms p first and the
+ * stencil reads it.  nsplit > 0 times the coarse right-hand side with that
+ * many shares per group (0: the mesh's own).  Host output. */
+int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, double* us_out5);
 
 /* Measurement aid for the persistent inner solver (opt.persistent), as seen
  * by its CTA 0 and summed over all iterations since the last reset, in ms:

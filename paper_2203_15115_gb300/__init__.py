@@ -40,7 +40,7 @@ EXPORTS = [
     "afd_deflation_wt", "afd_deflation_w", "afd_coarse_size", "afd_coarse_matrix", "afd_select_topk",
     "afd_ndof", "afd_nelem", "afd_destroy", "afd_last_error", "afd_al_init", "afd_al_update", "afd_al_weight",
     "afd_time_stiffness", "afd_kernel_launches", "afd_select_topk_noalloc", "afd_stencil_depth",
-    "afd_stencil_warps", "afd_solver_phase_times",
+    "afd_stencil_warps", "afd_solver_phase_times", "afd_time_dpcg_kernels",
     "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
 ]
 
@@ -49,7 +49,8 @@ class afd_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("group", ctypes.c_int), ("nu", ctypes.c_double),
                 ("h", ctypes.c_double), ("e_void", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("persistent", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("persistent", ctypes.c_int), ("stencil_warps", ctypes.c_int),
+                ("stencil_planes", ctypes.c_int), ("pdl", ctypes.c_int)]
 
 
 class afd_stats(ctypes.Structure):
@@ -115,6 +116,7 @@ def lib() -> ctypes.CDLL:
             "afd_stencil_depth": (i, [vp]),
             "afd_stencil_warps": (i, [vp]),
             "afd_solver_phase_times": (i, [vp, ctypes.POINTER(ctypes.c_double), i]),
+            "afd_time_dpcg_kernels": (i, [vp, i, i, i, ctypes.POINTER(ctypes.c_double)]),
             "afd_mesh_bytes": (ctypes.c_size_t, [i, i, i, i, ctypes.POINTER(afd_options)]),
             "afd_server_create": (i, [ctypes.POINTER(afd_server_config), ctypes.POINTER(vp)]),
             "afd_server_submit": (i, [vp, i, i, i, vp, vp, vp, d, ctypes.POINTER(i64)]),
@@ -299,6 +301,13 @@ def afd_stencil_depth(mesh) -> int:
 
 def afd_stencil_warps(mesh) -> int:
     return int(lib().afd_stencil_warps(mesh))
+
+
+def afd_time_dpcg_kernels(mesh, iters: int = 50, nsplit: int = 0, variant: int = 0) -> dict:
+    out = (ctypes.c_double * 5)()
+    _check(lib().afd_time_dpcg_kernels(mesh, iters, nsplit, variant, out))
+    return {"stencil_us": out[0], "update_us": out[1], "coarse_rhs_us": out[2], "coarse_step_us": out[3],
+            "prolong_us": out[4]}
 
 
 def afd_solver_phase_times(mesh, reset: bool = True) -> dict:

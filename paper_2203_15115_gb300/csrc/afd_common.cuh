@@ -183,6 +183,17 @@ __device__ __forceinline__ void hex8_apply(T (&u)[3][8], T E, const ElemConsts<T
 }
 
 // ----------------------------------------------------------------------------
+// Programmatic dependent launch (sm_90+): a kernel launched with the
+// programmatic-serialization attribute may start while its predecessor in the
+// stream is finishing.  pdl_release() lets the successor start launching once
+// every CTA of this grid has begun; pdl_acquire() waits until the predecessor
+// grid has completed and its writes are visible.  Both are no-ops for a
+// normal launch.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_acquire() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// ----------------------------------------------------------------------------
 // Reductions.  Values are summed per thread in the working type, combined
 // across the warp in the working type, and across warps and blocks in FP64 in
 // a fixed order (deterministic).

@@ -100,6 +100,7 @@ struct afd_mesh {
   int kz = 8;                  // node planes per CTA of the FP64 stencil
   int kz32 = 8, ty32 = 16;     // planes per CTA and warps per CTA of the FP32 stencil
   bool tuned = false;          // autotuner has chosen kz32 / ty32 for this mesh
+  bool pdl_now = false;        // launches being captured use programmatic dependent launch
   // state
   double* E64 = nullptr;
   uint8_t* fixed = nullptr;   // per node bits
@@ -122,6 +123,7 @@ struct afd_mesh {
   // coarse
   int nc = 0;
   int nsplit = 1;              // slabs per group in the coarse right-hand side
+  size_t cpart_cap = 0;        // doubles allocated in cpart
   double* Ec = nullptr;        // W^T K W, FP64 sums
   double* Einv64 = nullptr;    // its inverse, FP64 path
   float* Einv32 = nullptr;     // its inverse, mixed path
@@ -188,6 +190,25 @@ constexpr int FS_WEIGHTS = FS_MAXV + MAX_RHS;
 constexpr int FS_PARTS = FS_WEIGHTS + MAX_RHS;
 constexpr int FS_MAX_BLOCKS = RED_BLOCKS / 2;
 constexpr int FSMALL_SIZE = FS_PARTS + MAX_RHS * FS_MAX_BLOCKS;
+
+// Kernel launch with programmatic dependent launch (pdl = true) or a plain
+// stream-ordered launch; the kernels call pdl_release()/pdl_acquire().
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_ex(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args... args) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 static int grid_blocks(size_t n, int threads = 256, int cap = RED_BLOCKS) {
   size_t b = (n + threads - 1) / threads;
@@ -261,15 +282,15 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
   stencil_geom(m, F64, a.tiles_x, grid);
   grid.z = nrhs;
   if constexpr (F64) {
-    stencil_kernel<T, TY64, MODE, TF><<<grid, ST_TX * TY64, 0, m->s>>>(a);
+    CK(launch_ex(m->pdl_now, stencil_kernel<T, TY64, MODE, TF>, grid, dim3(ST_TX * TY64), 0, m->s, a));
   } else {
     static_assert(std::is_same<TF, float>::value, "the FP32 stencil takes FP32 right-hand sides");
     // the packed FP32 kernel forms p in ST_APPLY_DOT only, and always there
     if ((MODE == ST_APPLY_DOT) != (z != nullptr)) return fail(AFD_ERR_INVALID_ARG, "stencil mode / z mismatch");
     if (m->ty32 == 8)
-      stencil2_kernel<8, MODE><<<grid, ST_TX * 8, 0, m->s>>>(a);
+      CK(launch_ex(m->pdl_now, stencil2_kernel<8, MODE>, grid, dim3(ST_TX * 8), 0, m->s, a));
     else
-      stencil2_kernel<16, MODE><<<grid, ST_TX * 16, 0, m->s>>>(a);
+      CK(launch_ex(m->pdl_now, stencil2_kernel<16, MODE>, grid, dim3(ST_TX * 16), 0, m->s, a));
   }
   m->launches++;
   CK(cudaGetLastError());
@@ -309,7 +330,8 @@ static int ensure_rhs(afd_mesh* m, int nrhs) {
   TRY(dalloc(&m->v, (size_t)nrhs * m->nc)); TRY(dalloc(&m->mu, (size_t)nrhs * m->nc));
   TRY(dalloc(&m->wr, (size_t)nrhs * m->nc));
   dfree(m->cpart); dfree(m->grec); dfree(m->gcount); dfree(m->upart);
-  TRY(dalloc(&m->cpart, (size_t)nrhs * m->gp.ng * m->nsplit * 12));
+  m->cpart_cap = (size_t)nrhs * m->gp.ng * m->nsplit * 12;
+  TRY(dalloc(&m->cpart, m->cpart_cap));
   TRY(dalloc(&m->grec, (size_t)nrhs * m->gp.ng * 12));
   TRY(dalloc(&m->upart, (size_t)nrhs * RED_BLOCKS * 2));
   TRY(dalloc(&m->gcount, (size_t)nrhs * m->gp.ng));
@@ -409,6 +431,17 @@ static int build_coarse(afd_mesh* m) {
   return AFD_OK;
 }
 
+static int ensure_cpart(afd_mesh* m, int nsplit) {
+  const size_t need = (size_t)std::max(m->cap, 1) * m->gp.ng * nsplit * 12;
+  if (need <= m->cpart_cap) return AFD_OK;
+  invalidate_graphs(m);
+  dfree(m->cpart);
+  m->cpart_cap = 0;
+  TRY(dalloc(&m->cpart, need));
+  m->cpart_cap = need;
+  return AFD_OK;
+}
+
 // Stencil autotuner: the FP32 stencil's CTA shape (8 or 16 warps, i.e. 14 or
 // 30 finished node rows) and z depth trade redundant halo rows and element
 // layers against the number of CTAs (waves over the SMs).  Each candidate is
@@ -417,8 +450,13 @@ static int build_coarse(afd_mesh* m) {
 static int autotune_stencil(afd_mesh* m) {
   TRY(ensure_work(m, m->w32, 1));
   const Grid& g = m->gr;
-  static const int cand_kz[] = {2, 3, 4, 5, 6, 8, 12, 16, 24, 32};
-  static const int cand_ty[] = {8, 16};
+  static const int all_kz[] = {2, 3, 4, 5, 6, 8, 12, 16, 24, 32};
+  static const int all_ty[] = {8, 16};
+  // a shape the caller pinned (opt.stencil_warps / stencil_planes) is kept
+  const std::vector<int> cand_kz = m->opt.stencil_planes ? std::vector<int>{m->kz32}
+                                                         : std::vector<int>(all_kz, all_kz + 10);
+  const std::vector<int> cand_ty = m->opt.stencil_warps ? std::vector<int>{m->opt.stencil_warps}
+                                                        : std::vector<int>(all_ty, all_ty + 2);
   size_t maxp = 0;
   for (int ty : cand_ty)
     for (int kz : cand_kz) {
@@ -436,7 +474,7 @@ static int autotune_stencil(afd_mesh* m) {
   int best_kz = m->kz32, best_ty = m->ty32;
   for (int ty : cand_ty)
     for (int kz : cand_kz) {
-      if (kz > g.nnz && kz != cand_kz[0]) continue;
+      if (kz > g.nnz && kz != cand_kz.front()) continue;
       m->ty32 = ty;
       m->kz32 = kz;
       TRY((launch_stencil<float, ST_APPLY, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr, nullptr, nullptr,
@@ -463,6 +501,52 @@ static int autotune_stencil(afd_mesh* m) {
   invalidate_graphs(m);  // captured launches bake in the grid
   return AFD_OK;
 }
+
+// Shares per group of the coarse right-hand side: fewer shares amortise the
+// per-block 12-value reduction, more shares shorten each block's load chain.
+// Timed like the stencil (3 launches after one warm-up, one RHS, FP32) on the
+// mesh's own shells; needs the coarse data (build_coarse) in place.
+static int autotune_coarse_split(afd_mesh* m) {
+  TRY(ensure_work(m, m->w32, 1));
+  const Grid& g = m->gr;
+  static const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16};
+  CK(cudaMemsetAsync(m->w32.r, 0, (size_t)g.vs * sizeof(float), m->s));
+  CK(cudaMemsetAsync(m->w32.z, 0, (size_t)g.vs * sizeof(float), m->s));
+  CGState st0;
+  memset(&st0, 0, sizeof(st0));
+  CK(cudaMemcpyAsync(m->st, &st0, sizeof(CGState), cudaMemcpyHostToDevice, m->s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_ns = m->nsplit;
+  for (int ns : cand) {
+    if (ns > m->gp.g) break;
+    TRY(ensure_cpart(m, ns));
+    const dim3 ug(m->gp.ng, ns, 1);
+    for (int rep = 0; rep < 4; ++rep) {
+      if (rep == 1) CK(cudaEventRecord(e0, m->s));
+      k_coarse_rhs<float><<<ug, 256, 0, m->s>>>(g, m->gp, ns, m->w32.r, m->w32.z, m->aw_off, m->aw_node, m->w32.AW,
+                                               m->cpart, m->grec, m->gcount, m->st);
+      m->launches++;
+    }
+    CK(cudaEventRecord(e1, m->s));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaGetLastError());
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_ns = ns;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->nsplit = best_ns;
+  invalidate_graphs(m);
+  return AFD_OK;
+}
+
 
 // ---------------------------------------------------------------------------
 // FP32 inner DPCG iterations as one cooperative persistent kernel
@@ -627,11 +711,17 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
       T* pnew = P[(it + 1) & 1];
       TRY((launch_stencil<T, ST_APPLY_DOT, TB>(m, pold, w.q, w.E, nullptr, nullptr, m->partials, m->done, nrhs, w.K,
                                                 m->st, cnt_st, w.z, m->mu, pnew)));
-      k_update<T><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, x, w.r, w.z, pnew, w.q, w.invd, m->upart, m->st); m->launches++;
-      k_coarse_rhs<T><<<ug, 256, 0, m->s>>>(gr, m->gp, m->nsplit, w.r, w.z, m->aw_off, m->aw_node, w.AW, m->cpart,
-                                           m->grec, m->gcount, m->st); m->launches++;
-      k_coarse_step<T><<<crows, 256, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->grec, m->wr, 1, m->done, cnt_co,
-                                                   m->upart, RED_BLOCKS); m->launches++;
+      const bool pdl = m->pdl_now;
+      CK(launch_ex(pdl, k_update<T>, vg, dim3(RED_THREADS), 0, m->s, gr.ndof, gr.vs, x, w.r, w.z, (const T*)pnew,
+                   (const T*)w.q, (const T*)w.invd, m->upart, (const CGState*)m->st));
+      m->launches++;
+      CK(launch_ex(pdl, k_coarse_rhs<T>, ug, dim3(256), 0, m->s, gr, m->gp, m->nsplit, (const T*)w.r, (const T*)w.z,
+                   (const long long*)m->aw_off, (const int*)m->aw_node, (const T*)w.AW, m->cpart, m->grec, m->gcount,
+                   (const CGState*)m->st));
+      m->launches++;
+      CK(launch_ex(pdl, k_coarse_step<T>, dim3(crows), dim3(256), csmem, m->s, m->nc, nrhs, (const T*)Einv, m->mu,
+                   m->st, (const double*)m->grec, m->wr, 1, m->done, cnt_co, (const double*)m->upart, (int)RED_BLOCKS));
+      m->launches++;
     }
     CK(cudaGetLastError());
     return AFD_OK;
@@ -645,7 +735,9 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
     cudaGraph_t graph;
     const int64_t before = m->launches;
     CK(cudaStreamBeginCapture(m->s, cudaStreamCaptureModeThreadLocal));
+    m->pdl_now = m->opt.pdl != 0;
     int rc = enqueue_chunk();
+    m->pdl_now = false;
     w.graph_kernels = m->launches - before;  // captured, not run
     m->launches = before;
     cudaError_t e = cudaStreamEndCapture(m->s, &graph);
@@ -690,6 +782,9 @@ void afd_default_options(afd_options* o) {
   o->check_every = 16;
   o->autotune = 1;
   o->persistent = 0;
+  o->stencil_warps = 0;
+  o->stencil_planes = 0;
+  o->pdl = 0;
 }
 
 const char* afd_last_error(void) { return g_err.c_str(); }
@@ -709,7 +804,8 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
   if (opt) o = *opt;
   o.check_every += o.check_every & 1;  // p is double-buffered: chunks of even length
   if (!(o.nu > -1.0 && o.nu < 0.5) || !(o.h > 0.0) || !(o.e_void > 0.0) || o.max_iter < 1 || o.max_refine < 0 ||
-      o.check_every < 1 || o.group < 0 || (o.precision != AFD_MIXED && o.precision != AFD_FP64))
+      o.check_every < 1 || o.group < 0 || (o.precision != AFD_MIXED && o.precision != AFD_FP64) ||
+      (o.stencil_warps != 0 && o.stencil_warps != 8 && o.stencil_warps != 16) || o.stencil_planes < 0)
     return fail(AFD_ERR_INVALID_ARG, "invalid options");
   afd_mesh* m = new afd_mesh();
   m->opt = o;
@@ -732,7 +828,7 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
   m->nc = 6 * gp.ng;
   // shares per group of the merged update / coarse right-hand side kernel
   // (about 600 blocks) and of the K W build (about 2400 blocks of 128 threads)
-  m->nsplit = std::max(1, std::min(gp.g, (1200 + gp.ng - 1) / gp.ng));
+  m->nsplit = std::max(1, std::min(gp.g, (512 + gp.ng - 1) / gp.ng));
   m->nsplit_aw = std::max(1, std::min(16 * gp.g, (2400 + gp.ng - 1) / gp.ng));
   if (m->nc > 8192) {
     delete m;
@@ -750,6 +846,9 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
     // about two waves of 512-thread FP32 CTAs (1 resident per SM)
     kz = (long)g.nnz * gr.x / 304;
     m->kz32 = (int)std::max(4L, std::min<long>(kz, g.nnz));
+    if (o.stencil_warps) m->ty32 = o.stencil_warps;
+    if (o.stencil_planes) m->kz32 = std::min(o.stencil_planes, g.nnz);
+    if (o.stencil_warps && o.stencil_planes) m->tuned = true;   // pinned: nothing to tune
   }
   m->w32.K = make_elem_consts<float>(o.nu, o.h);
   m->w64.K = make_elem_consts<double>(o.nu, o.h);
@@ -970,7 +1069,10 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
   const int R = m->nrhs;
   const Grid& g = m->gr;
   TRY(build_coarse(m));
-  if (m->opt.autotune && !m->tuned && m->opt.precision == AFD_MIXED) TRY(autotune_stencil(m));
+  if (m->opt.autotune && !m->tuned && m->opt.precision == AFD_MIXED) {
+    TRY(autotune_stencil(m));
+    TRY(autotune_coarse_split(m));
+  }
   if (!warm_start || !m->has_solution) CK(cudaMemsetAsync(m->u64, 0, (size_t)R * g.vs * sizeof(double), m->s));
   std::vector<int> iters(R, 0), status(R, AFD_OK), refine(R, 0);
   std::vector<double> rel;
@@ -1327,6 +1429,95 @@ int64_t afd_kernel_launches(const afd_mesh* m) { return m ? m->launches : 0; }
 int afd_stencil_depth(const afd_mesh* m) { return m ? m->kz32 : 0; }
 
 int afd_stencil_warps(const afd_mesh* m) { return m ? m->ty32 : 0; }
+
+int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, double* us_out5) {
+  if (!m || !us_out5 || iters < 1 || nsplit < 0 || nsplit > 64 || variant < 0 || variant > 1)
+    return fail(AFD_ERR_INVALID_ARG, "bad argument");
+  if (!m->has_solution || m->opt.precision != AFD_MIXED || !m->w32.x || !m->coarse_valid)
+    return fail(AFD_ERR_STATE, "needs a completed AFD_MIXED solve on this mesh");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const int R = m->nrhs;
+  const Grid& gr = m->gr;
+  const int keep_split = m->nsplit;
+  if (nsplit > 0) {
+    TRY(ensure_cpart(m, nsplit));
+    m->nsplit = nsplit;
+  }
+  // continue the last inner iteration without a stopping test
+  std::vector<CGState> h(R);
+  CK(cudaMemcpyAsync(h.data(), m->st, R * sizeof(CGState), cudaMemcpyDeviceToHost, m->s));
+  CK(cudaStreamSynchronize(m->s));
+  std::vector<int> hd(R, 0);
+  for (int r = 0; r < R; ++r) {
+    h[r].done = 0;
+    h[r].status = 0;
+    h[r].target2 = -1.0;
+    h[r].max_iters = 1 << 30;
+    if (!(h[r].rz > 0.0)) h[r].rz = 1.0;
+  }
+  CK(cudaMemcpyAsync(m->st, h.data(), R * sizeof(CGState), cudaMemcpyHostToDevice, m->s));
+  CK(cudaMemcpyAsync(m->done, hd.data(), R * sizeof(int), cudaMemcpyHostToDevice, m->s));
+  Work<float>& w = m->w32;
+  const dim3 vg(RED_BLOCKS, R);
+  const dim3 ug(m->gp.ng, m->nsplit, R);
+  const int crows = (m->nc * 32 + 255) / 256;
+  const size_t csmem = (size_t)m->nc * sizeof(double);
+  unsigned int* cnt_st = m->counters;
+  unsigned int* cnt_co = m->counters + MAX_RHS;
+  float* P[2] = {w.p, w.t};
+  const dim3 pg(grid_blocks(gr.nnodes, 256, 4 * RED_BLOCKS), R);
+  cudaEvent_t ev[6];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  double acc[5] = {0, 0, 0, 0, 0};
+  int rc = AFD_OK;
+  for (int it = 0; it < iters && rc == AFD_OK; ++it) {
+    float* pold = P[it & 1];
+    float* pnew = P[(it + 1) & 1];
+    cudaEventRecord(ev[5], m->s);
+    if (variant == 1) {  // p = beta p + z + W mu in place, then the plain p.Kp stencil
+      k_prolong<float><<<pg, 256, 0, m->s>>>(0, gr, m->gp, P[0], w.z, m->mu, m->fixed, m->st);
+      m->launches++;
+      pnew = P[0];
+    }
+    cudaEventRecord(ev[0], m->s);
+    if (variant == 1)
+      rc = launch_stencil<float, ST_DOT_PLAIN, float>(m, pnew, w.q, w.E, nullptr, nullptr, m->partials, m->done, R,
+                                                     w.K, m->st, cnt_st);
+    else
+      rc = launch_stencil<float, ST_APPLY_DOT, float>(m, pold, w.q, w.E, nullptr, nullptr, m->partials, m->done, R,
+                                                     w.K, m->st, cnt_st, w.z, m->mu, pnew);
+    cudaEventRecord(ev[1], m->s);
+    k_update<float><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, w.x, w.r, w.z, pnew, w.q, w.invd, m->upart, m->st);
+    cudaEventRecord(ev[2], m->s);
+    k_coarse_rhs<float><<<ug, 256, 0, m->s>>>(gr, m->gp, m->nsplit, w.r, w.z, m->aw_off, m->aw_node, w.AW, m->cpart,
+                                             m->grec, m->gcount, m->st);
+    cudaEventRecord(ev[3], m->s);
+    k_coarse_step<float><<<crows, 256, csmem, m->s>>>(m->nc, R, m->Einv32, m->mu, m->st, m->grec, m->wr, 1, m->done,
+                                                     cnt_co, m->upart, RED_BLOCKS);
+    cudaEventRecord(ev[4], m->s);
+    m->launches += 4;
+    if (cudaEventSynchronize(ev[4]) != cudaSuccess) rc = fail(AFD_ERR_CUDA, "timing run failed");
+    for (int q = 0; q < 4 && rc == AFD_OK; ++q) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
+      acc[q] += ms;
+    }
+    if (rc == AFD_OK) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[5], ev[0]);
+      acc[4] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  for (int r = 0; r < R; ++r) hd[r] = 1;
+  CK(cudaMemcpyAsync(m->done, hd.data(), R * sizeof(int), cudaMemcpyHostToDevice, m->s));
+  m->nsplit = keep_split;
+  invalidate_graphs(m);
+  TRY(rc);
+  for (int q = 0; q < 5; ++q) us_out5[q] = acc[q] * 1e3 / iters;
+  return finish(m);
+}
 
 int afd_solver_phase_times(afd_mesh* m, double* out10, int reset) {
   if (!m || !out10) return fail(AFD_ERR_INVALID_ARG, "null argument");

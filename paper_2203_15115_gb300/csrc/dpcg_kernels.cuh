@@ -349,6 +349,7 @@ k_update(int ndof, int vs, T* __restrict__ x, T* __restrict__ r, T* __restrict__
   using V = typename Vec<T>::type;
   constexpr int NV = Vec<T>::n;
   __shared__ double red[64];
+  pdl_acquire();
   const int rhs = blockIdx.y;
   if (st[rhs].done) return;
   const T alpha = (T)st[rhs].alpha;
@@ -394,6 +395,7 @@ k_update(int ndof, int vs, T* __restrict__ x, T* __restrict__ r, T* __restrict__
     s[0] += rn * zn;
     s[1] += rn * rn;
   }
+  pdl_release();
   double o[2];
   block_sum_to_f64<2>(s, red, o);
   if (threadIdx.x == 0) {
@@ -445,6 +447,7 @@ k_coarse_rhs(Grid gr, Groups gp, int nsplit, const T* __restrict__ r, const T* _
              const long long* __restrict__ aw_off, const int* __restrict__ aw_node, const T* __restrict__ AW,
              double* __restrict__ part, double* __restrict__ rec, unsigned int* __restrict__ gcount, const CGState* st) {
   __shared__ double red[32 * 12];
+  pdl_acquire();
   __shared__ bool s_last;
   const int G = blockIdx.x, sp = blockIdx.y, rhs = blockIdx.z;
   if (st[rhs].done) return;
@@ -479,6 +482,7 @@ k_coarse_rhs(Grid gr, Groups gp, int nsplit, const T* __restrict__ r, const T* _
         s[6 + m] += aw[(size_t)m * nG + t] * z0 + aw[(size_t)(6 + m) * nG + t] * z1 + aw[(size_t)(12 + m) * nG + t] * z2;
     }
   }
+  pdl_release();
   double o[12];
   block_sum_to_f64<12>(s, red, o);
   double* mine = part + (((size_t)rhs * gp.ng + G) * nsplit + sp) * 12;
@@ -606,6 +610,7 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
               const double* __restrict__ rec, double* __restrict__ wr_out, int fin, int* done_flags,
               unsigned int* counter, const double* __restrict__ upd_partials, int upd_nparts) {
   extern __shared__ double vs[];   // nc values of v for the current RHS
+  pdl_acquire();
   __shared__ bool s_last;
   const int lane = threadIdx.x & 31;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -629,6 +634,7 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
     __syncthreads();
   }
   // last block: beta step for every RHS
+  pdl_release();
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;

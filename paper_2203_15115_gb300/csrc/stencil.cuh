@@ -24,7 +24,8 @@ namespace afd {
 enum StencilMode {
   ST_APPLY = 0,     // y = K u
   ST_RESIDUAL = 1,  // y = f - K u, partial sum y.y, optional float copy of y
-  ST_APPLY_DOT = 2  // y = K u, partial sum u.y
+  ST_APPLY_DOT = 2,  // y = K u, partial sum u.y; u formed as the search direction (see z below)
+  ST_DOT_PLAIN = 3   // y = K u, partial sum u.y, u read as given (FP32 packed kernel only)
 };
 
 template <typename T, typename TF>
@@ -71,6 +72,7 @@ struct StencilGeom {
 template <typename T, int TY, int MODE, typename TF>
 __global__ void __launch_bounds__(ST_TX * TY)
 stencil_kernel(const StencilArgs<T, TF> a) {
+  pdl_acquire();
   // TY warps: warps 0..TY-2 own element rows, the last warp only supplies the
   // x-edges of the row above the tile.  Exchange buffers: each is written,
   // then read after a barrier; the other exchange's barrier separates that
@@ -310,6 +312,7 @@ stencil_kernel(const StencilArgs<T, TF> a) {
       ucur[2] = u_l1[2];
     }
   }
+  pdl_release();
   if (MODE != ST_APPLY) {
     T pv[1] = {out_xy ? part : T(0)};
     double o[1];

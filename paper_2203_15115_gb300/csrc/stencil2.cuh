@@ -352,7 +352,7 @@ __device__ __forceinline__ float stencil2_tile(const StencilArgs<float, float>& 
             if (a.y32) a.y32[voff + 3 * (size_t)n + c] = out;
           } else {
             out = fx ? 0.f : yc;
-            if (MODE == ST_APPLY_DOT) part += uc * out;
+            if (MODE == ST_APPLY_DOT || MODE == ST_DOT_PLAIN) part += uc * out;
           }
           yp[c] = out;
         }
@@ -376,10 +376,12 @@ template <int TY, int MODE>
 __global__ void __launch_bounds__(ST_TX * TY, 16 / TY)
 stencil2_kernel(const StencilArgs<float, float> a) {
   __shared__ double red[32];
+  pdl_acquire();
   const int rhs = blockIdx.z;
   if (a.done && a.done[rhs]) return;
   const float beta = MODE == ST_APPLY_DOT ? (float)a.st[rhs].beta : 0.f;
   const float part = stencil2_tile<TY, MODE, LoadRO>(a, beta, blockIdx.x, blockIdx.y, rhs);
+  pdl_release();
   if (MODE != ST_APPLY) {
     float pv[1] = {part};
     double o[1];
@@ -387,7 +389,7 @@ stencil2_kernel(const StencilArgs<float, float> a) {
     const int nparts = gridDim.x * gridDim.y;
     double* parts = a.partials + (size_t)rhs * nparts;
     if (threadIdx.x == 0) parts[blockIdx.y * gridDim.x + blockIdx.x] = o[0];
-    if (MODE == ST_APPLY_DOT && a.st) {
+    if ((MODE == ST_APPLY_DOT || MODE == ST_DOT_PLAIN) && a.st) {
       __shared__ bool s_last;
       __threadfence();
       __syncthreads();
