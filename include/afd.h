@@ -247,8 +247,10 @@ typedef struct {
  * order as slots and budget free up (continuous batching: a request that
  * arrives while others are on the GPU starts as soon as one of them finishes
  * and leaves room); their kernels overlap on the device through the slots'
- * streams.  Each slot keeps its last mesh (moduli, vectors, coarse inverse)
- * and reuses it for a request of the same size. */
+ * streams.  Meshes (moduli, vectors, coarse inverse, tuned stencil shape)
+ * stay resident in a pool after their request: the next request of the same
+ * size takes an idle one without allocating, and idle meshes are destroyed
+ * least recently used first only when a new mesh needs the room. */
 int afd_server_create(const afd_server_config* cfg, afd_server** out);
 
 /* Queue one solve of K u = f (one load case) on an nx*ny*nz mesh: E
@@ -257,6 +259,21 @@ int afd_server_create(const afd_server_config* cfg, afd_server** out);
  * exceeds the budget. */
 int afd_server_submit(afd_server* s, int nx, int ny, int nz, const double* E, const double* f,
                       const uint8_t* fixed_dof_mask, double rel_tol, int64_t* id_out);
+
+/* afd_server_submit within a session (session > 0; 0 = none): a client's
+ * successive solves, e.g. the level-set iterations of one design (Sec. 3.8).
+ * The session keeps its own mesh; when a request's loads and fixed-DOF mask
+ * equal those of the session's previous solve, the solve starts from that
+ * solution (afd_solve's warm start) with the new moduli.  Requests of one
+ * session run one at a time, in submission order. */
+int afd_server_submit_session(afd_server* s, int64_t session, int nx, int ny, int nz, const double* E,
+                              const double* f, const uint8_t* fixed_dof_mask, double rel_tol, int64_t* id_out);
+
+/* End a session: its mesh stays resident as an ordinary pooled mesh. */
+int afd_server_end_session(afd_server* s, int64_t session);
+
+/* Meshes resident in the pool (busy or idle) and the bytes they hold. */
+int afd_server_resident(afd_server* s, int* meshes, double* bytes);
 
 /* Wait for request id and collect its result: stats, compliance J = f^T u,
  * latency from submit to completion (ms), and the displacement (u_out,

@@ -42,6 +42,7 @@ EXPORTS = [
     "afd_time_stiffness", "afd_kernel_launches", "afd_select_topk_noalloc", "afd_stencil_depth",
     "afd_stencil_warps", "afd_solver_phase_times", "afd_time_dpcg_kernels",
     "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
+    "afd_server_submit_session", "afd_server_end_session", "afd_server_resident",
 ]
 
 
@@ -122,6 +123,9 @@ def lib() -> ctypes.CDLL:
             "afd_server_submit": (i, [vp, i, i, i, vp, vp, vp, d, ctypes.POINTER(i64)]),
             "afd_server_wait": (i, [vp, i64, ctypes.POINTER(afd_stats), ctypes.POINTER(d), ctypes.POINTER(d), vp]),
             "afd_server_destroy": (None, [vp]),
+            "afd_server_submit_session": (i, [vp, i64, i, i, i, vp, vp, vp, d, ctypes.POINTER(i64)]),
+            "afd_server_end_session": (i, [vp, i64]),
+            "afd_server_resident": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -356,12 +360,12 @@ class Server:
         _check(lib().afd_server_create(ctypes.byref(cfg), ctypes.byref(self.h)))
         self.sizes = {}
 
-    def submit(self, nx: int, ny: int, nz: int, E, f, fixed, rel_tol: float) -> int:
+    def submit(self, nx: int, ny: int, nz: int, E, f, fixed, rel_tol: float, session: int = 0) -> int:
         pE, _, k1 = _arr(E, np.float64)
         pf, _, k2 = _arr(np.asarray(f).reshape(-1), np.float64)
         pm, _, k3 = _arr(fixed, np.uint8)
         rid = ctypes.c_int64()
-        _check(lib().afd_server_submit(self.h, nx, ny, nz, pE, pf, pm, rel_tol, ctypes.byref(rid)))
+        _check(lib().afd_server_submit_session(self.h, session, nx, ny, nz, pE, pf, pm, rel_tol, ctypes.byref(rid)))
         self.sizes[rid.value] = 3 * (nx + 1) * (ny + 1) * (nz + 1)
         return rid.value
 
@@ -374,6 +378,15 @@ class Server:
         rc = lib().afd_server_wait(self.h, rid, ctypes.byref(st), ctypes.byref(J), ctypes.byref(lat),
                                    ctypes.c_void_p(u.ctypes.data) if want_u else None)
         return rc, st.as_dict(), J.value, lat.value, u
+
+    def end_session(self, session: int):
+        _check(lib().afd_server_end_session(self.h, session))
+
+    def resident(self):
+        n = ctypes.c_int()
+        b = ctypes.c_double()
+        _check(lib().afd_server_resident(self.h, ctypes.byref(n), ctypes.byref(b)))
+        return n.value, b.value
 
     def close(self):
         if self.h:

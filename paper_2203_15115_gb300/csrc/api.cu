@@ -412,11 +412,30 @@ static int build_aw(afd_mesh* m, Work<T>& w) {
   return AFD_OK;
 }
 
+// The FP32 graph path forms (K W)^T z from the cut elements of each group;
+// the FP64 path and the persistent kernel read K W stored on the node shells.
+static bool uses_stored_aw(const afd_mesh* m) { return m->opt.precision == AFD_FP64 || m->opt.persistent; }
+
+template <typename T>
+static int launch_coarse_rhs(afd_mesh* m, Work<T>& w, int nsplit, int nrhs, bool pdl) {
+  const dim3 ug(m->gp.ng, nsplit, nrhs);
+  if (sizeof(T) == 4 && !uses_stored_aw(m))
+    CK(launch_ex(pdl, k_coarse_rhs_cut<T>, ug, dim3(256), 0, m->s, m->gr, m->gp, nsplit, (const T*)w.r,
+                 (const T*)w.z, (const T*)w.E, (const uint8_t*)m->fixed, (const int*)m->gbox, w.K, m->cpart, m->grec,
+                 m->gcount, (const CGState*)m->st));
+  else
+    CK(launch_ex(pdl, k_coarse_rhs<T>, ug, dim3(256), 0, m->s, m->gr, m->gp, nsplit, (const T*)w.r, (const T*)w.z,
+                 (const long long*)m->aw_off, (const int*)m->aw_node, (const T*)w.AW, m->cpart, m->grec, m->gcount,
+                 (const CGState*)m->st));
+  m->launches++;
+  return AFD_OK;
+}
+
 static int build_coarse(afd_mesh* m) {
   if (m->coarse_valid) return AFD_OK;
   TRY(assemble_coarse(m));
   if (m->opt.precision == AFD_FP64) TRY(build_aw<double>(m, m->w64));
-  else TRY(build_aw<float>(m, m->w32));
+  else if (uses_stored_aw(m)) TRY(build_aw<float>(m, m->w32));
   const size_t nn = (size_t)m->nc * m->nc;
   if (m->opt.precision == AFD_FP64) {
     if (!m->Einv64) TRY(dalloc(&m->Einv64, nn));
@@ -523,12 +542,9 @@ static int autotune_coarse_split(afd_mesh* m) {
   for (int ns : cand) {
     if (ns > m->gp.g) break;
     TRY(ensure_cpart(m, ns));
-    const dim3 ug(m->gp.ng, ns, 1);
     for (int rep = 0; rep < 4; ++rep) {
       if (rep == 1) CK(cudaEventRecord(e0, m->s));
-      k_coarse_rhs<float><<<ug, 256, 0, m->s>>>(g, m->gp, ns, m->w32.r, m->w32.z, m->aw_off, m->aw_node, m->w32.AW,
-                                               m->cpart, m->grec, m->gcount, m->st);
-      m->launches++;
+      TRY(launch_coarse_rhs<float>(m, m->w32, ns, 1, false));
     }
     CK(cudaEventRecord(e1, m->s));
     CK(cudaEventSynchronize(e1));
@@ -655,12 +671,10 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
   CK(cudaMemcpyAsync(m->st, h.data(), nrhs * sizeof(CGState), cudaMemcpyHostToDevice, m->s));
   CK(cudaMemcpyAsync(m->done, hd.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, m->s));
   const dim3 gg(m->gp.ng, nrhs);
-  const dim3 ug(m->gp.ng, m->nsplit, nrhs);
   const dim3 pg(grid_blocks(gr.nnodes, 256, 4 * RED_BLOCKS), nrhs);
   const int crows = (m->nc * 32 + 255) / 256;
   const size_t csmem = (size_t)m->nc * sizeof(double);
   const T* Einv = F64 ? (const T*)m->Einv64 : (const T*)m->Einv32;
-  unsigned int* cnt_st = m->counters;            // [rhs]
   unsigned int* cnt_co = m->counters + MAX_RHS;  // coarse step
   T* P[2] = {w.p, w.t};
   const dim3 vg(RED_BLOCKS, nrhs);
@@ -676,9 +690,9 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
   // initial step runs the vector update with alpha = 0 (p = q = 0).
   CK(cudaMemsetAsync(P[0], 0, (size_t)nrhs * gr.vs * sizeof(T), m->s));
   CK(cudaMemsetAsync(w.q, 0, (size_t)nrhs * gr.vs * sizeof(T), m->s));
-  k_update<T><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, x, w.r, w.z, P[0], w.q, w.invd, m->upart, m->st); m->launches++;
-  k_coarse_rhs<T><<<ug, 256, 0, m->s>>>(gr, m->gp, m->nsplit, w.r, w.z, m->aw_off, m->aw_node, w.AW, m->cpart, m->grec,
-                                       m->gcount, m->st); m->launches++;
+  k_update<T><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, x, w.r, w.z, P[0], w.q, w.invd, m->upart, m->st, nullptr,
+                                            0, m->done); m->launches++;
+  TRY(launch_coarse_rhs<T>(m, w, m->nsplit, nrhs, false));
   k_coarse_step<T><<<crows, 256, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->grec, m->wr, 2, m->done, cnt_co,
                                                m->upart, RED_BLOCKS); m->launches++;
   CK(cudaGetLastError());
@@ -710,15 +724,12 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
       T* pold = P[it & 1];
       T* pnew = P[(it + 1) & 1];
       TRY((launch_stencil<T, ST_APPLY_DOT, TB>(m, pold, w.q, w.E, nullptr, nullptr, m->partials, m->done, nrhs, w.K,
-                                                m->st, cnt_st, w.z, m->mu, pnew)));
+                                                m->st, nullptr, w.z, m->mu, pnew)));
       const bool pdl = m->pdl_now;
       CK(launch_ex(pdl, k_update<T>, vg, dim3(RED_THREADS), 0, m->s, gr.ndof, gr.vs, x, w.r, w.z, (const T*)pnew,
-                   (const T*)w.q, (const T*)w.invd, m->upart, (const CGState*)m->st));
+                   (const T*)w.q, (const T*)w.invd, m->upart, m->st, (const double*)m->partials, nsb, m->done));
       m->launches++;
-      CK(launch_ex(pdl, k_coarse_rhs<T>, ug, dim3(256), 0, m->s, gr, m->gp, m->nsplit, (const T*)w.r, (const T*)w.z,
-                   (const long long*)m->aw_off, (const int*)m->aw_node, (const T*)w.AW, m->cpart, m->grec, m->gcount,
-                   (const CGState*)m->st));
-      m->launches++;
+      TRY(launch_coarse_rhs<T>(m, w, m->nsplit, nrhs, pdl));
       CK(launch_ex(pdl, k_coarse_step<T>, dim3(crows), dim3(256), csmem, m->s, m->nc, nrhs, (const T*)Einv, m->mu,
                    m->st, (const double*)m->grec, m->wr, 1, m->done, cnt_co, (const double*)m->upart, (int)RED_BLOCKS));
       m->launches++;
@@ -1460,10 +1471,8 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
   CK(cudaMemcpyAsync(m->done, hd.data(), R * sizeof(int), cudaMemcpyHostToDevice, m->s));
   Work<float>& w = m->w32;
   const dim3 vg(RED_BLOCKS, R);
-  const dim3 ug(m->gp.ng, m->nsplit, R);
   const int crows = (m->nc * 32 + 255) / 256;
   const size_t csmem = (size_t)m->nc * sizeof(double);
-  unsigned int* cnt_st = m->counters;
   unsigned int* cnt_co = m->counters + MAX_RHS;
   float* P[2] = {w.p, w.t};
   const dim3 pg(grid_blocks(gr.nnodes, 256, 4 * RED_BLOCKS), R);
@@ -1483,15 +1492,15 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
     cudaEventRecord(ev[0], m->s);
     if (variant == 1)
       rc = launch_stencil<float, ST_DOT_PLAIN, float>(m, pnew, w.q, w.E, nullptr, nullptr, m->partials, m->done, R,
-                                                     w.K, m->st, cnt_st);
+                                                     w.K, m->st, nullptr);
     else
       rc = launch_stencil<float, ST_APPLY_DOT, float>(m, pold, w.q, w.E, nullptr, nullptr, m->partials, m->done, R,
-                                                     w.K, m->st, cnt_st, w.z, m->mu, pnew);
+                                                     w.K, m->st, nullptr, w.z, m->mu, pnew);
     cudaEventRecord(ev[1], m->s);
-    k_update<float><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, w.x, w.r, w.z, pnew, w.q, w.invd, m->upart, m->st);
+    k_update<float><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, w.x, w.r, w.z, pnew, w.q, w.invd, m->upart, m->st,
+                                                 m->partials, stencil_blocks(m, false), m->done);
     cudaEventRecord(ev[2], m->s);
-    k_coarse_rhs<float><<<ug, 256, 0, m->s>>>(gr, m->gp, m->nsplit, w.r, w.z, m->aw_off, m->aw_node, w.AW, m->cpart,
-                                             m->grec, m->gcount, m->st);
+    rc = launch_coarse_rhs<float>(m, w, m->nsplit, R, false);
     cudaEventRecord(ev[3], m->s);
     k_coarse_step<float><<<crows, 256, csmem, m->s>>>(m->nc, R, m->Einv32, m->mu, m->st, m->grec, m->wr, 1, m->done,
                                                      cnt_co, m->upart, RED_BLOCKS);
@@ -1551,7 +1560,7 @@ size_t afd_mesh_bytes(int nx, int ny, int nz, int n_rhs, const afd_options* opt)
   b += (size_t)n_rhs * vs * (3 * 8 + 8 * tsz);                      // f, u, r (FP64) + Krylov work
   b += nc * nc * (8 + tsz) + nc * GJ_NB * 2 * 8 + GJ_NB * GJ_NB * 8; // coarse matrix, inverse, sweep scratch
   const size_t box = (size_t)(g + 3) * (g + 3) * (g + 3);
-  b += ng * box * (18 * tsz + 4);                                   // K W on group shells (upper bound)
+  if (f64 || o.persistent) b += ng * box * (18 * tsz + 4);          // K W on group shells (upper bound)
   b += (size_t)n_rhs * (nc * 4 * 8 + ng * 64 * 12 * 8) + 64 * 1024 * 1024 / 8;  // coarse vectors, partials
   return b + b / 10;
 }

@@ -339,22 +339,24 @@ template <typename T> struct Vec;
 template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
 
-// x += alpha p; r -= alpha q; z = r * invd (invd per DOF, zero on fixed DOFs);
-// partial sums of r.z and r.r per block.  Flat over the DOFs of each RHS with
+// alpha = rho / p.q, with p.q summed by every block from the stencil's
+// per-CTA partials in the same fixed order (st_nparts = 0: alpha = 0, the
+// initial step); then x += alpha p; r -= alpha q; z = r * invd (invd per DOF,
+// zero on fixed DOFs); partial sums of r.z and r.r per block.  A p.q that is
+// not positive and finite stops the RHS (status -3 / -5, set by block 0).  Flat over the DOFs of each RHS with
 // 16-byte vector accesses (the RHS stride vs keeps every RHS aligned).
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS)
 k_update(int ndof, int vs, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
-         const T* __restrict__ q, const T* __restrict__ invd, double* partials, const CGState* st) {
+         const T* __restrict__ q, const T* __restrict__ invd, double* partials, CGState* st,
+         const double* __restrict__ st_parts, int st_nparts, int* done_flags) {
   using V = typename Vec<T>::type;
   constexpr int NV = Vec<T>::n;
   __shared__ double red[64];
   pdl_acquire();
   const int rhs = blockIdx.y;
   if (st[rhs].done) return;
-  const T alpha = (T)st[rhs].alpha;
   const size_t off = (size_t)rhs * vs;
-  T s[2] = {T(0), T(0)};
   const int nvec = ndof / NV;
   V* xv = (V*)(x + off);
   V* rv = (V*)(r + off);
@@ -362,9 +364,39 @@ k_update(int ndof, int vs, T* __restrict__ x, T* __restrict__ r, T* __restrict__
   const V* pv = (const V*)(p + off);
   const V* qv = (const V*)(q + off);
   const V* dv = (const V*)invd;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvec; t += gridDim.x * blockDim.x) {
-    V xx = xv[t], rr = rv[t];
-    const V pp = pv[t], qq = qv[t], dd = dv[t];
+  // the first vectors of this thread are loaded before alpha is formed
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  V x0, r0, p0, q0, d0;
+  if (t0 < nvec) {
+    x0 = xv[t0];
+    r0 = rv[t0];
+    p0 = pv[t0];
+    q0 = qv[t0];
+    d0 = dv[t0];
+  }
+  double alpha_d = 0.0;
+  if (st_nparts > 0) {
+    const double pap = sum_partials(st_parts + (size_t)rhs * st_nparts, st_nparts, 1, 0);
+    if (!(pap > 0.0) || !isfinite(pap)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st[rhs].status = isfinite(pap) ? -3 : -5;
+        st[rhs].done = 1;
+        if (done_flags) done_flags[rhs] = 1;
+      }
+      return;
+    }
+    alpha_d = st[rhs].rz / pap;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st[rhs].alpha = alpha_d;
+  }
+  const T alpha = (T)alpha_d;
+  T s[2] = {T(0), T(0)};
+  for (int t = t0; t < nvec; t += gridDim.x * blockDim.x) {
+    V xx, rr, pp, qq, dd;
+    if (t == t0) {
+      xx = x0; rr = r0; pp = p0; qq = q0; dd = d0;
+    } else {
+      xx = xv[t]; rr = rv[t]; pp = pv[t]; qq = qv[t]; dd = dv[t];
+    }
     T* xs = (T*)&xx;
     T* rs = (T*)&rr;
     const T* ps = (const T*)&pp;
@@ -507,6 +539,164 @@ k_coarse_rhs(Grid gr, Groups gp, int nsplit, const T* __restrict__ r, const T* _
   if (threadIdx.x == 0) gcount[(size_t)rhs * gp.ng + G] = 0u;
 }
 
+// Element shell of group G: the elements on which W_G (zero outside G and on
+// fixed DOFs) is not a rigid motion, so that their K_e W_G,e can be nonzero:
+// the elements touching G's nodes ([lo-1, hi] per axis, clipped) minus an
+// inner box of elements with all eight nodes in G ([lo, hi-1]).  When G holds
+// fixed nodes (bounding box fb, max < min for none) the inner box is cut back
+// on the one side that keeps it largest while clear of the elements touching
+// one ([fb_lo-1, fb_hi] per axis); an empty inner box leaves the whole box.
+// b[0..5] outer box, b[6..11] inner box (empty when an extent is < 1).
+__host__ __device__ inline void elem_shell_bounds(const Grid& gr, const Groups& gp, int G, const int* fb,
+                                                  int (&b)[12]) {
+  const int Gx = G % gp.ngx, Gy = (G / gp.ngx) % gp.ngy, Gz = G / (gp.ngx * gp.ngy);
+  const int X[3] = {Gx, Gy, Gz}, NG[3] = {gp.ngx, gp.ngy, gp.ngz}, N[3] = {gr.nx, gr.ny, gr.nz};
+  for (int d = 0; d < 3; ++d) {
+    const int lo = gp.g * X[d], hi = (X[d] == NG[d] - 1) ? N[d] : gp.g * X[d] + gp.g - 1;
+    b[2 * d] = lo > 0 ? lo - 1 : 0;
+    b[2 * d + 1] = hi < N[d] - 1 ? hi : N[d] - 1;
+    b[6 + 2 * d] = lo;
+    b[6 + 2 * d + 1] = hi - 1;
+  }
+  if (!fb || fb[1] < fb[0]) return;
+  int D[6];
+  bool inter = true;
+  for (int d = 0; d < 3; ++d) {
+    D[2 * d] = fb[2 * d] - 1;
+    D[2 * d + 1] = fb[2 * d + 1];
+    inter = inter && D[2 * d] <= b[6 + 2 * d + 1] && D[2 * d + 1] >= b[6 + 2 * d];
+  }
+  if (!inter) return;
+  long long best = 0;
+  int blo = 0, bhi = -1, bd = 0;
+  for (int d = 0; d < 3; ++d) {
+    for (int side = 0; side < 2; ++side) {
+      int lo = b[6 + 2 * d], hi = b[6 + 2 * d + 1];
+      if (side == 0)
+        lo = lo > D[2 * d + 1] + 1 ? lo : D[2 * d + 1] + 1;
+      else
+        hi = hi < D[2 * d] - 1 ? hi : D[2 * d] - 1;
+      long long vol = hi >= lo ? (long long)(hi - lo + 1) : 0;
+      for (int e = 0; e < 3; ++e)
+        if (e != d) {
+          const int ext = b[6 + 2 * e + 1] - b[6 + 2 * e] + 1;
+          vol *= ext > 0 ? ext : 0;
+        }
+      if (vol > best) {
+        best = vol;
+        blo = lo;
+        bhi = hi;
+        bd = d;
+      }
+    }
+  }
+  if (best > 0) {
+    b[6 + 2 * bd] = blo;
+    b[6 + 2 * bd + 1] = bhi;
+  } else {
+    b[7] = b[6] - 1;
+  }
+}
+
+// Right-hand side of the coarse solve without stored K W: per (group,
+// share, rhs), v_G = (W^T r)_G - (W^T K z)_G with
+//   (W^T K z)_G = sum over the group's element shell of W_G,e^T (E_e K0 z_e),
+// each element's forces applied in the modal form (hex8_apply) and restricted
+// to its nodes in G, masked at fixed DOFs (elements inside G without fixed
+// DOFs contribute nothing: the rigid motions are in the element null space).
+// Records and the last-block combination as in k_coarse_rhs.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_coarse_rhs_cut(Grid gr, Groups gp, int nsplit, const T* __restrict__ r, const T* __restrict__ z,
+                 const T* __restrict__ Emod, const uint8_t* __restrict__ fixed, const int* __restrict__ gbox,
+                 ElemConsts<T> K, double* __restrict__ part, double* __restrict__ rec,
+                 unsigned int* __restrict__ gcount, const CGState* st) {
+  __shared__ double red[32 * 12];
+  __shared__ bool s_last;
+  pdl_acquire();
+  const int G = blockIdx.x, sp = blockIdx.y, rhs = blockIdx.z;
+  if (st[rhs].done) return;
+  const int Gx = G % gp.ngx, Gy = (G / gp.ngx) % gp.ngy, Gz = G / (gp.ngx * gp.ngy);
+  int ilo, ihi, jlo, jhi, klo, khi;
+  group_range(Gx, gp.g, gp.ngx, gr.nx, ilo, ihi);
+  group_range(Gy, gp.g, gp.ngy, gr.ny, jlo, jhi);
+  group_range(Gz, gp.g, gp.ngz, gr.nz, klo, khi);
+  const T hh = (T)(0.5 * gp.h);
+  const size_t off = (size_t)rhs * gr.vs;
+  T s[12];
+#pragma unroll
+  for (int t = 0; t < 12; ++t) s[t] = T(0);
+  {
+    const int lz = khi - klo + 1;
+    const int kper = (lz + nsplit - 1) / nsplit;
+    const int kb = klo + sp * kper, ke = min(kb + kper, khi + 1);
+    group_wtr_planes(gr, r, off, ilo, ihi, jlo, jhi, klo, khi, kb, ke, hh, s, [](const T* p) { return __ldg(p); });
+  }
+  {
+    int b[12];
+    elem_shell_bounds(gr, gp, G, gbox ? gbox + 6 * G : nullptr, b);
+    Shell sh;
+    sh.init(b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], b[8], b[9], b[10], b[11], false);
+    const int per = (sh.count + nsplit - 1) / nsplit;
+    const int qb = sp * per, qe = min(qb + per, sh.count);
+    for (int t = qb + threadIdx.x; t < qe; t += blockDim.x) {
+      int ei, ej, ek;
+      sh.at(t, ei, ej, ek);
+      T v[3][8];
+      uint8_t fb[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int i = ei + (a & 1), j = ej + ((a >> 1) & 1), k = ek + ((a >> 2) & 1);
+        const int n = i + gr.nnx * (j + gr.nny * k);
+        fb[a] = fixed ? __ldg(fixed + n) : 0;
+        const T* zp = z + off + 3 * (size_t)n;
+        v[0][a] = __ldg(zp);
+        v[1][a] = __ldg(zp + 1);
+        v[2][a] = __ldg(zp + 2);
+      }
+      hex8_apply(v, __ldg(Emod + ei + gr.nx * (ej + gr.ny * ek)), K);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int i = ei + (a & 1), j = ej + ((a >> 1) & 1), k = ek + ((a >> 2) & 1);
+        if (i < ilo || i > ihi || j < jlo || j > jhi || k < klo || k > khi) continue;
+        const T y0 = (fb[a] & 1) ? T(0) : v[0][a];
+        const T y1 = (fb[a] & 2) ? T(0) : v[1][a];
+        const T y2 = (fb[a] & 4) ? T(0) : v[2][a];
+        const T rx = hh * (T)(2 * i - ilo - ihi), ry = hh * (T)(2 * j - jlo - jhi), rz = hh * (T)(2 * k - klo - khi);
+        s[6] += y0;
+        s[7] += y1;
+        s[8] += y2;
+        s[9] += ry * y2 - rz * y1;
+        s[10] += rz * y0 - rx * y2;
+        s[11] += rx * y1 - ry * y0;
+      }
+    }
+  }
+  pdl_release();
+  double o[12];
+  block_sum_to_f64<12>(s, red, o);
+  double* mine = part + (((size_t)rhs * gp.ng + G) * nsplit + sp) * 12;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      mine[m] = o[m];
+      mine[6 + m] = o[m] - o[6 + m];
+    }
+    __threadfence();
+    s_last = atomicAdd(&gcount[(size_t)rhs * gp.ng + G], 1u) == (unsigned)nsplit - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 12) {
+    const double* pp = part + (((size_t)rhs * gp.ng + G) * nsplit) * 12;
+    double v = 0.0;
+    for (int s2 = 0; s2 < nsplit; ++s2) v += pp[s2 * 12 + threadIdx.x];
+    rec[((size_t)rhs * gp.ng + G) * 12 + threadIdx.x] = v;
+  }
+  if (threadIdx.x == 0) gcount[(size_t)rhs * gp.ng + G] = 0u;
+}
+
 // gbox[6G..6G+5] = bounding box (imin, imax, jmin, jmax, kmin, kmax) of the
 // nodes of group G with a fixed DOF; initialised to (INT_MAX, -1, ...) so that
 // an empty box has max < min.
@@ -599,42 +789,53 @@ k_coarse_solve(int nc, int nrhs, const TE* __restrict__ Einv, const double* __re
 }
 
 // Coarse step of one DPCG iteration: v_G and (W^T r)_G are read from the
-// per-group k_coarse_rhs records, mu = Einv v (one warp per
-// row, all RHS), and the last block to finish takes the beta step for every
-// RHS from the k_update partials: rho = r.z + (W^T r).mu (the preconditioned residual y = z + W mu of
-// the two-level operator), r.r, beta = rho / rho_old, the convergence test
-// and the iteration count.  fin == 2 marks the initial step (beta = 0).
+// per-group k_coarse_rhs records, mu = Einv v (one warp per row, all RHS),
+// and each block leaves its rows' share of (W^T r).mu in cd_parts.  The last
+// block to finish takes the beta step for every RHS in one pass over the
+// k_update partials and the cd_parts: rho = r.z + (W^T r).mu (the
+// preconditioned residual y = z + W mu of the two-level operator), r.r,
+// beta = rho / rho_old, the convergence test and the iteration count.
+// fin == 2 marks the initial step (beta = 0).
 template <typename TE>
 __global__ void __launch_bounds__(256)
 k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict__ mu, CGState* st,
-              const double* __restrict__ rec, double* __restrict__ wr_out, int fin, int* done_flags,
+              const double* __restrict__ rec, double* __restrict__ cd_parts, int fin, int* done_flags,
               unsigned int* counter, const double* __restrict__ upd_partials, int upd_nparts) {
   extern __shared__ double vs[];   // nc values of v for the current RHS
-  pdl_acquire();
+  __shared__ double wcd[32];
+  __shared__ double red[32 * 3];
   __shared__ bool s_last;
-  const int lane = threadIdx.x & 31;
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  pdl_acquire();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int row = blockIdx.x * nwarps + warp;
   const int ng = nc / 6;
   for (int r = 0; r < nrhs; ++r) {
     if (st[r].done) continue;
-    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
-      const int G = q / 6, c = q % 6;
-      const double* pp = rec + ((size_t)r * ng + G) * 12;
-      vs[q] = pp[6 + c];
-      if (blockIdx.x == 0) wr_out[(size_t)r * nc + q] = pp[c];
-    }
+    const double* rr = rec + (size_t)r * ng * 12;
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) vs[q] = rr[(q / 6) * 12 + 6 + q % 6];
     __syncthreads();
+    double cd = 0.0;
     if (row < nc) {
       const TE* er = Einv + (size_t)row * nc;
       TE s = TE(0);
       for (int c = lane; c < nc; c += 32) s = fma(er[c], (TE)vs[c], s);
       s = warp_sum(s);
-      if (lane == 0) mu[(size_t)r * nc + row] = (double)s;
+      if (lane == 0) {
+        mu[(size_t)r * nc + row] = (double)s;
+        cd = rr[(row / 6) * 12 + row % 6] * (double)s;
+      }
+    }
+    if (lane == 0) wcd[warp] = cd;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nwarps; ++w) t += wcd[w];
+      cd_parts[(size_t)r * gridDim.x + blockIdx.x] = t;
     }
     __syncthreads();
   }
-  // last block: beta step for every RHS
   pdl_release();
+  // last block: beta step for every RHS
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
@@ -644,14 +845,18 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
   for (int r = 0; r < nrhs; ++r) {
     CGState& S = st[r];
     if (S.done) continue;
-    const double* pp = upd_partials + (size_t)r * upd_nparts * 2;
-    const double rz = sum_partials(pp, upd_nparts, 2, 0);
-    const double rr = sum_partials(pp, upd_nparts, 2, 1);
-    double c = 0.0;
-    for (int i = threadIdx.x; i < nc; i += blockDim.x) c += wr_out[(size_t)r * nc + i] * mu[(size_t)r * nc + i];
-    const double cdot = block_sum_bcast(c);
+    double ps[3] = {0.0, 0.0, 0.0};
+    const double2* up = (const double2*)(upd_partials + (size_t)r * upd_nparts * 2);
+    for (int i = threadIdx.x; i < upd_nparts; i += blockDim.x) {
+      const double2 v = up[i];
+      ps[0] += v.x;
+      ps[1] += v.y;
+    }
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) ps[2] += cd_parts[(size_t)r * gridDim.x + i];
+    double o[3];
+    block_sum_to_f64<3>(ps, red, o);
     if (threadIdx.x == 0) {
-      const double rho = rz + cdot;
+      const double rz = o[0], rr = o[1], rho = rz + o[2];
       if (!isfinite(rr) || !isfinite(rho)) {
         S.status = -5;
         S.done = 1;

@@ -2,6 +2,14 @@
 // a device-memory budget, each in its own slot (worker thread + CUDA stream),
 // so that the kernels of the requests in flight overlap on the GPU.  Built on
 // the public mesh API of afd.h only.
+//
+// Meshes live in a server-wide pool: a finished request leaves its mesh
+// (vectors, coarse factor, tuned stencil shape) resident and idle, the next
+// request of the same size takes it without allocating, and idle meshes are
+// destroyed least-recently-used first only when the budget needs the room.
+// A session (a client's successive level-set iterations) keeps its own mesh;
+// when its loads and supports are unchanged the next solve starts from the
+// previous solution.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +32,7 @@ using Clock = std::chrono::steady_clock;
 
 struct Request {
   int64_t id = 0;
+  int64_t session = 0;       // 0: none
   int nx = 0, ny = 0, nz = 0;
   std::vector<double> E, f;
   std::vector<uint8_t> fixed;
@@ -40,12 +49,23 @@ struct Request {
   std::string error;
 };
 
+// A resident mesh of the pool.
+struct PoolMesh {
+  afd_mesh* m = nullptr;      // null while being created
+  int nx = 0, ny = 0, nz = 0;
+  size_t bytes = 0;
+  int64_t session = 0;        // owner session (0: shared by size)
+  bool busy = false;
+  uint64_t last_used = 0;
+  // session meshes: the loads and supports of the last solve (warm start when unchanged)
+  std::vector<double> f_last;
+  std::vector<uint8_t> fixed_last;
+  bool has_solution = false;
+};
+
 struct Slot {
   std::thread th;
   cudaStream_t stream = nullptr;
-  afd_mesh* mesh = nullptr;   // kept for a request of the same size
-  int nx = 0, ny = 0, nz = 0;
-  size_t bytes = 0;           // budget held by the kept mesh
 };
 
 }  // namespace
@@ -57,94 +77,130 @@ struct afd_server {
   std::condition_variable cv_work, cv_done;
   std::deque<std::shared_ptr<Request>> queue;
   std::map<int64_t, std::shared_ptr<Request>> all;
+  std::vector<std::unique_ptr<PoolMesh>> pool;
   int64_t next_id = 1;
-  double in_use = 0.0;        // bytes held by meshes in flight or kept by slots
+  uint64_t tick = 0;
+  double in_use = 0.0;        // bytes of all resident meshes (busy, idle or being created)
   bool stopping = false;
   std::vector<std::unique_ptr<Slot>> slots;
 };
 
 namespace {
 
-// One slot: take the head of the queue when the budget allows (dropping the
-// slot's kept mesh if that makes room), solve it on the slot's stream, keep
-// the mesh for a later request of the same size.
+bool same_dims(const PoolMesh& p, const Request& r) { return p.nx == r.nx && p.ny == r.ny && p.nz == r.nz; }
+
+// Remove pool entry i (the caller destroys its mesh outside the lock).
+afd_mesh* pool_remove(afd_server* S, size_t i) {
+  afd_mesh* m = S->pool[i]->m;
+  S->in_use -= (double)S->pool[i]->bytes;
+  S->pool.erase(S->pool.begin() + (long)i);
+  return m;
+}
+
+// Admission of the queue head (lock held).  Returns the pool entry to solve
+// on (busy, possibly still to be created: m == null), or null when the head
+// has to wait.  Idle meshes to destroy are appended to `drop`.
+PoolMesh* admit(afd_server* S, const Request& h, std::vector<afd_mesh*>& drop) {
+  if (h.session) {
+    for (auto& p : S->pool)
+      if (p->session == h.session) {
+        if (p->busy) return nullptr;               // the session's previous request is still running
+        if (same_dims(*p, h)) {
+          p->busy = true;
+          return p.get();
+        }
+        p->busy = true;                            // resized session: replace its mesh below
+        for (size_t i = 0; i < S->pool.size(); ++i)
+          if (S->pool[i].get() == p.get()) {
+            drop.push_back(pool_remove(S, i));
+            break;
+          }
+        break;
+      }
+  } else {
+    PoolMesh* best = nullptr;
+    for (auto& p : S->pool)
+      if (!p->busy && p->session == 0 && p->m && same_dims(*p, h) && (!best || p->last_used > best->last_used))
+        best = p.get();
+    if (best) {
+      best->busy = true;
+      return best;
+    }
+  }
+  // a new mesh: make room by destroying idle meshes, least recently used first
+  while (S->in_use + (double)h.bytes > S->cfg.budget_bytes) {
+    size_t victim = S->pool.size();
+    for (size_t i = 0; i < S->pool.size(); ++i)
+      if (!S->pool[i]->busy && S->pool[i]->m &&
+          (victim == S->pool.size() || S->pool[i]->last_used < S->pool[victim]->last_used))
+        victim = i;
+    if (victim == S->pool.size()) return nullptr;   // everything resident is in use: wait
+    drop.push_back(pool_remove(S, victim));
+  }
+  S->pool.emplace_back(new PoolMesh());
+  PoolMesh* p = S->pool.back().get();
+  p->nx = h.nx;
+  p->ny = h.ny;
+  p->nz = h.nz;
+  p->bytes = h.bytes;
+  p->session = h.session;
+  p->busy = true;
+  S->in_use += (double)h.bytes;
+  return p;
+}
+
+// One slot: take the head of the queue when admission allows, solve it on a
+// pooled mesh with the slot's stream, give the mesh back to the pool.
 void worker(afd_server* S, Slot* slot) {
   cudaSetDevice(S->device);
   cudaStreamCreateWithFlags(&slot->stream, cudaStreamNonBlocking);
   for (;;) {
     std::shared_ptr<Request> req;
-    bool reuse = false;
-    afd_mesh* drop = nullptr;
+    PoolMesh* pm = nullptr;
+    std::vector<afd_mesh*> drop;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       for (;;) {
         if (S->queue.empty()) {
           if (S->stopping) {
-            drop = slot->mesh;
-            S->in_use -= (double)slot->bytes;
-            slot->mesh = nullptr;
-            slot->bytes = 0;
             lk.unlock();
-            if (drop) afd_destroy(drop);
             if (slot->stream) cudaStreamDestroy(slot->stream);
             return;
           }
           S->cv_work.wait(lk);
           continue;
         }
-        const std::shared_ptr<Request>& head = S->queue.front();
-        const bool same = slot->mesh && slot->nx == head->nx && slot->ny == head->ny && slot->nz == head->nz;
-        const double need = same ? 0.0 : (double)head->bytes;
-        const double freed = same ? 0.0 : (double)slot->bytes;
-        if (S->in_use - freed + need <= S->cfg.budget_bytes) {
-          req = head;
+        pm = admit(S, *S->queue.front(), drop);
+        if (pm) {
+          req = S->queue.front();
           S->queue.pop_front();
-          S->in_use += need - freed;
-          reuse = same;
-          if (!same) {
-            drop = slot->mesh;
-            slot->mesh = nullptr;
-            slot->bytes = req->bytes;
-            slot->nx = req->nx;
-            slot->ny = req->ny;
-            slot->nz = req->nz;
-          }
           break;
-        }
-        // the head does not fit: give back this slot's kept mesh so that it can
-        if (slot->mesh) {
-          afd_mesh* m = slot->mesh;
-          S->in_use -= (double)slot->bytes;
-          slot->mesh = nullptr;
-          slot->bytes = 0;
-          lk.unlock();
-          afd_destroy(m);
-          lk.lock();
-          S->cv_work.notify_all();
-          continue;
         }
         S->cv_work.wait(lk);
       }
     }
-    if (drop) afd_destroy(drop);
+    for (afd_mesh* d : drop) afd_destroy(d);
     int rc = AFD_OK;
     std::string err;
-    if (!reuse) {
-      rc = afd_create_mesh(req->nx, req->ny, req->nz, &S->cfg.opt, slot->stream, &slot->mesh);
-      if (rc != AFD_OK) {
-        err = afd_last_error();
-        slot->mesh = nullptr;
-      }
+    if (!pm->m) {
+      afd_mesh* nm = nullptr;
+      rc = afd_create_mesh(req->nx, req->ny, req->nz, &S->cfg.opt, slot->stream, &nm);
+      if (rc != AFD_OK) err = afd_last_error();
+      pm->m = nm;
+      pm->has_solution = false;
     }
-    afd_mesh* m = slot->mesh;
+    afd_mesh* m = pm->m;
     const size_t ndof = 3 * (size_t)(req->nx + 1) * (req->ny + 1) * (req->nz + 1);
     std::vector<double> u(ndof, 0.0);
     afd_stats st{};
     double J = 0.0;
+    // warm start: a session mesh whose last solve had the same loads and supports
+    const bool warm = rc == AFD_OK && req->session && pm->has_solution && pm->f_last == req->f &&
+                      pm->fixed_last == req->fixed;
     if (rc == AFD_OK) rc = afd_set_element_moduli(m, req->E.data(), 0);
-    if (rc == AFD_OK) rc = afd_set_loads_bcs(m, 1, req->f.data(), 0, req->fixed.data(), 0);
+    if (rc == AFD_OK && !warm) rc = afd_set_loads_bcs(m, 1, req->f.data(), 0, req->fixed.data(), 0);
     if (rc == AFD_OK) {
-      rc = afd_solve(m, req->tol, 0, &st, u.data(), 0);
+      rc = afd_solve(m, req->tol, warm ? 1 : 0, &st, u.data(), 0);
       if (rc == AFD_OK || rc == AFD_ERR_NOT_CONVERGED) {
         const int rj = afd_compliance(m, &J);
         if (rc == AFD_OK) rc = rj;
@@ -152,18 +208,26 @@ void worker(afd_server* S, Slot* slot) {
     }
     if (rc != AFD_OK && err.empty()) err = afd_last_error();
     const double ms = std::chrono::duration<double, std::milli>(Clock::now() - req->submitted).count();
+    afd_mesh* bad = nullptr;
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      if (rc != AFD_OK && rc != AFD_ERR_NOT_CONVERGED && slot->mesh) {
+      if ((rc != AFD_OK && rc != AFD_ERR_NOT_CONVERGED) || !pm->m) {
         // a failed mesh is not kept
-        afd_mesh* bad = slot->mesh;
-        slot->mesh = nullptr;
-        S->in_use -= (double)slot->bytes;
-        slot->bytes = 0;
-        afd_destroy(bad);
-      } else if (!slot->mesh) {
-        S->in_use -= (double)slot->bytes;
-        slot->bytes = 0;
+        for (size_t i = 0; i < S->pool.size(); ++i)
+          if (S->pool[i].get() == pm) {
+            bad = pool_remove(S, i);
+            break;
+          }
+      } else {
+        pm->busy = false;
+        pm->last_used = ++S->tick;
+        if (pm->session) {
+          pm->has_solution = rc == AFD_OK;
+          if (!warm) {
+            pm->f_last = req->f;
+            pm->fixed_last = req->fixed;
+          }
+        }
       }
       req->status = rc;
       req->stats = st;
@@ -177,6 +241,7 @@ void worker(afd_server* S, Slot* slot) {
       req->f.shrink_to_fit();
       req->done = true;
     }
+    if (bad) afd_destroy(bad);
     S->cv_done.notify_all();
     S->cv_work.notify_all();
   }
@@ -202,11 +267,12 @@ int afd_server_create(const afd_server_config* cfg, afd_server** out) {
   return AFD_OK;
 }
 
-int afd_server_submit(afd_server* S, int nx, int ny, int nz, const double* E, const double* f,
-                      const uint8_t* fixed_dof_mask, double rel_tol, int64_t* id_out) {
-  if (!S || !E || !f || !fixed_dof_mask || !id_out || nx < 1 || ny < 1 || nz < 1 || !(rel_tol > 0))
+int afd_server_submit_session(afd_server* S, int64_t session, int nx, int ny, int nz, const double* E, const double* f,
+                              const uint8_t* fixed_dof_mask, double rel_tol, int64_t* id_out) {
+  if (!S || !E || !f || !fixed_dof_mask || !id_out || nx < 1 || ny < 1 || nz < 1 || !(rel_tol > 0) || session < 0)
     return AFD_ERR_INVALID_ARG;
   auto r = std::make_shared<Request>();
+  r->session = session;
   r->nx = nx;
   r->ny = ny;
   r->nz = nz;
@@ -230,6 +296,26 @@ int afd_server_submit(afd_server* S, int nx, int ny, int nz, const double* E, co
   return AFD_OK;
 }
 
+int afd_server_submit(afd_server* S, int nx, int ny, int nz, const double* E, const double* f,
+                      const uint8_t* fixed_dof_mask, double rel_tol, int64_t* id_out) {
+  return afd_server_submit_session(S, 0, nx, ny, nz, E, f, fixed_dof_mask, rel_tol, id_out);
+}
+
+int afd_server_end_session(afd_server* S, int64_t session) {
+  if (!S || session <= 0) return AFD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (auto& p : S->pool)
+    if (p->session == session) {
+      // the mesh stays resident as an ordinary pooled mesh of its size
+      p->session = 0;
+      p->has_solution = false;
+      p->f_last.clear();
+      p->fixed_last.clear();
+    }
+  S->cv_work.notify_all();
+  return AFD_OK;
+}
+
 int afd_server_wait(afd_server* S, int64_t id, afd_stats* stats, double* J_out, double* latency_ms, double* u_out) {
   if (!S) return AFD_ERR_INVALID_ARG;
   std::shared_ptr<Request> r;
@@ -248,6 +334,14 @@ int afd_server_wait(afd_server* S, int64_t id, afd_stats* stats, double* J_out, 
   return r->status;
 }
 
+int afd_server_resident(afd_server* S, int* meshes, double* bytes) {
+  if (!S) return AFD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (meshes) *meshes = (int)S->pool.size();
+  if (bytes) *bytes = S->in_use;
+  return AFD_OK;
+}
+
 void afd_server_destroy(afd_server* S) {
   if (!S) return;
   {
@@ -257,5 +351,8 @@ void afd_server_destroy(afd_server* S) {
   S->cv_work.notify_all();
   for (auto& sl : S->slots)
     if (sl->th.joinable()) sl->th.join();
+  for (auto& p : S->pool)
+    if (p->m) afd_destroy(p->m);
+  S->pool.clear();
   delete S;
 }

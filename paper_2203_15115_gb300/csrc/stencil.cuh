@@ -42,8 +42,9 @@ struct StencilArgs {
   const int* done;        // [rhs] skip the work when nonzero (nullable)
   int kz;                 // node planes per CTA
   int tiles_x;            // CTAs along x
-  // ST_APPLY_DOT inside the solver: the last CTA of each RHS turns the u.y
-  // partials into the CG step length alpha = rho / (p.Ap) (nullable)
+  // ST_APPLY_DOT with a counter: the last CTA of each RHS turns the u.y
+  // partials into the CG step length alpha = rho / (p.Ap) (the solver leaves
+  // counter null and lets the vector update form alpha)
   CGState* st;
   unsigned int* counter;  // [rhs], zero between launches
   // Fused search-direction update (nullable z): the applied vector is
@@ -320,7 +321,7 @@ stencil_kernel(const StencilArgs<T, TF> a) {
     const int nparts = gridDim.x * gridDim.y;
     double* parts = a.partials + (size_t)rhs * nparts;
     if (threadIdx.x == 0) parts[blockIdx.y * gridDim.x + blockIdx.x] = o[0];
-    if (MODE == ST_APPLY_DOT && a.st) {
+    if (MODE == ST_APPLY_DOT && a.st && a.counter) {
       __shared__ bool s_last;
       __threadfence();
       __syncthreads();

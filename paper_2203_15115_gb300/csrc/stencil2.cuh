@@ -389,7 +389,7 @@ stencil2_kernel(const StencilArgs<float, float> a) {
     const int nparts = gridDim.x * gridDim.y;
     double* parts = a.partials + (size_t)rhs * nparts;
     if (threadIdx.x == 0) parts[blockIdx.y * gridDim.x + blockIdx.x] = o[0];
-    if ((MODE == ST_APPLY_DOT || MODE == ST_DOT_PLAIN) && a.st) {
+    if ((MODE == ST_APPLY_DOT || MODE == ST_DOT_PLAIN) && a.st && a.counter) {
       __shared__ bool s_last;
       __threadfence();
       __syncthreads();

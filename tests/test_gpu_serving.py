@@ -57,3 +57,48 @@ def test_oversize_request_is_refused():
         srv.submit(12, 6, 6, E, f, fixed, 1e-6)
     assert e.value.code == afd.AFD_ERR_OOM
     srv.close()
+
+
+def test_pool_reuses_meshes_of_the_same_size():
+    srv = afd.Server(max_slots=2, budget_bytes=100 * afd.afd_mesh_bytes(16, 8, 8))
+    for rep in range(3):
+        ids = [srv.submit(16, 8, 8, *_inputs(16, 8, 8, seed=rep * 2 + k), TOL) for k in range(2)]
+        for rid in ids:
+            rc, st, J, lat, u = srv.wait(rid, want_u=False)
+            assert rc == afd.AFD_OK
+    n, b = srv.resident()
+    assert n <= 2 and b <= 2 * afd.afd_mesh_bytes(16, 8, 8)
+    srv.close()
+
+
+def test_budget_evicts_idle_meshes():
+    big = afd.afd_mesh_bytes(24, 12, 12)
+    srv = afd.Server(max_slots=1, budget_bytes=1.2 * big)
+    for d in [(12, 6, 6), (16, 8, 8), (24, 12, 12), (12, 6, 6)]:
+        rid = srv.submit(*d, *_inputs(*d, seed=1), TOL)
+        rc, st, J, lat, u = srv.wait(rid, want_u=False)
+        assert rc == afd.AFD_OK
+        n, b = srv.resident()
+        assert b <= 1.2 * big
+    srv.close()
+
+
+def test_session_warm_start_matches_a_cold_solve():
+    """Successive solves of one session with the same loads start from the
+    previous solution (fewer iterations) and agree with a cold solve."""
+    nx, ny, nz = 24, 12, 12
+    E0, f, fixed = _inputs(nx, ny, nz, seed=7)
+    E1 = E0.copy()
+    E1[: nx * ny * 2] *= 0.97          # a small design change, as between level-set iterations
+    srv = afd.Server(max_slots=2, budget_bytes=100 * afd.afd_mesh_bytes(nx, ny, nz))
+    rc, st0, J0, _, u0 = srv.wait(srv.submit(nx, ny, nz, E0, f, fixed, TOL, session=5))
+    assert rc == afd.AFD_OK
+    rc, st1, J1, _, u1 = srv.wait(srv.submit(nx, ny, nz, E1, f, fixed, TOL, session=5))
+    assert rc == afd.AFD_OK
+    rc, stc, Jc, _, uc = srv.wait(srv.submit(nx, ny, nz, E1, f, fixed, TOL))
+    assert rc == afd.AFD_OK
+    assert st1["iters"] < stc["iters"], (st1["iters"], stc["iters"])
+    assert np.linalg.norm(u1 - uc) <= 1e-6 * np.linalg.norm(uc)
+    assert abs(J1 - Jc) <= 1e-8 * abs(Jc)
+    srv.end_session(5)
+    srv.close()
