@@ -201,6 +201,10 @@ int afd_stencil_depth(const afd_mesh* m);
  * rows, a CTA finishes 2 * warps - 2 of them); chosen with the depth. */
 int afd_stencil_warps(const afd_mesh* m);
 
+/* Pin the FP32 stencil's CTA shape (8 or 16 warps, planes >= 1, clipped to the
+ * mesh) on an existing mesh; the autotuner then leaves this mesh alone. */
+int afd_set_stencil_shape(afd_mesh* m, int warps, int planes);
+
 /* Measurement aid for the CUDA-graph inner solver: continues the last FP32
  * inner DPCG iteration of a completed AFD_MIXED solve for `iters` iterations
  * (no stopping test; the solution u is not touched), launching its kernels

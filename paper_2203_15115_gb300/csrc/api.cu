@@ -1441,6 +1441,15 @@ int afd_stencil_depth(const afd_mesh* m) { return m ? m->kz32 : 0; }
 
 int afd_stencil_warps(const afd_mesh* m) { return m ? m->ty32 : 0; }
 
+int afd_set_stencil_shape(afd_mesh* m, int warps, int planes) {
+  if (!m || (warps != 8 && warps != 16) || planes < 1) return fail(AFD_ERR_INVALID_ARG, "warps must be 8 or 16, planes >= 1");
+  m->ty32 = warps;
+  m->kz32 = std::min(planes, m->gr.nnz);
+  m->tuned = true;
+  invalidate_graphs(m);
+  return AFD_OK;
+}
+
 int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, double* us_out5) {
   if (!m || !us_out5 || iters < 1 || nsplit < 0 || nsplit > 64 || variant < 0 || variant > 1)
     return fail(AFD_ERR_INVALID_ARG, "bad argument");
