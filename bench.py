@@ -16,14 +16,16 @@ finished), an L2 flush (write of 512 MB) between timed steps, max over ranks.
 (host-to-device copies of the moduli and loads, device-to-host copies of u,
 J and the field inside the timed region).
 
-Two more legs run at N = 1 after the timed steps: "batched" (the 96x48x48
+Three more legs run at N = 1 after the timed steps: "levelset" (20 steps of
+compliance-constrained volume minimisation on the 384x192x192 mesh, warm
+started), "batched" (the 96x48x48
 mesh with 8 load cases in one multi-RHS solve, against one case at a time and
 against the FP64 path) and "serve" (256 requests of mixed mesh sizes through
 the serving loop under a 60 GB budget: saturated solves/s, and p50/p99 latency
 at 0.8 x that rate).  `cpu_baseline` times the CPU oracle on a bounded sample.
 
     python bench.py [--steps K] [--warmup W] [--impl ours|reference]
-                    [--no-serve] [--no-batched] [--no-cpu-baseline]
+                    [--no-serve] [--no-batched] [--no-levelset] [--no-cpu-baseline]
 
 Under torchrun (N > 1) every rank solves its own replica (independent
 problems, no collective on the data path): weak scaling.  `ms_per_step` is
@@ -281,6 +283,8 @@ def run_ours(args):
     mesh.close()
     if world == 1 and args.batched:
         out["batched"] = batched_leg(afd, torch, dev, flush)
+    if world == 1 and args.levelset:
+        out["levelset"] = levelset_leg(afd, torch, dev)
     if world == 1 and args.serve:
         del flush
         torch.cuda.empty_cache()
@@ -391,6 +395,32 @@ def serve_leg(afd, n_requests: int = 256, slots: int = 8, budget: float = 60e9, 
     dofs = [3 * (r["nx"] + 1) * (r["ny"] + 1) * (r["nz"] + 1) for r in reqs]
     return {"slots": slots, "budget_gb": budget / 1e9, "tol": tol, "mean_dofs": int(np.mean(dofs)),
             "burst": burst, "poisson_0.8x": poisson}
+
+
+def levelset_leg(afd, torch, dev):
+    """The 20-step compliance-constrained volume minimisation on the 384x192x192
+    mesh (43 M DOFs): solid start, 2 % of the volume removed per step by the
+    AL-weighted strain-energy level set, each solve warm-started from the
+    previous design's displacement, J <= 1.6 J_0.  Timed end to end on the host
+    clock (every library call returns after its stream has finished)."""
+    from synthetic import levelset_384x192x192
+
+    w = levelset_384x192x192(group=0)
+    m = afd.Mesh(w.nx, w.ny, w.nz, group=0)
+    m.set_element_moduli(torch.from_numpy(w.E).to(dev))
+    m.set_loads_bcs(torch.from_numpy(w.f).to(dev), torch.from_numpy(w.fixed).to(dev))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = afd.run_volume_minimisation(m, steps=20, dv=0.02, j_factor=1.6, tol=w.tol)
+    total = time.perf_counter() - t0
+    group = afd.afd_stencil_warps(m.h), afd.afd_stencil_depth(m.h)
+    m.close()
+    return {"workload": w.name, "dofs": w.ndof, "steps": 20, "total_s": round(total, 3),
+            "solve_ms": [round(h["ms"], 1) for h in hist], "inner_iters": [h["iters"] for h in hist],
+            "max_rel_residual": max(h["rel_residual"] for h in hist),
+            "J_over_J0_final": round(hist[-1]["J"] / hist[0]["J"], 5), "constraint_J_le": "1.6 J0",
+            "volume_fraction_final": round(hist[-1]["volume_fraction"], 4),
+            "stencil_warps_planes": list(group)}
 
 
 def batched_leg(afd, torch, dev, flush, reps: int = 3):
@@ -613,6 +643,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-serve", dest="serve", action="store_false", help="skip the serving-stream leg")
     ap.add_argument("--no-batched", dest="batched", action="store_false", help="skip the 8-load-case leg")
+    ap.add_argument("--no-levelset", dest="levelset", action="store_false",
+                    help="skip the 20-step level-set leg on 384x192x192")
     ap.add_argument("--profile-stencil", type=int, default=0, metavar="NX",
                     help="only time the FP32 stencil on an NX x NX/2 x NX/2 mesh (for ncu)")
     ap.add_argument("--launch-summary", metavar="CSV", help="summarise an ncu launch list of one timed step")

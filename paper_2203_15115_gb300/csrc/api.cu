@@ -350,7 +350,9 @@ static int ensure_rhs(afd_mesh* m, int nrhs) {
 template <typename T>
 static int invert_coarse(afd_mesh* m, T* A, double rel) {
   const int nc = m->nc;
-  k_max_diag<<<1, 256, 0, m->s>>>(m->Ec, nc, m->dmax); m->launches++;
+  // A holds the unit-diagonal scaled matrix: pivots are tested against 1
+  const double one = 1.0;
+  CK(cudaMemcpyAsync(m->dmax, &one, sizeof(double), cudaMemcpyHostToDevice, m->s));
   CK(cudaMemsetAsync(m->dstatus, 0, sizeof(int), m->s));
   T* P = (T*)m->gjP;
   T* B = (T*)m->gjB;
@@ -362,6 +364,7 @@ static int invert_coarse(afd_mesh* m, T* A, double rel) {
     k_gj_panel<T><<<(nc * nb + 255) / 256, 256, 0, m->s>>>(A, nc, k0, P, B, R); m->launches++;
     k_gj_update<T><<<ug, 256, 0, m->s>>>(A, nc, k0, P, B, R, k0 + GJ_NB >= nc ? 1 : 0); m->launches++;
   }
+  k_unscale_dense<T><<<grid_blocks((size_t)nc * nc, 256, 4096), 256, 0, m->s>>>(nc, m->Ec, A); m->launches++;
   CK(cudaGetLastError());
   int status = 0;
   CK(cudaMemcpyAsync(&status, m->dstatus, sizeof(int), cudaMemcpyDeviceToHost, m->s));
@@ -439,12 +442,12 @@ static int build_coarse(afd_mesh* m) {
   const size_t nn = (size_t)m->nc * m->nc;
   if (m->opt.precision == AFD_FP64) {
     if (!m->Einv64) TRY(dalloc(&m->Einv64, nn));
-    CK(cudaMemcpyAsync(m->Einv64, m->Ec, nn * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
+    k_scale_dense<double><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(m->nc, m->Ec, m->Einv64); m->launches++;
     TRY(invert_coarse<double>(m, m->Einv64, 1e-12));
   } else {
     if (!m->Einv32) TRY(dalloc(&m->Einv32, nn));
-    k_convert_dense<float><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(nn, m->Ec, m->Einv32); m->launches++;
-    TRY(invert_coarse<float>(m, m->Einv32, 1e-5));
+    k_scale_dense<float><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(m->nc, m->Ec, m->Einv32); m->launches++;
+    TRY(invert_coarse<float>(m, m->Einv32, 1e-6));
   }
   m->coarse_valid = true;
   return AFD_OK;

@@ -135,8 +135,33 @@ __global__ void k_convert_dense(size_t n, const double* __restrict__ a, T* __res
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) b[i] = (T)a[i];
 }
 
+// b = D^{-1/2} a D^{-1/2} (D = diag a) in type T: the coarse matrix with unit
+// diagonal, so that the inverse does not lose the small rigid modes of groups
+// whose elements are mostly void.  A diagonal <= 0 gives NaN, which the pivot
+// test reports as singular.
+template <typename T>
+__global__ void k_scale_dense(int n, const double* __restrict__ a, T* __restrict__ b) {
+  const size_t nn = (size_t)n * n;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = q / n, j = q % n;
+    const double di = a[i * n + i], dj = a[j * n + j];
+    b[q] = (di > 0.0 && dj > 0.0) ? (T)(a[q] / sqrt(di * dj)) : (T)NAN;
+  }
+}
+
+// b <- D^{-1/2} b D^{-1/2}: the inverse of the scaled matrix back to the
+// inverse of a.
+template <typename T>
+__global__ void k_unscale_dense(int n, const double* __restrict__ a, T* __restrict__ b) {
+  const size_t nn = (size_t)n * n;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = q / n, j = q % n;
+    b[q] = (T)((double)b[q] / sqrt(a[i * n + i] * a[j * n + j]));
+  }
+}
+
 // Invert the nb x nb diagonal block at k0 (unblocked sweeps in shared memory);
-// P = A_KK^{-1} (nb x nb).  A pivot <= rel * max|diag| (or NaN) sets *status.
+// P = A_KK^{-1} (nb x nb).  A pivot <= rel * (*dmax) (or NaN) sets *status.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gj_pivot(const T* A, int n, int k0, T* P, const double* dmax, double rel, int* status) {
   __shared__ T s[GJ_NB][GJ_NB + 1];
