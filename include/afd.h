@@ -80,6 +80,8 @@ typedef struct {
   int pdl;            /* 1: the kernels of a captured DPCG iteration chunk use programmatic dependent launch
                          (each may be scheduled while its predecessor finishes its reductions); 0 (default):
                          plain stream order, measured faster on the 128x64x64 workload */
+  double inner_aim;   /* AFD_MIXED: each inner solve aims at inner_aim * rel_tol in the true relative residual
+                         (not below inner_tol); default 0.5, in (0, 1) */
 } afd_options;
 
 typedef struct {

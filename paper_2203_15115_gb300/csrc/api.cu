@@ -799,6 +799,7 @@ void afd_default_options(afd_options* o) {
   o->stencil_warps = 0;
   o->stencil_planes = 0;
   o->pdl = 0;
+  o->inner_aim = 0.5;
 }
 
 const char* afd_last_error(void) { return g_err.c_str(); }
@@ -819,7 +820,8 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
   o.check_every += o.check_every & 1;  // p is double-buffered: chunks of even length
   if (!(o.nu > -1.0 && o.nu < 0.5) || !(o.h > 0.0) || !(o.e_void > 0.0) || o.max_iter < 1 || o.max_refine < 0 ||
       o.check_every < 1 || o.group < 0 || (o.precision != AFD_MIXED && o.precision != AFD_FP64) ||
-      (o.stencil_warps != 0 && o.stencil_warps != 8 && o.stencil_warps != 16) || o.stencil_planes < 0)
+      (o.stencil_warps != 0 && o.stencil_warps != 8 && o.stencil_warps != 16) || o.stencil_planes < 0 ||
+      !(o.inner_aim > 0.0 && o.inner_aim < 1.0))
     return fail(AFD_ERR_INVALID_ARG, "invalid options");
   afd_mesh* m = new afd_mesh();
   m->opt = o;
@@ -1117,7 +1119,7 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
         if (step == m->opt.max_refine || iters[r] >= m->opt.max_iter) { status[r] = AFD_ERR_NOT_CONVERGED; continue; }
         act[r] = 1;
         any = true;
-        double eta = std::min(0.5, std::max(m->opt.inner_tol, 0.1 * rel_tol / rel[r]));
+        double eta = std::min(0.5, std::max(m->opt.inner_tol, m->opt.inner_aim * rel_tol / rel[r]));
         const double rn = rel[r] * (m->fnorm[r] > 0 ? m->fnorm[r] : 1.0);
         t2[r] = (eta * rn) * (eta * rn);
       }
