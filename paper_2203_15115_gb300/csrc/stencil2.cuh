@@ -140,46 +140,49 @@ __device__ __forceinline__ float stencil2_tile(const StencilArgs<float, float>& 
   const bool out1 = oi && w <= TY - 2 && jb + 1 <= gr.ny;
 
   // Fused search direction p = z + W mu + beta p_old (as in stencil.cuh; in
-  // ST_APPLY_DOT, which the solver always launches with z); the two rows may
-  // lie in different groups along y, so A and B are per row.
+  // ST_APPLY_DOT, which the solver always launches with z).  For this column
+  // the rigid motion of group G is W mu = A_G + r_z B_G per row (the two rows
+  // may lie in different groups along y), A = t + omega x (r_x, r_y, 0),
+  // B = (omega_y, -omega_x, 0).  A and B change only when the plane index
+  // enters the next group along z; they are kept in this thread's slot of
+  // shared memory (not registers) together with nothing else: the lever arms
+  // are recomputed at each refresh.
   constexpr bool formp = MODE == ST_APPLY_DOT;
   const Groups gp = a.gp;
   const float hh = (float)(0.5 * gp.h);
-  float rx = 0.f, ry0 = 0.f, ry1 = 0.f;
-  int gxy0 = 0, gxy1 = 0;
-  int gz = -1, gz_next = 0, zlo = 0, zhi = 0;
-  float2 A0 = bc2(0.f), A1 = bc2(0.f), A2 = bc2(0.f), B0 = bc2(0.f), B1 = bc2(0.f);
+  __shared__ float2 sAB[formp ? 5 : 1][formp ? ST_TX * TY : 1];
+  int gz_next = 0;   // first plane of the next group along z (0: not loaded yet)
+  int zsum = 0;      // zlo + zhi of the current group along z
   const double* murhs = formp ? a.mu + (size_t)rhs * 6 * gp.ng : nullptr;
-  if (formp && ci) {
-    int lo, hi;
+  auto refresh_group = [&](int k) {
+    const int gz = group_of_axis(k, gp.g, gp.ngz);
+    int zlo, zhi, lo, hi;
+    group_range(gz, gp.g, gp.ngz, gr.nz, zlo, zhi);
+    gz_next = (gz == gp.ngz - 1) ? (1 << 30) : zhi + 1;
+    zsum = zlo + zhi;
+    if (!ci) return;
     const int Gx = group_of_axis(i, gp.g, gp.ngx);
     group_range(Gx, gp.g, gp.ngx, gr.nx, lo, hi);
-    rx = hh * (float)(2 * i - lo - hi);
+    const float rx = hh * (float)(2 * i - lo - hi);
     const int j0 = max(jb, 0), j1 = min(jb + 1, gr.nny - 1);
     const int Gy0 = group_of_axis(j0, gp.g, gp.ngy), Gy1 = group_of_axis(j1, gp.g, gp.ngy);
     group_range(Gy0, gp.g, gp.ngy, gr.ny, lo, hi);
-    ry0 = hh * (float)(2 * j0 - lo - hi);
+    const float ry0 = hh * (float)(2 * j0 - lo - hi);
     group_range(Gy1, gp.g, gp.ngy, gr.ny, lo, hi);
-    ry1 = hh * (float)(2 * j1 - lo - hi);
-    gxy0 = Gx + gp.ngx * Gy0;
-    gxy1 = Gx + gp.ngx * Gy1;
-  }
-  auto refresh_group = [&](int k) {
-    gz = group_of_axis(k, gp.g, gp.ngz);
-    group_range(gz, gp.g, gp.ngz, gr.nz, zlo, zhi);
-    gz_next = (gz == gp.ngz - 1) ? (1 << 30) : zhi + 1;
+    const float ry1 = hh * (float)(2 * j1 - lo - hi);
     const int gzo = gp.ngx * gp.ngy * gz;
-    const double* m0 = murhs + 6 * (gxy0 + gzo);
-    const double* m1 = murhs + 6 * (gxy1 + gzo);
+    const double* m0 = murhs + 6 * (Gx + gp.ngx * Gy0 + gzo);
+    const double* m1 = murhs + 6 * (Gx + gp.ngx * Gy1 + gzo);
     const float tx0 = (float)LD::ld(m0), ty0 = (float)LD::ld(m0 + 1), tz0 = (float)LD::ld(m0 + 2);
     const float ox0 = (float)LD::ld(m0 + 3), oy0 = (float)LD::ld(m0 + 4), oz0 = (float)LD::ld(m0 + 5);
     const float tx1 = (float)LD::ld(m1), ty1 = (float)LD::ld(m1 + 1), tz1 = (float)LD::ld(m1 + 2);
     const float ox1 = (float)LD::ld(m1 + 3), oy1 = (float)LD::ld(m1 + 4), oz1 = (float)LD::ld(m1 + 5);
-    A0 = make_float2(tx0 - oz0 * ry0, tx1 - oz1 * ry1);
-    A1 = make_float2(ty0 + oz0 * rx, ty1 + oz1 * rx);
-    A2 = make_float2(tz0 + (ox0 * ry0 - oy0 * rx), tz1 + (ox1 * ry1 - oy1 * rx));
-    B0 = make_float2(oy0, oy1);
-    B1 = make_float2(-ox0, -ox1);
+    const int me = threadIdx.x;
+    sAB[0][me] = make_float2(tx0 - oz0 * ry0, tx1 - oz1 * ry1);
+    sAB[1][me] = make_float2(ty0 + oz0 * rx, ty1 + oz1 * rx);
+    sAB[2][me] = make_float2(tz0 + (ox0 * ry0 - oy0 * rx), tz1 + (ox1 * ry1 - oy1 * rx));
+    sAB[3][me] = make_float2(oy0, oy1);
+    sAB[4][me] = make_float2(-ox0, -ox1);
   };
 
   // (u or the formed p) of both rows at plane k; fixed bits of both rows in fbits
@@ -202,7 +205,7 @@ __device__ __forceinline__ float stencil2_tile(const StencilArgs<float, float>& 
       p1[0] = LD::ld(q); p1[1] = LD::ld(q + 1); p1[2] = LD::ld(q + 2);
     }
     if constexpr (formp) {
-      if (k >= gz_next || gz < 0) refresh_group(k);
+      if (k >= gz_next) refresh_group(k);
       float z0[3] = {0.f, 0.f, 0.f}, z1[3] = {0.f, 0.f, 0.f};
       if (col0) {
         const float* q = a.z + voff + 3 * (size_t)n0;
@@ -212,10 +215,11 @@ __device__ __forceinline__ float stencil2_tile(const StencilArgs<float, float>& 
         const float* q = a.z + voff + 3 * (size_t)n1;
         z1[0] = LD::ld(q); z1[1] = LD::ld(q + 1); z1[2] = LD::ld(q + 2);
       }
-      const float2 rz = bc2(hh * (float)(2 * k - zlo - zhi)), bt = bc2(beta);
-      v[0] = fma2(bt, make_float2(p0[0], p1[0]), add2(make_float2(z0[0], z1[0]), fma2(rz, B0, A0)));
-      v[1] = fma2(bt, make_float2(p0[1], p1[1]), add2(make_float2(z0[1], z1[1]), fma2(rz, B1, A1)));
-      v[2] = fma2(bt, make_float2(p0[2], p1[2]), add2(make_float2(z0[2], z1[2]), A2));
+      const float2 rz = bc2(hh * (float)(2 * k - zsum)), bt = bc2(beta);
+      const int me = threadIdx.x;
+      v[0] = fma2(bt, make_float2(p0[0], p1[0]), add2(make_float2(z0[0], z1[0]), fma2(rz, sAB[3][me], sAB[0][me])));
+      v[1] = fma2(bt, make_float2(p0[1], p1[1]), add2(make_float2(z0[1], z1[1]), fma2(rz, sAB[4][me], sAB[1][me])));
+      v[2] = fma2(bt, make_float2(p0[2], p1[2]), add2(make_float2(z0[2], z1[2]), sAB[2][me]));
     } else {
       v[0] = make_float2(p0[0], p1[0]);
       v[1] = make_float2(p0[1], p1[1]);
