@@ -85,5 +85,31 @@ def select_top(values: np.ndarray, k: int):
     return kept, tau
 
 
+def casting_scan(T: np.ndarray, nx: int, ny: int, nz: int, axis: int, parting: int) -> np.ndarray:
+    """Casting constraint on the level-set field (Sec. 3.7), float32.
+
+    Reading: along every line of elements parallel to `axis` (0 = x, 1 = y,
+    2 = z), the elements with index >= `parting` form one half of the cast
+    part and those below it the other; each half is drawn away from the
+    parting plane.  On each half the field is replaced, from the far face
+    toward the parting plane, by
+        T'(k) = max(T(k), nextafter(T'(k_far_neighbour), +inf)),
+    i.e. a running maximum raised by one float32 step per element, so that T'
+    strictly increases toward the parting plane wherever it was propagated.
+    The kept set of any cut then covers, on every line and half, a run of
+    elements starting at the parting plane: no undercut for the draw.
+    Element order e = i + nx (j + ny k); T has nx*ny*nz values."""
+    a = np.asarray(T, dtype=np.float32).reshape(nz, ny, nx)
+    ax = {0: 2, 1: 1, 2: 0}[axis]           # numpy axis of the element index along `axis`
+    a = np.moveaxis(a, ax, 0).copy()         # (n_axis, ...)
+    n = a.shape[0]
+    up = np.float32(np.inf)
+    for k in range(n - 2, parting - 1, -1):  # upper half: from the far face k = n-1 down to `parting`
+        a[k] = np.maximum(a[k], np.nextafter(a[k + 1], up))
+    for k in range(1, min(parting, n)):      # lower half: from k = 0 up to parting-1
+        a[k] = np.maximum(a[k], np.nextafter(a[k - 1], up))
+    return np.moveaxis(a, 0, ax).reshape(-1).astype(np.float32)
+
+
 def apply_topology(kept: np.ndarray, e_void: float) -> np.ndarray:
     return np.where(np.asarray(kept) != 0, 1.0, e_void)

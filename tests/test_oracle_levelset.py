@@ -71,3 +71,61 @@ def test_combine_normalises_each_field():
     out = levelset.combine([a, b], [1.0, 2.0])
     assert out.dtype == np.float32
     assert np.allclose(out, [0.5 + 1.0, -1.0 + 0.5, 0.25 + 2.0], rtol=0, atol=1e-7)
+
+
+def _cast_brute(T, nx, ny, nz, axis, parting):
+    """Definition written per element: T'(e) = max over the elements f of its
+    line and half at or beyond e (away from the parting plane) of T(f) raised
+    by one float32 step per element between f and e."""
+    a = np.asarray(T, np.float32).reshape(nz, ny, nx)
+    out = np.empty_like(a)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                idx = [i, j, k]
+                c = idx[axis]
+                n = (nx, ny, nz)[axis]
+                far = range(c, n) if c >= parting else range(c, -1, -1)
+                best = None
+                for f in far:
+                    q = list(idx)
+                    q[axis] = f
+                    v = a[q[2], q[1], q[0]]
+                    for _ in range(abs(f - c)):
+                        v = np.nextafter(v, np.float32(np.inf))
+                    best = v if best is None else max(best, v)
+                out[k, j, i] = best
+    return out.reshape(-1)
+
+
+@pytest.mark.parametrize("axis,parting", [(0, 0), (1, 3), (2, 5), (0, 7), (2, 0)])
+def test_casting_scan_matches_its_definition(axis, parting):
+    rng = np.random.default_rng(3 + axis)
+    nx, ny, nz = 7, 5, 6
+    T = rng.standard_normal(nx * ny * nz).astype(np.float32)
+    T[::4] = T[1::4][: T[::4].size]           # plateaus and ties
+    got = levelset.casting_scan(T, nx, ny, nz, axis, parting)
+    assert np.array_equal(got, _cast_brute(T, nx, ny, nz, axis, parting))
+
+
+def test_casting_scan_properties_and_no_undercut():
+    rng = np.random.default_rng(11)
+    nx, ny, nz = 12, 8, 10
+    T = rng.random(nx * ny * nz).astype(np.float32)
+    for axis, parting in [(0, 4), (1, 0), (2, 10), (2, 3)]:
+        S = levelset.casting_scan(T, nx, ny, nz, axis, parting)
+        assert np.all(S >= T)
+        assert np.array_equal(levelset.casting_scan(S, nx, ny, nz, axis, parting), S)   # idempotent
+        n = (nx, ny, nz)[axis]
+        a = np.moveaxis(S.reshape(nz, ny, nx), {0: 2, 1: 1, 2: 0}[axis], 0)
+        # strictly increasing toward the parting plane on both halves
+        assert np.all(a[parting:-1] > a[parting + 1:]) if parting < n - 1 else True
+        assert np.all(a[1:parting] > a[:parting - 1]) if parting > 1 else True
+        for v in (0.3, 0.5, 0.8):
+            kept, _ = levelset.select_top(S, levelset.keep_count(v, S.size))
+            kk = np.moveaxis(kept.reshape(nz, ny, nx), {0: 2, 1: 1, 2: 0}[axis], 0).astype(bool)
+            # kept elements on each half are a run starting at the parting plane
+            up, lo = kk[parting:], kk[:parting][::-1]
+            for half in (up, lo):
+                if half.shape[0] > 1:
+                    assert not np.any(~half[:-1] & half[1:])
