@@ -141,6 +141,26 @@ int afd_pnorm_stress(afd_mesh* m, double p, double* out);
 int afd_levelset_update(afd_mesh* m, int kind, const double* weights, double volume_fraction,
                         double* tau_out, uint8_t* kept_out);
 
+/* afd_levelset_update with the casting constraint of Sec. 3.7 applied to the
+ * combined field before the cut (see afd_casting_scan): axis 0/1/2 = x/y/z,
+ * parting in [0, n_axis] elements (0 or n_axis: a one-piece draw).  The kept
+ * set then covers, on every line along the axis and on each side of the
+ * parting plane, a run of elements starting at the plane (no undercut). */
+int afd_levelset_update_cast(afd_mesh* m, int kind, const double* weights, double volume_fraction, int axis,
+                             int parting, double* tau_out, uint8_t* kept_out);
+
+/* Casting constraint (Sec. 3.7) on a per-element float field, in place on the
+ * device (keys: nx*ny*nz floats, element order e = i + nx (j + ny k)): along
+ * every line parallel to `axis`, each half of the part (element index >=
+ * parting, or below it) is replaced, from its far face toward the parting
+ * plane, by key'(c) = max(key(c), nextafter(key'(previous), +inf)), a running
+ * maximum raised by one float32 step per element.  The paper states the
+ * constraint (the level set must not decrease along the casting direction)
+ * without a formula; this is the reading.  Stream-ordered on cuda_stream;
+ * returns after it has finished.  AFD_ERR_INVALID_ARG for a bad axis or
+ * parting index. */
+int afd_casting_scan(float* keys, int nx, int ny, int nz, int axis, int parting, void* cuda_stream);
+
 /* ---- lower-level entry points (the pieces of the path, used by the tests) ---- */
 
 /* y = K u on the free DOFs (rows and columns of fixed DOFs act as zero), in

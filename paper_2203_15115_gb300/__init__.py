@@ -43,7 +43,8 @@ EXPORTS = [
     "afd_time_stiffness", "afd_kernel_launches", "afd_select_topk_noalloc", "afd_stencil_depth",
     "afd_stencil_warps", "afd_solver_phase_times", "afd_time_dpcg_kernels", "afd_set_stencil_shape",
     "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
-    "afd_server_submit_session", "afd_server_end_session", "afd_server_resident",
+    "afd_server_submit_session", "afd_server_end_session", "afd_server_resident", "afd_levelset_update_cast",
+    "afd_casting_scan",
 ]
 
 
@@ -128,6 +129,8 @@ def lib() -> ctypes.CDLL:
             "afd_server_submit_session": (i, [vp, i64, i, i, i, vp, vp, vp, d, ctypes.POINTER(i64)]),
             "afd_server_end_session": (i, [vp, i64]),
             "afd_server_resident": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
+            "afd_levelset_update_cast": (i, [vp, i, ctypes.POINTER(d), d, i, i, ctypes.POINTER(d), vp]),
+            "afd_casting_scan": (i, [vp, i, i, i, i, i, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -239,16 +242,31 @@ def afd_pnorm_stress(mesh, p: float, n_rhs: int) -> np.ndarray:
     return np.array(out[:])
 
 
-def afd_levelset_update(mesh, kind: int, weights, volume_fraction: float, kept_out: Optional[np.ndarray] = None) -> float:
+def afd_levelset_update(mesh, kind: int, weights, volume_fraction: float, kept_out: Optional[np.ndarray] = None,
+                        casting=None) -> float:
+    """casting = (axis, parting) applies afd_levelset_update_cast."""
     w = np.ascontiguousarray(weights, dtype=np.float64)
     tau = ctypes.c_double()
     pk = None
     if kept_out is not None:
         assert kept_out.dtype == np.uint8 and kept_out.flags.c_contiguous
         pk = ctypes.c_void_p(kept_out.ctypes.data)
-    _check(lib().afd_levelset_update(mesh, kind, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), volume_fraction,
-                                     ctypes.byref(tau), pk))
+    pw = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if casting is None:
+        _check(lib().afd_levelset_update(mesh, kind, pw, volume_fraction, ctypes.byref(tau), pk))
+    else:
+        axis, parting = casting
+        _check(lib().afd_levelset_update_cast(mesh, kind, pw, volume_fraction, int(axis), int(parting),
+                                              ctypes.byref(tau), pk))
     return tau.value
+
+
+def afd_casting_scan(keys, nx: int, ny: int, nz: int, axis: int, parting: int, stream=None) -> None:
+    """In-place casting scan of a device float32 tensor (torch) of nx*ny*nz keys."""
+    pk, on_dev, _k = _arr(keys, np.float32)
+    if not on_dev:
+        raise ValueError("afd_casting_scan takes a device tensor")
+    _check(lib().afd_casting_scan(pk, nx, ny, nz, axis, parting, stream if stream is not None else current_stream()))
 
 
 def afd_apply_stiffness(mesh, arith: int, n_rhs: int, u, y) -> None:
@@ -507,8 +525,8 @@ class Mesh:
     def pnorm_stress(self, p: float) -> np.ndarray:
         return afd_pnorm_stress(self.h, p, self.n_rhs)
 
-    def levelset_update(self, kind: int, weights, volume_fraction: float, kept_out=None) -> float:
-        return afd_levelset_update(self.h, kind, weights, volume_fraction, kept_out)
+    def levelset_update(self, kind: int, weights, volume_fraction: float, kept_out=None, casting=None) -> float:
+        return afd_levelset_update(self.h, kind, weights, volume_fraction, kept_out, casting)
 
     def close(self):
         if self.h:

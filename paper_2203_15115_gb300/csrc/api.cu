@@ -1357,8 +1357,48 @@ int afd_select_topk_noalloc(const float* keys, int64_t n, int64_t k, uint8_t* ke
   return select_topk_dev((cudaStream_t)cuda_stream, keys, n, k, kept, st, cnt, nullptr, nullptr, 0.0, tau_out, nullptr);
 }
 
+static int casting_args_ok(int nx, int ny, int nz, int axis, int parting) {
+  if (axis < 0 || axis > 2) return fail(AFD_ERR_INVALID_ARG, "casting axis must be 0, 1 or 2");
+  const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
+  if (parting < 0 || parting > n) return fail(AFD_ERR_INVALID_ARG, "parting index must be in [0, %d]", n);
+  return AFD_OK;
+}
+
+static int launch_casting_scan(cudaStream_t s, int nx, int ny, int nz, int axis, int parting, float* keys,
+                               int64_t* launches) {
+  const size_t nlines = axis == 0 ? (size_t)ny * nz : (axis == 1 ? (size_t)nx * nz : (size_t)nx * ny);
+  k_casting_scan<<<grid_blocks(nlines, 128, 8192), 128, 0, s>>>(nx, ny, nz, axis, parting, keys);
+  if (launches) ++*launches;
+  CK(cudaGetLastError());
+  return AFD_OK;
+}
+
+int afd_casting_scan(float* keys, int nx, int ny, int nz, int axis, int parting, void* cuda_stream) {
+  if (!keys || nx < 1 || ny < 1 || nz < 1) return fail(AFD_ERR_INVALID_ARG, "bad argument");
+  TRY(casting_args_ok(nx, ny, nz, axis, parting));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  TRY(launch_casting_scan(s, nx, ny, nz, axis, parting, keys, nullptr));
+  CK(cudaStreamSynchronize(s));
+  return AFD_OK;
+}
+
+static int levelset_update_impl(afd_mesh* m, int kind, const double* weights, double volume_fraction, int axis,
+                                int parting, double* tau_out, uint8_t* kept_out);
+
 int afd_levelset_update(afd_mesh* m, int kind, const double* weights, double volume_fraction, double* tau_out,
                         uint8_t* kept_out) {
+  return levelset_update_impl(m, kind, weights, volume_fraction, -1, 0, tau_out, kept_out);
+}
+
+int afd_levelset_update_cast(afd_mesh* m, int kind, const double* weights, double volume_fraction, int axis,
+                             int parting, double* tau_out, uint8_t* kept_out) {
+  if (!m) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  TRY(casting_args_ok(m->gr.nx, m->gr.ny, m->gr.nz, axis, parting));
+  return levelset_update_impl(m, kind, weights, volume_fraction, axis, parting, tau_out, kept_out);
+}
+
+static int levelset_update_impl(afd_mesh* m, int kind, const double* weights, double volume_fraction, int axis,
+                                int parting, double* tau_out, uint8_t* kept_out) {
   if (!m || !weights) return fail(AFD_ERR_INVALID_ARG, "null argument");
   if (kind < 0 || kind > 2) return fail(AFD_ERR_INVALID_ARG, "unknown field kind %d", kind);
   if (!std::isfinite(volume_fraction)) return fail(AFD_ERR_INVALID_ARG, "volume fraction must be finite");
@@ -1384,6 +1424,7 @@ int afd_levelset_update(afd_mesh* m, int kind, const double* weights, double vol
   CK(cudaMemcpyAsync(dw, wf.data(), R * sizeof(float), cudaMemcpyHostToDevice, m->s));
   k_combine<<<grid_blocks(n, 256, 4096), 256, 0, m->s>>>((int)n, R, m->fbuf, dw, dmaxv, m->fkeys); m->launches++;
   CK(cudaGetLastError());
+  if (axis >= 0) TRY(launch_casting_scan(m->s, m->gr.nx, m->gr.ny, m->gr.nz, axis, parting, m->fkeys, &m->launches));
   const double kd = std::floor(volume_fraction * (double)n + 0.5);
   const int64_t k = (int64_t)std::min<double>(std::max<double>(kd, 0.0), (double)n);
   float tau;

@@ -144,4 +144,52 @@ k_mark(int64_t n, const float* __restrict__ x, const SelectState* st, const uint
   }
 }
 
+// Casting constraint (Sec. 3.7) on the combined level-set keys, in place:
+// along every line of elements parallel to `axis` (0 = x, 1 = y, 2 = z) each
+// half of the part (element index along the axis >= parting, or below it)
+// takes, from its far face toward the parting plane,
+//   key'(c) = max(key(c), nextafter(key'(c_far_neighbour), +inf)),
+// a running maximum raised by one float32 step per element, so that the kept
+// set of any cut is a run of elements starting at the parting plane.  One
+// thread per line; lines along y and z are indexed so that neighbouring
+// threads read neighbouring elements.
+__global__ void k_casting_scan(int nx, int ny, int nz, int axis, int parting, float* __restrict__ keys) {
+  const int nlines = axis == 0 ? ny * nz : (axis == 1 ? nx * nz : nx * ny);
+  for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < nlines; L += gridDim.x * blockDim.x) {
+    size_t base, stride;
+    int n;
+    if (axis == 0) {
+      base = (size_t)nx * L;   // L = j + ny k
+      stride = 1;
+      n = nx;
+    } else if (axis == 1) {
+      const int i = L % nx, k = L / nx;
+      base = (size_t)i + (size_t)nx * ny * k;
+      stride = nx;
+      n = ny;
+    } else {
+      base = (size_t)L;        // L = i + nx j
+      stride = (size_t)nx * ny;
+      n = nz;
+    }
+    if (parting < n - 1) {     // upper half, from the far face c = n-1 down to parting
+      float v = keys[base + (size_t)(n - 1) * stride];
+      for (int c = n - 2; c >= parting; --c) {
+        float* q = keys + base + (size_t)c * stride;
+        v = fmaxf(*q, nextafterf(v, INFINITY));
+        *q = v;
+      }
+    }
+    if (parting > 1) {         // lower half, from c = 0 up to parting - 1
+      float v = keys[base];
+      const int top = parting < n ? parting : n;
+      for (int c = 1; c < top; ++c) {
+        float* q = keys + base + (size_t)c * stride;
+        v = fmaxf(*q, nextafterf(v, INFINITY));
+        *q = v;
+      }
+    }
+  }
+}
+
 }  // namespace afd

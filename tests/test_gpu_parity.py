@@ -272,3 +272,45 @@ def test_error_paths():
         m.solve(1e-6)
     assert e.value.code == afd.AFD_ERR_COARSE_SINGULAR
     m.close()
+
+
+@pytest.mark.parametrize("shape", [(7, 5, 6), (33, 17, 9), (64, 3, 40)])
+def test_casting_scan_bit_exact(shape):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx)
+    T = rng.standard_normal(nx * ny * nz).astype(np.float32)
+    T[::3] = T[1::3][: T[::3].size]         # ties and plateaus
+    for axis in (0, 1, 2):
+        n = shape[axis]
+        for parting in sorted({0, 1, n // 2, n - 1, n}):
+            d = torch.from_numpy(T.copy()).cuda()
+            afd.afd_casting_scan(d, nx, ny, nz, axis, parting)
+            torch.cuda.synchronize()
+            assert np.array_equal(d.cpu().numpy(), levelset.casting_scan(T, nx, ny, nz, axis, parting)), (axis, parting)
+    with pytest.raises(afd.AFDError):
+        afd.afd_casting_scan(torch.zeros(nx * ny * nz, device="cuda"), nx, ny, nz, 3, 0)
+    with pytest.raises(afd.AFDError):
+        afd.afd_casting_scan(torch.zeros(nx * ny * nz, device="cuda"), nx, ny, nz, 0, nx + 1)
+
+
+@pytest.mark.parametrize("axis,parting", [(2, 0), (2, 4), (1, 6), (0, 10)])
+def test_levelset_update_with_casting_matches_oracle(axis, parting):
+    """Combine, casting scan and cut on the GPU's own fields give the oracle's
+    kept set bit for bit, and the kept set has no undercut."""
+    w = small_cantilever(24, 12, 8, seed=8, n_spheres=4, rmin=1.5, rmax=3.5, group=4, n_rhs=2)
+    m, u, _ = _solve(w, afd.AFD_MIXED, 1e-9)
+    s = np.zeros((2, m.nelem), np.float32)
+    m.sensitivity(afd.AFD_SENS_STRAIN_ENERGY, s)
+    weights = [1.0, 0.5]
+    v = 0.7
+    keys = levelset.casting_scan(levelset.combine([s[0], s[1]], weights), w.nx, w.ny, w.nz, axis, parting)
+    kref, tref = levelset.select_top(keys, levelset.keep_count(v, keys.size))
+    kept = np.zeros(m.nelem, np.uint8)
+    tau = m.levelset_update(afd.AFD_SENS_STRAIN_ENERGY, weights, v, kept, casting=(axis, parting))
+    assert np.array_equal(kept, kref)
+    assert tau == np.float32(tref)
+    kk = np.moveaxis(kept.reshape(w.nz, w.ny, w.nx), {0: 2, 1: 1, 2: 0}[axis], 0).astype(bool)
+    for half in (kk[parting:], kk[:parting][::-1]):
+        if half.shape[0] > 1:
+            assert not np.any(~half[:-1] & half[1:])
+    m.close()
