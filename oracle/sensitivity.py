@@ -13,6 +13,11 @@ Readings of the paper:
   * Von Mises stress at the element centroid; the p-norm stress of Eq. 3.3 is
     (sum_e sigma_vm,e^p)^(1/p), no volume weighting (p is not given in the
     paper; it is an argument).
+  * Eq. 3.3 is garbled (tr(lambda) of a vector field, no adjoint equation).
+    Read consistently with Eq. 3.2 as
+        T_sigma = 4/(1+nu) sigma(u):eps(lambda) - (1-3 nu)/(1-nu^2) tr sigma(u) tr eps(lambda),
+    at the element centroid, with the adjoint lambda solving
+    K lambda = -d sigma_PN / d u on the free DOFs (zero on fixed DOFs).
 """
 from __future__ import annotations
 
@@ -73,3 +78,38 @@ def pnorm(values: np.ndarray, p: float) -> float:
     if m == 0.0:
         return 0.0
     return float(m * np.sum((v / m) ** p) ** (1.0 / p))
+
+
+def pnorm_stress_gradient(nx, ny, nz, E, u, p: float, nu: float = 0.3, h: float = 1.0) -> np.ndarray:
+    """d sigma_PN / d u, assembled over the nodes (FP64, no boundary conditions),
+    by the chain rule through the definitions above:
+      d sigma_PN / d s_e   = sigma_PN^(1-p) s_e^(p-1)           (s_e = von Mises of element e)
+      d s_e / d sigma_e     = 3/2 dev(sigma_e) / s_e
+      d s_e / d eps_e       = C : (d s_e / d sigma_e)          (C self-adjoint)
+      d eps_e / d u_(a,c)   = sym(e_c (x) grad N_a) at the centroid.
+    Elements with s_e = 0 contribute nothing."""
+    eps = centroid_strain(nx, ny, nz, u, h)
+    sig = centroid_stress(eps, E, nu)
+    vm = von_mises(sig)
+    PN = pnorm(vm, p)
+    dev = sig - np.trace(sig, axis1=1, axis2=2)[:, None, None] / 3.0 * np.eye(3)[None]
+    coef = np.zeros_like(vm)
+    nzv = vm > 0
+    coef[nzv] = PN ** (1.0 - p) * vm[nzv] ** (p - 1.0) * 1.5 / vm[nzv]
+    X = coef[:, None, None] * dev                                   # d sigma_PN / d sigma_e
+    lam, mu = fe.lame(1.0, nu)
+    D = np.asarray(E, dtype=np.float64)[:, None, None] * (2.0 * mu * X + lam * np.trace(X, axis1=1, axis2=2)[:, None, None] * np.eye(3)[None])
+    grad = fe.shape_gradients(np.array([0.5, 0.5, 0.5]), h)          # (8, 3)
+    ge = np.einsum("ecj,aj->eac", D, grad)                          # (N_e, 8, 3)
+    g = np.zeros(u.size, dtype=np.float64).reshape(-1, 3)
+    np.add.at(g, fe.element_nodes(nx, ny, nz), ge)
+    return g.reshape(-1)
+
+
+def stress_topological_sensitivity(nx, ny, nz, E, u, lam_adj, nu: float = 0.3, h: float = 1.0) -> np.ndarray:
+    """T_sigma of Eq. 3.3 (reading above) at each element centroid."""
+    eps = centroid_strain(nx, ny, nz, u, h)
+    sig = centroid_stress(eps, E, nu)
+    eps_l = centroid_strain(nx, ny, nz, lam_adj, h)
+    return 4.0 / (1.0 + nu) * np.einsum("eij,eij->e", sig, eps_l) - (1.0 - 3.0 * nu) / (1.0 - nu * nu) * \
+        np.trace(sig, axis1=1, axis2=2) * np.trace(eps_l, axis1=1, axis2=2)

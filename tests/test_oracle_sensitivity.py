@@ -87,3 +87,52 @@ def test_centroid_strain_of_a_bilinear_field():
     ref[0, 0] = 0.5
     ref[0, 1] = ref[1, 0] = 0.25
     assert np.allclose(eps, ref, atol=1e-15)
+
+
+def _voided_problem():
+    from synthetic import small_cantilever
+    w = small_cantilever(8, 4, 4, seed=2, n_spheres=2, rmin=1.0, rmax=1.8, group=2)
+    K = fe.assemble(w.nx, w.ny, w.nz, w.E)
+    u = fe.solve_direct(K, w.f[0], w.fixed)
+    return w, K, u
+
+
+@pytest.mark.parametrize("p", [2.0, 8.0])
+def test_pnorm_gradient_matches_central_differences(p):
+    w, K, u = _voided_problem()
+    g = sensitivity.pnorm_stress_gradient(w.nx, w.ny, w.nz, w.E, u, p)
+    PN = lambda v: sensitivity.pnorm(sensitivity.element_von_mises(w.nx, w.ny, w.nz, w.E, v), p)
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        d = rng.standard_normal(u.size)
+        d *= np.linalg.norm(u) / np.linalg.norm(d)
+        eps = 1e-5
+        fd = (PN(u + eps * d) - PN(u - eps * d)) / (2 * eps)
+        assert abs(g @ d - fd) <= 1e-6 * abs(fd) + 1e-12 * abs(PN(u))
+
+
+def test_stress_sensitivity_with_lambda_equal_u_is_eq32():
+    w, K, u = _voided_problem()
+    a = sensitivity.stress_topological_sensitivity(w.nx, w.ny, w.nz, w.E, u, u)
+    b = sensitivity.topological_compliance(w.nx, w.ny, w.nz, w.E, u)
+    assert np.allclose(a, b, rtol=1e-14, atol=1e-14 * np.abs(b).max())
+
+
+def test_adjoint_gives_the_load_derivative_of_the_pnorm_stress():
+    """With K lambda = -d sigma_PN/du (free DOFs), d sigma_PN / d f = -lambda:
+    checked by central differences of sigma_PN(u(f)) through direct solves."""
+    w, K, u = _voided_problem()
+    p = 6.0
+    free = w.fixed == 0
+    g = sensitivity.pnorm_stress_gradient(w.nx, w.ny, w.nz, w.E, u, p)
+    lam = fe.solve_direct(K, -g * free, w.fixed)
+    PN = lambda v: sensitivity.pnorm(sensitivity.element_von_mises(w.nx, w.ny, w.nz, w.E, v), p)
+    rng = np.random.default_rng(9)
+    for _ in range(3):
+        df = rng.standard_normal(u.size) * free
+        df *= np.linalg.norm(w.f[0]) / np.linalg.norm(df)
+        h = 1e-5
+        up = fe.solve_direct(K, w.f[0] + h * df, w.fixed)
+        um = fe.solve_direct(K, w.f[0] - h * df, w.fixed)
+        fd = (PN(up) - PN(um)) / (2 * h)
+        assert abs(-lam @ df - fd) <= 1e-6 * abs(fd) + 1e-12 * abs(PN(u))
