@@ -132,6 +132,19 @@ int afd_sensitivity(afd_mesh* m, int kind, float* out, int out_on_device);
  * load case (the stress measure of Eq. 3.3), FP64, host output. */
 int afd_pnorm_stress(afd_mesh* m, double p, double* out);
 
+/* Adjoint topological sensitivity of the p-norm stress (Eq. 3.3, read with
+ * the adjoint state): sigma_PN = (sum_e s_e^p)^(1/p) of the centroid von Mises
+ * stresses of the current solution (afd_pnorm_stress), the adjoint lambda
+ * solving K lambda = -d sigma_PN / d u on the free DOFs (the same solver,
+ * precision, coarse space and rel_tol as afd_solve; adj_stats per load case,
+ * nullable), and per element at the centroid
+ *   T_sigma = 4/(1+nu) sigma(u):eps(lambda) - (1-3 nu)/(1-nu^2) tr sigma(u) tr eps(lambda).
+ * out: n_rhs*nelem floats, RHS-major; lambda_out (nullable): n_rhs*ndof.
+ * The solution u is left unchanged.  AFD_ERR_NOT_CONVERGED if an adjoint
+ * solve stopped above rel_tol (out is still written). */
+int afd_stress_sensitivity(afd_mesh* m, double p, double rel_tol, float* out, int out_on_device, afd_stats* adj_stats,
+                           double* lambda_out, int lambda_on_device);
+
 /* Level-set update (Eqs. 3.6, 3.17-3.18): for every load case r compute the
  * field of `kind`, divide it by its largest magnitude, add the fields with
  * weights[r] (float32, fixed order), keep the k = round(v * nelem) elements

@@ -44,7 +44,7 @@ EXPORTS = [
     "afd_stencil_warps", "afd_solver_phase_times", "afd_time_dpcg_kernels", "afd_set_stencil_shape",
     "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
     "afd_server_submit_session", "afd_server_end_session", "afd_server_resident", "afd_levelset_update_cast",
-    "afd_casting_scan",
+    "afd_casting_scan", "afd_stress_sensitivity",
 ]
 
 
@@ -131,6 +131,7 @@ def lib() -> ctypes.CDLL:
             "afd_server_resident": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
             "afd_levelset_update_cast": (i, [vp, i, ctypes.POINTER(d), d, i, i, ctypes.POINTER(d), vp]),
             "afd_casting_scan": (i, [vp, i, i, i, i, i, vp]),
+            "afd_stress_sensitivity": (i, [vp, d, d, vp, i, ctypes.POINTER(afd_stats), vp, i]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -259,6 +260,18 @@ def afd_levelset_update(mesh, kind: int, weights, volume_fraction: float, kept_o
         _check(lib().afd_levelset_update_cast(mesh, kind, pw, volume_fraction, int(axis), int(parting),
                                               ctypes.byref(tau), pk))
     return tau.value
+
+
+def afd_stress_sensitivity(mesh, n_rhs: int, p: float, rel_tol: float, out, lambda_out=None):
+    """T_sigma of Eq. 3.3 into out (n_rhs x nelem float32); returns the adjoint
+    solves' stats; lambda_out (n_rhs x ndof float64) receives the adjoint."""
+    po, od, _k1 = _arr(out, np.float32)
+    st = (afd_stats * n_rhs)()
+    pl, ld = (None, 0)
+    if lambda_out is not None:
+        pl, ld, _k2 = _arr(lambda_out, np.float64)
+    _check(lib().afd_stress_sensitivity(mesh, p, rel_tol, po, od, st, pl, ld), [s.as_dict() for s in st])
+    return [s.as_dict() for s in st]
 
 
 def afd_casting_scan(keys, nx: int, ny: int, nz: int, axis: int, parting: int, stream=None) -> None:
@@ -524,6 +537,9 @@ class Mesh:
 
     def pnorm_stress(self, p: float) -> np.ndarray:
         return afd_pnorm_stress(self.h, p, self.n_rhs)
+
+    def stress_sensitivity(self, p: float, rel_tol: float, out, lambda_out=None):
+        return afd_stress_sensitivity(self.h, self.n_rhs, p, rel_tol, out, lambda_out)
 
     def levelset_update(self, kind: int, weights, volume_fraction: float, kept_out=None, casting=None) -> float:
         return afd_levelset_update(self.h, kind, weights, volume_fraction, kept_out, casting)

@@ -147,6 +147,9 @@ struct afd_mesh {
   size_t prec_cap = 0;
   GridBarrier* gbar = nullptr;
   unsigned long long* ptime = nullptr;   // [10] phase times of the persistent solver (ns), iterations, barrier waits
+  // adjoint stress sensitivity: lambda, its right-hand side, d sigma_PN / d eps per element, sigma_PN per RHS
+  double *lam64 = nullptr, *gadj = nullptr, *dsig = nullptr, *pn_d = nullptr;
+  int adj_cap = 0;
   int nsplit_aw = 1;
   bool coarse_valid = false;
   Work<float> w32;
@@ -920,6 +923,7 @@ void afd_destroy(afd_mesh* m) {
   dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gbox); dfree(m->aw_off); dfree(m->aw_node);
   dfree(m->grec); dfree(m->gcount); dfree(m->upart);
   dfree(m->ppart); dfree(m->prec); dfree(m->gbar); dfree(m->ptime);
+  dfree(m->lam64); dfree(m->gadj); dfree(m->dsig); dfree(m->pn_d);
   if (m->ev) cudaEventDestroy(m->ev);
   if (m->s) cudaStreamDestroy(m->s);
   delete m;
@@ -1243,6 +1247,75 @@ int afd_pnorm_stress(afd_mesh* m, double p, double* out) {
   CK(cudaStreamSynchronize(m->s));
   for (int r = 0; r < R; ++r) out[r] = (double)mx[r] * std::pow(s[r], 1.0 / p);
   return finish(m);
+}
+
+int afd_stress_sensitivity(afd_mesh* m, double p, double rel_tol, float* out, int out_on_device, afd_stats* adj_stats,
+                           double* lambda_out, int lambda_on_device) {
+  if (!m || !out) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (!(p >= 1.0) || !std::isfinite(p)) return fail(AFD_ERR_INVALID_ARG, "p must be >= 1");
+  if (!(rel_tol > 0.0) || !std::isfinite(rel_tol)) return fail(AFD_ERR_INVALID_ARG, "rel_tol must be > 0");
+  if (!m->has_solution) return fail(AFD_ERR_STATE, "no solution");
+  const int R = m->nrhs;
+  std::vector<double> pn(R);
+  TRY(afd_pnorm_stress(m, p, pn.data()));
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const Grid& g = m->gr;
+  if (m->adj_cap < R) {
+    dfree(m->lam64); dfree(m->gadj); dfree(m->dsig); dfree(m->pn_d);
+    m->adj_cap = 0;
+    TRY(dalloc(&m->lam64, (size_t)R * g.vs));
+    TRY(dalloc(&m->gadj, (size_t)R * g.vs));
+    TRY(dalloc(&m->dsig, (size_t)R * 6 * g.nelem));
+    TRY(dalloc(&m->pn_d, (size_t)R));
+    m->adj_cap = R;
+  }
+  FieldConsts F;
+  const double nu = m->opt.nu;
+  F.lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  F.mu = 1.0 / (2.0 * (1.0 + nu));
+  F.nu = nu;
+  F.inv4h = 1.0 / (4.0 * m->opt.h);
+  CK(cudaMemcpyAsync(m->pn_d, pn.data(), R * sizeof(double), cudaMemcpyHostToDevice, m->s));
+  k_pnorm_dsig<<<dim3(grid_blocks(g.nelem, 256, 8 * RED_BLOCKS), R), 256, 0, m->s>>>(g, m->u64, m->E64, F, p, m->pn_d,
+                                                                                    m->dsig); m->launches++;
+  CK(cudaMemsetAsync(m->gadj, 0, (size_t)R * g.vs * sizeof(double), m->s));
+  k_pnorm_adjoint_rhs<<<dim3(grid_blocks(g.nnodes, 256, 8 * RED_BLOCKS), R), 256, 0, m->s>>>(g, m->dsig, m->fixed,
+                                                                                            F.inv4h, m->gadj); m->launches++;
+  TRY(ensure_partials(m, (size_t)R * RED_BLOCKS));
+  k_dot<double, double><<<dim3(RED_BLOCKS, R), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->gadj, m->gadj, m->partials); m->launches++;
+  CK(cudaGetLastError());
+  std::vector<double> gg;
+  TRY(reduce_partials_host(m, R, RED_BLOCKS, gg));
+  std::vector<double> gnorm(R);
+  for (int r = 0; r < R; ++r) gnorm[r] = std::sqrt(gg[r]);
+  // the adjoint problem K lambda = g on the same mesh, moduli, supports and coarse space:
+  // swap it into the load / solution buffers for one solve, then swap back
+  std::swap(m->f64, m->gadj);
+  std::swap(m->u64, m->lam64);
+  std::swap(m->fnorm, gnorm);
+  invalidate_graphs(m);
+  const int rc = afd_solve(m, rel_tol, 0, adj_stats, nullptr, 0);
+  const std::string err = g_err;
+  std::swap(m->f64, m->gadj);
+  std::swap(m->u64, m->lam64);
+  std::swap(m->fnorm, gnorm);
+  invalidate_graphs(m);
+  m->has_solution = true;
+  if (rc != AFD_OK && rc != AFD_ERR_NOT_CONVERGED) return fail(rc, "adjoint solve: %s", err.c_str());
+  float* dst = out_on_device ? out : m->fbuf;
+  k_stress_topo<<<dim3(grid_blocks(g.nelem, 256, 8 * RED_BLOCKS), R), 256, 0, m->s>>>(g, m->u64, m->lam64, m->E64, F,
+                                                                                      dst); m->launches++;
+  CK(cudaGetLastError());
+  if (!out_on_device)
+    CK(cudaMemcpyAsync(out, m->fbuf, (size_t)R * g.nelem * sizeof(float), cudaMemcpyDeviceToHost, m->s));
+  if (lambda_out)
+    CK(cudaMemcpy2DAsync(lambda_out, (size_t)g.ndof * sizeof(double), m->lam64, (size_t)g.vs * sizeof(double),
+                         (size_t)g.ndof * sizeof(double), R,
+                         lambda_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->s));
+  TRY(finish(m));
+  if (rc != AFD_OK) return fail(rc, "adjoint solve did not reach rel_tol %.3g", rel_tol);
+  return AFD_OK;
 }
 
 // Top-k selection on device keys (stream s); kept/E written on the device.

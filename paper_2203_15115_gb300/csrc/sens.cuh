@@ -146,4 +146,126 @@ __global__ void k_invdiag(Grid gr, const double* __restrict__ Emod, double d0, T
   }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint p-norm stress sensitivity (Eq. 3.3, read with the adjoint state):
+//   sigma_PN = (sum_e s_e^p)^(1/p), s_e the centroid von Mises stress,
+//   K lambda = -d sigma_PN / d u,
+//   T_sigma = 4/(1+nu) sigma(u):eps(lambda) - (1-3 nu)/(1-nu^2) tr sigma(u) tr eps(lambda).
+// FP64 throughout (once per topology).
+// ---------------------------------------------------------------------------
+
+// Centroid strain (xx, yy, zz, xy, yz, zx; tensor shear) of element (i,j,k)
+// from the nodal vector v (stride 3 per node), FP64.
+__device__ __forceinline__ void centroid_strain64(const Grid& gr, const double* v, int i, int j, int k, double inv4h,
+                                                  double (&eps)[6]) {
+  double h[3][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int n = (i + (a & 1)) + gr.nnx * ((j + ((a >> 1) & 1)) + gr.nny * (k + ((a >> 2) & 1)));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h[c][a] = v[3 * (size_t)n + c];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) wht8_fwd(h[c]);
+  // centroid gradient F_dj = h[d][1<<j] / (4h)
+  eps[0] = h[0][1] * inv4h;
+  eps[1] = h[1][2] * inv4h;
+  eps[2] = h[2][4] * inv4h;
+  eps[3] = 0.5 * (h[0][2] + h[1][1]) * inv4h;
+  eps[4] = 0.5 * (h[1][4] + h[2][2]) * inv4h;
+  eps[5] = 0.5 * (h[2][1] + h[0][4]) * inv4h;
+}
+
+// D[rhs][q][e] (q = xx, yy, zz, xy, yz, zx) = d sigma_PN / d eps_e
+//   = 2 mu E_e (3/2) sigma_PN^(1-p) s_e^(p-2) dev(sigma_e)   (dev is traceless)
+__global__ void __launch_bounds__(256)
+k_pnorm_dsig(Grid gr, const double* __restrict__ u, const double* __restrict__ Emod, FieldConsts F, double p,
+             const double* __restrict__ pn, double* __restrict__ D) {
+  const int rhs = blockIdx.y;
+  const double* ur = u + (size_t)rhs * gr.vs;
+  const double PN = pn[rhs];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < gr.nelem; e += gridDim.x * blockDim.x) {
+    const int i = e % gr.nx, j = (e / gr.nx) % gr.ny, k = e / (gr.nx * gr.ny);
+    double eps[6];
+    centroid_strain64(gr, ur, i, j, k, F.inv4h, eps);
+    const double E = Emod[e];
+    const double tre = eps[0] + eps[1] + eps[2];
+    const double lam = F.lam * E, mu2 = 2.0 * F.mu * E;
+    double sg[6];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) sg[q] = lam * tre + mu2 * eps[q];
+#pragma unroll
+    for (int q = 3; q < 6; ++q) sg[q] = mu2 * eps[q];
+    const double pm = (sg[0] + sg[1] + sg[2]) / 3.0;
+    double dv[6] = {sg[0] - pm, sg[1] - pm, sg[2] - pm, sg[3], sg[4], sg[5]};
+    const double dd = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2] + 2.0 * (dv[3] * dv[3] + dv[4] * dv[4] + dv[5] * dv[5]);
+    const double vm = sqrt(1.5 * dd);
+    const double coef = (vm > 0.0 && PN > 0.0) ? 1.5 * pow(PN, 1.0 - p) * pow(vm, p - 2.0) : 0.0;
+    const double f = mu2 * coef;
+    double* Dr = D + (size_t)rhs * 6 * gr.nelem;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) Dr[(size_t)q * gr.nelem + e] = f * dv[q];
+  }
+}
+
+// g[rhs][3n+c] = -sum over the elements e of node n of sum_j D_e[c][j] dN_a/dx_j
+// at the centroid (dN_a/dx_j = (2 a_j - 1) / (4h)); zero on fixed DOFs.
+// Gathered per node in a fixed element order (deterministic).
+__global__ void __launch_bounds__(256)
+k_pnorm_adjoint_rhs(Grid gr, const double* __restrict__ D, const uint8_t* __restrict__ fixed, double inv4h,
+                    double* __restrict__ g) {
+  const int rhs = blockIdx.y;
+  const double* Dr = D + (size_t)rhs * 6 * gr.nelem;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gr.nnodes; n += gridDim.x * blockDim.x) {
+    const int i = n % gr.nnx, j = (n / gr.nnx) % gr.nny, k = n / (gr.nnx * gr.nny);
+    double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      // element (i - bx, j - by, k - bz) holds node n as its local node a = b
+      const int ei = i - (b & 1), ej = j - ((b >> 1) & 1), ek = k - ((b >> 2) & 1);
+      if (ei < 0 || ei >= gr.nx || ej < 0 || ej >= gr.ny || ek < 0 || ek >= gr.nz) continue;
+      const size_t e = (size_t)ei + (size_t)gr.nx * (ej + (size_t)gr.ny * ek);
+      const double gx = (2 * (b & 1) - 1) * inv4h, gy = (2 * ((b >> 1) & 1) - 1) * inv4h,
+                   gz = (2 * ((b >> 2) & 1) - 1) * inv4h;
+      const double xx = Dr[e], yy = Dr[gr.nelem + e], zz = Dr[2 * (size_t)gr.nelem + e];
+      const double xy = Dr[3 * (size_t)gr.nelem + e], yz = Dr[4 * (size_t)gr.nelem + e],
+                   zx = Dr[5 * (size_t)gr.nelem + e];
+      acc[0] += xx * gx + xy * gy + zx * gz;
+      acc[1] += xy * gx + yy * gy + yz * gz;
+      acc[2] += zx * gx + yz * gy + zz * gz;
+    }
+    const uint8_t fb = fixed ? fixed[n] : 0;
+    double* gr_ = g + (size_t)rhs * gr.vs + 3 * (size_t)n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gr_[c] = ((fb >> c) & 1) ? 0.0 : -acc[c];
+  }
+}
+
+// out[rhs][e] = T_sigma at the centroid from u and the adjoint lambda.
+__global__ void __launch_bounds__(256)
+k_stress_topo(Grid gr, const double* __restrict__ u, const double* __restrict__ lam_adj,
+              const double* __restrict__ Emod, FieldConsts F, float* __restrict__ out) {
+  const int rhs = blockIdx.y;
+  const double* ur = u + (size_t)rhs * gr.vs;
+  const double* lr = lam_adj + (size_t)rhs * gr.vs;
+  const double nu = F.nu;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < gr.nelem; e += gridDim.x * blockDim.x) {
+    const int i = e % gr.nx, j = (e / gr.nx) % gr.ny, k = e / (gr.nx * gr.ny);
+    double eu[6], el[6];
+    centroid_strain64(gr, ur, i, j, k, F.inv4h, eu);
+    centroid_strain64(gr, lr, i, j, k, F.inv4h, el);
+    const double E = Emod[e];
+    const double tre = eu[0] + eu[1] + eu[2];
+    const double lam = F.lam * E, mu2 = 2.0 * F.mu * E;
+    double sg[6];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) sg[q] = lam * tre + mu2 * eu[q];
+#pragma unroll
+    for (int q = 3; q < 6; ++q) sg[q] = mu2 * eu[q];
+    const double se = sg[0] * el[0] + sg[1] * el[1] + sg[2] * el[2] + 2.0 * (sg[3] * el[3] + sg[4] * el[4] + sg[5] * el[5]);
+    const double trs = sg[0] + sg[1] + sg[2], trl = el[0] + el[1] + el[2];
+    out[(size_t)rhs * gr.nelem + e] = (float)(4.0 / (1.0 + nu) * se - (1.0 - 3.0 * nu) / (1.0 - nu * nu) * trs * trl);
+  }
+}
+
 }  // namespace afd

@@ -314,3 +314,32 @@ def test_levelset_update_with_casting_matches_oracle(axis, parting):
         if half.shape[0] > 1:
             assert not np.any(~half[:-1] & half[1:])
     m.close()
+
+
+@pytest.mark.parametrize("precision", [afd.AFD_MIXED, afd.AFD_FP64])
+def test_stress_sensitivity_matches_oracle_adjoint(precision):
+    """Eq. 3.3 with the adjoint state: lambda solves K lambda = -d sigma_PN/du and
+    T_sigma follows from sigma(u) and eps(lambda), against the oracle's direct
+    solves.  sigma_PN comes from the float32 von Mises field, whose rounding
+    enters the adjoint right-hand side scaled by (p - 1): tolerance 2e-6."""
+    w = small_cantilever(20, 10, 8, seed=6, n_spheres=4, rmin=1.5, rmax=3.0, group=4, n_rhs=2)
+    m, u, _ = _solve(w, precision, 1e-10)
+    K = fe.assemble(w.nx, w.ny, w.nz, w.E)
+    p = 6.0
+    out = np.zeros((2, m.nelem), np.float32)
+    lam = np.zeros_like(w.f)
+    st = m.stress_sensitivity(p, 1e-10, out, lam)
+    free = w.fixed == 0
+    for r in range(2):
+        assert st[r]["rel_residual"] <= 1e-10
+        uref = fe.solve_direct(K, w.f[r], w.fixed)
+        g = sensitivity.pnorm_stress_gradient(w.nx, w.ny, w.nz, w.E, uref, p)
+        lref = fe.solve_direct(K, -g * free, w.fixed)
+        assert np.linalg.norm(lam[r] - lref) <= 2e-6 * np.linalg.norm(lref)
+        T = sensitivity.stress_topological_sensitivity(w.nx, w.ny, w.nz, w.E, uref, lref)
+        assert np.max(np.abs(out[r] - T)) <= 2e-6 * np.max(np.abs(T))
+    # the primal solution is untouched by the adjoint solve
+    J = m.compliance()
+    for r in range(2):
+        assert abs(J[r] - float(w.f[r] @ u[r])) <= 1e-12 * abs(J[r])
+    m.close()
