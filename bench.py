@@ -280,11 +280,14 @@ def run_ours(args):
         "clocks": clk,
         "last_step": {k: v for k, v in last.items() if k != "stats"},
     }
+    if world == 1 and args.batched:
+        out["next_rows"] = next_rows_leg(afd, torch, dev, mesh, w, peak, peak_kind)
     mesh.close()
     if world == 1 and args.batched:
         out["batched"] = batched_leg(afd, torch, dev, flush)
     if world == 1 and args.levelset:
         out["levelset"] = levelset_leg(afd, torch, dev)
+        out["constrained"] = constrained_leg(afd, torch, dev)
     if world == 1 and args.serve:
         del flush
         torch.cuda.empty_cache()
@@ -421,6 +424,68 @@ def levelset_leg(afd, torch, dev):
             "J_over_J0_final": round(hist[-1]["J"] / hist[0]["J"], 5), "constraint_J_le": "1.6 J0",
             "volume_fraction_final": round(hist[-1]["volume_fraction"], 4),
             "stencil_warps_planes": list(group)}
+
+
+def next_rows_leg(afd, torch, dev, mesh, w, peak, peak_kind):
+    """The widened rows on GB300: the casting scan (Sec. 3.7) of a 384x192x192
+    level-set field, an HBM-bound kernel (4 B read + 4 B written per element),
+    timed with CUDA events over 20 calls per axis; and the adjoint p-norm stress
+    sensitivity (Eq. 3.3: d sigma_PN/du, the adjoint solve to 1e-6, T_sigma) on
+    the benchmark mesh, timed on the host clock."""
+    nx, ny, nz = 384, 192, 192
+    keys = torch.rand(nx * ny * nz, dtype=torch.float32, device=dev)
+    cast = {}
+    for axis, parting in ((2, 96), (1, 0), (0, 192)):
+        afd.afd_casting_scan(keys, nx, ny, nz, axis, parting)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            afd.afd_casting_scan(keys, nx, ny, nz, axis, parting)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        b = 8 * nx * ny * nz
+        cast["xyz"[axis]] = {"ms": round(ms, 4), "GB/s": round(b / (ms * 1e-3) / 1e9, 1),
+                             "frac": round(b / (ms * 1e-3) / 1e9 / peak, 4)}
+    del keys
+    out = torch.empty((1, w.nx * w.ny * w.nz), dtype=torch.float32, device=dev)
+    mesh.solve(w.tol)
+    mesh.stress_sensitivity(8.0, w.tol, out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = mesh.stress_sensitivity(8.0, w.tol, out)
+    torch.cuda.synchronize()
+    adj_ms = (time.perf_counter() - t0) * 1e3
+    return {"casting_scan_384x192x192": {"bytes_per_call": 8 * nx * ny * nz, "peak": peak, "peak_source": peak_kind,
+                                         "per_axis": cast},
+            "stress_sensitivity_128x64x64": {"p": 8.0, "ms": round(adj_ms, 3), "adjoint_iters": st[0]["iters"],
+                                             "adjoint_rel_residual": st[0]["rel_residual"]}}
+
+
+def constrained_leg(afd, torch, dev, max_fea: int = 40):
+    """The algorithm of Sec. 3.8 on the solid 128x64x64 cantilever: minimise
+    the volume with hard constraints J <= 1.5 J_0 and sigma_PN <= 2 sigma_0
+    (p = 8), volume steps of 0.05 halved on violation, each analysis a mixed
+    solve to 1e-6 warm-started, plus the adjoint stress sensitivity.  Timed on
+    the host clock over at most `max_fea` analyses."""
+    from synthetic import clamp_face_x0, edge_load
+
+    nx, ny, nz = 128, 64, 64
+    m = afd.Mesh(nx, ny, nz, group=16)
+    m.set_loads_bcs(edge_load(nx, ny, nz)[None], clamp_face_x0(nx, ny, nz))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = afd.run_constrained_topology(m, np.ones(nx * ny * nz), compliance=1.5, stress=2.0, p=8.0, dv0=0.05,
+                                       v_min=0.3, max_fea=max_fea, tol=1e-6)
+    total = time.perf_counter() - t0
+    m.close()
+    h = res["history"]
+    return {"workload": "cantilever_128x64x64_solid", "constraints": "J <= 1.5 J0, sigma_PN(p=8) <= 2 sigma0 (hard)",
+            "total_s": round(total, 3), "analyses": res["fea"], "stop": res["stop"],
+            "final_volume_fraction": round(res["volume_fraction"], 4),
+            "final_J_over_J0": round(max(x["J"] for x in h if x["v"] == res["volume_fraction"] and not x["violated"])
+                                     / res["reference"]["J"], 5),
+            "violations": sum(1 for x in h if x["violated"]), "ms_per_analysis": round(total * 1e3 / res["fea"], 1)}
 
 
 def batched_leg(afd, torch, dev, flush, reps: int = 3):

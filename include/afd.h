@@ -162,6 +162,17 @@ int afd_levelset_update(afd_mesh* m, int kind, const double* weights, double vol
 int afd_levelset_update_cast(afd_mesh* m, int kind, const double* weights, double volume_fraction, int axis,
                              int parting, double* tau_out, uint8_t* kept_out);
 
+/* Level-set update from caller-given fields (Eqs. 3.6, 3.17-3.18), e.g. the
+ * compliance and stress sensitivities of the Sec. 3.8 algorithm: nfields
+ * per-element float32 fields (field-major, nfields*nelem, host or device),
+ * each divided by its largest magnitude, multiplied by weights[i] and added
+ * (float32, fixed order), then the casting scan when axis >= 0 (parting as in
+ * afd_levelset_update_cast; axis < 0: none), the cut keeping round(v nelem)
+ * elements, and the new moduli (kept 1, others opt.e_void). */
+int afd_levelset_update_fields(afd_mesh* m, const float* fields, int fields_on_device, int nfields,
+                               const double* weights, double volume_fraction, int axis, int parting, double* tau_out,
+                               uint8_t* kept_out);
+
 /* Casting constraint (Sec. 3.7) on a per-element float field, in place on the
  * device (keys: nx*ny*nz floats, element order e = i + nx (j + ny k)): along
  * every line parallel to `axis`, each half of the part (element index >=

@@ -44,7 +44,7 @@ EXPORTS = [
     "afd_stencil_warps", "afd_solver_phase_times", "afd_time_dpcg_kernels", "afd_set_stencil_shape",
     "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
     "afd_server_submit_session", "afd_server_end_session", "afd_server_resident", "afd_levelset_update_cast",
-    "afd_casting_scan", "afd_stress_sensitivity",
+    "afd_casting_scan", "afd_stress_sensitivity", "afd_levelset_update_fields",
 ]
 
 
@@ -132,6 +132,7 @@ def lib() -> ctypes.CDLL:
             "afd_levelset_update_cast": (i, [vp, i, ctypes.POINTER(d), d, i, i, ctypes.POINTER(d), vp]),
             "afd_casting_scan": (i, [vp, i, i, i, i, i, vp]),
             "afd_stress_sensitivity": (i, [vp, d, d, vp, i, ctypes.POINTER(afd_stats), vp, i]),
+            "afd_levelset_update_fields": (i, [vp, vp, i, i, ctypes.POINTER(d), d, i, i, ctypes.POINTER(d), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -272,6 +273,24 @@ def afd_stress_sensitivity(mesh, n_rhs: int, p: float, rel_tol: float, out, lamb
         pl, ld, _k2 = _arr(lambda_out, np.float64)
     _check(lib().afd_stress_sensitivity(mesh, p, rel_tol, po, od, st, pl, ld), [s.as_dict() for s in st])
     return [s.as_dict() for s in st]
+
+
+def afd_levelset_update_fields(mesh, fields, weights, volume_fraction: float, casting=None, kept_out=None) -> float:
+    """Level-set cut of sum_i weights[i] * fields[i] / max|fields[i]| (fields: (nf, nelem)
+    float32, numpy or torch); casting = (axis, parting) or None."""
+    nf = int(fields.shape[0])
+    pf, on_dev, _k = _arr(fields, np.float32)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    assert w.size == nf
+    tau = ctypes.c_double()
+    pk = None
+    if kept_out is not None:
+        assert kept_out.dtype == np.uint8 and kept_out.flags.c_contiguous
+        pk = ctypes.c_void_p(kept_out.ctypes.data)
+    axis, parting = casting if casting is not None else (-1, 0)
+    _check(lib().afd_levelset_update_fields(mesh, pf, on_dev, nf, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            volume_fraction, int(axis), int(parting), ctypes.byref(tau), pk))
+    return tau.value
 
 
 def afd_casting_scan(keys, nx: int, ny: int, nz: int, axis: int, parting: int, stream=None) -> None:
@@ -495,6 +514,103 @@ def run_volume_minimisation(mesh: "Mesh", steps: int = 20, dv: float = 0.02, j_f
         if on_step:
             on_step(hist[-1])
     return hist
+
+
+def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] = None, stress: Optional[float] = None,
+                             p: float = 8.0, dv0: float = 0.05, dv_min: Optional[float] = None, v_min: float = 0.05,
+                             max_fea: int = 200, conv: float = 0.01, tol: float = 1e-6, casting=None,
+                             on_step=None) -> dict:
+    """The algorithm of Sec. 3.8 for min |Omega| with hard constraints
+    J <= compliance * J_0 and sigma_PN <= stress * sigma_0 (either may be None),
+    over the library's calls (each step runs in its kernels):
+      2. analysis: solve (warm start), J, sigma_PN (p-norm of Eq. 3.3);
+      3. g_i = value / (alpha_i value_0) - 1 and the AL update (Eqs. 3.11-3.12);
+      4./9. a violated hard constraint returns to the last feasible design with
+         the volume step halved (stop when it falls below dv_min, default 0.1 dv0);
+      5./6. the augmented level set (Eq. 3.17): strain-energy field weighted by
+         the compliance constraint's (mu + gamma g)+, the adjoint stress field
+         T_sigma by the stress constraint's, optional casting, cut at the
+         target volume;
+      7./8. when J changed by less than `conv` since the previous analysis at
+         the same target, the target drops by the volume step (stop below
+         v_min).
+    The volume objective's sensitivity is constant and does not change the
+    ranking.  Returns the history, the final feasible design's kept mask and
+    volume fraction, and why it stopped."""
+    ne = mesh.nelem
+    dv_min = 0.1 * dv0 if dv_min is None else dv_min
+    cons = [c for c in (("J", compliance), ("sigma", stress)) if c[1] is not None]
+    al = {name: afd_al_init() for name, _ in cons}
+    E_cur = np.asarray(E_init, dtype=np.float64).copy()
+    mesh.set_element_moduli(E_cur)
+    e_void = mesh.options.e_void
+
+    def analyse(warm):
+        st = mesh.solve(tol, warm_start=warm)
+        J = float(mesh.compliance()[0])
+        sig = float(mesh.pnorm_stress(p)[0]) if stress is not None else None
+        return st[0], {"J": J, "sigma": sig}
+
+    st, val = analyse(False)
+    fea = 1
+    ref = dict(val)
+    feasible = {"E": E_cur.copy(), "v": 1.0, "kept": np.ones(ne, np.uint8)}
+    v_design, dv = 1.0, dv0
+    v_target = 1.0 - dv
+    J_prev = None
+    kept = np.ones(ne, np.uint8)
+    hist = []
+    reason = "max_fea"
+    while True:
+        g = {name: val[name] / (alpha * ref[name]) - 1.0 for name, alpha in cons}
+        for name, _ in cons:
+            afd_al_update(al[name], g[name])
+        violated = any(g[name] > 0.0 for name, _ in cons)
+        rec = {"fea": fea, "v": v_design, "target": v_target, "dv": dv, "J": val["J"], "sigma": val["sigma"],
+               "g": dict(g), "violated": violated, "iters": st["iters"], "rel_residual": st["rel_residual"],
+               "mu": {n: al[n].mu for n, _ in cons}, "gamma": {n: al[n].gamma for n, _ in cons}}
+        hist.append(rec)
+        if on_step:
+            on_step(rec)
+        if fea >= max_fea:
+            break
+        if violated:
+            dv *= 0.5
+            if dv < dv_min:
+                reason = "dv_min"
+                break
+            E_cur = feasible["E"].copy()
+            mesh.set_element_moduli(E_cur)
+            v_design, v_target = feasible["v"], feasible["v"] - dv
+            st, val = analyse(True)
+            fea += 1
+            J_prev = None
+        else:
+            feasible = {"E": E_cur.copy(), "v": v_design, "kept": kept.copy()}
+            if J_prev is not None and abs(val["J"] - J_prev) <= conv * abs(J_prev):
+                if v_target - dv < v_min:
+                    reason = "v_min"
+                    break
+                v_target -= dv
+            J_prev = val["J"]
+        fields, weights = [], []
+        if compliance is not None:
+            f = np.zeros((1, ne), np.float32)
+            mesh.sensitivity(AFD_SENS_STRAIN_ENERGY, f)
+            fields.append(f[0])
+            weights.append(afd_al_weight(al["J"]))
+        if stress is not None:
+            f = np.zeros((1, ne), np.float32)
+            mesh.stress_sensitivity(p, tol, f)
+            fields.append(f[0])
+            weights.append(afd_al_weight(al["sigma"]))
+        afd_levelset_update_fields(mesh.h, np.stack(fields), weights, v_target, casting, kept)
+        E_cur = np.where(kept != 0, 1.0, e_void)
+        v_design = v_target
+        st, val = analyse(True)
+        fea += 1
+    return {"history": hist, "kept": feasible["kept"], "E": feasible["E"], "volume_fraction": feasible["v"],
+            "stop": reason, "fea": fea, "reference": ref}
 
 
 class Mesh:

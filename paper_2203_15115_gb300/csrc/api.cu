@@ -149,6 +149,8 @@ struct afd_mesh {
   unsigned long long* ptime = nullptr;   // [10] phase times of the persistent solver (ns), iterations, barrier waits
   // adjoint stress sensitivity: lambda, its right-hand side, d sigma_PN / d eps per element, sigma_PN per RHS
   double *lam64 = nullptr, *gadj = nullptr, *dsig = nullptr, *pn_d = nullptr;
+  float* lsbuf = nullptr;      // caller fields of afd_levelset_update_fields
+  size_t lsbuf_cap = 0;
   int adj_cap = 0;
   int nsplit_aw = 1;
   bool coarse_valid = false;
@@ -923,7 +925,7 @@ void afd_destroy(afd_mesh* m) {
   dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gbox); dfree(m->aw_off); dfree(m->aw_node);
   dfree(m->grec); dfree(m->gcount); dfree(m->upart);
   dfree(m->ppart); dfree(m->prec); dfree(m->gbar); dfree(m->ptime);
-  dfree(m->lam64); dfree(m->gadj); dfree(m->dsig); dfree(m->pn_d);
+  dfree(m->lam64); dfree(m->gadj); dfree(m->dsig); dfree(m->pn_d); dfree(m->lsbuf);
   if (m->ev) cudaEventDestroy(m->ev);
   if (m->s) cudaStreamDestroy(m->s);
   delete m;
@@ -1470,15 +1472,7 @@ int afd_levelset_update_cast(afd_mesh* m, int kind, const double* weights, doubl
   return levelset_update_impl(m, kind, weights, volume_fraction, axis, parting, tau_out, kept_out);
 }
 
-static int levelset_update_impl(afd_mesh* m, int kind, const double* weights, double volume_fraction, int axis,
-                                int parting, double* tau_out, uint8_t* kept_out) {
-  if (!m || !weights) return fail(AFD_ERR_INVALID_ARG, "null argument");
-  if (kind < 0 || kind > 2) return fail(AFD_ERR_INVALID_ARG, "unknown field kind %d", kind);
-  if (!std::isfinite(volume_fraction)) return fail(AFD_ERR_INVALID_ARG, "volume fraction must be finite");
-  if (!m->has_solution) return fail(AFD_ERR_STATE, "no solution");
-  DeviceGuard dg(m->device);
-  TRY(enter(m));
-  const int R = m->nrhs;
+static int ensure_select(afd_mesh* m) {
   const int64_t n = m->gr.nelem;
   if (!m->fkeys) {
     TRY(dalloc(&m->fkeys, (size_t)n));
@@ -1488,14 +1482,24 @@ static int levelset_update_impl(afd_mesh* m, int kind, const double* weights, do
     m->sel = st;
     TRY(dalloc(&m->selcnt, (size_t)((n + SEL_CHUNK - 1) / SEL_CHUNK)));
   }
-  TRY(fields_to(m, kind, m->fbuf));
+  return AFD_OK;
+}
+
+// Back end of every level-set update: nf fields (field-major in `fields`,
+// device) divided by their largest magnitude, weighted and added in float32
+// (Eq. 3.17), the casting scan (axis >= 0), the cut at round(v N_e) (Eq. 3.6)
+// and the new moduli.
+static int levelset_cut(afd_mesh* m, const float* fields, int nf, const double* weights, double volume_fraction,
+                        int axis, int parting, double* tau_out, uint8_t* kept_out) {
+  const int64_t n = m->gr.nelem;
+  TRY(ensure_select(m));
   float* dmaxv = m->fsmall + FS_MAXV;
   float* dw = m->fsmall + FS_WEIGHTS;
-  TRY(maxabs_per_rhs(m, m->fbuf, R, dmaxv));
-  std::vector<float> wf(R);
-  for (int r = 0; r < R; ++r) wf[r] = (float)weights[r];
-  CK(cudaMemcpyAsync(dw, wf.data(), R * sizeof(float), cudaMemcpyHostToDevice, m->s));
-  k_combine<<<grid_blocks(n, 256, 4096), 256, 0, m->s>>>((int)n, R, m->fbuf, dw, dmaxv, m->fkeys); m->launches++;
+  TRY(maxabs_per_rhs(m, fields, nf, dmaxv));
+  std::vector<float> wf(nf);
+  for (int r = 0; r < nf; ++r) wf[r] = (float)weights[r];
+  CK(cudaMemcpyAsync(dw, wf.data(), nf * sizeof(float), cudaMemcpyHostToDevice, m->s));
+  k_combine<<<grid_blocks(n, 256, 4096), 256, 0, m->s>>>((int)n, nf, fields, dw, dmaxv, m->fkeys); m->launches++;
   CK(cudaGetLastError());
   if (axis >= 0) TRY(launch_casting_scan(m->s, m->gr.nx, m->gr.ny, m->gr.nz, axis, parting, m->fkeys, &m->launches));
   const double kd = std::floor(volume_fraction * (double)n + 0.5);
@@ -1506,6 +1510,40 @@ static int levelset_update_impl(afd_mesh* m, int kind, const double* weights, do
   if (kept_out) CK(cudaMemcpyAsync(kept_out, m->kept, (size_t)n, cudaMemcpyDeviceToHost, m->s));
   if (tau_out) *tau_out = (double)tau;
   return finish(m);
+}
+
+static int levelset_update_impl(afd_mesh* m, int kind, const double* weights, double volume_fraction, int axis,
+                                int parting, double* tau_out, uint8_t* kept_out) {
+  if (!m || !weights) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (kind < 0 || kind > 2) return fail(AFD_ERR_INVALID_ARG, "unknown field kind %d", kind);
+  if (!std::isfinite(volume_fraction)) return fail(AFD_ERR_INVALID_ARG, "volume fraction must be finite");
+  if (!m->has_solution) return fail(AFD_ERR_STATE, "no solution");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  TRY(fields_to(m, kind, m->fbuf));
+  return levelset_cut(m, m->fbuf, m->nrhs, weights, volume_fraction, axis, parting, tau_out, kept_out);
+}
+
+int afd_levelset_update_fields(afd_mesh* m, const float* fields, int fields_on_device, int nfields,
+                               const double* weights, double volume_fraction, int axis, int parting, double* tau_out,
+                               uint8_t* kept_out) {
+  if (!m || !fields || !weights) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (nfields < 1 || nfields > MAX_RHS) return fail(AFD_ERR_INVALID_ARG, "nfields must be in [1, %d]", MAX_RHS);
+  if (!std::isfinite(volume_fraction)) return fail(AFD_ERR_INVALID_ARG, "volume fraction must be finite");
+  if (axis >= 0) TRY(casting_args_ok(m->gr.nx, m->gr.ny, m->gr.nz, axis, parting));
+  if (!m->has_moduli) return fail(AFD_ERR_STATE, "moduli not set");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const size_t need = (size_t)nfields * m->gr.nelem;
+  if (need > m->lsbuf_cap) {
+    dfree(m->lsbuf);
+    m->lsbuf_cap = 0;
+    TRY(dalloc(&m->lsbuf, need));
+    m->lsbuf_cap = need;
+  }
+  CK(cudaMemcpyAsync(m->lsbuf, fields, need * sizeof(float),
+                     fields_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, m->s));
+  return levelset_cut(m, m->lsbuf, nfields, weights, volume_fraction, axis, parting, tau_out, kept_out);
 }
 
 int afd_apply_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y) {

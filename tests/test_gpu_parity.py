@@ -343,3 +343,47 @@ def test_stress_sensitivity_matches_oracle_adjoint(precision):
     for r in range(2):
         assert abs(J[r] - float(w.f[r] @ u[r])) <= 1e-12 * abs(J[r])
     m.close()
+
+
+def test_constrained_topology_driver_keeps_the_hard_constraints():
+    """The Sec. 3.8 loop with hard compliance and stress constraints: the final
+    feasible design meets both under the oracle's direct solve, its kept count
+    matches its volume fraction, the volume steps follow the algorithm, and the
+    AL scalars follow the oracle's Eqs. 3.11-3.12 on the recorded g."""
+    nx, ny, nz = 24, 12, 12
+    E0 = np.ones(nx * ny * nz)
+    f, fixed = edge_load(nx, ny, nz), clamp_face_x0(nx, ny, nz)
+    m = afd.Mesh(nx, ny, nz, group=4)
+    m.set_loads_bcs(f[None], fixed)
+    res = afd.run_constrained_topology(m, E0, compliance=1.5, stress=2.0, p=8.0, dv0=0.05, v_min=0.3, max_fea=50,
+                                       tol=1e-8)
+    m.close()
+    hist = res["history"]
+    assert res["stop"] in ("dv_min", "v_min", "max_fea")
+    assert res["volume_fraction"] < 1.0
+    K0 = fe.assemble(nx, ny, nz, E0)
+    u0 = fe.solve_direct(K0, f, fixed)
+    J0 = fe.compliance(f, u0)
+    s0 = sensitivity.pnorm(sensitivity.element_von_mises(nx, ny, nz, E0, u0), 8.0)
+    assert abs(res["reference"]["J"] - J0) <= 1e-6 * J0
+    E = res["E"]
+    u = fe.solve_direct(fe.assemble(nx, ny, nz, E), f, fixed)
+    assert fe.compliance(f, u) <= 1.5 * J0 * (1 + 1e-6)
+    assert sensitivity.pnorm(sensitivity.element_von_mises(nx, ny, nz, E, u), 8.0) <= 2.0 * s0 * (1 + 1e-5)
+    assert int(res["kept"].sum()) == levelset.keep_count(res["volume_fraction"], E.size)
+    mu = {"J": levelset.MU0, "sigma": levelset.MU0}
+    gamma = {"J": levelset.GAMMA0, "sigma": levelset.GAMMA0}
+    g_prev = {"J": 0.0, "sigma": 0.0}
+    for k, h in enumerate(hist, start=1):
+        for name in ("J", "sigma"):
+            g = h["g"][name]
+            mu[name] = levelset.multiplier_update(mu[name], gamma[name], g)
+            gamma[name] = levelset.penalty_update(gamma[name], g, g_prev[name], k)
+            g_prev[name] = g
+            assert abs(h["mu"][name] - mu[name]) <= 1e-9 * max(1.0, abs(mu[name]))
+            assert abs(h["gamma"][name] - gamma[name]) <= 1e-9 * gamma[name]
+        assert h["violated"] == any(h["g"][n] > 0 for n in ("J", "sigma"))
+        assert h["rel_residual"] <= 1e-8
+    for a, b in zip(hist, hist[1:]):
+        if a["violated"]:
+            assert b["dv"] == a["dv"] / 2
