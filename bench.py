@@ -50,10 +50,10 @@ sys.path.insert(0, ROOT)
 METRIC = "dCG solve ms & GDOF/s matvec at rel-res 1e-6, mixed vs FP64 on GB300; serve p50/p99"
 VOLUME_FRACTION = 0.9
 UNIT = "ms per topology step (dCG solve to rel-res 1e-6 + coarse setup + J + sensitivity + level-set)"
-# DRAM bytes (read + write) per launch of the FP32 apply kernel, from one ncu capture
-# (profiles/stencil_fp32_128x64x64_dram.md), keyed by mesh and CTA shape (warps, planes);
-# any other shape reports null.
-STENCIL_DRAM_BYTES = {(128, 64, 64, 8, 6): 9198592}
+# DRAM bytes (read + write) per launch of the FP32 apply kernel, each from one ncu capture
+# (profiles/stencil_fp32_128x64x64_dram.md, profiles/stencil_fp32_384x192x192_async_dram.md), keyed by mesh
+# and CTA shape (warps, planes, async staging); any other shape reports null.
+STENCIL_DRAM_BYTES = {(128, 64, 64, 8, 6, 0): 9198592, (384, 192, 192, 8, 12, 1): 378244608}
 
 
 def rank_info():
@@ -190,7 +190,7 @@ def run_ours(args):
     bytes32 = 2 * 3 * nn * 4 + 4 * ne + nn          # read u, write y, read E, read fixed bits
     peak, peak_kind = measured_peaks()
     achieved = bytes32 / (mv_ms * 1e-3) / 1e9
-    shape = (afd.afd_stencil_warps(mesh.h), afd.afd_stencil_depth(mesh.h))
+    shape = (afd.afd_stencil_warps(mesh.h), afd.afd_stencil_depth(mesh.h), afd.afd_stencil_async(mesh.h))
     traffic = STENCIL_DRAM_BYTES.get((w.nx, w.ny, w.nz) + shape)
 
     # HBM roofline on the largest mesh of the method (384x192x192, 43 M DOFs): the
@@ -259,6 +259,7 @@ def run_ours(args):
         "config": {"workload": w.name, "elements": ne, "dofs": 3 * nn, "group": mesh.options.group or "auto",
                    "stencil_planes_per_cta": afd.afd_stencil_depth(mesh.h),
                    "stencil_warps_per_cta": afd.afd_stencil_warps(mesh.h),
+                   "stencil_async_staging": afd.afd_stencil_async(mesh.h),
                    "inner_solver": "persistent cooperative kernel" if mesh.options.persistent else "CUDA-graph chunks",
                    "tol": w.tol, "volume_fraction": VOLUME_FRACTION, "l2": "flushed (512 MB write) between timed steps",
                    "parallelism": f"replicas x{world}"},
@@ -310,12 +311,13 @@ def large_mesh_roofline(afd, torch, dev, peak, peak_kind, n=384):
     u = torch.randn((1, mesh.ndof), dtype=torch.float32, device=dev)
     y = torch.empty_like(u)
     best = None
-    for warps, planes in ((8, 4), (8, 6), (8, 8), (8, 12), (16, 8), (16, 16)):
-        afd.afd_set_stencil_shape(mesh.h, warps, planes)
-        afd.afd_time_stiffness(mesh.h, afd.AFD_F32, 1, u, y, 5)
-        ms = afd.afd_time_stiffness(mesh.h, afd.AFD_F32, 1, u, y, 50)
-        if best is None or ms < best[0]:
-            best = (ms, warps, planes)
+    for staging in (0, 1):
+        for warps, planes in ((8, 4), (8, 6), (8, 8), (8, 12), (16, 8), (16, 16)):
+            afd.afd_set_stencil_shape(mesh.h, warps, planes, staging)
+            afd.afd_time_stiffness(mesh.h, afd.AFD_F32, 1, u, y, 5)
+            ms = afd.afd_time_stiffness(mesh.h, afd.AFD_F32, 1, u, y, 50)
+            if best is None or ms < best[0]:
+                best = (ms, warps, planes, staging)
     mesh.close()
     del u, y
     nn = (nx + 1) * (ny + 1) * (nz + 1)
@@ -324,7 +326,8 @@ def large_mesh_roofline(afd, torch, dev, peak, peak_kind, n=384):
     return {"kernel": "stencil2_kernel<TY,ST_APPLY> (K u, FP32)", "bound": "hbm", "achieved": round(ach, 1),
             "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "frac_of_nominal_8TBs": round(ach / 8000.0, 4),
             "peak_source": peak_kind, "bytes_per_launch": b, "ms_per_launch": round(best[0], 5),
-            "gdofs": round(3 * nn / (best[0] * 1e-3) / 1e9, 2), "warps": best[1], "planes": best[2]}
+            "gdofs": round(3 * nn / (best[0] * 1e-3) / 1e9, 2), "warps": best[1], "planes": best[2],
+            "async_staging": best[3], "traffic": STENCIL_DRAM_BYTES.get((nx, ny, nz) + best[1:])}
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
@@ -657,10 +660,11 @@ def launch_summary(path: str):
         print(f"{k[:60]:60s} {c:8d} {t:10.1f} {t / total:7.1%}")
 
 
-def profile_stencil(n: int, launches: int, warps: int = 0, planes: int = 0):
+def profile_stencil(n: int, launches: int, warps: int = 0, planes: int = 0, staging: int = 0):
     """Apply K u on an n x n/2 x n/2 all-solid mesh (FP32, one RHS) `launches`
-    times, in the CTA shape given (0 = the size heuristic): a case for ncu
-    captures of the stencil kernel (n >= 320 is larger than L2)."""
+    times, in the CTA shape and plane staging given (0 = the size heuristic,
+    register prefetch): a case for ncu captures of the stencil kernel (n >= 320
+    is larger than L2)."""
     import torch
 
     import paper_2203_15115_gb300 as afd
@@ -668,17 +672,20 @@ def profile_stencil(n: int, launches: int, warps: int = 0, planes: int = 0):
     nx, ny, nz = n, n // 2, n // 2
     mesh = afd.Mesh(nx, ny, nz, stencil_warps=warps, stencil_planes=planes)
     mesh.set_element_moduli(np.ones(nx * ny * nz))
+    if warps and planes:
+        afd.afd_set_stencil_shape(mesh.h, warps, planes, staging)
     u = torch.randn((1, mesh.ndof), dtype=torch.float32, device="cuda")
     y = torch.empty_like(u)
     ms = afd.afd_time_stiffness(mesh.h, afd.AFD_F32, 1, u, y, launches)
     nn = (nx + 1) * (ny + 1) * (nz + 1)
     b = 2 * 3 * nn * 4 + 4 * nx * ny * nz + nn
     print(json.dumps({"mesh": [nx, ny, nz], "ms": ms, "GB/s": b / (ms * 1e-3) / 1e9, "bytes": b,
-                      "warps": afd.afd_stencil_warps(mesh.h), "planes": afd.afd_stencil_depth(mesh.h)}))
+                      "warps": afd.afd_stencil_warps(mesh.h), "planes": afd.afd_stencil_depth(mesh.h),
+                      "async_staging": afd.afd_stencil_async(mesh.h)}))
     mesh.close()
 
 
-def profile_solve(warps: int, planes: int, solves: int):
+def profile_solve(warps: int, planes: int, solves: int, staging: int = 0):
     """`solves` mixed solves of the 128x64x64 voided cantilever with the FP32
     stencil in a pinned CTA shape (no autotuning): the solver's kernels in
     their solve-time configuration, for ncu captures."""
@@ -690,6 +697,7 @@ def profile_solve(warps: int, planes: int, solves: int):
     w = cantilever_128x64x64_voids()
     mesh = afd.Mesh(w.nx, w.ny, w.nz, group=w.group, stencil_warps=warps or 8, stencil_planes=planes or 6)
     mesh.set_loads_bcs(w.f, w.fixed)
+    afd.afd_set_stencil_shape(mesh.h, warps or 8, planes or 6, staging)
     for _ in range(solves):
         mesh.set_element_moduli(w.E)
         st = mesh.solve(w.tol)
@@ -717,13 +725,15 @@ def main():
                     help="only run --steps mixed solves of the 128x64x64 workload in a pinned stencil shape (for ncu)")
     ap.add_argument("--stencil-warps", type=int, default=0, help="pinned FP32 stencil warps per CTA (profile modes)")
     ap.add_argument("--stencil-planes", type=int, default=0, help="pinned FP32 stencil planes per CTA (profile modes)")
+    ap.add_argument("--stencil-async", type=int, default=0, choices=(0, 1),
+                    help="pinned FP32 stencil plane staging, 1 = cp.async (profile modes)")
     args = ap.parse_args()
     if args.launch_summary:
         launch_summary(args.launch_summary)
     elif args.profile_stencil:
-        profile_stencil(args.profile_stencil, max(1, args.steps), args.stencil_warps, args.stencil_planes)
+        profile_stencil(args.profile_stencil, max(1, args.steps), args.stencil_warps, args.stencil_planes, args.stencil_async)
     elif args.profile_solve:
-        profile_solve(args.stencil_warps, args.stencil_planes, max(1, args.steps))
+        profile_solve(args.stencil_warps, args.stencil_planes, max(1, args.steps), args.stencil_async)
     elif args.impl == "reference":
         run_reference(args)
     else:

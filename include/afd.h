@@ -248,8 +248,14 @@ int afd_stencil_depth(const afd_mesh* m);
 int afd_stencil_warps(const afd_mesh* m);
 
 /* Pin the FP32 stencil's CTA shape (8 or 16 warps, planes >= 1, clipped to the
- * mesh) on an existing mesh; the autotuner then leaves this mesh alone. */
-int afd_set_stencil_shape(afd_mesh* m, int warps, int planes);
+ * mesh) and its plane staging (async_staging = 1: each thread stages the next
+ * planes' node values in shared memory with cp.async, two planes ahead; 0:
+ * register prefetch one plane ahead) on an existing mesh; the autotuner then
+ * leaves this mesh alone. */
+int afd_set_stencil_shape(afd_mesh* m, int warps, int planes, int async_staging);
+
+/* 1 when the FP32 stencil stages planes with cp.async (chosen with the shape). */
+int afd_stencil_async(const afd_mesh* m);
 
 /* Measurement aid for the CUDA-graph inner solver: continues the last FP32
  * inner DPCG iteration of a completed AFD_MIXED solve for `iters` iterations

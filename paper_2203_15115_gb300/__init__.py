@@ -42,6 +42,7 @@ EXPORTS = [
     "afd_ndof", "afd_nelem", "afd_destroy", "afd_last_error", "afd_al_init", "afd_al_update", "afd_al_weight",
     "afd_time_stiffness", "afd_kernel_launches", "afd_select_topk_noalloc", "afd_stencil_depth",
     "afd_stencil_warps", "afd_solver_phase_times", "afd_time_dpcg_kernels", "afd_set_stencil_shape",
+    "afd_stencil_async",
     "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
     "afd_server_submit_session", "afd_server_end_session", "afd_server_resident", "afd_levelset_update_cast",
     "afd_casting_scan", "afd_stress_sensitivity", "afd_levelset_update_fields",
@@ -118,7 +119,8 @@ def lib() -> ctypes.CDLL:
             "afd_select_topk_noalloc": (i, [vp, i64, i64, vp, ctypes.POINTER(ctypes.c_float), vp]),
             "afd_stencil_depth": (i, [vp]),
             "afd_stencil_warps": (i, [vp]),
-            "afd_set_stencil_shape": (i, [vp, i, i]),
+            "afd_set_stencil_shape": (i, [vp, i, i, i]),
+            "afd_stencil_async": (i, [vp]),
             "afd_solver_phase_times": (i, [vp, ctypes.POINTER(ctypes.c_double), i]),
             "afd_time_dpcg_kernels": (i, [vp, i, i, i, ctypes.POINTER(ctypes.c_double)]),
             "afd_mesh_bytes": (ctypes.c_size_t, [i, i, i, i, ctypes.POINTER(afd_options)]),
@@ -359,8 +361,12 @@ def afd_stencil_warps(mesh) -> int:
     return int(lib().afd_stencil_warps(mesh))
 
 
-def afd_set_stencil_shape(mesh, warps: int, planes: int) -> None:
-    _check(lib().afd_set_stencil_shape(mesh, warps, planes))
+def afd_set_stencil_shape(mesh, warps: int, planes: int, async_staging: int = 0) -> None:
+    _check(lib().afd_set_stencil_shape(mesh, warps, planes, async_staging))
+
+
+def afd_stencil_async(mesh) -> int:
+    return int(lib().afd_stencil_async(mesh))
 
 
 def afd_time_dpcg_kernels(mesh, iters: int = 50, nsplit: int = 0, variant: int = 0) -> dict:

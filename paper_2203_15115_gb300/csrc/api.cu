@@ -99,6 +99,7 @@ struct afd_mesh {
   cudaEvent_t ev = nullptr;
   int kz = 8;                  // node planes per CTA of the FP64 stencil
   int kz32 = 8, ty32 = 16;     // planes per CTA and warps per CTA of the FP32 stencil
+  int async32 = 0;             // 1: the FP32 stencil stages planes with cp.async
   bool tuned = false;          // autotuner has chosen kz32 / ty32 for this mesh
   bool pdl_now = false;        // launches being captured use programmatic dependent launch
   // state
@@ -292,10 +293,29 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
     static_assert(std::is_same<TF, float>::value, "the FP32 stencil takes FP32 right-hand sides");
     // the packed FP32 kernel forms p in ST_APPLY_DOT only, and always there
     if ((MODE == ST_APPLY_DOT) != (z != nullptr)) return fail(AFD_ERR_INVALID_ARG, "stencil mode / z mismatch");
-    if (m->ty32 == 8)
-      CK(launch_ex(m->pdl_now, stencil2_kernel<8, MODE>, grid, dim3(ST_TX * 8), 0, m->s, a));
-    else
-      CK(launch_ex(m->pdl_now, stencil2_kernel<16, MODE>, grid, dim3(ST_TX * 16), 0, m->s, a));
+    // the asynchronous staging ring lives in dynamic shared memory
+    if (m->async32) {
+      static bool opted[2] = {false, false};
+      const int ti = m->ty32 == 8 ? 0 : 1;
+      const size_t dyn =
+          (m->ty32 == 8 ? stencil2_ring_floats<8, MODE>() : stencil2_ring_floats<16, MODE>()) * sizeof(float);
+      if (!opted[ti]) {
+        if (m->ty32 == 8)
+          CK(cudaFuncSetAttribute(stencil2_kernel<8, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        else
+          CK(cudaFuncSetAttribute(stencil2_kernel<16, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        opted[ti] = true;
+      }
+      if (m->ty32 == 8)
+        CK(launch_ex(m->pdl_now, stencil2_kernel<8, MODE, true>, grid, dim3(ST_TX * 8), dyn, m->s, a));
+      else
+        CK(launch_ex(m->pdl_now, stencil2_kernel<16, MODE, true>, grid, dim3(ST_TX * 16), dyn, m->s, a));
+    } else {
+      if (m->ty32 == 8)
+        CK(launch_ex(m->pdl_now, stencil2_kernel<8, MODE, false>, grid, dim3(ST_TX * 8), 0, m->s, a));
+      else
+        CK(launch_ex(m->pdl_now, stencil2_kernel<16, MODE, false>, grid, dim3(ST_TX * 16), 0, m->s, a));
+    }
   }
   m->launches++;
   CK(cudaGetLastError());
@@ -498,12 +518,14 @@ static int autotune_stencil(afd_mesh* m) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_kz = m->kz32, best_ty = m->ty32;
+  int best_kz = m->kz32, best_ty = m->ty32, best_as = m->async32;
+  for (int as = 0; as < 2; ++as)
   for (int ty : cand_ty)
     for (int kz : cand_kz) {
       if (kz > g.nnz && kz != cand_kz.front()) continue;
       m->ty32 = ty;
       m->kz32 = kz;
+      m->async32 = as;
       TRY((launch_stencil<float, ST_APPLY, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr, nullptr, nullptr,
                                                     1, m->w32.K)));
       CK(cudaEventRecord(e0, m->s));
@@ -518,12 +540,14 @@ static int autotune_stencil(afd_mesh* m) {
         best = ms;
         best_kz = kz;
         best_ty = ty;
+        best_as = as;
       }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   m->kz32 = best_kz;
   m->ty32 = best_ty;
+  m->async32 = best_as;
   m->tuned = true;
   invalidate_graphs(m);  // captured launches bake in the grid
   return AFD_OK;
@@ -680,7 +704,7 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
   CK(cudaMemcpyAsync(m->done, hd.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, m->s));
   const dim3 gg(m->gp.ng, nrhs);
   const dim3 pg(grid_blocks(gr.nnodes, 256, 4 * RED_BLOCKS), nrhs);
-  const int crows = (m->nc * 32 + 255) / 256;
+  const int crows = (m->nc * 32 + CSTEP_THREADS - 1) / CSTEP_THREADS;
   const size_t csmem = (size_t)m->nc * sizeof(double);
   const T* Einv = F64 ? (const T*)m->Einv64 : (const T*)m->Einv32;
   unsigned int* cnt_co = m->counters + MAX_RHS;  // coarse step
@@ -689,7 +713,7 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
   // r = b - K x ; x += W Einv W^T r ; r = b - K x  (deflated start)
   TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, w.r, w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
   k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, w.r, nullptr, m->fixed, m->v, nullptr, m->st); m->launches++;
-  k_coarse_solve<T><<<crows, 256, 0, m->s>>>(m->nc, nrhs, Einv, m->v, m->mu, m->st); m->launches++;
+  k_coarse_solve<T><<<(m->nc * 32 + 255) / 256, 256, 0, m->s>>>(m->nc, nrhs, Einv, m->v, m->mu, m->st); m->launches++;
   k_prolong<T><<<pg, 256, 0, m->s>>>(2, gr, m->gp, x, nullptr, m->mu, m->fixed, m->st); m->launches++;
   TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, w.r, w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
   // Two-level preconditioned residual y = z + W Einv W^T (r - K z), z = M^-1 r
@@ -701,7 +725,7 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
   k_update<T><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, x, w.r, w.z, P[0], w.q, w.invd, m->upart, m->st, nullptr,
                                             0, m->done); m->launches++;
   TRY(launch_coarse_rhs<T>(m, w, m->nsplit, nrhs, false));
-  k_coarse_step<T><<<crows, 256, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->grec, m->wr, 2, m->done, cnt_co,
+  k_coarse_step<T><<<crows, CSTEP_THREADS, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->grec, m->wr, 2, m->done, cnt_co,
                                                m->upart, RED_BLOCKS); m->launches++;
   CK(cudaGetLastError());
 
@@ -738,7 +762,7 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
                    (const T*)w.q, (const T*)w.invd, m->upart, m->st, (const double*)m->partials, nsb, m->done));
       m->launches++;
       TRY(launch_coarse_rhs<T>(m, w, m->nsplit, nrhs, pdl));
-      CK(launch_ex(pdl, k_coarse_step<T>, dim3(crows), dim3(256), csmem, m->s, m->nc, nrhs, (const T*)Einv, m->mu,
+      CK(launch_ex(pdl, k_coarse_step<T>, dim3(crows), dim3(CSTEP_THREADS), csmem, m->s, m->nc, nrhs, (const T*)Einv, m->mu,
                    m->st, (const double*)m->grec, m->wr, 1, m->done, cnt_co, (const double*)m->upart, (int)RED_BLOCKS));
       m->launches++;
     }
@@ -881,7 +905,7 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
   }
   if ((rc = dalloc(&m->E64, (size_t)g.nelem)) != AFD_OK || (rc = dalloc(&m->w32.E, (size_t)g.nelem)) != AFD_OK ||
       (rc = dalloc(&m->w64.E, (size_t)g.nelem)) != AFD_OK || (rc = dalloc(&m->w32.invdiag, (size_t)g.nnodes)) != AFD_OK ||
-      (rc = dalloc(&m->w64.invdiag, (size_t)g.nnodes)) != AFD_OK || (rc = dalloc(&m->fixed, (size_t)g.nnodes)) != AFD_OK ||
+      (rc = dalloc(&m->w64.invdiag, (size_t)g.nnodes)) != AFD_OK || (rc = dalloc(&m->fixed, (size_t)(g.nnodes + 3) / 4 * 4)) != AFD_OK ||
       (rc = dalloc(&m->w32.invd, (size_t)g.vs)) != AFD_OK || (rc = dalloc(&m->w64.invd, (size_t)g.vs)) != AFD_OK ||
       (rc = dalloc(&m->fsmall, (size_t)FSMALL_SIZE)) != AFD_OK ||
       (rc = dalloc(&m->counters, (size_t)MAX_RHS + 1)) != AFD_OK ||
@@ -890,7 +914,7 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
     afd_destroy(m);
     return rc;
   }
-  cudaMemsetAsync(m->fixed, 0, g.nnodes, m->s);
+  cudaMemsetAsync(m->fixed, 0, (size_t)(g.nnodes + 3) / 4 * 4, m->s);   // padded: read as 4-byte words
   cudaMemsetAsync(m->counters, 0, (MAX_RHS + 1) * sizeof(unsigned int), m->s);
   if (cudaStreamSynchronize(m->s) != cudaSuccess) {
     afd_destroy(m);
@@ -1598,9 +1622,13 @@ int afd_stencil_depth(const afd_mesh* m) { return m ? m->kz32 : 0; }
 
 int afd_stencil_warps(const afd_mesh* m) { return m ? m->ty32 : 0; }
 
-int afd_set_stencil_shape(afd_mesh* m, int warps, int planes) {
-  if (!m || (warps != 8 && warps != 16) || planes < 1) return fail(AFD_ERR_INVALID_ARG, "warps must be 8 or 16, planes >= 1");
+int afd_stencil_async(const afd_mesh* m) { return m ? m->async32 : 0; }
+
+int afd_set_stencil_shape(afd_mesh* m, int warps, int planes, int async_staging) {
+  if (!m || (warps != 8 && warps != 16) || planes < 1 || async_staging < 0 || async_staging > 1)
+    return fail(AFD_ERR_INVALID_ARG, "warps must be 8 or 16, planes >= 1, async_staging 0 or 1");
   m->ty32 = warps;
+  m->async32 = async_staging;
   m->kz32 = std::min(planes, m->gr.nnz);
   m->tuned = true;
   invalidate_graphs(m);
@@ -1637,7 +1665,7 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
   CK(cudaMemcpyAsync(m->done, hd.data(), R * sizeof(int), cudaMemcpyHostToDevice, m->s));
   Work<float>& w = m->w32;
   const dim3 vg(RED_BLOCKS, R);
-  const int crows = (m->nc * 32 + 255) / 256;
+  const int crows = (m->nc * 32 + CSTEP_THREADS - 1) / CSTEP_THREADS;
   const size_t csmem = (size_t)m->nc * sizeof(double);
   unsigned int* cnt_co = m->counters + MAX_RHS;
   float* P[2] = {w.p, w.t};
@@ -1668,7 +1696,7 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
     cudaEventRecord(ev[2], m->s);
     rc = launch_coarse_rhs<float>(m, w, m->nsplit, R, false);
     cudaEventRecord(ev[3], m->s);
-    k_coarse_step<float><<<crows, 256, csmem, m->s>>>(m->nc, R, m->Einv32, m->mu, m->st, m->grec, m->wr, 1, m->done,
+    k_coarse_step<float><<<crows, CSTEP_THREADS, csmem, m->s>>>(m->nc, R, m->Einv32, m->mu, m->st, m->grec, m->wr, 1, m->done,
                                                      cnt_co, m->upart, RED_BLOCKS);
     cudaEventRecord(ev[4], m->s);
     m->launches += 4;

@@ -12,6 +12,7 @@ namespace afd {
 
 constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs: grid of the vector kernels
 constexpr int RED_THREADS = 256;
+constexpr int CSTEP_THREADS = 128;  // threads of a coarse-step block: one warp per row of the inverse
 
 // Per-RHS scalar state of the (inner) deflated PCG.
 struct CGState {
@@ -788,6 +789,52 @@ k_coarse_solve(int nc, int nrhs, const TE* __restrict__ Einv, const double* __re
   }
 }
 
+// One row of the dense coarse inverse times v (staged in shared memory in the
+// row's own type), by one warp.  The row is read as 16-byte vectors when its
+// length allows, in batches of 8 vectors per lane whose loads are all issued
+// before any is consumed: a row of n_c = 768 FP32 values is one memory round
+// trip instead of a chain of dependent ones.
+template <typename TE> struct Vec16;
+template <> struct Vec16<float> { using T = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using T = double2; static constexpr int N = 2; };
+__device__ __forceinline__ float vdot(float4 a, float4 b, float s) {
+  s = fmaf(a.x, b.x, s);
+  s = fmaf(a.y, b.y, s);
+  s = fmaf(a.z, b.z, s);
+  return fmaf(a.w, b.w, s);
+}
+__device__ __forceinline__ double vdot(double2 a, double2 b, double s) {
+  s = fma(a.x, b.x, s);
+  return fma(a.y, b.y, s);
+}
+template <typename TE>
+__device__ __forceinline__ TE coarse_row_dot(const TE* __restrict__ er, const TE* vt, int nc, int lane) {
+  using VT = typename Vec16<TE>::T;
+  constexpr int V = Vec16<TE>::N, U = 8;
+  TE s = TE(0);
+  if (nc % V == 0) {
+    const VT* ev = reinterpret_cast<const VT*>(er);
+    const VT* vv = reinterpret_cast<const VT*>(vt);
+    const int nv = nc / V;
+    for (int base = 0; base < nv; base += 32 * U) {
+      VT e[U];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int c = base + lane + 32 * j;
+        if (c < nv) e[j] = __ldg(ev + c);
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int c = base + lane + 32 * j;
+        if (c < nv) s = vdot(e[j], vv[c], s);
+      }
+    }
+  } else {
+    for (int c = lane; c < nc; c += 32) s = fma(er[c], vt[c], s);
+  }
+  return warp_sum(s);
+}
+
 // Coarse step of one DPCG iteration: v_G and (W^T r)_G are read from the
 // per-group k_coarse_rhs records, mu = Einv v (one warp per row, all RHS),
 // and each block leaves its rows' share of (W^T r).mu in cd_parts.  The last
@@ -801,7 +848,8 @@ __global__ void __launch_bounds__(256)
 k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict__ mu, CGState* st,
               const double* __restrict__ rec, double* __restrict__ cd_parts, int fin, int* done_flags,
               unsigned int* counter, const double* __restrict__ upd_partials, int upd_nparts) {
-  extern __shared__ double vs[];   // nc values of v for the current RHS
+  extern __shared__ __align__(16) double vs[];   // nc values of v for the current RHS (as TE)
+  TE* vt = reinterpret_cast<TE*>(vs);
   __shared__ double wcd[32];
   __shared__ double red[32 * 3];
   __shared__ bool s_last;
@@ -812,14 +860,11 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
   for (int r = 0; r < nrhs; ++r) {
     if (st[r].done) continue;
     const double* rr = rec + (size_t)r * ng * 12;
-    for (int q = threadIdx.x; q < nc; q += blockDim.x) vs[q] = rr[(q / 6) * 12 + 6 + q % 6];
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) vt[q] = (TE)rr[(q / 6) * 12 + 6 + q % 6];
     __syncthreads();
     double cd = 0.0;
     if (row < nc) {
-      const TE* er = Einv + (size_t)row * nc;
-      TE s = TE(0);
-      for (int c = lane; c < nc; c += 32) s = fma(er[c], (TE)vs[c], s);
-      s = warp_sum(s);
+      const TE s = coarse_row_dot<TE>(Einv + (size_t)row * nc, vt, nc, lane);
       if (lane == 0) {
         mu[(size_t)r * nc + row] = (double)s;
         cd = rr[(row / 6) * 12 + row % 6] * (double)s;

@@ -30,6 +30,19 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// Asynchronous global -> shared copies of 4 bytes (cp.async, sm_80+), used to
+// stage node values a few planes ahead without holding registers.  With
+// valid = false nothing is read and the destination is zero-filled (the
+// source operand must still be a mapped address).
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem_src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Modal forces of two elements (modal_forces in afd_common.cuh, lane-wise),
 // h[c][0] (the rigid translation) is neither read nor written.
 __device__ __forceinline__ void modal_forces2(float2 (&h)[3][8], float2 E, const ElemConsts<float>& K) {
@@ -108,9 +121,18 @@ struct LoadCA {
 // Returns this thread's partial sum (ST_RESIDUAL: y.y, ST_APPLY_DOT: p.Ap,
 // else 0) over the nodes it finishes.  beta: ST_APPLY_DOT's search-direction
 // coefficient.  Called by every thread of the CTA.
-template <int TY, int MODE, typename LD>
+// Dynamic shared memory of the asynchronous staging ring (bytes): RING
+// planes x (node values of both rows [+ z] + two fixed-mask words + two moduli)
+// per thread.
+constexpr int ST_RING = 3;
+template <int TY, int MODE>
+constexpr int stencil2_ring_floats() {
+  return ST_RING * ((MODE == ST_APPLY_DOT ? 12 : 6) + 4) * ST_TX * TY;
+}
+
+template <int TY, int MODE, typename LD, bool ASYNC = false>
 __device__ __forceinline__ float stencil2_tile(const StencilArgs<float, float>& a, float beta, int tile, int zc,
-                                               int rhs) {
+                                               int rhs, float* ring = nullptr) {
   // Exchange buffers (each written, then read after a barrier; the other
   // exchange's barrier separates that read from the next write):
   //   xe: (S, D) x-edge values of row jb for the warp below, per component
@@ -232,6 +254,80 @@ __device__ __forceinline__ float stencil2_tile(const StencilArgs<float, float>& 
     }
   };
 
+  // Asynchronous staging (ASYNC): plane k's node values (and z), the fixed-mask
+  // words of its two nodes and the moduli of element layer k-1 are copied
+  // into this thread's slot of a ring of ST_RING planes; consume() waits for
+  // nothing itself (the caller's cp_async_wait does) and forms the values.
+  constexpr int NQ = formp ? 12 : 6;
+  constexpr int NT = ST_TX * TY;
+  const int me = threadIdx.x;
+  auto issue = [&](int k, int slot) {
+    if (k <= k1) {
+      const bool kin = k >= 0 && k < gr.nnz;
+      const bool v0 = kin && col0, v1 = kin && col1;
+      const size_t n0 = v0 ? (size_t)(i + gr.nnx * (jb + gr.nny * k)) : 0;
+      const size_t n1 = v1 ? (size_t)(i + gr.nnx * (jb + 1 + gr.nny * k)) : 0;
+      float* rs = ring + (size_t)slot * NQ * NT;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        cp_async4(rs + c * NT + me, u + 3 * n0 + c, v0);
+        cp_async4(rs + (3 + c) * NT + me, u + 3 * n1 + c, v1);
+      }
+      if constexpr (formp) {
+        const float* zb = a.z + voff;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          cp_async4(rs + (6 + c) * NT + me, zb + 3 * n0 + c, v0);
+          cp_async4(rs + (9 + c) * NT + me, zb + 3 * n1 + c, v1);
+        }
+      }
+      unsigned* fr = (unsigned*)(ring + (size_t)ST_RING * NQ * NT) + (size_t)slot * 2 * NT;
+      const bool hf = a.fixed != nullptr;
+      const void* fsrc0 = hf ? (const void*)(a.fixed + (n0 & ~(size_t)3)) : (const void*)u;
+      const void* fsrc1 = hf ? (const void*)(a.fixed + (n1 & ~(size_t)3)) : (const void*)u;
+      cp_async4(fr + me, fsrc0, v0 && hf);
+      cp_async4(fr + NT + me, fsrc1, v1 && hf);
+      float* er = ring + (size_t)ST_RING * (NQ + 2) * NT + (size_t)slot * 2 * NT;
+      const int L = k - 1;
+      const bool lin = L >= 0 && L < gr.nz;
+      const size_t eA = (lin && elA) ? (size_t)(i + gr.nx * (jb + gr.ny * L)) : 0;
+      const size_t eB = (lin && elB) ? (size_t)(i + gr.nx * (jb + 1 + gr.ny * L)) : 0;
+      cp_async4(er + me, a.E + eA, lin && elA);
+      cp_async4(er + NT + me, a.E + eB, lin && elB);
+    }
+    cp_async_commit();
+  };
+  auto consume = [&](int k, int slot, float2 (&v)[3], unsigned& fbits, float2& Eo) {
+    const float* rs = ring + (size_t)slot * NQ * NT;
+    const unsigned* fr = (const unsigned*)(ring + (size_t)ST_RING * NQ * NT) + (size_t)slot * 2 * NT;
+    const float* er = ring + (size_t)ST_RING * (NQ + 2) * NT + (size_t)slot * 2 * NT;
+    Eo = make_float2(er[me], er[NT + me]);
+    const bool kin = k >= 0 && k < gr.nnz;
+    const int n0 = i + gr.nnx * (jb + gr.nny * (kin ? k : 0));
+    const unsigned f0 = (kin && col0) ? (fr[me] >> (8 * (n0 & 3))) & 0xffu : 0u;
+    const unsigned f1 = (kin && col1) ? (fr[NT + me] >> (8 * ((n0 + gr.nnx) & 3))) & 0xffu : 0u;
+    fbits = f0 | (f1 << 8);
+    if constexpr (formp) {
+      if (kin && k >= gz_next) refresh_group(k);
+      const float2 rz = bc2(hh * (float)(2 * k - zsum)), bt = bc2(beta);
+      v[0] = fma2(bt, make_float2(rs[me], rs[3 * NT + me]),
+                  add2(make_float2(rs[6 * NT + me], rs[9 * NT + me]), fma2(rz, sAB[3][me], sAB[0][me])));
+      v[1] = fma2(bt, make_float2(rs[NT + me], rs[4 * NT + me]),
+                  add2(make_float2(rs[7 * NT + me], rs[10 * NT + me]), fma2(rz, sAB[4][me], sAB[1][me])));
+      v[2] = fma2(bt, make_float2(rs[2 * NT + me], rs[5 * NT + me]),
+                  add2(make_float2(rs[8 * NT + me], rs[11 * NT + me]), sAB[2][me]));
+    } else {
+      v[0] = make_float2(rs[me], rs[3 * NT + me]);
+      v[1] = make_float2(rs[NT + me], rs[4 * NT + me]);
+      v[2] = make_float2(rs[2 * NT + me], rs[5 * NT + me]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (!kin || !col0 || ((f0 >> c) & 1u)) v[c].x = 0.f;
+      if (!kin || !col1 || ((f1 >> c) & 1u)) v[c].y = 0.f;
+    }
+  };
+
   // Face values of elements A and B on one node plane: F[c][q], q = mx + 2 my.
   auto face_values = [&](const float2 (&un)[3], float2 (&F)[3][4]) {
     float2 S[3], D[3];
@@ -261,18 +357,36 @@ __device__ __forceinline__ float stencil2_tile(const StencilArgs<float, float>& 
 #pragma unroll
     for (int q = 0; q < 4; ++q) Fb[c][q] = Tprev[c][q] = bc2(0.f);
 
-  {
-    float2 un0[3];
-    unsigned fdummy;
-    load_node(k0 - 1, un0, fdummy);
-    face_values(un0, Fb);
-    __syncthreads();  // the loop's first x-edge write follows this read
-  }
   float2 ucur[3] = {bc2(0.f), bc2(0.f), bc2(0.f)};   // formed u at plane l (dot and p write)
   unsigned fcur = 0u, fnext;
   float part = 0.f;
   float2 un[3];
-  load_node(k0, un, fnext);
+  float2 Enext = bc2(0.f);   // ASYNC: moduli of the element layer below plane `un`
+  if constexpr (ASYNC) {
+    // plane k -> ring slot (k - k0 + 1) % ST_RING
+    issue(k0 - 1, 0);
+    issue(k0, 1);
+    issue(k0 + 1, 2);
+    cp_async_wait<2>();
+    {
+      float2 un0[3], Ed;
+      unsigned fdummy;
+      consume(k0 - 1, 0, un0, fdummy, Ed);
+      face_values(un0, Fb);
+      __syncthreads();  // the loop's first x-edge write follows this read
+    }
+    cp_async_wait<1>();
+    consume(k0, 1, un, fnext, Enext);
+  } else {
+    {
+      float2 un0[3];
+      unsigned fdummy;
+      load_node(k0 - 1, un0, fdummy);
+      face_values(un0, Fb);
+      __syncthreads();  // the loop's first x-edge write follows this read
+    }
+    load_node(k0, un, fnext);
+  }
 
   for (int l = k0 - 1; l < k1; ++l) {
     float2 Ft[3][4];
@@ -280,12 +394,17 @@ __device__ __forceinline__ float stencil2_tile(const StencilArgs<float, float>& 
     const float2 u_l1[3] = {un[0], un[1], un[2]};
     const unsigned f_l1 = fnext;
     float2 E = bc2(0.f);
-    if (l >= 0 && l < gr.nz) {
-      const int e0 = i + gr.nx * (jb + gr.ny * l);
-      if (elA) E.x = __ldg(a.E + e0);
-      if (elB) E.y = __ldg(a.E + e0 + gr.nx);
+    if constexpr (ASYNC) {
+      E = Enext;
+      issue(l + 3, (l + 3 - k0 + 1) % ST_RING);   // into the slot of plane l
+    } else {
+      if (l >= 0 && l < gr.nz) {
+        const int e0 = i + gr.nx * (jb + gr.ny * l);
+        if (elA) E.x = __ldg(a.E + e0);
+        if (elB) E.y = __ldg(a.E + e0 + gr.nx);
+      }
+      if (l + 2 <= k1) load_node(l + 2, un, fnext);
     }
-    if (l + 2 <= k1) load_node(l + 2, un, fnext);
 
     float2 h[3][8];
 #pragma unroll
@@ -368,15 +487,22 @@ __device__ __forceinline__ float stencil2_tile(const StencilArgs<float, float>& 
         }
       }
     }
+    if constexpr (ASYNC) {
+      if (l + 2 <= k1) {
+        cp_async_wait<1>();   // plane l+2 has landed (plane l+3 may still be in flight)
+        consume(l + 2, (l + 2 - k0 + 1) % ST_RING, un, fnext, Enext);
+      }
+    }
     ucur[0] = u_l1[0];
     ucur[1] = u_l1[1];
     ucur[2] = u_l1[2];
     fcur = f_l1;
   }
+  if constexpr (ASYNC) cp_async_wait<0>();   // no copy may land after the tile
   return MODE == ST_APPLY ? 0.f : part;
 }
 
-template <int TY, int MODE>
+template <int TY, int MODE, bool ASYNC>
 __global__ void __launch_bounds__(ST_TX * TY, 16 / TY)
 stencil2_kernel(const StencilArgs<float, float> a) {
   __shared__ double red[32];
@@ -384,7 +510,8 @@ stencil2_kernel(const StencilArgs<float, float> a) {
   const int rhs = blockIdx.z;
   if (a.done && a.done[rhs]) return;
   const float beta = MODE == ST_APPLY_DOT ? (float)a.st[rhs].beta : 0.f;
-  const float part = stencil2_tile<TY, MODE, LoadRO>(a, beta, blockIdx.x, blockIdx.y, rhs);
+  extern __shared__ float st2_ring[];
+  const float part = stencil2_tile<TY, MODE, LoadRO, ASYNC>(a, beta, blockIdx.x, blockIdx.y, rhs, st2_ring);
   pdl_release();
   if (MODE != ST_APPLY) {
     float pv[1] = {part};
