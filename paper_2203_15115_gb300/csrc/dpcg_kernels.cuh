@@ -347,7 +347,7 @@ template <> struct Vec<double> { using type = double2; static constexpr int n = 
 // not positive and finite stops the RHS (status -3 / -5, set by block 0).  Flat over the DOFs of each RHS with
 // 16-byte vector accesses (the RHS stride vs keeps every RHS aligned).
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS)
+__global__ void __launch_bounds__(RED_THREADS, RED_BLOCKS / 152)
 k_update(int ndof, int vs, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
          const T* __restrict__ q, const T* __restrict__ invd, double* partials, CGState* st,
          const double* __restrict__ st_parts, int st_nparts, int* done_flags) {
@@ -365,15 +365,20 @@ k_update(int ndof, int vs, T* __restrict__ x, T* __restrict__ r, T* __restrict__
   const V* pv = (const V*)(p + off);
   const V* qv = (const V*)(q + off);
   const V* dv = (const V*)invd;
-  // the first vectors of this thread are loaded before alpha is formed
+  // The first vectors of this thread and r.z are loaded before alpha is
+  // formed, and each pass of the loop loads the next pass's vectors before it
+  // computes its own: the kernel streams 32 bytes per DOF mostly from L2, and
+  // its time is a chain of load latencies unless loads stay in flight.
+  const int stride = gridDim.x * blockDim.x;
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
-  V x0, r0, p0, q0, d0;
+  const double rz_cur = st[rhs].rz;
+  V cx, cr, cp, cq, cd;
   if (t0 < nvec) {
-    x0 = xv[t0];
-    r0 = rv[t0];
-    p0 = pv[t0];
-    q0 = qv[t0];
-    d0 = dv[t0];
+    cx = xv[t0];
+    cr = rv[t0];
+    cp = pv[t0];
+    cq = qv[t0];
+    cd = dv[t0];
   }
   double alpha_d = 0.0;
   if (st_nparts > 0) {
@@ -386,23 +391,26 @@ k_update(int ndof, int vs, T* __restrict__ x, T* __restrict__ r, T* __restrict__
       }
       return;
     }
-    alpha_d = st[rhs].rz / pap;
+    alpha_d = rz_cur / pap;
     if (blockIdx.x == 0 && threadIdx.x == 0) st[rhs].alpha = alpha_d;
   }
   const T alpha = (T)alpha_d;
   T s[2] = {T(0), T(0)};
-  for (int t = t0; t < nvec; t += gridDim.x * blockDim.x) {
-    V xx, rr, pp, qq, dd;
-    if (t == t0) {
-      xx = x0; rr = r0; pp = p0; qq = q0; dd = d0;
-    } else {
-      xx = xv[t]; rr = rv[t]; pp = pv[t]; qq = qv[t]; dd = dv[t];
+  for (int t = t0; t < nvec; t += stride) {
+    const int tn = t + stride;
+    V nx, nr, np, nq, nd;
+    if (tn < nvec) {
+      nx = xv[tn];
+      nr = rv[tn];
+      np = pv[tn];
+      nq = qv[tn];
+      nd = dv[tn];
     }
-    T* xs = (T*)&xx;
-    T* rs = (T*)&rr;
-    const T* ps = (const T*)&pp;
-    const T* qs = (const T*)&qq;
-    const T* ds = (const T*)&dd;
+    T* xs = (T*)&cx;
+    T* rs = (T*)&cr;
+    const T* ps = (const T*)&cp;
+    const T* qs = (const T*)&cq;
+    const T* ds = (const T*)&cd;
     V zz;
     T* zs = (T*)&zz;
 #pragma unroll
@@ -413,9 +421,14 @@ k_update(int ndof, int vs, T* __restrict__ x, T* __restrict__ r, T* __restrict__
       s[0] += rs[c] * zs[c];
       s[1] += rs[c] * rs[c];
     }
-    xv[t] = xx;
-    rv[t] = rr;
+    xv[t] = cx;
+    rv[t] = cr;
     zv[t] = zz;
+    cx = nx;
+    cr = nr;
+    cp = np;
+    cq = nq;
+    cd = nd;
   }
   // tail DOFs
   for (int d = nvec * NV + blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
@@ -607,7 +620,7 @@ __host__ __device__ inline void elem_shell_bounds(const Grid& gr, const Groups& 
 // DOFs contribute nothing: the rigid motions are in the element null space).
 // Records and the last-block combination as in k_coarse_rhs.
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)   // FP32: 4 blocks per SM
 k_coarse_rhs_cut(Grid gr, Groups gp, int nsplit, const T* __restrict__ r, const T* __restrict__ z,
                  const T* __restrict__ Emod, const uint8_t* __restrict__ fixed, const int* __restrict__ gbox,
                  ElemConsts<T> K, double* __restrict__ part, double* __restrict__ rec,
@@ -848,6 +861,8 @@ __global__ void __launch_bounds__(256)
 k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict__ mu, CGState* st,
               const double* __restrict__ rec, double* __restrict__ cd_parts, int fin, int* done_flags,
               unsigned int* counter, const double* __restrict__ upd_partials, int upd_nparts) {
+  using VT = typename Vec16<TE>::T;
+  constexpr int V = Vec16<TE>::N, U = 8;
   extern __shared__ __align__(16) double vs[];   // nc values of v for the current RHS (as TE)
   TE* vt = reinterpret_cast<TE*>(vs);
   __shared__ double wcd[32];
@@ -857,17 +872,45 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int row = blockIdx.x * nwarps + warp;
   const int ng = nc / 6;
+  // The row of the inverse does not depend on the iteration: its loads are
+  // issued first, so that they overlap the loads of v and of the state (the
+  // kernel is a chain of memory latencies, not bandwidth).  Rows that fit in
+  // one batch of U vectors per lane stay in registers for every RHS.
+  const int nv = nc / V;
+  const bool in_regs = nc % V == 0 && nv <= 32 * U;
+  VT e[U];
+  if (in_regs && row < nc) {
+    const VT* ev = reinterpret_cast<const VT*>(Einv + (size_t)row * nc);
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int c = lane + 32 * j;
+      if (c < nv) e[j] = __ldg(ev + c);
+    }
+  }
   for (int r = 0; r < nrhs; ++r) {
     if (st[r].done) continue;
     const double* rr = rec + (size_t)r * ng * 12;
+    const double wtr = (row < nc && lane == 0) ? rr[(row / 6) * 12 + row % 6] : 0.0;
     for (int q = threadIdx.x; q < nc; q += blockDim.x) vt[q] = (TE)rr[(q / 6) * 12 + 6 + q % 6];
     __syncthreads();
     double cd = 0.0;
     if (row < nc) {
-      const TE s = coarse_row_dot<TE>(Einv + (size_t)row * nc, vt, nc, lane);
+      TE s;
+      if (in_regs) {
+        const VT* vv = reinterpret_cast<const VT*>(vt);
+        s = TE(0);
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          const int c = lane + 32 * j;
+          if (c < nv) s = vdot(e[j], vv[c], s);
+        }
+        s = warp_sum(s);
+      } else {
+        s = coarse_row_dot<TE>(Einv + (size_t)row * nc, vt, nc, lane);
+      }
       if (lane == 0) {
         mu[(size_t)r * nc + row] = (double)s;
-        cd = rr[(row / 6) * 12 + row % 6] * (double)s;
+        cd = wtr * (double)s;
       }
     }
     if (lane == 0) wcd[warp] = cd;
@@ -890,6 +933,15 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
   for (int r = 0; r < nrhs; ++r) {
     CGState& S = st[r];
     if (S.done) continue;
+    // the state's fields are loaded with the partials, not after their sum
+    double rz_old = 0.0, target2 = 0.0;
+    int iters = 0, max_iters = 0;
+    if (threadIdx.x == 0) {
+      rz_old = S.rz;
+      target2 = S.target2;
+      iters = S.iters;
+      max_iters = S.max_iters;
+    }
     double ps[3] = {0.0, 0.0, 0.0};
     const double2* up = (const double2*)(upd_partials + (size_t)r * upd_nparts * 2);
     for (int i = threadIdx.x; i < upd_nparts; i += blockDim.x) {
@@ -902,23 +954,26 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
     block_sum_to_f64<3>(ps, red, o);
     if (threadIdx.x == 0) {
       const double rz = o[0], rr = o[1], rho = rz + o[2];
+      int done = 0;
       if (!isfinite(rr) || !isfinite(rho)) {
         S.status = -5;
-        S.done = 1;
+        done = 1;
       } else {
-        S.beta = fin == 2 ? 0.0 : rho / S.rz;
-        if (fin != 2) S.iters += 1;
+        S.beta = fin == 2 ? 0.0 : rho / rz_old;
+        if (fin != 2) iters += 1;
+        S.iters = iters;
         S.rz = rho;
         S.rr = rr;
-        if (rr <= S.target2) {
-          S.done = 1;
+        if (rr <= target2) {
+          done = 1;
           S.status = 0;
-        } else if (S.iters >= S.max_iters) {
-          S.done = 1;
+        } else if (iters >= max_iters) {
+          done = 1;
           S.status = -3;
         }
       }
-      if (done_flags) done_flags[r] = S.done;
+      S.done = done;
+      if (done_flags) done_flags[r] = done;
     }
     __syncthreads();
   }
