@@ -489,6 +489,24 @@ static int ensure_cpart(afd_mesh* m, int nsplit) {
   return AFD_OK;
 }
 
+// Dynamic shared memory of k_coarse_step<T> (v staged in the inverse's type),
+// opted in above the 48 KB default once per type; a coarse problem whose v
+// does not fit in a CTA's shared memory is refused.
+template <typename T>
+static int coarse_step_smem(const afd_mesh* m, size_t& bytes) {
+  bytes = (size_t)m->nc * sizeof(T);
+  constexpr size_t kMax = 200 * 1024;
+  if (bytes > kMax)
+    return fail(AFD_ERR_INVALID_ARG, "coarse problem too large for the dense inverse (6 x groups above 25600 for FP64, "
+                                     "51200 for mixed): use a larger group");
+  static bool opted = false;
+  if (bytes > 40 * 1024 && !opted) {
+    CK(cudaFuncSetAttribute(k_coarse_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax));
+    opted = true;
+  }
+  return AFD_OK;
+}
+
 // Stencil autotuner: the FP32 stencil's CTA shape (8 or 16 warps, i.e. 14 or
 // 30 finished node rows) and z depth trade redundant halo rows and element
 // layers against the number of CTAs (waves over the SMs).  Each candidate is
@@ -705,7 +723,8 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
   const dim3 gg(m->gp.ng, nrhs);
   const dim3 pg(grid_blocks(gr.nnodes, 256, 4 * RED_BLOCKS), nrhs);
   const int crows = (m->nc * 32 + CSTEP_THREADS - 1) / CSTEP_THREADS;
-  const size_t csmem = (size_t)m->nc * sizeof(double);
+  size_t csmem = 0;
+  TRY(coarse_step_smem<T>(m, csmem));
   const T* Einv = F64 ? (const T*)m->Einv64 : (const T*)m->Einv32;
   unsigned int* cnt_co = m->counters + MAX_RHS;  // coarse step
   T* P[2] = {w.p, w.t};
@@ -1666,7 +1685,8 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
   Work<float>& w = m->w32;
   const dim3 vg(RED_BLOCKS, R);
   const int crows = (m->nc * 32 + CSTEP_THREADS - 1) / CSTEP_THREADS;
-  const size_t csmem = (size_t)m->nc * sizeof(double);
+  size_t csmem = 0;
+  TRY(coarse_step_smem<float>(m, csmem));
   unsigned int* cnt_co = m->counters + MAX_RHS;
   float* P[2] = {w.p, w.t};
   const dim3 pg(grid_blocks(gr.nnodes, 256, 4 * RED_BLOCKS), R);

@@ -387,3 +387,19 @@ def test_constrained_topology_driver_keeps_the_hard_constraints():
     for a, b in zip(hist, hist[1:]):
         if a["violated"]:
             assert b["dv"] == a["dv"] / 2
+
+
+def test_fp64_solve_with_a_coarse_problem_above_48kb_of_shared_memory():
+    """n_c = 6144 (g = 4 on 64x32x32): the coarse step stages 48 KB of v in
+    shared memory, above the default per-block limit.  The deflation space does
+    not change the solution, so it must match the default grouping's."""
+    w = small_cantilever(64, 32, 32, seed=5, n_spheres=8, rmin=2.0, rmax=5.0, group=4)
+    m, u, stats = _solve(w, afd.AFD_FP64, 1e-10, group=4)
+    assert afd.afd_coarse_size(m.h) == 6144
+    assert stats[0]["rel_residual"] <= 1e-10
+    m.close()
+    m2, u2, _ = _solve(w, afd.AFD_FP64, 1e-10, group=16)
+    m2.close()
+    K = fe.assemble(w.nx, w.ny, w.nz, w.E)
+    assert fe.relative_residual(K, u[0], w.f[0], w.fixed) <= 1.0001e-10
+    assert np.linalg.norm(u[0] - u2[0]) <= 1e-6 * np.linalg.norm(u2[0])
