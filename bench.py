@@ -53,6 +53,23 @@ UNIT = "ms per topology step (dCG solve to rel-res 1e-6 + coarse setup + J + sen
 # DRAM bytes (read + write) per launch of the FP32 apply kernel, each from one ncu capture
 # (profiles/stencil_fp32_128x64x64_dram.md, profiles/stencil_fp32_384x192x192_async_dram.md), keyed by mesh
 # and CTA shape (warps, planes, async staging); any other shape reports null.
+# FP32 operations of the modal hex8 apply per element (x/y butterflies 18, z butterfly 21, modal forces 42,
+# transposed z 30, y 12 and x 15 stages: 138 operations, 9 of them FMAs counted twice), and the FP32 peak from the
+# unit counts: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2070 MHz.
+STENCIL_FLOPS_PER_ELEMENT = 147
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def alu_roofline(n_elements: int, ms: float) -> dict:
+    """The ALU side of the stencil's roofline: algorithmic FP32 flops per launch
+    over the launch time, against the FP32 peak of the unit counts."""
+    tf = STENCIL_FLOPS_PER_ELEMENT * n_elements / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "flops_per_launch": STENCIL_FLOPS_PER_ELEMENT * n_elements,
+            "achieved": round(tf, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+            "frac": round(tf / FP32_PEAK_TFLOPS, 4),
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}
+
+
 STENCIL_DRAM_BYTES = {(128, 64, 64, 8, 6, 0): 9198592, (384, 192, 192, 8, 12, 1): 378244608}
 
 
@@ -273,7 +290,8 @@ def run_ours(args):
         "roofline": {"kernel": "stencil2_kernel<TY,ST_APPLY> (K u, FP32, packed float2)", "bound": "hbm",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "peak_source": peak_kind, "bytes_per_launch": bytes32},
+                     "peak_source": peak_kind, "bytes_per_launch": bytes32,
+                     "alu": alu_roofline(ne, mv_ms)},
         "roofline_384x192x192": roofline_large,
         "e2e": {"value": round(float(np.median(e2e)), 3), "unit": "ms per topology step, host buffers",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -327,7 +345,8 @@ def large_mesh_roofline(afd, torch, dev, peak, peak_kind, n=384):
             "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "frac_of_nominal_8TBs": round(ach / 8000.0, 4),
             "peak_source": peak_kind, "bytes_per_launch": b, "ms_per_launch": round(best[0], 5),
             "gdofs": round(3 * nn / (best[0] * 1e-3) / 1e9, 2), "warps": best[1], "planes": best[2],
-            "async_staging": best[3], "traffic": STENCIL_DRAM_BYTES.get((nx, ny, nz) + best[1:])}
+            "async_staging": best[3], "traffic": STENCIL_DRAM_BYTES.get((nx, ny, nz) + best[1:]),
+            "alu": alu_roofline(nx * ny * nz, best[0])}
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:

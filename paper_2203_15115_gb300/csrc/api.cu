@@ -1485,7 +1485,10 @@ static int casting_args_ok(int nx, int ny, int nz, int axis, int parting) {
 static int launch_casting_scan(cudaStream_t s, int nx, int ny, int nz, int axis, int parting, float* keys,
                                int64_t* launches) {
   const size_t nlines = axis == 0 ? (size_t)ny * nz : (axis == 1 ? (size_t)nx * nz : (size_t)nx * ny);
-  k_casting_scan<<<grid_blocks(nlines, 128, 8192), 128, 0, s>>>(nx, ny, nz, axis, parting, keys);
+  if (axis == 0)
+    k_casting_scan_x<<<(unsigned)((nlines + CASTX_L - 1) / CASTX_L), CASTX_T, 0, s>>>(nx, (int)nlines, parting, keys);
+  else
+    k_casting_scan_strided<<<grid_blocks(nlines, 128, 8192), 128, 0, s>>>(nx, ny, nz, axis, parting, keys);
   if (launches) ++*launches;
   CK(cudaGetLastError());
   return AFD_OK;

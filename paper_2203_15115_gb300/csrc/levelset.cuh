@@ -150,19 +150,20 @@ k_mark(int64_t n, const float* __restrict__ x, const SelectState* st, const uint
 // takes, from its far face toward the parting plane,
 //   key'(c) = max(key(c), nextafter(key'(c_far_neighbour), +inf)),
 // a running maximum raised by one float32 step per element, so that the kept
-// set of any cut is a run of elements starting at the parting plane.  One
-// thread per line; lines along y and z are indexed so that neighbouring
-// threads read neighbouring elements.
-__global__ void k_casting_scan(int nx, int ny, int nz, int axis, int parting, float* __restrict__ keys) {
-  const int nlines = axis == 0 ? ny * nz : (axis == 1 ? nx * nz : nx * ny);
+// set of any cut is a run of elements starting at the parting plane.  Each
+// line is one dependent chain of these steps; the kernels below differ only in
+// how they bring the keys to the chain.
+__device__ __forceinline__ float casting_step(float key, float v) { return fmaxf(key, nextafterf(v, INFINITY)); }
+
+// Lines along y or z (strided): one thread per line, neighbouring threads on
+// neighbouring elements, keys loaded CAST_U at a time ahead of the chain.
+constexpr int CAST_U = 8;
+__global__ void k_casting_scan_strided(int nx, int ny, int nz, int axis, int parting, float* __restrict__ keys) {
+  const int nlines = axis == 1 ? nx * nz : nx * ny;
   for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < nlines; L += gridDim.x * blockDim.x) {
     size_t base, stride;
     int n;
-    if (axis == 0) {
-      base = (size_t)nx * L;   // L = j + ny k
-      stride = 1;
-      n = nx;
-    } else if (axis == 1) {
+    if (axis == 1) {
       const int i = L % nx, k = L / nx;
       base = (size_t)i + (size_t)nx * ny * k;
       stride = nx;
@@ -172,22 +173,98 @@ __global__ void k_casting_scan(int nx, int ny, int nz, int axis, int parting, fl
       stride = (size_t)nx * ny;
       n = nz;
     }
+    float* line = keys + base;
     if (parting < n - 1) {     // upper half, from the far face c = n-1 down to parting
-      float v = keys[base + (size_t)(n - 1) * stride];
-      for (int c = n - 2; c >= parting; --c) {
-        float* q = keys + base + (size_t)c * stride;
-        v = fmaxf(*q, nextafterf(v, INFINITY));
-        *q = v;
+      float v = line[(size_t)(n - 1) * stride];
+      for (int c0 = n - 2; c0 >= parting; c0 -= CAST_U) {
+        float kv[CAST_U];
+#pragma unroll
+        for (int u = 0; u < CAST_U; ++u)
+          if (c0 - u >= parting) kv[u] = line[(size_t)(c0 - u) * stride];
+#pragma unroll
+        for (int u = 0; u < CAST_U; ++u)
+          if (c0 - u >= parting) {
+            v = casting_step(kv[u], v);
+            line[(size_t)(c0 - u) * stride] = v;
+          }
       }
     }
     if (parting > 1) {         // lower half, from c = 0 up to parting - 1
-      float v = keys[base];
+      float v = line[0];
       const int top = parting < n ? parting : n;
-      for (int c = 1; c < top; ++c) {
-        float* q = keys + base + (size_t)c * stride;
-        v = fmaxf(*q, nextafterf(v, INFINITY));
-        *q = v;
+      for (int c0 = 1; c0 < top; c0 += CAST_U) {
+        float kv[CAST_U];
+#pragma unroll
+        for (int u = 0; u < CAST_U; ++u)
+          if (c0 + u < top) kv[u] = line[(size_t)(c0 + u) * stride];
+#pragma unroll
+        for (int u = 0; u < CAST_U; ++u)
+          if (c0 + u < top) {
+            v = casting_step(kv[u], v);
+            line[(size_t)(c0 + u) * stride] = v;
+          }
       }
+    }
+  }
+}
+
+// Lines along x (contiguous): a block takes CASTX_L lines and walks them in
+// chunks of CASTX_CH columns in the direction of the scan.  All threads load a
+// chunk into shared memory (coalesced along x), the first warp runs the
+// chains (thread l on line l; rows padded by one word so that the warp's
+// reads fall in distinct banks), and all threads store the chunk back.
+constexpr int CASTX_L = 32, CASTX_CH = 128, CASTX_T = 256;
+__global__ void __launch_bounds__(CASTX_T) k_casting_scan_x(int nx, int nlines, int parting, float* __restrict__ keys) {
+  __shared__ float t[CASTX_L][CASTX_CH + 1];
+  const int line0 = blockIdx.x * CASTX_L;
+  const int nl = min(CASTX_L, nlines - line0);
+  const int me = threadIdx.x;
+  float v = 0.f;   // the chain's running value (first warp)
+  auto chunk = [&](int a, int b, bool down, bool first) {
+    const int w = b - a + 1;
+    for (int idx = me; idx < nl * w; idx += CASTX_T) {
+      const int l = idx / w, c = idx - l * w;
+      t[l][c] = keys[(size_t)(line0 + l) * nx + a + c];
+    }
+    __syncthreads();
+    if (me < nl) {
+      float* row = t[me];
+      if (down) {
+        int c = w - 1;
+        if (first) v = row[c--];
+        for (; c >= 0; --c) {
+          v = casting_step(row[c], v);
+          row[c] = v;
+        }
+      } else {
+        int c = 0;
+        if (first) v = row[c++];
+        for (; c < w; ++c) {
+          v = casting_step(row[c], v);
+          row[c] = v;
+        }
+      }
+    }
+    __syncthreads();
+    for (int idx = me; idx < nl * w; idx += CASTX_T) {
+      const int l = idx / w, c = idx - l * w;
+      keys[(size_t)(line0 + l) * nx + a + c] = t[l][c];
+    }
+    __syncthreads();   // the next chunk's loads overwrite t
+  };
+  if (parting < nx - 1) {      // upper half, from the far face down to parting
+    bool first = true;
+    for (int b = nx - 1; b >= parting; b -= CASTX_CH) {
+      chunk(max(parting, b - CASTX_CH + 1), b, true, first);
+      first = false;
+    }
+  }
+  if (parting > 1) {           // lower half, from column 0 up to parting - 1
+    const int top = parting < nx ? parting : nx;
+    bool first = true;
+    for (int a = 0; a < top; a += CASTX_CH) {
+      chunk(a, min(top - 1, a + CASTX_CH - 1), false, first);
+      first = false;
     }
   }
 }

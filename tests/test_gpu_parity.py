@@ -274,7 +274,7 @@ def test_error_paths():
     m.close()
 
 
-@pytest.mark.parametrize("shape", [(7, 5, 6), (33, 17, 9), (64, 3, 40)])
+@pytest.mark.parametrize("shape", [(7, 5, 6), (33, 17, 9), (64, 3, 40), (300, 7, 5), (5, 261, 3), (4, 3, 140)])
 def test_casting_scan_bit_exact(shape):
     nx, ny, nz = shape
     rng = np.random.default_rng(nx)
@@ -282,7 +282,7 @@ def test_casting_scan_bit_exact(shape):
     T[::3] = T[1::3][: T[::3].size]         # ties and plateaus
     for axis in (0, 1, 2):
         n = shape[axis]
-        for parting in sorted({0, 1, n // 2, n - 1, n}):
+        for parting in sorted({0, 1, n // 2, n - 1, n} | {p for p in (127, 128, 129, 171) if p < n}):
             d = torch.from_numpy(T.copy()).cuda()
             afd.afd_casting_scan(d, nx, ny, nz, axis, parting)
             torch.cuda.synchronize()
