@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <limits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -264,7 +265,7 @@ template <typename T, int MODE, typename TF>
 static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f, float* y32, double* partials,
                           const int* done, int nrhs, const ElemConsts<T>& K, CGState* st = nullptr,
                           unsigned int* counter = nullptr, const T* z = nullptr, const double* mu = nullptr,
-                          T* pout = nullptr) {
+                          T* pout = nullptr, const IterPartials* ip = nullptr) {
   constexpr bool F64 = sizeof(T) == 8;
   StencilArgs<T, TF> a;
   a.gr = m->gr;
@@ -284,6 +285,7 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
   a.mu = mu;
   a.pout = pout;
   a.gp = m->gp;
+  a.ip = ip ? *ip : IterPartials{nullptr, 0, nullptr, 0, 0};
   dim3 grid;
   stencil_geom(m, F64, a.tiles_x, grid);
   grid.z = nrhs;
@@ -716,6 +718,7 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
     h[r].target2 = target2[r];
     h[r].max_iters = max_iters;
     h[r].done = active[r] ? 0 : 1;
+    h[r].rzs[0] = std::numeric_limits<double>::infinity();   // beta_0 = rho_0 / inf = 0
     hd[r] = h[r].done;
   }
   CK(cudaMemcpyAsync(m->st, h.data(), nrhs * sizeof(CGState), cudaMemcpyHostToDevice, m->s));
@@ -774,8 +777,9 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
     for (int it = 0; it < m->opt.check_every; ++it) {
       T* pold = P[it & 1];
       T* pnew = P[(it + 1) & 1];
+      const IterPartials ip{m->upart, RED_BLOCKS, m->wr, crows, it & 1};
       TRY((launch_stencil<T, ST_APPLY_DOT, TB>(m, pold, w.q, w.E, nullptr, nullptr, m->partials, m->done, nrhs, w.K,
-                                                m->st, nullptr, w.z, m->mu, pnew)));
+                                                m->st, nullptr, w.z, m->mu, pnew, &ip)));
       const bool pdl = m->pdl_now;
       CK(launch_ex(pdl, k_update<T>, vg, dim3(RED_THREADS), 0, m->s, gr.ndof, gr.vs, x, w.r, w.z, (const T*)pnew,
                    (const T*)w.q, (const T*)w.invd, m->upart, m->st, (const double*)m->partials, nsb, m->done));
@@ -1682,6 +1686,8 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
     h[r].target2 = -1.0;
     h[r].max_iters = 1 << 30;
     if (!(h[r].rz > 0.0)) h[r].rz = 1.0;
+    h[r].rzs[0] = h[r].rzs[1] = h[r].rz;
+    h[r].its[0] = h[r].its[1] = 0;
   }
   CK(cudaMemcpyAsync(m->st, h.data(), R * sizeof(CGState), cudaMemcpyHostToDevice, m->s));
   CK(cudaMemcpyAsync(m->done, hd.data(), R * sizeof(int), cudaMemcpyHostToDevice, m->s));
@@ -1710,9 +1716,11 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
     if (variant == 1)
       rc = launch_stencil<float, ST_DOT_PLAIN, float>(m, pnew, w.q, w.E, nullptr, nullptr, m->partials, m->done, R,
                                                      w.K, m->st, nullptr);
-    else
+    else {
+      const IterPartials ip{m->upart, RED_BLOCKS, m->wr, crows, it & 1};
       rc = launch_stencil<float, ST_APPLY_DOT, float>(m, pold, w.q, w.E, nullptr, nullptr, m->partials, m->done, R,
-                                                     w.K, m->st, nullptr, w.z, m->mu, pnew);
+                                                     w.K, m->st, nullptr, w.z, m->mu, pnew, &ip);
+    }
     cudaEventRecord(ev[1], m->s);
     k_update<float><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, w.x, w.r, w.z, pnew, w.q, w.invd, m->upart, m->st,
                                                  m->partials, stencil_blocks(m, false), m->done);

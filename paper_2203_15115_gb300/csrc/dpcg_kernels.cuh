@@ -24,6 +24,21 @@ struct CGState {
   int max_iters;
   int done;         // 1: converged or stopped; kernels skip this RHS
   int status;       // 0 ok, AFD_ERR_NOT_CONVERGED, AFD_ERR_NAN
+  // rho of the previous iteration and the iteration count, in two slots by
+  // the iteration's parity (dpcg_iteration_start reads slot par, writes par^1)
+  double rzs[2];
+  int its[2];
+};
+
+// Where the stencil that starts an iteration finds the partial sums of the
+// previous one: (r.z, r.r) per vector-update block and (W^T r).mu per
+// coarse-step block, and the parity of the iteration.
+struct IterPartials {
+  const double* upd;   // [rhs][nupd][2]
+  int nupd;
+  const double* cd;    // [rhs][ncd]
+  int ncd;
+  int par;
 };
 
 // Block-wide sum in a fixed order (per-thread strided sums, warp tree, then
@@ -44,6 +59,72 @@ __device__ inline double block_sum_bcast(double s) {
   const double out = sh[32];
   __syncthreads();
   return out;
+}
+
+// Start of iteration i of the DPCG loop, taken by every CTA of the stencil
+// that applies K to the next search direction: rho_i = r.z + (W^T r).mu and
+// r.r from the partials of the vector update and the coarse step of
+// iteration i-1, the stopping test (converged, not finite, or out of
+// iterations) and beta_i = rho_i / rho_{i-1}.  Every CTA sums the same
+// partials in the same order and takes the same decision; CTA (0, 0) records
+// it in the state.  rho_{i-1} and i are read from slot par and rho_i, i+1
+// written to slot par^1, so the recording never meets another CTA's read.
+// Returns false (in every thread) when the RHS stops.
+__device__ inline bool dpcg_iteration_start(CGState* st, int rhs, int* done_flags, const IterPartials& ip,
+                                            double& beta) {
+  __shared__ double red[32 * 3];
+  __shared__ int s_go;
+  __shared__ double s_beta;
+  // the state's fields are loaded with the partials, not after their sum
+  double rho_old = 0.0, target2 = 0.0;
+  int it = 0, max_iters = 0;
+  if (threadIdx.x == 0) {
+    const CGState& S = st[rhs];
+    rho_old = S.rzs[ip.par];
+    it = S.its[ip.par];
+    target2 = S.target2;
+    max_iters = S.max_iters;
+  }
+  double ps[3] = {0.0, 0.0, 0.0};
+  const double2* up = (const double2*)(ip.upd + (size_t)rhs * ip.nupd * 2);
+  for (int i = threadIdx.x; i < ip.nupd; i += blockDim.x) {
+    const double2 v = up[i];
+    ps[0] += v.x;
+    ps[1] += v.y;
+  }
+  const double* cd = ip.cd + (size_t)rhs * ip.ncd;
+  for (int i = threadIdx.x; i < ip.ncd; i += blockDim.x) ps[2] += cd[i];
+  double o[3];
+  block_sum_to_f64<3>(ps, red, o);
+  if (threadIdx.x == 0) {
+    CGState& S = st[rhs];
+    const double rho = o[0] + o[2], rr = o[1];
+    int status = 1;
+    if (!isfinite(rr) || !isfinite(rho)) status = -5;
+    else if (rr <= target2) status = 0;
+    else if (it >= max_iters) status = -3;
+    const bool lead = blockIdx.x == 0 && blockIdx.y == 0;
+    const double b = rho / rho_old;
+    if (lead) {
+      S.rz = rho;
+      S.rr = rr;
+      S.iters = it;
+      if (status != 1) {
+        S.status = status;
+        S.done = 1;
+        if (done_flags) done_flags[rhs] = 1;
+      } else {
+        S.beta = b;
+        S.rzs[ip.par ^ 1] = rho;
+        S.its[ip.par ^ 1] = it + 1;
+      }
+    }
+    s_go = status == 1;
+    s_beta = b;
+  }
+  __syncthreads();
+  beta = s_beta;
+  return s_go != 0;
 }
 
 // Sum nparts partials (stride `stride`, component `comp`) of one RHS in a fixed order.
@@ -850,12 +931,14 @@ __device__ __forceinline__ TE coarse_row_dot(const TE* __restrict__ er, const TE
 
 // Coarse step of one DPCG iteration: v_G and (W^T r)_G are read from the
 // per-group k_coarse_rhs records, mu = Einv v (one warp per row, all RHS),
-// and each block leaves its rows' share of (W^T r).mu in cd_parts.  The last
-// block to finish takes the beta step for every RHS in one pass over the
-// k_update partials and the cd_parts: rho = r.z + (W^T r).mu (the
-// preconditioned residual y = z + W mu of the two-level operator), r.r,
-// beta = rho / rho_old, the convergence test and the iteration count.
-// fin == 2 marks the initial step (beta = 0).
+// and each block leaves its rows' share of (W^T r).mu in cd_parts, from which
+// rho = r.z + (W^T r).mu (the preconditioned residual y = z + W mu of the
+// two-level operator) follows.  Inside the loop (fin == 1) that is all: the
+// next stencil forms rho, r.r, beta and the stopping test
+// (dpcg_iteration_start).  For the initial step (fin == 2) the last block to
+// finish takes them here, in one pass over the k_update partials and the
+// cd_parts (beta = 0), so that an initial residual already below the target
+// stops before the loop.
 template <typename TE>
 __global__ void __launch_bounds__(256)
 k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict__ mu, CGState* st,
@@ -923,7 +1006,10 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
     __syncthreads();
   }
   pdl_release();
-  // last block: beta step for every RHS
+  // fin == 1: the loop's stencil forms beta and the stopping test from the
+  // cd_parts (dpcg_iteration_start); the initial step (fin == 2) takes them
+  // here, in the last block, for every RHS
+  if (fin == 1) return;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;

@@ -54,6 +54,10 @@ struct StencilArgs {
   const double* mu;       // [rhs][6 N_g]
   T* pout;
   Groups gp;
+  // ST_APPLY_DOT inside the solver loop (non-null ip.upd): beta and the
+  // stopping test are formed at kernel start from the previous iteration's
+  // partials (dpcg_iteration_start); otherwise beta is read from st
+  IterPartials ip;
 };
 
 constexpr int ST_TX = 32;  // lanes per warp; lanes 1..30 finish nodes, lane 31 is a halo column
@@ -104,7 +108,16 @@ stencil_kernel(const StencilArgs<T, TF> a) {
   // A_G = t + omega x (r_x, r_y, 0), B_G = (omega_y, -omega_x, 0); A, B are
   // refreshed when the plane index enters the next group along z.
   const bool formp = a.z != nullptr;
-  const T beta = formp ? (T)a.st[rhs].beta : T(0);
+  T beta = T(0);
+  if (formp) {
+    if (a.ip.upd) {
+      double b;
+      if (!dpcg_iteration_start(a.st, rhs, const_cast<int*>(a.done), a.ip, b)) return;
+      beta = (T)b;
+    } else {
+      beta = (T)a.st[rhs].beta;
+    }
+  }
   const Groups gp = a.gp;
   const T hh = (T)(0.5 * gp.h);
   T rx = T(0), ry = T(0);

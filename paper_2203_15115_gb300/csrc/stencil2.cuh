@@ -509,7 +509,21 @@ stencil2_kernel(const StencilArgs<float, float> a) {
   pdl_acquire();
   const int rhs = blockIdx.z;
   if (a.done && a.done[rhs]) return;
-  const float beta = MODE == ST_APPLY_DOT ? (float)a.st[rhs].beta : 0.f;
+  // ST_APPLY_DOT in the solver loop: beta and the stopping test from the
+  // previous iteration's partials.  beta goes through shared memory so that
+  // the tile can re-read it instead of holding a register across the march.
+  __shared__ float s_beta;
+  if (MODE == ST_APPLY_DOT) {
+    if (a.ip.upd) {
+      double b;
+      if (!dpcg_iteration_start(a.st, rhs, const_cast<int*>(a.done), a.ip, b)) return;
+      if (threadIdx.x == 0) s_beta = (float)b;
+    } else {
+      if (threadIdx.x == 0) s_beta = (float)a.st[rhs].beta;
+    }
+    __syncthreads();
+  }
+  const float beta = MODE == ST_APPLY_DOT ? s_beta : 0.f;
   extern __shared__ float st2_ring[];
   const float part = stencil2_tile<TY, MODE, LoadRO, ASYNC>(a, beta, blockIdx.x, blockIdx.y, rhs, st2_ring);
   pdl_release();
