@@ -86,7 +86,9 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms.  Samples
+    are time-stamped as they arrive; only those between begin() and stop()
+    (plus the first one after) describe the timed region."""
 
     FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
@@ -96,24 +98,33 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.t_begin = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            t0 = time.monotonic()   # wait for the first sample, so the timed region is covered
+            while not self.lines and time.monotonic() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
+    def begin(self):
+        self.t_begin = time.monotonic()
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t_end = time.monotonic()
+        time.sleep(0.1)   # the sample that covers the end of the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -121,7 +132,10 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        tb = self.t_begin if self.t_begin is not None else 0.0
+        inside = [ln for t, ln in self.lines if tb <= t <= t_end]
+        after = [ln for t, ln in self.lines if t > t_end][:1]
+        for ln in inside + after:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -179,6 +193,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    clocks.begin()
     for _ in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -631,8 +646,11 @@ def run_reference(args):
 
     w = cantilever_128x64x64_voids()
     vals, note = [], ""
+    # the PCG part of each sample shrinks with the number of steps, so that the
+    # run stays within a few minutes (each sample also assembles K, ~5 s)
+    budget = max(1.0, min(4.0, 60.0 / max(1, args.warmup + args.steps)))
     for i in range(args.warmup + args.steps):
-        v, note = oracle_step_sample(w, budget_s=4.0)
+        v, note = oracle_step_sample(w, budget_s=budget)
         if i >= args.warmup and v is not None:
             vals.append(v)
     v = round(float(np.median(vals)), 1) if vals else None
@@ -673,7 +691,7 @@ def launch_summary(path: str):
         c, t = agg.get(short, (0, 0.0))
         agg[short] = (c + 1, t + us)
     total = sum(t for _, t in agg.values())
-    print(f"launches in the timed step: {len(step)}, total device time {total:.1f} us (serialised, cold)")
+    print(f"launches in the timed step: {len(step)}, total device time {total:.1f} us (serialised)")
     print(f"{'kernel':60s} {'launches':>8s} {'total us':>10s} {'share':>7s}")
     for k, (c, t) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
         print(f"{k[:60]:60s} {c:8d} {t:10.1f} {t / total:7.1%}")
@@ -729,7 +747,7 @@ def profile_solve(warps: int, planes: int, solves: int, staging: int = 0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

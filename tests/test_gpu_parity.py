@@ -403,3 +403,26 @@ def test_fp64_solve_with_a_coarse_problem_above_48kb_of_shared_memory():
     K = fe.assemble(w.nx, w.ny, w.nz, w.E)
     assert fe.relative_residual(K, u[0], w.f[0], w.fixed) <= 1.0001e-10
     assert np.linalg.norm(u[0] - u2[0]) <= 1e-6 * np.linalg.norm(u2[0])
+
+
+@pytest.mark.parametrize("precision", [afd.AFD_MIXED, afd.AFD_FP64])
+def test_iteration_budget_stops_the_solve_with_not_converged(precision):
+    """The stopping test at each iteration's start: with max_iter = 7 the loop
+    stops after exactly 7 iterations and the solve reports NOT_CONVERGED,
+    with the iterate it reached (residual below the initial one)."""
+    w = small_cantilever(20, 10, 10, seed=4, n_spheres=4, rmin=1.5, rmax=3.0, group=4)
+    m = afd.Mesh(w.nx, w.ny, w.nz, precision=precision, group=w.group, max_iter=7)
+    m.set_element_moduli(w.E)
+    m.set_loads_bcs(w.f, w.fixed)
+    u = np.zeros_like(w.f)
+    rc, stats = m.solve(1e-10, u_out=u, check=False)
+    assert rc == afd.AFD_ERR_NOT_CONVERGED
+    assert stats[0]["status"] == afd.AFD_ERR_NOT_CONVERGED
+    assert stats[0]["iters"] == 7
+    assert 0.0 < stats[0]["rel_residual"] < 1.0
+    K = fe.assemble(w.nx, w.ny, w.nz, w.E)
+    assert abs(fe.relative_residual(K, u[0], w.f[0], w.fixed) - stats[0]["rel_residual"]) <= 1e-6
+    with pytest.raises(afd.AFDError) as e:
+        m.solve(1e-10)
+    assert e.value.code == afd.AFD_ERR_NOT_CONVERGED
+    m.close()
