@@ -145,6 +145,36 @@ int afd_pnorm_stress(afd_mesh* m, double p, double* out);
 int afd_stress_sensitivity(afd_mesh* m, double p, double rel_tol, float* out, int out_on_device, afd_stats* adj_stats,
                            double* lambda_out, int lambda_on_device);
 
+/* Modal analysis for the eigenvalue constraint of Sec. 3.8 (Eq. 3.4 needs the
+ * modes): the n_modes smallest eigenpairs of K_ff phi = lambda M_ff phi
+ * (lambda = omega^2) on the mesh's moduli and supports.  The paper gives no
+ * mass matrix; M is lumped, every node of element e receiving
+ * rho_e h^3 / 8 per direction with rho_e = rho * E_e (density follows the
+ * modulus).  Subspace iteration on a block of n_modes + max(2, ceil(n_modes/2))
+ * vectors: each step solves K Y = M X with the mesh's solver (its precision
+ * and options, to min(1e-6, max(1e-10, tol/10)), started from X / lambda)
+ * and takes the Rayleigh-Ritz pairs of span(Y) (FP64 Gram matrices, a small
+ * generalised eigenproblem on the device).  Stops when every requested pair
+ * has ||K phi - lambda M phi|| <= tol ||K phi|| (free DOFs), else after
+ * max_iter steps with AFD_ERR_NOT_CONVERGED (outputs still written).
+ * n_modes in [1, 10]; rho > 0.
+ * lam_out: n_modes doubles (host), ascending.  modes_out (nullable):
+ * n_modes*ndof, M-orthonormal, zero on fixed DOFs, sign arbitrary.
+ * iters_out / solve_iters_out (nullable): subspace steps; inner DPCG
+ * iterations summed over the steps (the largest per step).
+ * The load cases are kept; the static solution is discarded (afd_solve
+ * again before afd_compliance or afd_sensitivity).  The modes stay in the
+ * mesh for afd_eigen_sensitivity. */
+int afd_modal(afd_mesh* m, int n_modes, double rho, double tol, int max_iter, double* lam_out, double* modes_out,
+              int modes_on_device, int* iters_out, int* solve_iters_out);
+
+/* Topological sensitivity of the eigenvalues (Eq. 3.4) for the modes of the
+ * last afd_modal, per element at the centroid:
+ *   T_lambda = sigma(phi):eps(phi) - lambda rho_e |phi(centroid)|^2,
+ * phi(centroid) the mean of the element's eight nodal vectors.
+ * out: n_modes*nelem floats, mode-major.  AFD_ERR_STATE without modes. */
+int afd_eigen_sensitivity(afd_mesh* m, float* out, int out_on_device);
+
 /* Level-set update (Eqs. 3.6, 3.17-3.18): for every load case r compute the
  * field of `kind`, divide it by its largest magnitude, add the fields with
  * weights[r] (float32, fixed order), keep the k = round(v * nelem) elements

@@ -45,7 +45,8 @@ EXPORTS = [
     "afd_stencil_async",
     "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
     "afd_server_submit_session", "afd_server_end_session", "afd_server_resident", "afd_levelset_update_cast",
-    "afd_casting_scan", "afd_stress_sensitivity", "afd_levelset_update_fields",
+    "afd_casting_scan", "afd_stress_sensitivity", "afd_levelset_update_fields", "afd_modal",
+    "afd_eigen_sensitivity",
 ]
 
 
@@ -134,6 +135,8 @@ def lib() -> ctypes.CDLL:
             "afd_levelset_update_cast": (i, [vp, i, ctypes.POINTER(d), d, i, i, ctypes.POINTER(d), vp]),
             "afd_casting_scan": (i, [vp, i, i, i, i, i, vp]),
             "afd_stress_sensitivity": (i, [vp, d, d, vp, i, ctypes.POINTER(afd_stats), vp, i]),
+            "afd_modal": (i, [vp, i, d, d, i, ctypes.POINTER(d), vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
+            "afd_eigen_sensitivity": (i, [vp, vp, i]),
             "afd_levelset_update_fields": (i, [vp, vp, i, i, ctypes.POINTER(d), d, i, i, ctypes.POINTER(d), vp]),
         }
         for name, (res, args) in sig.items():
@@ -275,6 +278,31 @@ def afd_stress_sensitivity(mesh, n_rhs: int, p: float, rel_tol: float, out, lamb
         pl, ld, _k2 = _arr(lambda_out, np.float64)
     _check(lib().afd_stress_sensitivity(mesh, p, rel_tol, po, od, st, pl, ld), [s.as_dict() for s in st])
     return [s.as_dict() for s in st]
+
+
+def afd_modal(mesh, n_modes: int, rho: float = 1.0, tol: float = 1e-6, max_iter: int = 100, modes_out=None,
+              check: bool = True):
+    """The n_modes smallest eigenpairs of K phi = lambda M phi (lumped mass,
+    rho_e = rho E_e).  Returns (lambda (n_modes,), info dict); modes_out
+    (n_modes x ndof float64, numpy or torch) receives the M-orthonormal modes.
+    With check=False a stop at max_iter returns normally (info["rc"])."""
+    lam = (ctypes.c_double * n_modes)()
+    steps, solves = ctypes.c_int(0), ctypes.c_int(0)
+    pm, md = (None, 0)
+    if modes_out is not None:
+        pm, md, _k = _arr(modes_out, np.float64)
+    rc = lib().afd_modal(mesh, n_modes, rho, tol, max_iter, lam, pm, md, ctypes.byref(steps), ctypes.byref(solves))
+    info = {"rc": rc, "steps": steps.value, "solve_iters": solves.value}
+    if check or rc not in (AFD_OK, AFD_ERR_NOT_CONVERGED):
+        _check(rc, info)
+    return np.array(lam[:], dtype=np.float64), info
+
+
+def afd_eigen_sensitivity(mesh, out) -> None:
+    """T_lambda of Eq. 3.4 for the modes of the last afd_modal into out
+    (n_modes x nelem float32, numpy or torch)."""
+    po, od, _k = _arr(out, np.float32)
+    _check(lib().afd_eigen_sensitivity(mesh, po, od))
 
 
 def afd_levelset_update_fields(mesh, fields, weights, volume_fraction: float, casting=None, kept_out=None) -> float:
@@ -662,6 +690,13 @@ class Mesh:
 
     def stress_sensitivity(self, p: float, rel_tol: float, out, lambda_out=None):
         return afd_stress_sensitivity(self.h, self.n_rhs, p, rel_tol, out, lambda_out)
+
+    def modal(self, n_modes: int, rho: float = 1.0, tol: float = 1e-6, max_iter: int = 100, modes_out=None,
+              check: bool = True):
+        return afd_modal(self.h, n_modes, rho, tol, max_iter, modes_out, check)
+
+    def eigen_sensitivity(self, out) -> None:
+        afd_eigen_sensitivity(self.h, out)
 
     def levelset_update(self, kind: int, weights, volume_fraction: float, kept_out=None, casting=None) -> float:
         return afd_levelset_update(self.h, kind, weights, volume_fraction, kept_out, casting)

@@ -28,6 +28,7 @@
 #include "stencil.cuh"
 #include "stencil2.cuh"
 #include "dpcg_persistent.cuh"
+#include "modal.cuh"
 
 using namespace afd;
 
@@ -154,6 +155,14 @@ struct afd_mesh {
   float* lsbuf = nullptr;      // caller fields of afd_levelset_update_fields
   size_t lsbuf_cap = 0;
   int adj_cap = 0;
+  // modal analysis: Ritz block X, K Y, K X (or M Y), lumped mass, Gram partials,
+  // small matrices; the last result (modes = first modal_n rows of mX)
+  double *mX = nullptr, *mKY = nullptr, *mKX = nullptr, *mmass = nullptr, *mparts = nullptr;
+  double *mA = nullptr, *mB = nullptr, *mV = nullptr, *mlam = nullptr;
+  int* minfo = nullptr;
+  int modal_cap = 0, modal_n = 0;
+  double modal_rho = 1.0;
+  bool modal_valid = false;
   int nsplit_aw = 1;
   bool coarse_valid = false;
   Work<float> w32;
@@ -973,6 +982,8 @@ void afd_destroy(afd_mesh* m) {
   dfree(m->grec); dfree(m->gcount); dfree(m->upart);
   dfree(m->ppart); dfree(m->prec); dfree(m->gbar); dfree(m->ptime);
   dfree(m->lam64); dfree(m->gadj); dfree(m->dsig); dfree(m->pn_d); dfree(m->lsbuf);
+  dfree(m->mX); dfree(m->mKY); dfree(m->mKX); dfree(m->mmass); dfree(m->mparts);
+  dfree(m->mA); dfree(m->mB); dfree(m->mV); dfree(m->mlam); dfree(m->minfo);
   if (m->ev) cudaEventDestroy(m->ev);
   if (m->s) cudaStreamDestroy(m->s);
   delete m;
@@ -1365,6 +1376,184 @@ int afd_stress_sensitivity(afd_mesh* m, double p, double rel_tol, float* out, in
   TRY(finish(m));
   if (rc != AFD_OK) return fail(rc, "adjoint solve did not reach rel_tol %.3g", rel_tol);
   return AFD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Modal analysis (the eigenvalue constraint of Sec. 3.8; Eq. 3.4 needs its
+// modes): subspace iteration with Rayleigh-Ritz on the mesh's own solver.
+// ---------------------------------------------------------------------------
+constexpr int MODAL_GRAM_BLOCKS = 304;
+
+static int modal_gram(afd_mesh* m, int kp, const double* Y, const double* Z, double* out) {
+  const Grid& g = m->gr;
+  k_gram<<<MODAL_GRAM_BLOCKS, 256, 0, m->s>>>(g.ndof, g.vs, kp, Y, Z, m->mparts); m->launches++;
+  k_gram_final<<<1, 256, 0, m->s>>>(MODAL_GRAM_BLOCKS, kp * kp, m->mparts, out); m->launches++;
+  CK(cudaGetLastError());
+  return AFD_OK;
+}
+
+int afd_modal(afd_mesh* m, int n_modes, double rho, double tol, int max_iter, double* lam_out, double* modes_out,
+              int modes_on_device, int* iters_out, int* solve_iters_out) {
+  if (!m || !lam_out) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  const int guard = std::max(2, (n_modes + 1) / 2);
+  const int kp = n_modes + guard;
+  if (n_modes < 1 || kp > MODAL_MAX)
+    return fail(AFD_ERR_INVALID_ARG, "n_modes must be in [1, %d]", MODAL_MAX - 2 - (MODAL_MAX - 2) / 3);
+  if (!(rho > 0.0) || !std::isfinite(rho)) return fail(AFD_ERR_INVALID_ARG, "rho must be > 0");
+  if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 1) return fail(AFD_ERR_INVALID_ARG, "bad tol / max_iter");
+  if (!m->has_moduli || !m->has_loads) return fail(AFD_ERR_STATE, "set moduli and supports before afd_modal");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const Grid& g = m->gr;
+  // the load cases are kept: saved here, restored at the end
+  const int R0 = m->nrhs;
+  const std::vector<double> fnorm0 = m->fnorm;
+  double* fsave = nullptr;
+  TRY(dalloc(&fsave, (size_t)R0 * g.vs));
+  CK(cudaMemcpyAsync(fsave, m->f64, (size_t)R0 * g.vs * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
+  int rc = AFD_OK;
+  std::string err;
+  auto run = [&]() -> int {
+    TRY(ensure_rhs(m, kp));
+    if (m->modal_cap < kp) {
+      dfree(m->mX); dfree(m->mKY); dfree(m->mKX); dfree(m->mmass); dfree(m->mparts);
+      dfree(m->mA); dfree(m->mB); dfree(m->mV); dfree(m->mlam); dfree(m->minfo);
+      m->modal_cap = 0;
+      TRY(dalloc(&m->mX, (size_t)kp * g.vs));
+      TRY(dalloc(&m->mKY, (size_t)kp * g.vs));
+      TRY(dalloc(&m->mKX, (size_t)kp * g.vs));
+      TRY(dalloc(&m->mmass, (size_t)g.vs));
+      TRY(dalloc(&m->mparts, (size_t)MODAL_GRAM_BLOCKS * MODAL_MAX * MODAL_MAX));
+      TRY(dalloc(&m->mA, (size_t)MODAL_MAX * MODAL_MAX));
+      TRY(dalloc(&m->mB, (size_t)MODAL_MAX * MODAL_MAX));
+      TRY(dalloc(&m->mV, (size_t)MODAL_MAX * MODAL_MAX));
+      TRY(dalloc(&m->mlam, (size_t)MODAL_MAX));
+      TRY(dalloc(&m->minfo, 1));
+      m->modal_cap = kp;
+    }
+    m->modal_valid = false;
+    const double h = m->opt.h;
+    CK(cudaMemsetAsync(m->mmass, 0, (size_t)g.vs * sizeof(double), m->s));
+    CK(cudaMemsetAsync(m->mX, 0, (size_t)kp * g.vs * sizeof(double), m->s));
+    k_lumped_mass<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->E64, rho * h * h * h / 8.0, m->fixed,
+                                                                      m->mmass); m->launches++;
+    const dim3 vgrid(grid_blocks(g.ndof, 256, 2048), kp);
+    k_modal_start<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, 0x2203151150ull, m->mmass, m->mX); m->launches++;
+    CK(cudaGetLastError());
+    const double solve_tol = std::min(1e-6, std::max(1e-10, 0.1 * tol));
+    std::vector<double> lam(kp, 0.0), inv(kp, 0.0);
+    int steps = 0, solve_iters = 0;
+    bool converged = false;
+    TRY(ensure_partials(m, (size_t)kp * 2 * RED_BLOCKS));
+    for (int it = 0; it < max_iter && !converged; ++it) {
+      // right-hand sides M X in the solver's load buffer, their norms
+      k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->mX, m->f64); m->launches++;
+      k_dot<double, double><<<dim3(RED_BLOCKS, kp), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->f64, m->f64, m->partials);
+      m->launches++;
+      CK(cudaGetLastError());
+      std::vector<double> bb;
+      TRY(reduce_partials_host(m, kp, RED_BLOCKS, bb));
+      m->nrhs = kp;
+      m->fnorm.assign(kp, 0.0);
+      for (int r = 0; r < kp; ++r) m->fnorm[r] = std::sqrt(bb[r]);
+      // Y = K^-1 M X, started from X / lambda once Ritz values exist
+      int warm = 0;
+      if (it > 0) {
+        for (int r = 0; r < kp; ++r) inv[r] = lam[r] > 0.0 ? 1.0 / lam[r] : 0.0;
+        CK(cudaMemcpyAsync(m->mlam, inv.data(), kp * sizeof(double), cudaMemcpyHostToDevice, m->s));
+        k_scale_rhs<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mlam, m->mX, m->u64); m->launches++;
+        m->has_solution = true;
+        warm = 1;
+      }
+      std::vector<afd_stats> st(kp);
+      const int src = afd_solve(m, solve_tol, warm, st.data(), nullptr, 0);
+      if (src != AFD_OK && src != AFD_ERR_NOT_CONVERGED) return src;
+      int mx = 0;
+      for (int r = 0; r < kp; ++r) mx = std::max(mx, st[r].iters);
+      solve_iters += mx;
+      // Rayleigh-Ritz on span(Y): A = Y^T K Y (FP64 apply), B = Y^T M Y
+      TRY((launch_stencil<double, ST_APPLY, double>(m, m->u64, m->mKY, m->w64.E, nullptr, nullptr, nullptr, nullptr,
+                                                      kp, m->w64.K)));
+      TRY(modal_gram(m, kp, m->u64, m->mKY, m->mA));
+      k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->u64, m->mKX); m->launches++;
+      TRY(modal_gram(m, kp, m->u64, m->mKX, m->mB));
+      k_small_geig<<<1, 32, 0, m->s>>>(kp, m->mA, m->mB, m->mlam, m->mV, m->minfo); m->launches++;
+      k_ritz_combine<<<grid_blocks(g.ndof, 256, 2048), 256, 0, m->s>>>(g.ndof, g.vs, kp, m->u64, m->mV, m->mX);
+      m->launches++;
+      k_ritz_combine<<<grid_blocks(g.ndof, 256, 2048), 256, 0, m->s>>>(g.ndof, g.vs, kp, m->mKY, m->mV, m->mKX);
+      m->launches++;
+      k_modal_residual<<<dim3(RED_BLOCKS, n_modes), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->mKX, m->mX, m->mmass,
+                                                                          m->mlam, m->partials); m->launches++;
+      CK(cudaGetLastError());
+      int info = 0;
+      CK(cudaMemcpyAsync(lam.data(), m->mlam, kp * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+      CK(cudaMemcpyAsync(&info, m->minfo, sizeof(int), cudaMemcpyDeviceToHost, m->s));
+      std::vector<double> hp((size_t)n_modes * RED_BLOCKS * 2);
+      CK(cudaMemcpyAsync(hp.data(), m->partials, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+      CK(cudaStreamSynchronize(m->s));
+      if (info != 0) return fail(AFD_ERR_NAN, "Rayleigh-Ritz step failed (%s)", info == 1 ? "Y^T M Y not positive definite"
+                                                                                        : "Jacobi sweeps did not converge");
+      steps = it + 1;
+      converged = true;
+      for (int r = 0; r < n_modes; ++r) {
+        double e2 = 0.0, k2 = 0.0;
+        for (int b = 0; b < RED_BLOCKS; ++b) {
+          e2 += hp[((size_t)r * RED_BLOCKS + b) * 2];
+          k2 += hp[((size_t)r * RED_BLOCKS + b) * 2 + 1];
+        }
+        if (!std::isfinite(e2) || !std::isfinite(lam[r])) return fail(AFD_ERR_NAN, "modal iteration is not finite");
+        if (!(std::sqrt(e2) <= tol * std::sqrt(k2))) converged = false;
+      }
+    }
+    for (int r = 0; r < n_modes; ++r) lam_out[r] = lam[r];
+    if (modes_out)
+      CK(cudaMemcpy2DAsync(modes_out, (size_t)g.ndof * sizeof(double), m->mX, (size_t)g.vs * sizeof(double),
+                           (size_t)g.ndof * sizeof(double), n_modes,
+                           modes_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->s));
+    if (iters_out) *iters_out = steps;
+    if (solve_iters_out) *solve_iters_out = solve_iters;
+    m->modal_n = n_modes;
+    m->modal_rho = rho;
+    m->modal_valid = true;
+    return converged ? AFD_OK : AFD_ERR_NOT_CONVERGED;
+  };
+  rc = run();
+  if (rc != AFD_OK) err = g_err;
+  // restore the load cases; the static solution is gone
+  if (m->f64 && m->cap >= R0)
+    CK(cudaMemcpyAsync(m->f64, fsave, (size_t)R0 * g.vs * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
+  CK(cudaStreamSynchronize(m->s));
+  dfree(fsave);
+  m->nrhs = R0;
+  m->fnorm = fnorm0;
+  m->has_solution = false;
+  invalidate_graphs(m);
+  TRY(finish(m));
+  if (rc == AFD_ERR_NOT_CONVERGED) return fail(rc, "modal iteration did not reach tol %.3g in %d steps", tol, max_iter);
+  if (rc != AFD_OK) return fail(rc, "%s", err.c_str());
+  return AFD_OK;
+}
+
+int afd_eigen_sensitivity(afd_mesh* m, float* out, int out_on_device) {
+  if (!m || !out) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (!m->modal_valid) return fail(AFD_ERR_STATE, "no modes: call afd_modal first");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const Grid& g = m->gr;
+  FieldConsts F;
+  const double nu = m->opt.nu;
+  F.lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  F.mu = 1.0 / (2.0 * (1.0 + nu));
+  F.nu = nu;
+  F.inv4h = 1.0 / (4.0 * m->opt.h);
+  const int n = m->modal_n;
+  float* dst = out_on_device ? out : m->fbuf;   // fbuf holds >= modal block x N_e floats
+  k_eigen_topo<<<dim3(grid_blocks(g.nelem, 256, 8 * RED_BLOCKS), n), 256, 0, m->s>>>(g, m->mX, m->mlam, m->E64, F,
+                                                                                     m->modal_rho, dst); m->launches++;
+  CK(cudaGetLastError());
+  if (!out_on_device)
+    CK(cudaMemcpyAsync(out, m->fbuf, (size_t)n * g.nelem * sizeof(float), cudaMemcpyDeviceToHost, m->s));
+  return finish(m);
 }
 
 // Top-k selection on device keys (stream s); kept/E written on the device.

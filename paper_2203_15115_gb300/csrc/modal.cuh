@@ -1,0 +1,282 @@
+// Modal analysis on the deflated solver (the eigenvalue constraint of Sec. 3.8
+// and its topological sensitivity, Eq. 3.4): the lowest eigenpairs of
+// K_ff phi = lambda M_ff phi with a lumped mass, by subspace iteration -- each
+// step solves K Y = M X for a block of vectors with the batched solver and
+// takes the Rayleigh-Ritz pairs of span(Y).
+//
+// Mass model (the paper gives none): every node of element e receives
+// rho_e h^3 / 8 per direction with rho_e = rho E_e (density follows the
+// modulus, so voids add no spurious low-frequency local modes).
+#pragma once
+
+#include "afd_common.cuh"
+#include "dpcg_kernels.cuh"
+#include "sens.cuh"
+
+namespace afd {
+
+constexpr int MODAL_MAX = 16;   // largest block of the subspace iteration
+
+// Lumped mass per DOF (zero on fixed DOFs): m_n = (rho h^3 / 8) sum_{e at n} E_e.
+__global__ void k_lumped_mass(Grid gr, const double* __restrict__ Emod, double rho_h3_8,
+                              const uint8_t* __restrict__ fixed, double* __restrict__ mass) {
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gr.nnodes; n += gridDim.x * blockDim.x) {
+    const int i = n % gr.nnx, j = (n / gr.nnx) % gr.nny, k = n / (gr.nnx * gr.nny);
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int ei = i - 1 + (a & 1), ej = j - 1 + ((a >> 1) & 1), ek = k - 1 + ((a >> 2) & 1);
+      if (ei >= 0 && ei < gr.nx && ej >= 0 && ej < gr.ny && ek >= 0 && ek < gr.nz)
+        s += Emod[ei + gr.nx * (ej + gr.ny * ek)];
+    }
+    const uint8_t fb = fixed ? fixed[n] : 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mass[3 * (size_t)n + c] = ((fb >> c) & 1) ? 0.0 : rho_h3_8 * s;
+  }
+}
+
+// SplitMix64 (Steele, Lea and Flood; the constants of Vigna's published
+// reference), used as a counter-based generator: one 64-bit output per (seed,
+// counter), mapped to a double in [-1, 1).
+__device__ __forceinline__ double splitmix_unit(uint64_t seed, uint64_t counter) {
+  uint64_t z = seed + (counter + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// Starting block: pseudo-random vectors, zero on fixed DOFs (mass zero there).
+__global__ void k_modal_start(int ndof, int vs, uint64_t seed, const double* __restrict__ mass, double* __restrict__ X) {
+  const int r = blockIdx.y;
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x)
+    X[(size_t)r * vs + d] = mass[d] > 0.0 ? splitmix_unit(seed, (uint64_t)r * ndof + d) : 0.0;
+}
+
+// B[r] = M X[r] (diagonal mass); with inv = true, B[r] = X[r] * s[r] (the warm
+// start X / lambda of the next solve).
+__global__ void k_mass_apply(int ndof, int vs, const double* __restrict__ mass, const double* __restrict__ X,
+                             double* __restrict__ B) {
+  const int r = blockIdx.y;
+  const size_t off = (size_t)r * vs;
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x)
+    B[off + d] = mass[d] * X[off + d];
+}
+__global__ void k_scale_rhs(int ndof, int vs, const double* __restrict__ s, const double* __restrict__ X,
+                            double* __restrict__ Y) {
+  const int r = blockIdx.y;
+  const size_t off = (size_t)r * vs;
+  const double sr = s[r];
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x)
+    Y[off + d] = sr * X[off + d];
+}
+
+// Gram matrix partials: parts[b][i kp + j] = sum over this block's DOFs of
+// Y[i] Z[j], in a fixed order (tiles of GRAM_T DOFs through shared memory,
+// thread i kp + j accumulating its pair).  Reduced by k_gram_final.
+constexpr int GRAM_T = 64;
+__global__ void __launch_bounds__(256) k_gram(int ndof, int vs, int kp, const double* __restrict__ Y,
+                                              const double* __restrict__ Z, double* __restrict__ parts) {
+  __shared__ double ys[MODAL_MAX][GRAM_T + 1];
+  __shared__ double zs[MODAL_MAX][GRAM_T + 1];
+  const int t = threadIdx.x, np = kp * kp;
+  const int pi = t / kp, pj = t % kp;
+  double acc = 0.0;
+  for (int base = blockIdx.x * GRAM_T; base < ndof; base += gridDim.x * GRAM_T) {
+    for (int q = t; q < kp * GRAM_T; q += blockDim.x) {
+      const int r = q / GRAM_T, c = q % GRAM_T, d = base + c;
+      ys[r][c] = d < ndof ? Y[(size_t)r * vs + d] : 0.0;
+      zs[r][c] = d < ndof ? Z[(size_t)r * vs + d] : 0.0;
+    }
+    __syncthreads();
+    if (t < np)
+      for (int c = 0; c < GRAM_T; ++c) acc = fma(ys[pi][c], zs[pj][c], acc);
+    __syncthreads();
+  }
+  if (t < np) parts[(size_t)blockIdx.x * np + t] = acc;
+}
+__global__ void k_gram_final(int nparts, int np, const double* __restrict__ parts, double* __restrict__ out) {
+  const int t = threadIdx.x;
+  if (t >= np) return;
+  double s = 0.0;
+  for (int b = 0; b < nparts; ++b) s += parts[(size_t)b * np + t];
+  out[t] = s;
+}
+
+// The small generalised symmetric eigenproblem A v = lambda B v (kp x kp,
+// row-major, B SPD) of the Rayleigh-Ritz step, by one thread: Cholesky
+// B = L L^T, C = L^-1 A L^-T, cyclic Jacobi rotations on C until every
+// off-diagonal entry is below 1e-15 of the diagonal scale (at most 64 sweeps),
+// then V = L^-T Q, eigenvalues ascending.  V^T B V = I.  info: 0 ok, 1 B not
+// positive definite, 2 no convergence.
+__global__ void k_small_geig(int kp, const double* __restrict__ A, const double* __restrict__ Bm,
+                             double* __restrict__ lam, double* __restrict__ V, int* info) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double L[MODAL_MAX][MODAL_MAX], C[MODAL_MAX][MODAL_MAX], Q[MODAL_MAX][MODAL_MAX];
+  const int n = kp;
+  *info = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) L[i][j] = 0.0;
+  for (int j = 0; j < n; ++j) {                        // Cholesky, lower
+    double d = Bm[j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    if (!(d > 0.0)) { *info = 1; return; }
+    L[j][j] = sqrt(d);
+    for (int i = j + 1; i < n; ++i) {
+      double s = Bm[i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      L[i][j] = s / L[j][j];
+    }
+  }
+  // W = L^-1 A (forward substitution per column), then C = W L^-T (per row)
+  for (int c = 0; c < n; ++c)
+    for (int i = 0; i < n; ++i) {
+      double s = A[i * n + c];
+      for (int k = 0; k < i; ++k) s -= L[i][k] * C[k][c];
+      C[i][c] = s / L[i][i];
+    }
+  for (int r = 0; r < n; ++r)
+    for (int i = 0; i < n; ++i) {
+      double s = C[r][i];
+      for (int k = 0; k < i; ++k) s -= L[i][k] * Q[r][k];
+      Q[r][i] = s / L[i][i];
+    }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) C[i][j] = 0.5 * (Q[i][j] + Q[j][i]);   // symmetric to rounding
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Q[i][j] = i == j ? 1.0 : 0.0;
+  bool conv = false;
+  for (int sweep = 0; sweep < 64 && !conv; ++sweep) {
+    double scale = 0.0;
+    for (int i = 0; i < n; ++i) scale = fmax(scale, fabs(C[i][i]));
+    conv = true;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (fabs(C[p][q]) <= 1e-15 * scale) continue;
+        conv = false;
+        // rotation that zeroes C[p][q] (Rutishauser's form)
+        const double theta = (C[q][q] - C[p][p]) / (2.0 * C[p][q]);
+        const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / sqrt(tt * tt + 1.0), sn = tt * cs;
+        for (int k = 0; k < n; ++k) {                  // C <- C J (columns p, q)
+          const double a = C[k][p], b = C[k][q];
+          C[k][p] = cs * a - sn * b;
+          C[k][q] = sn * a + cs * b;
+        }
+        for (int k = 0; k < n; ++k) {                  // C <- J^T C (rows p, q)
+          const double a = C[p][k], b = C[q][k];
+          C[p][k] = cs * a - sn * b;
+          C[q][k] = sn * a + cs * b;
+        }
+        for (int k = 0; k < n; ++k) {                  // Q <- Q J
+          const double a = Q[k][p], b = Q[k][q];
+          Q[k][p] = cs * a - sn * b;
+          Q[k][q] = sn * a + cs * b;
+        }
+      }
+  }
+  if (!conv) *info = 2;
+  // ascending order (selection sort on the diagonal, columns of Q follow)
+  int ord[MODAL_MAX];
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (C[ord[j]][ord[j]] < C[ord[i]][ord[i]]) {
+        const int t = ord[i];
+        ord[i] = ord[j];
+        ord[j] = t;
+      }
+  // V = L^-T Q (back substitution per column)
+  for (int c = 0; c < n; ++c) {
+    const int oc = ord[c];
+    lam[c] = C[oc][oc];
+    for (int i = n - 1; i >= 0; --i) {
+      double s = Q[i][oc];
+      for (int k = i + 1; k < n; ++k) s -= L[k][i] * V[k * n + c];
+      V[i * n + c] = s / L[i][i];
+    }
+  }
+}
+
+// X[r] = sum_j Y[j] V[j][r] for r < kp (the Ritz vectors of span(Y)).
+__global__ void k_ritz_combine(int ndof, int vs, int kp, const double* __restrict__ Y, const double* __restrict__ V,
+                               double* __restrict__ X) {
+  __shared__ double sv[MODAL_MAX * MODAL_MAX];
+  for (int q = threadIdx.x; q < kp * kp; q += blockDim.x) sv[q] = V[q];
+  __syncthreads();
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
+    double y[MODAL_MAX];
+#pragma unroll
+    for (int j = 0; j < MODAL_MAX; ++j) y[j] = j < kp ? Y[(size_t)j * vs + d] : 0.0;
+    for (int r = 0; r < kp; ++r) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < MODAL_MAX; ++j)
+        if (j < kp) s = fma(y[j], sv[j * kp + r], s);
+      X[(size_t)r * vs + d] = s;
+    }
+  }
+}
+
+// Residual partials of the first n Ritz pairs: parts[(r * gridDim.x + b) * 2]
+// = sum (K x_r - lambda_r M x_r)^2, [.. + 1] = sum (K x_r)^2.
+__global__ void __launch_bounds__(RED_THREADS)
+k_modal_residual(int ndof, int vs, const double* __restrict__ KX, const double* __restrict__ X,
+                 const double* __restrict__ mass, const double* __restrict__ lam, double* __restrict__ parts) {
+  __shared__ double red[32 * 2];
+  const int r = blockIdx.y;
+  const size_t off = (size_t)r * vs;
+  const double l = lam[r];
+  double s[2] = {0.0, 0.0};
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
+    const double kx = KX[off + d];
+    const double e = mass[d] > 0.0 ? kx - l * mass[d] * X[off + d] : 0.0;
+    s[0] = fma(e, e, s[0]);
+    s[1] = mass[d] > 0.0 ? fma(kx, kx, s[1]) : s[1];
+  }
+  double o[2];
+  block_sum_to_f64<2>(s, red, o);
+  if (threadIdx.x == 0) {
+    parts[((size_t)r * gridDim.x + blockIdx.x) * 2] = o[0];
+    parts[((size_t)r * gridDim.x + blockIdx.x) * 2 + 1] = o[1];
+  }
+}
+
+// T_lambda of Eq. 3.4 at each element centroid for mode r (phi[r], lam[r]):
+// sigma(phi):eps(phi) - lam rho E_e |phi(centroid)|^2, phi(centroid) = the
+// mean of the eight nodal vectors (the WHT's constant coefficient / 8).
+__global__ void __launch_bounds__(256)
+k_eigen_topo(Grid gr, const double* __restrict__ phi, const double* __restrict__ lam, const double* __restrict__ Emod,
+             FieldConsts F, double rho, float* __restrict__ out) {
+  const int r = blockIdx.y;
+  const double* pr = phi + (size_t)r * gr.vs;
+  const double lr = lam[r];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < gr.nelem; e += gridDim.x * blockDim.x) {
+    const int i = e % gr.nx, j = (e / gr.nx) % gr.ny, k = e / (gr.nx * gr.ny);
+    double h[3][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int n = (i + (a & 1)) + gr.nnx * ((j + ((a >> 1) & 1)) + gr.nny * (k + ((a >> 2) & 1)));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) h[c][a] = pr[3 * (size_t)n + c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) wht8_fwd(h[c]);
+    double eps[6];
+    eps[0] = h[0][1] * F.inv4h;
+    eps[1] = h[1][2] * F.inv4h;
+    eps[2] = h[2][4] * F.inv4h;
+    eps[3] = 0.5 * (h[0][2] + h[1][1]) * F.inv4h;
+    eps[4] = 0.5 * (h[1][4] + h[2][2]) * F.inv4h;
+    eps[5] = 0.5 * (h[2][1] + h[0][4]) * F.inv4h;
+    const double E = Emod[e];
+    const double tre = eps[0] + eps[1] + eps[2];
+    const double la = F.lam * E, mu2 = 2.0 * F.mu * E;
+    const double se = (la * tre + mu2 * eps[0]) * eps[0] + (la * tre + mu2 * eps[1]) * eps[1] +
+                      (la * tre + mu2 * eps[2]) * eps[2] + 2.0 * mu2 * (eps[3] * eps[3] + eps[4] * eps[4] + eps[5] * eps[5]);
+    const double cx = 0.125 * h[0][0], cy = 0.125 * h[1][0], cz = 0.125 * h[2][0];
+    out[(size_t)r * gr.nelem + e] = (float)(se - lr * rho * E * (cx * cx + cy * cy + cz * cz));
+  }
+}
+
+}  // namespace afd

@@ -1,0 +1,87 @@
+"""Modal analysis and the eigenvalue sensitivity (Eq. 3.4) on the GPU against
+the oracle (oracle/modal.py)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import paper_2203_15115_gb300 as afd  # noqa: E402
+from oracle import fe, modal  # noqa: E402
+from synthetic import small_cantilever  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs cuda")
+    afd.lib()
+
+
+def _case(seed=6):
+    # depth != height and seeded voids: no symmetric pairs of modes
+    return small_cantilever(14, 6, 4, seed=seed, n_spheres=4, rmin=1.0, rmax=2.5, group=2)
+
+
+@pytest.mark.parametrize("precision", [afd.AFD_FP64, afd.AFD_MIXED])
+def test_modal_matches_oracle(precision):
+    w = _case()
+    n, rho, tol = 4, 1.7, 1e-8
+    lam_o, phi_o = modal.modes(w.nx, w.ny, w.nz, w.E, w.fixed, n, rho=rho)
+    assert np.all(np.diff(lam_o) > 1e-3 * lam_o[1:])            # simple eigenvalues: modes comparable one by one
+    m = afd.Mesh(w.nx, w.ny, w.nz, precision=precision, group=w.group)
+    m.set_element_moduli(w.E)
+    m.set_loads_bcs(w.f, w.fixed)
+    phi = np.zeros((n, m.ndof))
+    lam, info = m.modal(n, rho=rho, tol=tol, modes_out=phi)
+    assert info["steps"] >= 1
+    assert np.allclose(lam, lam_o, rtol=1e-9)
+    mass = modal.lumped_mass(w.nx, w.ny, w.nz, w.E, rho)
+    G = phi @ (mass[:, None] * phi.T)
+    assert np.allclose(G, np.eye(n), atol=1e-10)
+    fixed = w.fixed.reshape(-1)
+    assert np.all(phi[:, fixed == 1] == 0.0)
+    K = fe.assemble(w.nx, w.ny, w.nz, w.E)
+    fr = fe.free_dofs(fixed)
+    for i in range(n):
+        assert abs(abs(phi[i] @ (mass * phi_o[i])) - 1.0) < 1e-7
+        r = (K @ phi[i] - lam[i] * mass * phi[i])[fr]
+        assert np.linalg.norm(r) <= 1.01 * tol * np.linalg.norm((K @ phi[i])[fr])
+    # the eigenvalue sensitivity of each mode, against the oracle on the same mode
+    T = np.zeros((n, m.nelem), np.float32)
+    m.eigen_sensitivity(T)
+    for i in range(n):
+        ref = modal.eigen_sensitivity(w.nx, w.ny, w.nz, w.E, phi[i], lam[i], rho)
+        assert np.linalg.norm(T[i] - ref) <= 1e-6 * np.linalg.norm(ref)
+    m.close()
+
+
+def test_modal_keeps_the_load_cases_and_reports_its_budget():
+    w = _case(seed=8)
+    m = afd.Mesh(w.nx, w.ny, w.nz, group=w.group)
+    m.set_element_moduli(w.E)
+    m.set_loads_bcs(w.f, w.fixed)
+    u0 = np.zeros_like(w.f)
+    m.solve(1e-8, u_out=u0)
+    J0 = m.compliance()[0]
+    with pytest.raises(afd.AFDError) as e:
+        m.eigen_sensitivity(np.zeros((2, m.nelem), np.float32))
+    assert e.value.code == afd.AFD_ERR_STATE
+    lam, info = m.modal(2, tol=1e-12, max_iter=1, check=False)
+    assert info["rc"] == afd.AFD_ERR_NOT_CONVERGED and info["steps"] == 1
+    assert np.all(np.isfinite(lam)) and lam[0] > 0
+    with pytest.raises(afd.AFDError) as e:
+        m.compliance()                                  # the static solution was discarded
+    assert e.value.code == afd.AFD_ERR_STATE
+    u1 = np.zeros_like(w.f)
+    m.solve(1e-8, u_out=u1)
+    assert np.linalg.norm(u1 - u0) <= 1e-6 * np.linalg.norm(u0)
+    assert abs(m.compliance()[0] - J0) <= 1e-7 * abs(J0)
+    with pytest.raises(afd.AFDError) as e:
+        m.modal(0)
+    assert e.value.code == afd.AFD_ERR_INVALID_ARG
+    with pytest.raises(afd.AFDError) as e:
+        m.modal(11)
+    assert e.value.code == afd.AFD_ERR_INVALID_ARG
+    m.close()
