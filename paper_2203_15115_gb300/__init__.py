@@ -553,18 +553,25 @@ def run_volume_minimisation(mesh: "Mesh", steps: int = 20, dv: float = 0.02, j_f
 def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] = None, stress: Optional[float] = None,
                              p: float = 8.0, dv0: float = 0.05, dv_min: Optional[float] = None, v_min: float = 0.05,
                              max_fea: int = 200, conv: float = 0.01, tol: float = 1e-6, casting=None,
-                             on_step=None) -> dict:
+                             on_step=None, eigen: Optional[float] = None, rho: float = 1.0,
+                             eig_tol: float = 1e-6) -> dict:
     """The algorithm of Sec. 3.8 for min |Omega| with hard constraints
-    J <= compliance * J_0 and sigma_PN <= stress * sigma_0 (either may be None),
-    over the library's calls (each step runs in its kernels):
-      2. analysis: solve (warm start), J, sigma_PN (p-norm of Eq. 3.3);
-      3. g_i = value / (alpha_i value_0) - 1 and the AL update (Eqs. 3.11-3.12);
+    J <= compliance * J_0, sigma_PN <= stress * sigma_0 and lambda_1 >=
+    eigen * lambda_1,0 (the fundamental eigenvalue of the lumped-mass modal
+    problem, afd_modal; any of the three may be None), over the library's
+    calls (each step runs in its kernels):
+      2. analysis: solve (warm start), J, sigma_PN (p-norm of Eq. 3.3), their
+         fields (strain energy, adjoint T_sigma), and with `eigen` the modal
+         analysis (1 mode to eig_tol, density rho) and T_lambda (Eq. 3.4);
+      3. g_i = value / (alpha_i value_0) - 1 for the upper bounds (J, sigma),
+         g = 1 - lambda_1 / (alpha lambda_1,0) for the eigenvalue's lower bound,
+         and the AL update (Eqs. 3.11-3.12);
       4./9. a violated hard constraint returns to the last feasible design with
          the volume step halved (stop when it falls below dv_min, default 0.1 dv0);
       5./6. the augmented level set (Eq. 3.17): strain-energy field weighted by
          the compliance constraint's (mu + gamma g)+, the adjoint stress field
-         T_sigma by the stress constraint's, optional casting, cut at the
-         target volume;
+         T_sigma by the stress constraint's, T_lambda by the eigenvalue
+         constraint's, optional casting, cut at the target volume;
       7./8. when J changed by less than `conv` since the previous analysis at
          the same target, the target drops by the volume step (stop below
          v_min).
@@ -573,19 +580,39 @@ def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] =
     volume fraction, and why it stopped."""
     ne = mesh.nelem
     dv_min = 0.1 * dv0 if dv_min is None else dv_min
-    cons = [c for c in (("J", compliance), ("sigma", stress)) if c[1] is not None]
+    cons = [c for c in (("J", compliance), ("sigma", stress), ("lambda", eigen)) if c[1] is not None]
     al = {name: afd_al_init() for name, _ in cons}
     E_cur = np.asarray(E_init, dtype=np.float64).copy()
     mesh.set_element_moduli(E_cur)
     e_void = mesh.options.e_void
 
     def analyse(warm):
+        # the static fields first: the modal analysis discards the static solution
         st = mesh.solve(tol, warm_start=warm)
         J = float(mesh.compliance()[0])
         sig = float(mesh.pnorm_stress(p)[0]) if stress is not None else None
-        return st[0], {"J": J, "sigma": sig}
+        flds = {}
+        if compliance is not None:
+            f = np.zeros((1, ne), np.float32)
+            mesh.sensitivity(AFD_SENS_STRAIN_ENERGY, f)
+            flds["J"] = f[0]
+        if stress is not None:
+            f = np.zeros((1, ne), np.float32)
+            mesh.stress_sensitivity(p, tol, f)
+            flds["sigma"] = f[0]
+        lam1 = None
+        if eigen is not None:
+            lam, _ = mesh.modal(1, rho=rho, tol=eig_tol)
+            lam1 = float(lam[0])
+            f = np.zeros((1, ne), np.float32)
+            mesh.eigen_sensitivity(f)
+            flds["lambda"] = f[0]
+        return st[0], {"J": J, "sigma": sig, "lambda": lam1}, flds
 
-    st, val = analyse(False)
+    def gval(name, alpha, v, r):
+        return 1.0 - v / (alpha * r) if name == "lambda" else v / (alpha * r) - 1.0
+
+    st, val, flds = analyse(False)
     fea = 1
     ref = dict(val)
     feasible = {"E": E_cur.copy(), "v": 1.0, "kept": np.ones(ne, np.uint8)}
@@ -596,11 +623,12 @@ def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] =
     hist = []
     reason = "max_fea"
     while True:
-        g = {name: val[name] / (alpha * ref[name]) - 1.0 for name, alpha in cons}
+        g = {name: gval(name, alpha, val[name], ref[name]) for name, alpha in cons}
         for name, _ in cons:
             afd_al_update(al[name], g[name])
         violated = any(g[name] > 0.0 for name, _ in cons)
         rec = {"fea": fea, "v": v_design, "target": v_target, "dv": dv, "J": val["J"], "sigma": val["sigma"],
+               "lambda": val["lambda"],
                "g": dict(g), "violated": violated, "iters": st["iters"], "rel_residual": st["rel_residual"],
                "mu": {n: al[n].mu for n, _ in cons}, "gamma": {n: al[n].gamma for n, _ in cons}}
         hist.append(rec)
@@ -616,7 +644,7 @@ def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] =
             E_cur = feasible["E"].copy()
             mesh.set_element_moduli(E_cur)
             v_design, v_target = feasible["v"], feasible["v"] - dv
-            st, val = analyse(True)
+            st, val, flds = analyse(True)
             fea += 1
             J_prev = None
         else:
@@ -627,21 +655,12 @@ def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] =
                     break
                 v_target -= dv
             J_prev = val["J"]
-        fields, weights = [], []
-        if compliance is not None:
-            f = np.zeros((1, ne), np.float32)
-            mesh.sensitivity(AFD_SENS_STRAIN_ENERGY, f)
-            fields.append(f[0])
-            weights.append(afd_al_weight(al["J"]))
-        if stress is not None:
-            f = np.zeros((1, ne), np.float32)
-            mesh.stress_sensitivity(p, tol, f)
-            fields.append(f[0])
-            weights.append(afd_al_weight(al["sigma"]))
+        fields = [flds[name] for name, _ in cons]
+        weights = [afd_al_weight(al[name]) for name, _ in cons]
         afd_levelset_update_fields(mesh.h, np.stack(fields), weights, v_target, casting, kept)
         E_cur = np.where(kept != 0, 1.0, e_void)
         v_design = v_target
-        st, val = analyse(True)
+        st, val, flds = analyse(True)
         fea += 1
     return {"history": hist, "kept": feasible["kept"], "E": feasible["E"], "volume_fraction": feasible["v"],
             "stop": reason, "fea": fea, "reference": ref}

@@ -85,3 +85,35 @@ def test_modal_keeps_the_load_cases_and_reports_its_budget():
         m.modal(11)
     assert e.value.code == afd.AFD_ERR_INVALID_ARG
     m.close()
+
+
+def test_constrained_topology_driver_with_an_eigenvalue_constraint():
+    """Sec. 3.8 with J <= 2 J_0 and lambda_1 >= 0.8 lambda_1,0 (lumped-mass
+    fundamental eigenvalue): the final feasible design meets both under the
+    oracle (direct solve, Lanczos eigensolver), each record carries lambda_1
+    and the eigenvalue constraint's g = 1 - lambda_1 / (0.8 lambda_1,0)."""
+    from oracle import levelset
+    from synthetic import clamp_face_x0, edge_load
+
+    nx, ny, nz = 20, 8, 6
+    E0 = np.ones(nx * ny * nz)
+    f, fixed = edge_load(nx, ny, nz), clamp_face_x0(nx, ny, nz)
+    m = afd.Mesh(nx, ny, nz, group=2)
+    m.set_loads_bcs(f[None], fixed)
+    res = afd.run_constrained_topology(m, E0, compliance=2.0, eigen=0.8, dv0=0.05, v_min=0.5, max_fea=14,
+                                       tol=1e-8, eig_tol=1e-8)
+    m.close()
+    hist = res["history"]
+    lam0 = modal.modes(nx, ny, nz, E0, fixed, 1)[0][0]
+    assert abs(res["reference"]["lambda"] - lam0) <= 1e-8 * lam0
+    for h in hist:
+        assert h["lambda"] is not None and h["lambda"] > 0
+        assert abs(h["g"]["lambda"] - (1.0 - h["lambda"] / (0.8 * lam0))) <= 1e-8
+        assert h["violated"] == (h["g"]["J"] > 0 or h["g"]["lambda"] > 0)
+    E = res["E"]
+    K0 = fe.assemble(nx, ny, nz, E0)
+    J0 = fe.compliance(f, fe.solve_direct(K0, f, fixed))
+    assert fe.compliance(f, fe.solve_direct(fe.assemble(nx, ny, nz, E), f, fixed)) <= 2.0 * J0 * (1 + 1e-6)
+    assert modal.modes(nx, ny, nz, E, fixed, 1)[0][0] >= 0.8 * lam0 * (1 - 1e-6)
+    assert int(res["kept"].sum()) == levelset.keep_count(res["volume_fraction"], E.size)
+    assert res["volume_fraction"] < 1.0
