@@ -27,6 +27,7 @@ __all__ = [
     "element_count",
     "clamp_face_x0",
     "edge_load",
+    "axial_face_load",
     "sphere_voids",
     "void_fraction_spheres",
     "top_point_loads",
@@ -59,6 +60,14 @@ def edge_load(nx: int, ny: int, nz: int, total: float = -1.0) -> np.ndarray:
     the face x = nx (nodes i = nx, k = 0, j = 0..ny)."""
     f = np.zeros((nz + 1, ny + 1, nx + 1, 3), dtype=np.float64)
     f[0, :, nx, 2] = total / (ny + 1)
+    return f.reshape(-1)
+
+
+def axial_face_load(nx: int, ny: int, nz: int, total: float = -1.0) -> np.ndarray:
+    """Load ``total`` in x spread evenly over the nodes of the face x = nx (a
+    compressive end load for a column clamped at x = 0 when negative)."""
+    f = np.zeros((nz + 1, ny + 1, nx + 1, 3), dtype=np.float64)
+    f[:, :, nx, 0] = total / ((ny + 1) * (nz + 1))
     return f.reshape(-1)
 
 
