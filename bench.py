@@ -470,7 +470,9 @@ def next_rows_leg(afd, torch, dev, mesh, w, peak, peak_kind):
     sensitivity (Eq. 3.3: d sigma_PN/du, the adjoint solve to 1e-6, T_sigma) on
     the benchmark mesh, timed on the host clock; and the modal analysis of the
     benchmark mesh (its 4 lowest modes to a relative residual of 1e-6, lumped
-    mass) with the eigenvalue sensitivity of Eq. 3.4, timed on the host clock."""
+    mass) with the eigenvalue sensitivity of Eq. 3.4, and the linear buckling
+    of its solved state (2 load factors to 1e-6) with Eq. 3.5's field, both
+    timed on the host clock."""
     nx, ny, nz = 384, 192, 192
     keys = torch.rand(nx * ny * nz, dtype=torch.float32, device=dev)
     cast = {}
@@ -495,6 +497,14 @@ def next_rows_leg(afd, torch, dev, mesh, w, peak, peak_kind):
     st = mesh.stress_sensitivity(8.0, w.tol, out)
     torch.cuda.synchronize()
     adj_ms = (time.perf_counter() - t0) * 1e3
+    # linear buckling of the solved state (load case 0), 2 factors to 1e-6, with Eq. 3.5's field
+    bsens = torch.empty((2, w.nx * w.ny * w.nz), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    blam, binfo = mesh.buckling(2, tol=1e-6, max_iter=200)
+    mesh.buckling_sensitivity(bsens)
+    torch.cuda.synchronize()
+    buck_ms = (time.perf_counter() - t0) * 1e3
     n_modes = 4
     tsens = torch.empty((n_modes, w.nx * w.ny * w.nz), dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
@@ -509,7 +519,10 @@ def next_rows_leg(afd, torch, dev, mesh, w, peak, peak_kind):
                                              "adjoint_rel_residual": st[0]["rel_residual"]},
             "modal_128x64x64": {"n_modes": n_modes, "tol": 1e-6, "ms": round(modal_ms, 1),
                                 "subspace_steps": info["steps"], "inner_iters": info["solve_iters"],
-                                "lambda": [float(x) for x in lam]}}
+                                "lambda": [float(x) for x in lam]},
+            "buckling_128x64x64": {"n_modes": 2, "tol": 1e-6, "ms": round(buck_ms, 1),
+                                   "subspace_steps": binfo["steps"], "inner_iters": binfo["solve_iters"],
+                                   "load_factors": [float(x) for x in blam]}}
 
 
 def constrained_leg(afd, torch, dev, max_fea: int = 40):

@@ -175,6 +175,33 @@ int afd_modal(afd_mesh* m, int n_modes, double rho, double tol, int max_iter, do
  * out: n_modes*nelem floats, mode-major.  AFD_ERR_STATE without modes. */
 int afd_eigen_sensitivity(afd_mesh* m, float* out, int out_on_device);
 
+/* Linear buckling for the buckling constraint of Sec. 3.8 (Eq. 3.5 needs the
+ * modes): the n_modes smallest positive load factors lambda of
+ * (K + lambda K_G) phi = 0 on the free DOFs, lambda the factor on load case 0
+ * at which the structure buckles.  The pre-buckling state is the mesh's
+ * current static solution of load case 0 (afd_solve first): its stress at each
+ * element centroid, held constant over the element, gives the geometric
+ * stiffness K_G^e[(a,i),(b,j)] = delta_ij int grad N_a . S_e grad N_b (exact
+ * cube integrals).  Subspace iteration as in afd_modal on (-K_G) phi = mu K phi,
+ * lambda = 1/mu (largest mu first; Rayleigh-Ritz with Y^T K_G Y and Y^T K Y).
+ * Stops when every requested pair has ||K phi + lambda K_G phi|| <= tol ||K phi||,
+ * else after max_iter steps with AFD_ERR_NOT_CONVERGED (outputs written).
+ * AFD_ERR_NAN if the load gives fewer than n_modes positive factors.
+ * lam_out: n_modes doubles ascending; modes_out (nullable): n_modes*ndof,
+ * K-orthonormal, zero on fixed DOFs, sign arbitrary.  n_modes in [1, 10].
+ * The load cases are kept; the static solution is discarded.  The modes
+ * stay in the mesh for afd_buckling_sensitivity (a later afd_modal replaces
+ * them, and the other way round). */
+int afd_buckling(afd_mesh* m, int n_modes, double tol, int max_iter, double* lam_out, double* modes_out,
+                 int modes_on_device, int* iters_out, int* solve_iters_out);
+
+/* Sensitivity of the buckling load factors (Eq. 3.5) for the modes of the last
+ * afd_buckling, per element: phi_e^T (E_e K0 - lambda K_sigma^e) phi_e with
+ * the paper's K_sigma read as -K_G (its buckling equation (K - lambda
+ * K_sigma) phi = 0), so that the element terms of a mode sum to zero.
+ * out: n_modes*nelem floats, mode-major.  AFD_ERR_STATE without modes. */
+int afd_buckling_sensitivity(afd_mesh* m, float* out, int out_on_device);
+
 /* Level-set update (Eqs. 3.6, 3.17-3.18): for every load case r compute the
  * field of `kind`, divide it by its largest magnitude, add the fields with
  * weights[r] (float32, fixed order), keep the k = round(v * nelem) elements

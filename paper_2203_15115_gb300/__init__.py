@@ -46,7 +46,7 @@ EXPORTS = [
     "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
     "afd_server_submit_session", "afd_server_end_session", "afd_server_resident", "afd_levelset_update_cast",
     "afd_casting_scan", "afd_stress_sensitivity", "afd_levelset_update_fields", "afd_modal",
-    "afd_eigen_sensitivity",
+    "afd_eigen_sensitivity", "afd_buckling", "afd_buckling_sensitivity",
 ]
 
 
@@ -137,6 +137,8 @@ def lib() -> ctypes.CDLL:
             "afd_stress_sensitivity": (i, [vp, d, d, vp, i, ctypes.POINTER(afd_stats), vp, i]),
             "afd_modal": (i, [vp, i, d, d, i, ctypes.POINTER(d), vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
             "afd_eigen_sensitivity": (i, [vp, vp, i]),
+            "afd_buckling": (i, [vp, i, d, i, ctypes.POINTER(d), vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
+            "afd_buckling_sensitivity": (i, [vp, vp, i]),
             "afd_levelset_update_fields": (i, [vp, vp, i, i, ctypes.POINTER(d), d, i, i, ctypes.POINTER(d), vp]),
         }
         for name, (res, args) in sig.items():
@@ -303,6 +305,29 @@ def afd_eigen_sensitivity(mesh, out) -> None:
     (n_modes x nelem float32, numpy or torch)."""
     po, od, _k = _arr(out, np.float32)
     _check(lib().afd_eigen_sensitivity(mesh, po, od))
+
+
+def afd_buckling(mesh, n_modes: int, tol: float = 1e-6, max_iter: int = 100, modes_out=None, check: bool = True):
+    """The n_modes smallest positive buckling load factors of load case 0's
+    static state (afd_solve first).  Returns (lambda (n_modes,), info dict);
+    modes_out (n_modes x ndof float64) receives the K-orthonormal modes."""
+    lam = (ctypes.c_double * n_modes)()
+    steps, solves = ctypes.c_int(0), ctypes.c_int(0)
+    pm, md = (None, 0)
+    if modes_out is not None:
+        pm, md, _k = _arr(modes_out, np.float64)
+    rc = lib().afd_buckling(mesh, n_modes, tol, max_iter, lam, pm, md, ctypes.byref(steps), ctypes.byref(solves))
+    info = {"rc": rc, "steps": steps.value, "solve_iters": solves.value}
+    if check or rc not in (AFD_OK, AFD_ERR_NOT_CONVERGED):
+        _check(rc, info)
+    return np.array(lam[:], dtype=np.float64), info
+
+
+def afd_buckling_sensitivity(mesh, out) -> None:
+    """Eq. 3.5 for the modes of the last afd_buckling into out (n_modes x
+    nelem float32, numpy or torch)."""
+    po, od, _k = _arr(out, np.float32)
+    _check(lib().afd_buckling_sensitivity(mesh, po, od))
 
 
 def afd_levelset_update_fields(mesh, fields, weights, volume_fraction: float, casting=None, kept_out=None) -> float:
@@ -716,6 +741,12 @@ class Mesh:
 
     def eigen_sensitivity(self, out) -> None:
         afd_eigen_sensitivity(self.h, out)
+
+    def buckling(self, n_modes: int, tol: float = 1e-6, max_iter: int = 100, modes_out=None, check: bool = True):
+        return afd_buckling(self.h, n_modes, tol, max_iter, modes_out, check)
+
+    def buckling_sensitivity(self, out) -> None:
+        afd_buckling_sensitivity(self.h, out)
 
     def levelset_update(self, kind: int, weights, volume_fraction: float, kept_out=None, casting=None) -> float:
         return afd_levelset_update(self.h, kind, weights, volume_fraction, kept_out, casting)

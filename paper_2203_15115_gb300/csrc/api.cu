@@ -163,6 +163,9 @@ struct afd_mesh {
   int modal_cap = 0, modal_n = 0;
   double modal_rho = 1.0;
   bool modal_valid = false;
+  // buckling: K_G Y, K_G X, the state stress (6 x nelem), residual coefficients / load factors
+  double *bGY = nullptr, *bGX = nullptr, *bS6 = nullptr, *bcoef = nullptr;
+  bool buckling_valid = false;
   int nsplit_aw = 1;
   bool coarse_valid = false;
   Work<float> w32;
@@ -984,6 +987,7 @@ void afd_destroy(afd_mesh* m) {
   dfree(m->lam64); dfree(m->gadj); dfree(m->dsig); dfree(m->pn_d); dfree(m->lsbuf);
   dfree(m->mX); dfree(m->mKY); dfree(m->mKX); dfree(m->mmass); dfree(m->mparts);
   dfree(m->mA); dfree(m->mB); dfree(m->mV); dfree(m->mlam); dfree(m->minfo);
+  dfree(m->bGY); dfree(m->bGX); dfree(m->bS6); dfree(m->bcoef);
   if (m->ev) cudaEventDestroy(m->ev);
   if (m->s) cudaStreamDestroy(m->s);
   delete m;
@@ -1392,134 +1396,182 @@ static int modal_gram(afd_mesh* m, int kp, const double* Y, const double* Z, dou
   return AFD_OK;
 }
 
-int afd_modal(afd_mesh* m, int n_modes, double rho, double tol, int max_iter, double* lam_out, double* modes_out,
-              int modes_on_device, int* iters_out, int* solve_iters_out) {
-  if (!m || !lam_out) return fail(AFD_ERR_INVALID_ARG, "null argument");
-  const int guard = std::max(2, (n_modes + 1) / 2);
-  const int kp = n_modes + guard;
-  if (n_modes < 1 || kp > MODAL_MAX)
-    return fail(AFD_ERR_INVALID_ARG, "n_modes must be in [1, %d]", MODAL_MAX - 2 - (MODAL_MAX - 2) / 3);
-  if (!(rho > 0.0) || !std::isfinite(rho)) return fail(AFD_ERR_INVALID_ARG, "rho must be > 0");
-  if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 1) return fail(AFD_ERR_INVALID_ARG, "bad tol / max_iter");
-  if (!m->has_moduli || !m->has_loads) return fail(AFD_ERR_STATE, "set moduli and supports before afd_modal");
-  DeviceGuard dg(m->device);
-  TRY(enter(m));
+// The geometric element table c_geo[q][a][b] for the cube of edge h: the
+// integrals of d_k N_a d_l N_b, in closed form per axis (1D integrals of the
+// linear shape functions: int phi_p phi_q = 1/3 or 1/6, int phi_p' phi_q =
+// (2p - 1)/2, int phi_p' phi_q' = (2p - 1)(2q - 1)), summed over (k, l) and
+// (l, k) for the off-diagonal stress components q = xy, yz, zx.
+static int upload_geo_table(afd_mesh* m) {
+  const double h = m->opt.h;
+  static const int kk[6] = {0, 1, 2, 0, 1, 2}, ll[6] = {0, 1, 2, 1, 2, 0};
+  double t[6][8][8];
+  auto bit = [](int a, int d) { return (a >> d) & 1; };
+  auto m1 = [](int p, int q) { return p == q ? 1.0 / 3.0 : 1.0 / 6.0; };
+  auto H = [&](int k, int l, int a, int b) {
+    if (k == l) {
+      double v = h * (2 * bit(a, k) - 1) * (2 * bit(b, k) - 1);
+      for (int d = 0; d < 3; ++d)
+        if (d != k) v *= m1(bit(a, d), bit(b, d));
+      return v;
+    }
+    const int mm = 3 - k - l;
+    return h * 0.5 * (2 * bit(a, k) - 1) * 0.5 * (2 * bit(b, l) - 1) * m1(bit(a, mm), bit(b, mm));
+  };
+  for (int q = 0; q < 6; ++q)
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b)
+        t[q][a][b] = q < 3 ? H(kk[q], kk[q], a, b) : H(kk[q], ll[q], a, b) + H(ll[q], kk[q], a, b);
+  CK(cudaMemcpyToSymbolAsync(c_geo, t, sizeof(t), 0, cudaMemcpyHostToDevice, m->s));
+  return AFD_OK;
+}
+
+// The shared subspace iteration of afd_modal (kind 0: K phi = lambda M phi,
+// M the lumped mass in mmass) and afd_buckling (kind 1: (-K_G) phi = mu K phi,
+// K_G from the state stress in bS6, lambda = 1/mu).  Each step: the
+// right-hand sides B X into the solver's load buffer, Y = K^-1 B X by the
+// mesh's solver (started from X / lambda, resp. X mu), the Rayleigh-Ritz pairs
+// of span(Y) from FP64 Gram matrices (kind 0: Y^T K Y and Y^T M Y; kind 1:
+// Y^T K_G Y and Y^T K Y, whose ascending eigenvalues are -mu, the largest mu
+// first), the Ritz vectors and their residuals.  vals: the kp Ritz values
+// (kind 0: lambda; kind 1: -mu).  The caller keeps the load cases.
+static int subspace_eigs(afd_mesh* m, int kind, int n_modes, int kp, double tol, int max_iter,
+                         std::vector<double>& vals, bool& converged, int& steps, int& solve_iters) {
   const Grid& g = m->gr;
-  // the load cases are kept: saved here, restored at the end
+  const dim3 vgrid(grid_blocks(g.ndof, 256, 2048), kp);
+  const dim3 ngrid(grid_blocks(g.nnodes, 256, 2048), kp);
+  k_modal_start<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, 0x2203151150ull, m->mmass, m->mX); m->launches++;
+  CK(cudaGetLastError());
+  const double solve_tol = std::min(1e-6, std::max(1e-10, 0.1 * tol));
+  vals.assign(kp, 0.0);
+  std::vector<double> sc(kp, 0.0);
+  steps = solve_iters = 0;
+  converged = false;
+  TRY(ensure_partials(m, (size_t)kp * 2 * RED_BLOCKS));
+  for (int it = 0; it < max_iter && !converged; ++it) {
+    // right-hand sides B X in the solver's load buffer, their norms
+    if (kind == 0) {
+      k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->mX, m->f64); m->launches++;
+    } else {
+      k_geo_apply<<<ngrid, 256, 0, m->s>>>(g, m->bS6, m->fixed, -1.0, m->mX, m->f64); m->launches++;
+    }
+    TRY(ensure_partials(m, (size_t)kp * 2 * RED_BLOCKS));
+    k_dot<double, double><<<dim3(RED_BLOCKS, kp), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->f64, m->f64, m->partials);
+    m->launches++;
+    CK(cudaGetLastError());
+    std::vector<double> bb;
+    TRY(reduce_partials_host(m, kp, RED_BLOCKS, bb));
+    m->nrhs = kp;
+    m->fnorm.assign(kp, 0.0);
+    for (int r = 0; r < kp; ++r) m->fnorm[r] = std::sqrt(bb[r]);
+    // Y = K^-1 B X, started from X / lambda (kind 0) or X mu (kind 1) once Ritz values exist
+    int warm = 0;
+    if (it > 0) {
+      for (int r = 0; r < kp; ++r) sc[r] = kind == 0 ? (vals[r] > 0.0 ? 1.0 / vals[r] : 0.0) : -vals[r];
+      CK(cudaMemcpyAsync(m->mlam, sc.data(), kp * sizeof(double), cudaMemcpyHostToDevice, m->s));
+      k_scale_rhs<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mlam, m->mX, m->u64); m->launches++;
+      m->has_solution = true;
+      warm = 1;
+    }
+    std::vector<afd_stats> st(kp);
+    const int src = afd_solve(m, solve_tol, warm, st.data(), nullptr, 0);
+    if (src != AFD_OK && src != AFD_ERR_NOT_CONVERGED) return src;
+    int mx = 0;
+    for (int r = 0; r < kp; ++r) mx = std::max(mx, st[r].iters);
+    solve_iters += mx;
+    // Rayleigh-Ritz on span(Y) (K Y by the FP64 stencil)
+    TRY((launch_stencil<double, ST_APPLY, double>(m, m->u64, m->mKY, m->w64.E, nullptr, nullptr, nullptr, nullptr,
+                                                    kp, m->w64.K)));
+    if (kind == 0) {
+      TRY(modal_gram(m, kp, m->u64, m->mKY, m->mA));
+      k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->u64, m->mKX); m->launches++;
+      TRY(modal_gram(m, kp, m->u64, m->mKX, m->mB));
+    } else {
+      k_geo_apply<<<ngrid, 256, 0, m->s>>>(g, m->bS6, m->fixed, 1.0, m->u64, m->bGY); m->launches++;
+      TRY(modal_gram(m, kp, m->u64, m->bGY, m->mA));
+      TRY(modal_gram(m, kp, m->u64, m->mKY, m->mB));
+    }
+    k_small_geig<<<1, 32, 0, m->s>>>(kp, m->mA, m->mB, m->mlam, m->mV, m->minfo); m->launches++;
+    const unsigned cb = grid_blocks(g.ndof, 256, 2048);
+    k_ritz_combine<<<cb, 256, 0, m->s>>>(g.ndof, g.vs, kp, m->u64, m->mV, m->mX); m->launches++;
+    k_ritz_combine<<<cb, 256, 0, m->s>>>(g.ndof, g.vs, kp, m->mKY, m->mV, m->mKX); m->launches++;
+    if (kind == 0) {
+      k_modal_residual<<<dim3(RED_BLOCKS, n_modes), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->mKX, m->mX, m->mmass,
+                                                                          m->mlam, m->partials); m->launches++;
+    } else {
+      // K x + lambda K_G x = K x - (1/nu) K_G x with nu = -mu the Ritz value
+      k_ritz_combine<<<cb, 256, 0, m->s>>>(g.ndof, g.vs, kp, m->bGY, m->mV, m->bGX); m->launches++;
+      k_invert_vals<<<1, 32, 0, m->s>>>(kp, m->mlam, m->bcoef); m->launches++;
+      k_pair_residual<<<dim3(RED_BLOCKS, n_modes), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->mKX, m->bGX, m->mmass,
+                                                                         m->bcoef, m->partials); m->launches++;
+    }
+    CK(cudaGetLastError());
+    int info = 0;
+    CK(cudaMemcpyAsync(vals.data(), m->mlam, kp * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+    CK(cudaMemcpyAsync(&info, m->minfo, sizeof(int), cudaMemcpyDeviceToHost, m->s));
+    std::vector<double> hp((size_t)n_modes * RED_BLOCKS * 2);
+    CK(cudaMemcpyAsync(hp.data(), m->partials, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+    CK(cudaStreamSynchronize(m->s));
+    if (info != 0)
+      return fail(AFD_ERR_NAN, "Rayleigh-Ritz step failed (%s)",
+                  info == 1 ? "the Gram matrix is not positive definite" : "Jacobi sweeps did not converge");
+    steps = it + 1;
+    converged = true;
+    for (int r = 0; r < n_modes; ++r) {
+      double e2 = 0.0, k2 = 0.0;
+      for (int b = 0; b < RED_BLOCKS; ++b) {
+        e2 += hp[((size_t)r * RED_BLOCKS + b) * 2];
+        k2 += hp[((size_t)r * RED_BLOCKS + b) * 2 + 1];
+      }
+      if (!std::isfinite(e2) || !std::isfinite(vals[r])) return fail(AFD_ERR_NAN, "eigen iteration is not finite");
+      if (!(std::sqrt(e2) <= tol * std::sqrt(k2))) converged = false;
+    }
+  }
+  return AFD_OK;
+}
+
+// Buffers of the subspace iteration for a block of kp vectors (buckling adds
+// K_G Y, K_G X, the state stress and the residual coefficients).
+static int ensure_eig_buffers(afd_mesh* m, int kp, bool buckling) {
+  const Grid& g = m->gr;
+  if (m->modal_cap < kp) {
+    dfree(m->mX); dfree(m->mKY); dfree(m->mKX); dfree(m->mmass); dfree(m->mparts);
+    dfree(m->mA); dfree(m->mB); dfree(m->mV); dfree(m->mlam); dfree(m->minfo);
+    dfree(m->bGY); dfree(m->bGX);
+    m->modal_cap = 0;
+    TRY(dalloc(&m->mX, (size_t)kp * g.vs));
+    TRY(dalloc(&m->mKY, (size_t)kp * g.vs));
+    TRY(dalloc(&m->mKX, (size_t)kp * g.vs));
+    TRY(dalloc(&m->mmass, (size_t)g.vs));
+    TRY(dalloc(&m->mparts, (size_t)MODAL_GRAM_BLOCKS * MODAL_MAX * MODAL_MAX));
+    TRY(dalloc(&m->mA, (size_t)MODAL_MAX * MODAL_MAX));
+    TRY(dalloc(&m->mB, (size_t)MODAL_MAX * MODAL_MAX));
+    TRY(dalloc(&m->mV, (size_t)MODAL_MAX * MODAL_MAX));
+    TRY(dalloc(&m->mlam, (size_t)MODAL_MAX));
+    TRY(dalloc(&m->minfo, 1));
+    m->modal_cap = kp;
+  }
+  if (buckling) {
+    if (!m->bGY) {
+      TRY(dalloc(&m->bGY, (size_t)m->modal_cap * g.vs));
+      TRY(dalloc(&m->bGX, (size_t)m->modal_cap * g.vs));
+    }
+    if (!m->bS6) TRY(dalloc(&m->bS6, (size_t)6 * g.nelem));
+    if (!m->bcoef) TRY(dalloc(&m->bcoef, (size_t)MODAL_MAX));
+  }
+  return AFD_OK;
+}
+
+// Saves the load cases, runs `body`, restores them; the static solution is discarded.
+template <typename F>
+static int with_saved_loads(afd_mesh* m, F&& body) {
+  const Grid& g = m->gr;
   const int R0 = m->nrhs;
   const std::vector<double> fnorm0 = m->fnorm;
   double* fsave = nullptr;
   TRY(dalloc(&fsave, (size_t)R0 * g.vs));
   CK(cudaMemcpyAsync(fsave, m->f64, (size_t)R0 * g.vs * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
-  int rc = AFD_OK;
-  std::string err;
-  auto run = [&]() -> int {
-    TRY(ensure_rhs(m, kp));
-    if (m->modal_cap < kp) {
-      dfree(m->mX); dfree(m->mKY); dfree(m->mKX); dfree(m->mmass); dfree(m->mparts);
-      dfree(m->mA); dfree(m->mB); dfree(m->mV); dfree(m->mlam); dfree(m->minfo);
-      m->modal_cap = 0;
-      TRY(dalloc(&m->mX, (size_t)kp * g.vs));
-      TRY(dalloc(&m->mKY, (size_t)kp * g.vs));
-      TRY(dalloc(&m->mKX, (size_t)kp * g.vs));
-      TRY(dalloc(&m->mmass, (size_t)g.vs));
-      TRY(dalloc(&m->mparts, (size_t)MODAL_GRAM_BLOCKS * MODAL_MAX * MODAL_MAX));
-      TRY(dalloc(&m->mA, (size_t)MODAL_MAX * MODAL_MAX));
-      TRY(dalloc(&m->mB, (size_t)MODAL_MAX * MODAL_MAX));
-      TRY(dalloc(&m->mV, (size_t)MODAL_MAX * MODAL_MAX));
-      TRY(dalloc(&m->mlam, (size_t)MODAL_MAX));
-      TRY(dalloc(&m->minfo, 1));
-      m->modal_cap = kp;
-    }
-    m->modal_valid = false;
-    const double h = m->opt.h;
-    CK(cudaMemsetAsync(m->mmass, 0, (size_t)g.vs * sizeof(double), m->s));
-    CK(cudaMemsetAsync(m->mX, 0, (size_t)kp * g.vs * sizeof(double), m->s));
-    k_lumped_mass<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->E64, rho * h * h * h / 8.0, m->fixed,
-                                                                      m->mmass); m->launches++;
-    const dim3 vgrid(grid_blocks(g.ndof, 256, 2048), kp);
-    k_modal_start<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, 0x2203151150ull, m->mmass, m->mX); m->launches++;
-    CK(cudaGetLastError());
-    const double solve_tol = std::min(1e-6, std::max(1e-10, 0.1 * tol));
-    std::vector<double> lam(kp, 0.0), inv(kp, 0.0);
-    int steps = 0, solve_iters = 0;
-    bool converged = false;
-    TRY(ensure_partials(m, (size_t)kp * 2 * RED_BLOCKS));
-    for (int it = 0; it < max_iter && !converged; ++it) {
-      // right-hand sides M X in the solver's load buffer, their norms
-      k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->mX, m->f64); m->launches++;
-      k_dot<double, double><<<dim3(RED_BLOCKS, kp), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->f64, m->f64, m->partials);
-      m->launches++;
-      CK(cudaGetLastError());
-      std::vector<double> bb;
-      TRY(reduce_partials_host(m, kp, RED_BLOCKS, bb));
-      m->nrhs = kp;
-      m->fnorm.assign(kp, 0.0);
-      for (int r = 0; r < kp; ++r) m->fnorm[r] = std::sqrt(bb[r]);
-      // Y = K^-1 M X, started from X / lambda once Ritz values exist
-      int warm = 0;
-      if (it > 0) {
-        for (int r = 0; r < kp; ++r) inv[r] = lam[r] > 0.0 ? 1.0 / lam[r] : 0.0;
-        CK(cudaMemcpyAsync(m->mlam, inv.data(), kp * sizeof(double), cudaMemcpyHostToDevice, m->s));
-        k_scale_rhs<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mlam, m->mX, m->u64); m->launches++;
-        m->has_solution = true;
-        warm = 1;
-      }
-      std::vector<afd_stats> st(kp);
-      const int src = afd_solve(m, solve_tol, warm, st.data(), nullptr, 0);
-      if (src != AFD_OK && src != AFD_ERR_NOT_CONVERGED) return src;
-      int mx = 0;
-      for (int r = 0; r < kp; ++r) mx = std::max(mx, st[r].iters);
-      solve_iters += mx;
-      // Rayleigh-Ritz on span(Y): A = Y^T K Y (FP64 apply), B = Y^T M Y
-      TRY((launch_stencil<double, ST_APPLY, double>(m, m->u64, m->mKY, m->w64.E, nullptr, nullptr, nullptr, nullptr,
-                                                      kp, m->w64.K)));
-      TRY(modal_gram(m, kp, m->u64, m->mKY, m->mA));
-      k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->u64, m->mKX); m->launches++;
-      TRY(modal_gram(m, kp, m->u64, m->mKX, m->mB));
-      k_small_geig<<<1, 32, 0, m->s>>>(kp, m->mA, m->mB, m->mlam, m->mV, m->minfo); m->launches++;
-      k_ritz_combine<<<grid_blocks(g.ndof, 256, 2048), 256, 0, m->s>>>(g.ndof, g.vs, kp, m->u64, m->mV, m->mX);
-      m->launches++;
-      k_ritz_combine<<<grid_blocks(g.ndof, 256, 2048), 256, 0, m->s>>>(g.ndof, g.vs, kp, m->mKY, m->mV, m->mKX);
-      m->launches++;
-      k_modal_residual<<<dim3(RED_BLOCKS, n_modes), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->mKX, m->mX, m->mmass,
-                                                                          m->mlam, m->partials); m->launches++;
-      CK(cudaGetLastError());
-      int info = 0;
-      CK(cudaMemcpyAsync(lam.data(), m->mlam, kp * sizeof(double), cudaMemcpyDeviceToHost, m->s));
-      CK(cudaMemcpyAsync(&info, m->minfo, sizeof(int), cudaMemcpyDeviceToHost, m->s));
-      std::vector<double> hp((size_t)n_modes * RED_BLOCKS * 2);
-      CK(cudaMemcpyAsync(hp.data(), m->partials, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, m->s));
-      CK(cudaStreamSynchronize(m->s));
-      if (info != 0) return fail(AFD_ERR_NAN, "Rayleigh-Ritz step failed (%s)", info == 1 ? "Y^T M Y not positive definite"
-                                                                                        : "Jacobi sweeps did not converge");
-      steps = it + 1;
-      converged = true;
-      for (int r = 0; r < n_modes; ++r) {
-        double e2 = 0.0, k2 = 0.0;
-        for (int b = 0; b < RED_BLOCKS; ++b) {
-          e2 += hp[((size_t)r * RED_BLOCKS + b) * 2];
-          k2 += hp[((size_t)r * RED_BLOCKS + b) * 2 + 1];
-        }
-        if (!std::isfinite(e2) || !std::isfinite(lam[r])) return fail(AFD_ERR_NAN, "modal iteration is not finite");
-        if (!(std::sqrt(e2) <= tol * std::sqrt(k2))) converged = false;
-      }
-    }
-    for (int r = 0; r < n_modes; ++r) lam_out[r] = lam[r];
-    if (modes_out)
-      CK(cudaMemcpy2DAsync(modes_out, (size_t)g.ndof * sizeof(double), m->mX, (size_t)g.vs * sizeof(double),
-                           (size_t)g.ndof * sizeof(double), n_modes,
-                           modes_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->s));
-    if (iters_out) *iters_out = steps;
-    if (solve_iters_out) *solve_iters_out = solve_iters;
-    m->modal_n = n_modes;
-    m->modal_rho = rho;
-    m->modal_valid = true;
-    return converged ? AFD_OK : AFD_ERR_NOT_CONVERGED;
-  };
-  rc = run();
-  if (rc != AFD_OK) err = g_err;
-  // restore the load cases; the static solution is gone
+  const int rc = body();
+  const std::string err = g_err;
   if (m->f64 && m->cap >= R0)
     CK(cudaMemcpyAsync(m->f64, fsave, (size_t)R0 * g.vs * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
   CK(cudaStreamSynchronize(m->s));
@@ -1529,9 +1581,131 @@ int afd_modal(afd_mesh* m, int n_modes, double rho, double tol, int max_iter, do
   m->has_solution = false;
   invalidate_graphs(m);
   TRY(finish(m));
-  if (rc == AFD_ERR_NOT_CONVERGED) return fail(rc, "modal iteration did not reach tol %.3g in %d steps", tol, max_iter);
-  if (rc != AFD_OK) return fail(rc, "%s", err.c_str());
+  if (rc != AFD_OK) g_err = err;
+  return rc;
+}
+
+static int eig_block(int n_modes, int& kp) {
+  kp = n_modes + std::max(2, (n_modes + 1) / 2);
+  if (n_modes < 1 || kp > MODAL_MAX)
+    return fail(AFD_ERR_INVALID_ARG, "n_modes must be in [1, %d]", MODAL_MAX - 2 - (MODAL_MAX - 2) / 3);
   return AFD_OK;
+}
+
+int afd_modal(afd_mesh* m, int n_modes, double rho, double tol, int max_iter, double* lam_out, double* modes_out,
+              int modes_on_device, int* iters_out, int* solve_iters_out) {
+  if (!m || !lam_out) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  int kp = 0;
+  TRY(eig_block(n_modes, kp));
+  if (!(rho > 0.0) || !std::isfinite(rho)) return fail(AFD_ERR_INVALID_ARG, "rho must be > 0");
+  if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 1) return fail(AFD_ERR_INVALID_ARG, "bad tol / max_iter");
+  if (!m->has_moduli || !m->has_loads) return fail(AFD_ERR_STATE, "set moduli and supports before afd_modal");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const Grid& g = m->gr;
+  bool converged = false;
+  const int rc = with_saved_loads(m, [&]() -> int {
+    TRY(ensure_rhs(m, kp));
+    TRY(ensure_eig_buffers(m, kp, false));
+    m->modal_valid = false;
+    m->buckling_valid = false;
+    const double h = m->opt.h;
+    CK(cudaMemsetAsync(m->mmass, 0, (size_t)g.vs * sizeof(double), m->s));
+    CK(cudaMemsetAsync(m->mX, 0, (size_t)kp * g.vs * sizeof(double), m->s));
+    k_lumped_mass<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->E64, rho * h * h * h / 8.0, m->fixed,
+                                                                      m->mmass); m->launches++;
+    std::vector<double> vals;
+    int steps = 0, solve_iters = 0;
+    TRY(subspace_eigs(m, 0, n_modes, kp, tol, max_iter, vals, converged, steps, solve_iters));
+    for (int r = 0; r < n_modes; ++r) lam_out[r] = vals[r];
+    if (modes_out)
+      CK(cudaMemcpy2DAsync(modes_out, (size_t)g.ndof * sizeof(double), m->mX, (size_t)g.vs * sizeof(double),
+                           (size_t)g.ndof * sizeof(double), n_modes,
+                           modes_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->s));
+    if (iters_out) *iters_out = steps;
+    if (solve_iters_out) *solve_iters_out = solve_iters;
+    m->modal_n = n_modes;
+    m->modal_rho = rho;
+    m->modal_valid = true;
+    return AFD_OK;
+  });
+  if (rc != AFD_OK) return fail(rc, "%s", g_err.c_str());
+  if (!converged) return fail(AFD_ERR_NOT_CONVERGED, "modal iteration did not reach tol %.3g in %d steps", tol, max_iter);
+  return AFD_OK;
+}
+
+int afd_buckling(afd_mesh* m, int n_modes, double tol, int max_iter, double* lam_out, double* modes_out,
+                 int modes_on_device, int* iters_out, int* solve_iters_out) {
+  if (!m || !lam_out) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  int kp = 0;
+  TRY(eig_block(n_modes, kp));
+  if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 1) return fail(AFD_ERR_INVALID_ARG, "bad tol / max_iter");
+  if (!m->has_solution) return fail(AFD_ERR_STATE, "no static solution: afd_solve first (load case 0 is the state)");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const Grid& g = m->gr;
+  bool converged = false;
+  // the state stress of load case 0 before anything overwrites the solution
+  TRY(ensure_eig_buffers(m, kp, true));
+  FieldConsts F;
+  const double nu = m->opt.nu;
+  F.lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  F.mu = 1.0 / (2.0 * (1.0 + nu));
+  F.nu = nu;
+  F.inv4h = 1.0 / (4.0 * m->opt.h);
+  k_state_stress<<<grid_blocks(g.nelem, 256, 8 * RED_BLOCKS), 256, 0, m->s>>>(g, m->u64, m->E64, F, m->bS6);
+  m->launches++;
+  TRY(upload_geo_table(m));
+  const int rc = with_saved_loads(m, [&]() -> int {
+    TRY(ensure_rhs(m, kp));
+    TRY(ensure_eig_buffers(m, kp, true));
+    m->modal_valid = false;
+    m->buckling_valid = false;
+    // the free-DOF mask of the residual (any positive value on free DOFs)
+    CK(cudaMemsetAsync(m->mmass, 0, (size_t)g.vs * sizeof(double), m->s));
+    CK(cudaMemsetAsync(m->mX, 0, (size_t)kp * g.vs * sizeof(double), m->s));
+    k_lumped_mass<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->E64, 1.0, m->fixed, m->mmass);
+    m->launches++;
+    std::vector<double> vals;
+    int steps = 0, solve_iters = 0;
+    TRY(subspace_eigs(m, 1, n_modes, kp, tol, max_iter, vals, converged, steps, solve_iters));
+    for (int r = 0; r < n_modes; ++r)
+      if (!(vals[r] < 0.0)) return fail(AFD_ERR_NAN, "fewer than %d positive buckling factors for this load", n_modes);
+    std::vector<double> lam(n_modes);
+    for (int r = 0; r < n_modes; ++r) lam[r] = lam_out[r] = -1.0 / vals[r];
+    CK(cudaMemcpyAsync(m->bcoef, lam.data(), n_modes * sizeof(double), cudaMemcpyHostToDevice, m->s));
+    if (modes_out)
+      CK(cudaMemcpy2DAsync(modes_out, (size_t)g.ndof * sizeof(double), m->mX, (size_t)g.vs * sizeof(double),
+                           (size_t)g.ndof * sizeof(double), n_modes,
+                           modes_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->s));
+    if (iters_out) *iters_out = steps;
+    if (solve_iters_out) *solve_iters_out = solve_iters;
+    m->modal_n = n_modes;
+    m->buckling_valid = true;
+    return AFD_OK;
+  });
+  if (rc != AFD_OK) return fail(rc, "%s", g_err.c_str());
+  if (!converged)
+    return fail(AFD_ERR_NOT_CONVERGED, "buckling iteration did not reach tol %.3g in %d steps", tol, max_iter);
+  return AFD_OK;
+}
+
+int afd_buckling_sensitivity(afd_mesh* m, float* out, int out_on_device) {
+  if (!m || !out) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (!m->buckling_valid) return fail(AFD_ERR_STATE, "no buckling modes: call afd_buckling first");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const Grid& g = m->gr;
+  const int n = m->modal_n;
+  TRY(upload_geo_table(m));
+  float* dst = out_on_device ? out : m->fbuf;
+  k_buckling_topo<<<dim3(grid_blocks(g.nelem, 256, 8 * RED_BLOCKS), n), 256, 0, m->s>>>(g, m->mX, m->bcoef, m->E64,
+                                                                                        m->bS6, m->w64.K, dst);
+  m->launches++;
+  CK(cudaGetLastError());
+  if (!out_on_device)
+    CK(cudaMemcpyAsync(out, m->fbuf, (size_t)n * g.nelem * sizeof(float), cudaMemcpyDeviceToHost, m->s));
+  return finish(m);
 }
 
 int afd_eigen_sensitivity(afd_mesh* m, float* out, int out_on_device) {

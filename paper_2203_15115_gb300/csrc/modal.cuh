@@ -279,4 +279,143 @@ k_eigen_topo(Grid gr, const double* __restrict__ phi, const double* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Linear buckling (Eq. 3.5): the geometric stiffness K_G of the pre-buckling
+// stress, (K + lambda K_G) phi = 0, and the element sensitivity.
+// ---------------------------------------------------------------------------
+
+// Stress of the pre-buckling state u0 at each element centroid (xx, yy, zz,
+// xy, yz, zx), held constant over the element.
+__global__ void __launch_bounds__(256)
+k_state_stress(Grid gr, const double* __restrict__ u0, const double* __restrict__ Emod, FieldConsts F,
+               double* __restrict__ S6) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < gr.nelem; e += gridDim.x * blockDim.x) {
+    const int i = e % gr.nx, j = (e / gr.nx) % gr.ny, k = e / (gr.nx * gr.ny);
+    double eps[6];
+    centroid_strain64(gr, u0, i, j, k, F.inv4h, eps);
+    const double E = Emod[e];
+    const double tre = eps[0] + eps[1] + eps[2];
+    const double la = F.lam * E, mu2 = 2.0 * F.mu * E;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) S6[(size_t)q * gr.nelem + e] = la * tre + mu2 * eps[q];
+#pragma unroll
+    for (int q = 3; q < 6; ++q) S6[(size_t)q * gr.nelem + e] = mu2 * eps[q];
+  }
+}
+
+// Element geometric matrix G_e[a][b] = sum_q S_e[q] GEO[q][a][b]: GEO[q] the
+// integrals of grad N_a (.) grad N_b over the cube for the stress components
+// q = xx, yy, zz, xy, yz, zx (off-diagonal pairs summed), set by the host.
+__constant__ double c_geo[6][8][8];
+
+// Y[r] = sign * K_G X[r], gathered per node over its (up to) eight elements;
+// zero on fixed DOFs.  One RHS per blockIdx.y.
+__global__ void __launch_bounds__(256)
+k_geo_apply(Grid gr, const double* __restrict__ S6, const uint8_t* __restrict__ fixed, double sign,
+            const double* __restrict__ X, double* __restrict__ Y) {
+  const int r = blockIdx.y;
+  const size_t off = (size_t)r * gr.vs;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < gr.nnodes; n += gridDim.x * blockDim.x) {
+    const int i = n % gr.nnx, j = (n / gr.nnx) % gr.nny, k = n / (gr.nnx * gr.nny);
+    double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int ei = i - 1 + (o & 1), ej = j - 1 + ((o >> 1) & 1), ek = k - 1 + ((o >> 2) & 1);
+      if (ei < 0 || ei >= gr.nx || ej < 0 || ej >= gr.ny || ek < 0 || ek >= gr.nz) continue;
+      const int e = ei + gr.nx * (ej + gr.ny * ek);
+      const int a = 7 - o;   // this node's local index in element e
+      double s[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) s[q] = S6[(size_t)q * gr.nelem + e];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        double g = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) g = fma(s[q], c_geo[q][a][b], g);
+        const int m = (ei + (b & 1)) + gr.nnx * ((ej + ((b >> 1) & 1)) + gr.nny * (ek + ((b >> 2) & 1)));
+        const double* xm = X + off + 3 * (size_t)m;
+        acc[0] = fma(g, xm[0], acc[0]);
+        acc[1] = fma(g, xm[1], acc[1]);
+        acc[2] = fma(g, xm[2], acc[2]);
+      }
+    }
+    const uint8_t fb = fixed ? fixed[n] : 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Y[off + 3 * (size_t)n + c] = ((fb >> c) & 1) ? 0.0 : sign * acc[c];
+  }
+}
+
+// Residual partials of the first n pairs with a general second operator:
+// parts[(r * gridDim.x + b) * 2] = sum (A x_r - c_r B x_r)^2 over DOFs with
+// mass/mask > 0, [.. + 1] = sum (A x_r)^2.
+__global__ void __launch_bounds__(RED_THREADS)
+k_pair_residual(int ndof, int vs, const double* __restrict__ AX, const double* __restrict__ BX,
+                const double* __restrict__ mask, const double* __restrict__ coef, double* __restrict__ parts) {
+  __shared__ double red[32 * 2];
+  const int r = blockIdx.y;
+  const size_t off = (size_t)r * vs;
+  const double c = coef[r];
+  double s[2] = {0.0, 0.0};
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
+    if (!(mask[d] > 0.0)) continue;
+    const double ax = AX[off + d];
+    const double e = ax - c * BX[off + d];
+    s[0] = fma(e, e, s[0]);
+    s[1] = fma(ax, ax, s[1]);
+  }
+  double o[2];
+  block_sum_to_f64<2>(s, red, o);
+  if (threadIdx.x == 0) {
+    parts[((size_t)r * gridDim.x + blockIdx.x) * 2] = o[0];
+    parts[((size_t)r * gridDim.x + blockIdx.x) * 2 + 1] = o[1];
+  }
+}
+
+// coef[r] = 1 / vals[r]: with the Ritz values nu = -mu of the buckling
+// pencil, K x + lambda K_G x = K x - coef K_G x (lambda = 1/mu).
+__global__ void k_invert_vals(int kp, const double* __restrict__ vals, double* __restrict__ coef) {
+  const int r = threadIdx.x;
+  if (r < kp) coef[r] = 1.0 / vals[r];
+}
+
+// Eq. 3.5 per element for mode r (phi[r], lam[r]), with the paper's K_sigma
+// read as -K_G: phi_e^T E_e K0 phi_e + lam phi_e^T (G_e kron I3) phi_e.
+__global__ void __launch_bounds__(256)
+k_buckling_topo(Grid gr, const double* __restrict__ phi, const double* __restrict__ lam,
+                const double* __restrict__ Emod, const double* __restrict__ S6, ElemConsts<double> K,
+                float* __restrict__ out) {
+  const int r = blockIdx.y;
+  const double* pr = phi + (size_t)r * gr.vs;
+  const double lr = lam[r];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < gr.nelem; e += gridDim.x * blockDim.x) {
+    const int i = e % gr.nx, j = (e / gr.nx) % gr.ny, k = e / (gr.nx * gr.ny);
+    double v[3][8], w[3][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int n = (i + (a & 1)) + gr.nnx * ((j + ((a >> 1) & 1)) + gr.nny * (k + ((a >> 2) & 1)));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[c][a] = w[c][a] = pr[3 * (size_t)n + c];
+    }
+    const double E = Emod[e];
+    hex8_apply(w, E, K);   // w = E K0 phi_e
+    double s[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) s[q] = S6[(size_t)q * gr.nelem + e];
+    double se = 0.0, geo = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) se = fma(v[c][a], w[c][a], se);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        double g = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) g = fma(s[q], c_geo[q][a][b], g);
+        geo = fma(g, v[0][a] * v[0][b] + v[1][a] * v[1][b] + v[2][a] * v[2][b], geo);
+      }
+    }
+    out[(size_t)r * gr.nelem + e] = (float)(se + lr * geo);
+  }
+}
+
 }  // namespace afd

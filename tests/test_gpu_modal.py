@@ -117,3 +117,53 @@ def test_constrained_topology_driver_with_an_eigenvalue_constraint():
     assert modal.modes(nx, ny, nz, E, fixed, 1)[0][0] >= 0.8 * lam0 * (1 - 1e-6)
     assert int(res["kept"].sum()) == levelset.keep_count(res["volume_fraction"], E.size)
     assert res["volume_fraction"] < 1.0
+
+
+def _column():
+    from synthetic import axial_face_load, clamp_face_x0
+
+    nx, ny, nz = 16, 4, 3
+    E = np.ones(nx * ny * nz)
+    E[::7] = 0.5
+    return nx, ny, nz, E, axial_face_load(nx, ny, nz, -1.0), clamp_face_x0(nx, ny, nz)
+
+
+@pytest.mark.parametrize("precision", [afd.AFD_FP64, afd.AFD_MIXED])
+def test_buckling_matches_oracle(precision):
+    from oracle import buckling
+
+    nx, ny, nz, E, f, fixed = _column()
+    n, tol = 3, 1e-8
+    lam_o, phi_o, S = buckling.buckling(nx, ny, nz, E, f, fixed, n)
+    m = afd.Mesh(nx, ny, nz, precision=precision, group=2)
+    m.set_element_moduli(E)
+    m.set_loads_bcs(f[None], fixed)
+    with pytest.raises(afd.AFDError) as e:
+        m.buckling(n)                                    # no static state yet
+    assert e.value.code == afd.AFD_ERR_STATE
+    m.solve(1e-11)
+    phi = np.zeros((n, m.ndof))
+    lam, info = m.buckling(n, tol=tol, modes_out=phi)
+    assert info["steps"] >= 1
+    assert np.allclose(lam, lam_o, rtol=1e-8)
+    K = fe.assemble(nx, ny, nz, E)
+    Kg = buckling.assemble_geometric(nx, ny, nz, S)
+    assert np.allclose(phi @ (K @ phi.T), np.eye(n), atol=1e-9)     # K-orthonormal
+    assert np.all(phi[:, fixed == 1] == 0.0)
+    fr = fe.free_dofs(fixed)
+    for i in range(n):
+        assert abs(abs(phi[i] @ (K @ phi_o[i])) - 1.0) < 1e-7
+        r = ((K + lam[i] * Kg) @ phi[i])[fr]
+        assert np.linalg.norm(r) <= 10 * tol * np.linalg.norm((K @ phi[i])[fr])
+    T = np.zeros((n, m.nelem), np.float32)
+    m.buckling_sensitivity(T)
+    for i in range(n):
+        ref = buckling.buckling_sensitivity(nx, ny, nz, E, S, phi[i], lam[i])
+        assert np.linalg.norm(T[i] - ref) <= 1e-6 * np.linalg.norm(ref)
+        assert abs(float(T[i].astype(np.float64).sum())) <= 1e-5 * float(np.abs(T[i]).sum())
+    # the modes of a modal analysis replace the buckling modes
+    m.modal(1)
+    with pytest.raises(afd.AFDError) as e:
+        m.buckling_sensitivity(T)
+    assert e.value.code == afd.AFD_ERR_STATE
+    m.close()
