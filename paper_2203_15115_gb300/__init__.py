@@ -579,24 +579,30 @@ def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] =
                              p: float = 8.0, dv0: float = 0.05, dv_min: Optional[float] = None, v_min: float = 0.05,
                              max_fea: int = 200, conv: float = 0.01, tol: float = 1e-6, casting=None,
                              on_step=None, eigen: Optional[float] = None, rho: float = 1.0,
-                             eig_tol: float = 1e-6) -> dict:
-    """The algorithm of Sec. 3.8 for min |Omega| with hard constraints
-    J <= compliance * J_0, sigma_PN <= stress * sigma_0 and lambda_1 >=
-    eigen * lambda_1,0 (the fundamental eigenvalue of the lumped-mass modal
-    problem, afd_modal; any of the three may be None), over the library's
-    calls (each step runs in its kernels):
+                             eig_tol: float = 1e-6, buckling: Optional[float] = None, soft=()) -> dict:
+    """The algorithm of Sec. 3.8 (with Eq. 3.21's four constraints) for
+    min |Omega| subject to J <= compliance * J_0, sigma_PN <= stress * sigma_0,
+    lambda_1 >= eigen * lambda_1,0 (the fundamental eigenvalue of the
+    lumped-mass modal problem, afd_modal) and P >= buckling * P_0 (the
+    smallest positive buckling load factor of load case 0, afd_buckling); any
+    may be None.  Constraints named in `soft` ("lambda", "P"; Sec. 3.6) steer
+    the level set through their AL weights but never count as violated.  Over
+    the library's calls (each step runs in its kernels):
       2. analysis: solve (warm start), J, sigma_PN (p-norm of Eq. 3.3), their
-         fields (strain energy, adjoint T_sigma), and with `eigen` the modal
-         analysis (1 mode to eig_tol, density rho) and T_lambda (Eq. 3.4);
+         fields (strain energy, adjoint T_sigma); with `buckling` the buckling
+         analysis of that state (1 factor to eig_tol) and Eq. 3.5's field; with
+         `eigen` the modal analysis (1 mode to eig_tol, density rho) and
+         T_lambda (Eq. 3.4);
       3. g_i = value / (alpha_i value_0) - 1 for the upper bounds (J, sigma),
-         g = 1 - lambda_1 / (alpha lambda_1,0) for the eigenvalue's lower bound,
-         and the AL update (Eqs. 3.11-3.12);
+         g = 1 - value / (alpha value_0) for the lower bounds (lambda, P), and
+         the AL update (Eqs. 3.11-3.12);
       4./9. a violated hard constraint returns to the last feasible design with
          the volume step halved (stop when it falls below dv_min, default 0.1 dv0);
+         soft constraints are not checked;
       5./6. the augmented level set (Eq. 3.17): strain-energy field weighted by
          the compliance constraint's (mu + gamma g)+, the adjoint stress field
-         T_sigma by the stress constraint's, T_lambda by the eigenvalue
-         constraint's, optional casting, cut at the target volume;
+         T_sigma by the stress constraint's, T_lambda and T_P by the eigenvalue
+         and buckling constraints', optional casting, cut at the target volume;
       7./8. when J changed by less than `conv` since the previous analysis at
          the same target, the target drops by the volume step (stop below
          v_min).
@@ -605,7 +611,11 @@ def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] =
     volume fraction, and why it stopped."""
     ne = mesh.nelem
     dv_min = 0.1 * dv0 if dv_min is None else dv_min
-    cons = [c for c in (("J", compliance), ("sigma", stress), ("lambda", eigen)) if c[1] is not None]
+    cons = [c for c in (("J", compliance), ("sigma", stress), ("lambda", eigen), ("P", buckling)) if c[1] is not None]
+    soft = set(soft)
+    if not soft <= {"lambda", "P"}:
+        raise ValueError("only the eigenvalue and buckling constraints can be soft")
+    hard = [name for name, _ in cons if name not in soft]
     al = {name: afd_al_init() for name, _ in cons}
     E_cur = np.asarray(E_init, dtype=np.float64).copy()
     mesh.set_element_moduli(E_cur)
@@ -625,6 +635,13 @@ def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] =
             f = np.zeros((1, ne), np.float32)
             mesh.stress_sensitivity(p, tol, f)
             flds["sigma"] = f[0]
+        P1 = None
+        if buckling is not None:   # the state is the solution just computed
+            lamb, _ = mesh.buckling(1, tol=eig_tol)
+            P1 = float(lamb[0])
+            f = np.zeros((1, ne), np.float32)
+            mesh.buckling_sensitivity(f)
+            flds["P"] = f[0]
         lam1 = None
         if eigen is not None:
             lam, _ = mesh.modal(1, rho=rho, tol=eig_tol)
@@ -632,10 +649,10 @@ def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] =
             f = np.zeros((1, ne), np.float32)
             mesh.eigen_sensitivity(f)
             flds["lambda"] = f[0]
-        return st[0], {"J": J, "sigma": sig, "lambda": lam1}, flds
+        return st[0], {"J": J, "sigma": sig, "lambda": lam1, "P": P1}, flds
 
     def gval(name, alpha, v, r):
-        return 1.0 - v / (alpha * r) if name == "lambda" else v / (alpha * r) - 1.0
+        return 1.0 - v / (alpha * r) if name in ("lambda", "P") else v / (alpha * r) - 1.0
 
     st, val, flds = analyse(False)
     fea = 1
@@ -651,9 +668,9 @@ def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] =
         g = {name: gval(name, alpha, val[name], ref[name]) for name, alpha in cons}
         for name, _ in cons:
             afd_al_update(al[name], g[name])
-        violated = any(g[name] > 0.0 for name, _ in cons)
+        violated = any(g[name] > 0.0 for name in hard)
         rec = {"fea": fea, "v": v_design, "target": v_target, "dv": dv, "J": val["J"], "sigma": val["sigma"],
-               "lambda": val["lambda"],
+               "lambda": val["lambda"], "P": val["P"],
                "g": dict(g), "violated": violated, "iters": st["iters"], "rel_residual": st["rel_residual"],
                "mu": {n: al[n].mu for n, _ in cons}, "gamma": {n: al[n].gamma for n, _ in cons}}
         hist.append(rec)

@@ -167,3 +167,37 @@ def test_buckling_matches_oracle(precision):
         m.buckling_sensitivity(T)
     assert e.value.code == afd.AFD_ERR_STATE
     m.close()
+
+
+def test_constrained_topology_driver_with_a_soft_buckling_constraint():
+    """Sec. 3.6/3.8: J <= 2 J_0 hard and P >= 1.2 P_0 soft on a compressed
+    column.  The soft constraint starts violated (g_P > 0) yet never stops or
+    rejects a design; its multiplier follows Eqs. 3.11-3.12; P is the oracle's
+    smallest positive buckling factor of each analysed design's state."""
+    from oracle import buckling, levelset
+
+    nx, ny, nz, E0, f, fixed = _column()
+    E0 = np.ones_like(E0)
+    m = afd.Mesh(nx, ny, nz, group=2)
+    m.set_loads_bcs(f[None], fixed)
+    res = afd.run_constrained_topology(m, E0, compliance=2.0, buckling=1.2, soft=("P",), dv0=0.05, v_min=0.6,
+                                       max_fea=10, tol=1e-9, eig_tol=1e-8)
+    m.close()
+    hist = res["history"]
+    P0 = buckling.buckling(nx, ny, nz, E0, f, fixed, 1)[0][0]
+    assert abs(res["reference"]["P"] - P0) <= 1e-7 * P0
+    assert hist[0]["g"]["P"] > 0                                   # the soft constraint starts violated
+    mu, gamma, g_prev = levelset.MU0, levelset.GAMMA0, 0.0
+    for k, h in enumerate(hist, start=1):
+        assert h["violated"] == (h["g"]["J"] > 0)                  # only the hard constraint counts
+        assert abs(h["g"]["P"] - (1.0 - h["P"] / (1.2 * P0))) <= 1e-9
+        mu = levelset.multiplier_update(mu, gamma, h["g"]["P"])
+        gamma = levelset.penalty_update(gamma, h["g"]["P"], g_prev, k)
+        g_prev = h["g"]["P"]
+        assert abs(h["mu"]["P"] - mu) <= 1e-9 * max(1.0, abs(mu))
+    assert res["volume_fraction"] < 1.0
+    E = res["E"]
+    K0 = fe.assemble(nx, ny, nz, E0)
+    J0 = fe.compliance(f, fe.solve_direct(K0, f, fixed))
+    assert fe.compliance(f, fe.solve_direct(fe.assemble(nx, ny, nz, E), f, fixed)) <= 2.0 * J0 * (1 + 1e-6)
+    assert int(res["kept"].sum()) == levelset.keep_count(res["volume_fraction"], E.size)
