@@ -182,13 +182,17 @@ int afd_eigen_sensitivity(afd_mesh* m, float* out, int out_on_device);
  * current static solution of load case 0 (afd_solve first): its stress at each
  * element centroid, held constant over the element, gives the geometric
  * stiffness K_G^e[(a,i),(b,j)] = delta_ij int grad N_a . S_e grad N_b (exact
- * cube integrals).  Subspace iteration as in afd_modal on (-K_G) phi = mu K phi,
- * lambda = 1/mu (largest mu first; Rayleigh-Ritz with Y^T K_G Y and Y^T K Y).
+ * cube integrals).  Block LOBPCG for the smallest eigenvalues theta of
+ * K_G phi = theta K phi (lambda = -1/theta), block n_modes + 2, with
+ * K^-1 by the mesh's solver (relative tolerance 1e-5) as the preconditioner
+ * and Rayleigh-Ritz on [X, W, P] (FP64 Gram matrices, directions scaled and
+ * truncated against dependence on the device).  It targets the smallest
+ * positive factors even when the reversed load buckles first.
  * Stops when every requested pair has ||K phi + lambda K_G phi|| <= tol ||K phi||,
  * else after max_iter steps with AFD_ERR_NOT_CONVERGED (outputs written).
  * AFD_ERR_NAN if the load gives fewer than n_modes positive factors.
  * lam_out: n_modes doubles ascending; modes_out (nullable): n_modes*ndof,
- * K-orthonormal, zero on fixed DOFs, sign arbitrary.  n_modes in [1, 10].
+ * K-orthonormal, zero on fixed DOFs, sign arbitrary.  n_modes in [1, 3].
  * The load cases are kept; the static solution is discarded.  The modes
  * stay in the mesh for afd_buckling_sensitivity (a later afd_modal replaces
  * them, and the other way round). */

@@ -163,9 +163,12 @@ struct afd_mesh {
   int modal_cap = 0, modal_n = 0;
   double modal_rho = 1.0;
   bool modal_valid = false;
-  // buckling: K_G Y, K_G X, the state stress (6 x nelem), residual coefficients / load factors
-  double *bGY = nullptr, *bGX = nullptr, *bS6 = nullptr, *bcoef = nullptr;
+  // buckling: the state stress (6 x nelem), Ritz values / load factors
+  double *bS6 = nullptr, *bcoef = nullptr;
   bool buckling_valid = false;
+  // LOBPCG blocks [X | W | P] and their K and K_G images, double-buffered (3 kp rows each)
+  double *lS[2] = {nullptr, nullptr}, *lKS[2] = {nullptr, nullptr}, *lGS[2] = {nullptr, nullptr};
+  int lobpcg_cap = 0;
   int nsplit_aw = 1;
   bool coarse_valid = false;
   Work<float> w32;
@@ -987,7 +990,8 @@ void afd_destroy(afd_mesh* m) {
   dfree(m->lam64); dfree(m->gadj); dfree(m->dsig); dfree(m->pn_d); dfree(m->lsbuf);
   dfree(m->mX); dfree(m->mKY); dfree(m->mKX); dfree(m->mmass); dfree(m->mparts);
   dfree(m->mA); dfree(m->mB); dfree(m->mV); dfree(m->mlam); dfree(m->minfo);
-  dfree(m->bGY); dfree(m->bGX); dfree(m->bS6); dfree(m->bcoef);
+  dfree(m->bS6); dfree(m->bcoef);
+  for (int q = 0; q < 2; ++q) { dfree(m->lS[q]); dfree(m->lKS[q]); dfree(m->lGS[q]); }
   if (m->ev) cudaEventDestroy(m->ev);
   if (m->s) cudaStreamDestroy(m->s);
   delete m;
@@ -1425,20 +1429,16 @@ static int upload_geo_table(afd_mesh* m) {
   return AFD_OK;
 }
 
-// The shared subspace iteration of afd_modal (kind 0: K phi = lambda M phi,
-// M the lumped mass in mmass) and afd_buckling (kind 1: (-K_G) phi = mu K phi,
-// K_G from the state stress in bS6, lambda = 1/mu).  Each step: the
-// right-hand sides B X into the solver's load buffer, Y = K^-1 B X by the
-// mesh's solver (started from X / lambda, resp. X mu), the Rayleigh-Ritz pairs
-// of span(Y) from FP64 Gram matrices (kind 0: Y^T K Y and Y^T M Y; kind 1:
-// Y^T K_G Y and Y^T K Y, whose ascending eigenvalues are -mu, the largest mu
-// first), the Ritz vectors and their residuals.  vals: the kp Ritz values
-// (kind 0: lambda; kind 1: -mu).  The caller keeps the load cases.
-static int subspace_eigs(afd_mesh* m, int kind, int n_modes, int kp, double tol, int max_iter,
-                         std::vector<double>& vals, bool& converged, int& steps, int& solve_iters) {
+// The subspace iteration of afd_modal (K phi = lambda M phi, M the lumped
+// mass in mmass).  Each step: the right-hand sides M X into the solver's load
+// buffer, Y = K^-1 M X by the mesh's solver (started from X / lambda), the
+// Rayleigh-Ritz pairs of span(Y) from FP64 Gram matrices Y^T K Y and Y^T M Y,
+// the Ritz vectors and their residuals.  vals: the kp Ritz values (ascending).
+// The caller keeps the load cases.
+static int subspace_eigs(afd_mesh* m, int n_modes, int kp, double tol, int max_iter, std::vector<double>& vals,
+                         bool& converged, int& steps, int& solve_iters) {
   const Grid& g = m->gr;
   const dim3 vgrid(grid_blocks(g.ndof, 256, 2048), kp);
-  const dim3 ngrid(grid_blocks(g.nnodes, 256, 2048), kp);
   k_modal_start<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, 0x2203151150ull, m->mmass, m->mX); m->launches++;
   CK(cudaGetLastError());
   const double solve_tol = std::min(1e-6, std::max(1e-10, 0.1 * tol));
@@ -1448,12 +1448,8 @@ static int subspace_eigs(afd_mesh* m, int kind, int n_modes, int kp, double tol,
   converged = false;
   TRY(ensure_partials(m, (size_t)kp * 2 * RED_BLOCKS));
   for (int it = 0; it < max_iter && !converged; ++it) {
-    // right-hand sides B X in the solver's load buffer, their norms
-    if (kind == 0) {
-      k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->mX, m->f64); m->launches++;
-    } else {
-      k_geo_apply<<<ngrid, 256, 0, m->s>>>(g, m->bS6, m->fixed, -1.0, m->mX, m->f64); m->launches++;
-    }
+    // right-hand sides M X in the solver's load buffer, their norms
+    k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->mX, m->f64); m->launches++;
     TRY(ensure_partials(m, (size_t)kp * 2 * RED_BLOCKS));
     k_dot<double, double><<<dim3(RED_BLOCKS, kp), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->f64, m->f64, m->partials);
     m->launches++;
@@ -1463,10 +1459,10 @@ static int subspace_eigs(afd_mesh* m, int kind, int n_modes, int kp, double tol,
     m->nrhs = kp;
     m->fnorm.assign(kp, 0.0);
     for (int r = 0; r < kp; ++r) m->fnorm[r] = std::sqrt(bb[r]);
-    // Y = K^-1 B X, started from X / lambda (kind 0) or X mu (kind 1) once Ritz values exist
+    // Y = K^-1 M X, started from X / lambda once Ritz values exist
     int warm = 0;
     if (it > 0) {
-      for (int r = 0; r < kp; ++r) sc[r] = kind == 0 ? (vals[r] > 0.0 ? 1.0 / vals[r] : 0.0) : -vals[r];
+      for (int r = 0; r < kp; ++r) sc[r] = vals[r] > 0.0 ? 1.0 / vals[r] : 0.0;
       CK(cudaMemcpyAsync(m->mlam, sc.data(), kp * sizeof(double), cudaMemcpyHostToDevice, m->s));
       k_scale_rhs<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mlam, m->mX, m->u64); m->launches++;
       m->has_solution = true;
@@ -1481,29 +1477,15 @@ static int subspace_eigs(afd_mesh* m, int kind, int n_modes, int kp, double tol,
     // Rayleigh-Ritz on span(Y) (K Y by the FP64 stencil)
     TRY((launch_stencil<double, ST_APPLY, double>(m, m->u64, m->mKY, m->w64.E, nullptr, nullptr, nullptr, nullptr,
                                                     kp, m->w64.K)));
-    if (kind == 0) {
-      TRY(modal_gram(m, kp, m->u64, m->mKY, m->mA));
-      k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->u64, m->mKX); m->launches++;
-      TRY(modal_gram(m, kp, m->u64, m->mKX, m->mB));
-    } else {
-      k_geo_apply<<<ngrid, 256, 0, m->s>>>(g, m->bS6, m->fixed, 1.0, m->u64, m->bGY); m->launches++;
-      TRY(modal_gram(m, kp, m->u64, m->bGY, m->mA));
-      TRY(modal_gram(m, kp, m->u64, m->mKY, m->mB));
-    }
+    TRY(modal_gram(m, kp, m->u64, m->mKY, m->mA));
+    k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->u64, m->mKX); m->launches++;
+    TRY(modal_gram(m, kp, m->u64, m->mKX, m->mB));
     k_small_geig<<<1, 32, 0, m->s>>>(kp, m->mA, m->mB, m->mlam, m->mV, m->minfo); m->launches++;
     const unsigned cb = grid_blocks(g.ndof, 256, 2048);
     k_ritz_combine<<<cb, 256, 0, m->s>>>(g.ndof, g.vs, kp, m->u64, m->mV, m->mX); m->launches++;
     k_ritz_combine<<<cb, 256, 0, m->s>>>(g.ndof, g.vs, kp, m->mKY, m->mV, m->mKX); m->launches++;
-    if (kind == 0) {
-      k_modal_residual<<<dim3(RED_BLOCKS, n_modes), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->mKX, m->mX, m->mmass,
-                                                                          m->mlam, m->partials); m->launches++;
-    } else {
-      // K x + lambda K_G x = K x - (1/nu) K_G x with nu = -mu the Ritz value
-      k_ritz_combine<<<cb, 256, 0, m->s>>>(g.ndof, g.vs, kp, m->bGY, m->mV, m->bGX); m->launches++;
-      k_invert_vals<<<1, 32, 0, m->s>>>(kp, m->mlam, m->bcoef); m->launches++;
-      k_pair_residual<<<dim3(RED_BLOCKS, n_modes), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->mKX, m->bGX, m->mmass,
-                                                                         m->bcoef, m->partials); m->launches++;
-    }
+    k_modal_residual<<<dim3(RED_BLOCKS, n_modes), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->mKX, m->mX, m->mmass,
+                                                                        m->mlam, m->partials); m->launches++;
     CK(cudaGetLastError());
     int info = 0;
     CK(cudaMemcpyAsync(vals.data(), m->mlam, kp * sizeof(double), cudaMemcpyDeviceToHost, m->s));
@@ -1529,14 +1511,134 @@ static int subspace_eigs(afd_mesh* m, int kind, int n_modes, int kp, double tol,
   return AFD_OK;
 }
 
-// Buffers of the subspace iteration for a block of kp vectors (buckling adds
-// K_G Y, K_G X, the state stress and the residual coefficients).
+// Buckling by block LOBPCG on G phi = theta K phi (G = K_G, theta = -mu =
+// -1/lambda), for the smallest theta: the most negative theta is the smallest
+// positive load factor.  Subspace iteration would follow the largest |theta|,
+// and under many loads the reversed load's factors (theta > 0) are the larger
+// ones.  Each step: the residual block R = G X - K X Theta, W = K^-1 R by the
+// mesh's solver (the preconditioner; relative tolerance 1e-5), K W and G W,
+// then Rayleigh-Ritz on span[X, W, P] (rows contiguous in lS) with FP64 Gram
+// matrices and the truncating small eigensolver; X and the new direction P
+// (the W, P part of the Ritz coefficients) are rebuilt with their K and G
+// images into the other buffer.  vals: the kp Ritz values theta.
+static int lobpcg_buckling(afd_mesh* m, int n_modes, int kp, double tol, int max_iter, std::vector<double>& vals,
+                           bool& converged, int& steps, int& solve_iters) {
+  const Grid& g = m->gr;
+  const size_t blk = (size_t)kp * g.vs;
+  const dim3 vgrid(grid_blocks(g.ndof, 256, 2048), kp);
+  const dim3 ngrid(grid_blocks(g.nnodes, 256, 2048), kp);
+  const unsigned cb = grid_blocks(g.ndof, 256, 2048);
+  int cur = 0;
+  steps = solve_iters = 0;
+  converged = false;
+  vals.assign(kp, 0.0);
+  std::vector<double> V;
+  auto images = [&](const double* Xs, double* KXs, double* GXs) -> int {   // K and G of kp rows
+    TRY((launch_stencil<double, ST_APPLY, double>(m, Xs, KXs, m->w64.E, nullptr, nullptr, nullptr, nullptr, kp,
+                                                    m->w64.K)));
+    k_geo_apply<<<ngrid, 256, 0, m->s>>>(g, m->bS6, m->fixed, 1.0, Xs, GXs); m->launches++;
+    CK(cudaGetLastError());
+    return AFD_OK;
+  };
+  auto rayleigh_ritz = [&](int mrows, std::vector<double>& th, std::vector<double>& Vh) -> int {
+    TRY(modal_gram(m, mrows, m->lS[cur], m->lGS[cur], m->mA));
+    TRY(modal_gram(m, mrows, m->lS[cur], m->lKS[cur], m->mB));
+    k_small_geig_robust<<<1, 32, 0, m->s>>>(mrows, kp, m->mA, m->mB, m->mlam, m->mV, m->minfo); m->launches++;
+    int info = 0;
+    th.assign(kp, 0.0);
+    Vh.assign((size_t)mrows * kp, 0.0);
+    CK(cudaMemcpyAsync(th.data(), m->mlam, kp * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+    CK(cudaMemcpyAsync(Vh.data(), m->mV, Vh.size() * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+    CK(cudaMemcpyAsync(&info, m->minfo, sizeof(int), cudaMemcpyDeviceToHost, m->s));
+    CK(cudaStreamSynchronize(m->s));
+    if (info != 0)
+      return fail(AFD_ERR_NAN, "Rayleigh-Ritz step failed (%s)",
+                  info == 3 ? "the block lost rank" : "Jacobi sweeps did not converge");
+    for (double t : th)
+      if (!std::isfinite(t)) return fail(AFD_ERR_NAN, "buckling iteration is not finite");
+    return AFD_OK;
+  };
+  // X and P (with_p) of the next buffer from the coefficients of span[X, W, P]
+  auto rebuild = [&](int mrows, const std::vector<double>& Vh, bool with_p) -> int {
+    const int nxt = 1 - cur;
+    const double* src[3] = {m->lS[cur], m->lKS[cur], m->lGS[cur]};
+    double* dst[3] = {m->lS[nxt], m->lKS[nxt], m->lGS[nxt]};
+    CK(cudaMemcpyAsync(m->mV, Vh.data(), Vh.size() * sizeof(double), cudaMemcpyHostToDevice, m->s));
+    for (int q = 0; q < 3; ++q) {
+      k_block_combine<<<cb, 256, 0, m->s>>>(g.ndof, g.vs, mrows, kp, src[q], m->mV, dst[q]); m->launches++;
+    }
+    if (with_p) {
+      std::vector<double> Vp(Vh);
+      for (int i = 0; i < kp; ++i)
+        for (int c = 0; c < kp; ++c) Vp[(size_t)i * kp + c] = 0.0;   // drop the X rows: P = W Vw + P Vp
+      CK(cudaMemcpyAsync(m->mB, Vp.data(), Vp.size() * sizeof(double), cudaMemcpyHostToDevice, m->s));
+      for (int q = 0; q < 3; ++q) {
+        k_block_combine<<<cb, 256, 0, m->s>>>(g.ndof, g.vs, mrows, kp, src[q], m->mB, dst[q] + 2 * blk);
+        m->launches++;
+      }
+    }
+    CK(cudaGetLastError());
+    cur = nxt;
+    return AFD_OK;
+  };
+  // start: random X, Rayleigh-Ritz on X alone
+  k_modal_start<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, 0x2203151150ull, m->mmass, m->lS[cur]); m->launches++;
+  TRY(images(m->lS[cur], m->lKS[cur], m->lGS[cur]));
+  TRY(rayleigh_ritz(kp, vals, V));
+  TRY(rebuild(kp, V, false));
+  bool have_p = false;
+  TRY(ensure_partials(m, (size_t)kp * 2 * RED_BLOCKS));
+  for (int it = 0; it < max_iter; ++it) {
+    // residual block into the solver's load buffer, its norms, the convergence test
+    CK(cudaMemcpyAsync(m->bcoef, vals.data(), kp * sizeof(double), cudaMemcpyHostToDevice, m->s));
+    TRY(ensure_partials(m, (size_t)kp * 2 * RED_BLOCKS));
+    k_lobpcg_residual<<<dim3(RED_BLOCKS, kp), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->lGS[cur], m->lKS[cur],
+                                                                     m->mmass, m->bcoef, m->f64, m->partials);
+    m->launches++;
+    CK(cudaGetLastError());
+    std::vector<double> hp((size_t)kp * RED_BLOCKS * 2);
+    CK(cudaMemcpyAsync(hp.data(), m->partials, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+    CK(cudaStreamSynchronize(m->s));
+    std::vector<double> rn(kp, 0.0), kn(kp, 0.0);
+    for (int r = 0; r < kp; ++r)
+      for (int b = 0; b < RED_BLOCKS; ++b) {
+        rn[r] += hp[((size_t)r * RED_BLOCKS + b) * 2];
+        kn[r] += hp[((size_t)r * RED_BLOCKS + b) * 2 + 1];
+      }
+    converged = true;
+    for (int r = 0; r < n_modes; ++r)
+      if (!(std::sqrt(rn[r]) <= tol * std::fabs(vals[r]) * std::sqrt(kn[r]))) converged = false;
+    if (converged) break;
+    // W = K^-1 R
+    m->nrhs = kp;
+    m->fnorm.assign(kp, 0.0);
+    for (int r = 0; r < kp; ++r) m->fnorm[r] = std::sqrt(rn[r]);
+    std::vector<afd_stats> st(kp);
+    const int src = afd_solve(m, 1e-5, 0, st.data(), nullptr, 0);
+    if (src != AFD_OK && src != AFD_ERR_NOT_CONVERGED) return src;
+    int mx = 0;
+    for (int r = 0; r < kp; ++r) mx = std::max(mx, st[r].iters);
+    solve_iters += mx;
+    CK(cudaMemcpyAsync(m->lS[cur] + blk, m->u64, blk * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
+    TRY(images(m->lS[cur] + blk, m->lKS[cur] + blk, m->lGS[cur] + blk));
+    const int mrows = have_p ? 3 * kp : 2 * kp;
+    TRY(rayleigh_ritz(mrows, vals, V));
+    TRY(rebuild(mrows, V, true));
+    have_p = true;
+    steps = it + 1;
+  }
+  // the modes in mX for the sensitivity and the caller
+  CK(cudaMemcpyAsync(m->mX, m->lS[cur], blk * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
+  return AFD_OK;
+}
+
+// Buffers of the eigensolvers for a block of kp vectors (buckling adds the
+// state stress, the Ritz values / load factors and the LOBPCG blocks).
 static int ensure_eig_buffers(afd_mesh* m, int kp, bool buckling) {
   const Grid& g = m->gr;
   if (m->modal_cap < kp) {
     dfree(m->mX); dfree(m->mKY); dfree(m->mKX); dfree(m->mmass); dfree(m->mparts);
     dfree(m->mA); dfree(m->mB); dfree(m->mV); dfree(m->mlam); dfree(m->minfo);
-    dfree(m->bGY); dfree(m->bGX);
     m->modal_cap = 0;
     TRY(dalloc(&m->mX, (size_t)kp * g.vs));
     TRY(dalloc(&m->mKY, (size_t)kp * g.vs));
@@ -1551,12 +1653,17 @@ static int ensure_eig_buffers(afd_mesh* m, int kp, bool buckling) {
     m->modal_cap = kp;
   }
   if (buckling) {
-    if (!m->bGY) {
-      TRY(dalloc(&m->bGY, (size_t)m->modal_cap * g.vs));
-      TRY(dalloc(&m->bGX, (size_t)m->modal_cap * g.vs));
-    }
     if (!m->bS6) TRY(dalloc(&m->bS6, (size_t)6 * g.nelem));
     if (!m->bcoef) TRY(dalloc(&m->bcoef, (size_t)MODAL_MAX));
+    if (m->lobpcg_cap < kp) {
+      for (int q = 0; q < 2; ++q) {
+        dfree(m->lS[q]); dfree(m->lKS[q]); dfree(m->lGS[q]);
+        TRY(dalloc(&m->lS[q], (size_t)3 * kp * g.vs));
+        TRY(dalloc(&m->lKS[q], (size_t)3 * kp * g.vs));
+        TRY(dalloc(&m->lGS[q], (size_t)3 * kp * g.vs));
+      }
+      m->lobpcg_cap = kp;
+    }
   }
   return AFD_OK;
 }
@@ -1616,7 +1723,7 @@ int afd_modal(afd_mesh* m, int n_modes, double rho, double tol, int max_iter, do
                                                                       m->mmass); m->launches++;
     std::vector<double> vals;
     int steps = 0, solve_iters = 0;
-    TRY(subspace_eigs(m, 0, n_modes, kp, tol, max_iter, vals, converged, steps, solve_iters));
+    TRY(subspace_eigs(m, n_modes, kp, tol, max_iter, vals, converged, steps, solve_iters));
     for (int r = 0; r < n_modes; ++r) lam_out[r] = vals[r];
     if (modes_out)
       CK(cudaMemcpy2DAsync(modes_out, (size_t)g.ndof * sizeof(double), m->mX, (size_t)g.vs * sizeof(double),
@@ -1637,8 +1744,8 @@ int afd_modal(afd_mesh* m, int n_modes, double rho, double tol, int max_iter, do
 int afd_buckling(afd_mesh* m, int n_modes, double tol, int max_iter, double* lam_out, double* modes_out,
                  int modes_on_device, int* iters_out, int* solve_iters_out) {
   if (!m || !lam_out) return fail(AFD_ERR_INVALID_ARG, "null argument");
-  int kp = 0;
-  TRY(eig_block(n_modes, kp));
+  const int kp = n_modes + 2;
+  if (n_modes < 1 || 3 * kp > MODAL_MAX) return fail(AFD_ERR_INVALID_ARG, "n_modes must be in [1, 3]");
   if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 1) return fail(AFD_ERR_INVALID_ARG, "bad tol / max_iter");
   if (!m->has_solution) return fail(AFD_ERR_STATE, "no static solution: afd_solve first (load case 0 is the state)");
   DeviceGuard dg(m->device);
@@ -1668,7 +1775,7 @@ int afd_buckling(afd_mesh* m, int n_modes, double tol, int max_iter, double* lam
     m->launches++;
     std::vector<double> vals;
     int steps = 0, solve_iters = 0;
-    TRY(subspace_eigs(m, 1, n_modes, kp, tol, max_iter, vals, converged, steps, solve_iters));
+    TRY(lobpcg_buckling(m, n_modes, kp, tol, max_iter, vals, converged, steps, solve_iters));
     for (int r = 0; r < n_modes; ++r)
       if (!(vals[r] < 0.0)) return fail(AFD_ERR_NAN, "fewer than %d positive buckling factors for this load", n_modes);
     std::vector<double> lam(n_modes);

@@ -198,6 +198,156 @@ __global__ void k_small_geig(int kp, const double* __restrict__ A, const double*
   }
 }
 
+// Cyclic Jacobi on a symmetric n x n matrix C (n <= MODAL_MAX) in place:
+// eigenvalues on the diagonal, eigenvectors in the columns of Q.  At most 64
+// sweeps; returns false without convergence.
+__device__ bool jacobi_sym(int n, double (&C)[MODAL_MAX][MODAL_MAX], double (&Q)[MODAL_MAX][MODAL_MAX]) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Q[i][j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double scale = 0.0;
+    for (int i = 0; i < n; ++i) scale = fmax(scale, fabs(C[i][i]));
+    bool conv = true;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (fabs(C[p][q]) <= 1e-15 * scale) continue;
+        conv = false;
+        const double theta = (C[q][q] - C[p][p]) / (2.0 * C[p][q]);
+        const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / sqrt(tt * tt + 1.0), sn = tt * cs;
+        for (int k = 0; k < n; ++k) {
+          const double a = C[k][p], b = C[k][q];
+          C[k][p] = cs * a - sn * b;
+          C[k][q] = sn * a + cs * b;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double a = C[p][k], b = C[q][k];
+          C[p][k] = cs * a - sn * b;
+          C[q][k] = sn * a + cs * b;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double a = Q[k][p], b = Q[k][q];
+          Q[k][p] = cs * a - sn * b;
+          Q[k][q] = sn * a + cs * b;
+        }
+      }
+    if (conv) return true;
+  }
+  return false;
+}
+
+// Rayleigh-Ritz of A v = theta B v (m x m, row-major) when B may be nearly
+// singular (the blocks of LOBPCG grow nearly dependent as it converges): with
+// the columns scaled to unit B-norm, B = U diag(d) U^T by Jacobi, the directions with d > 1e-12 max d kept,
+// Z = U_keep diag(d_keep)^-1/2, C = Z^T A Z by Jacobi, V = Z Q.  The k
+// smallest theta (ascending) and their m x k coefficients (row-major, V^T B V
+// = I) are written.  info: 0 ok, 2 no convergence, 3 fewer than k directions.
+__global__ void k_small_geig_robust(int m, int k, const double* __restrict__ A, const double* __restrict__ Bm,
+                                    double* __restrict__ lam, double* __restrict__ V, int* info) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double C[MODAL_MAX][MODAL_MAX], U[MODAL_MAX][MODAL_MAX], Z[MODAL_MAX][MODAL_MAX];
+  double sc[MODAL_MAX];
+  *info = 0;
+  // columns scaled to unit B-norm first (W and P shrink with the residual; a
+  // zero column is dropped), so that the truncation below sees only true
+  // dependence, not scale
+  for (int i = 0; i < m; ++i) {
+    const double d = Bm[i * m + i];
+    sc[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+  }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) C[i][j] = 0.5 * (Bm[i * m + j] + Bm[j * m + i]) * sc[i] * sc[j];
+  if (!jacobi_sym(m, C, U)) { *info = 2; return; }
+  double dmax = 0.0;
+  for (int i = 0; i < m; ++i) dmax = fmax(dmax, C[i][i]);
+  int r = 0;
+  for (int j = 0; j < m; ++j) {
+    const double d = C[j][j];
+    if (!(d > 1e-12 * dmax)) continue;
+    const double s = 1.0 / sqrt(d);
+    for (int i = 0; i < m; ++i) Z[i][r] = U[i][j] * s;
+    ++r;
+  }
+  if (r < k) { *info = 3; return; }
+  // C = Z^T A' Z (r x r) with A' the scaled A, symmetrised
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b < r; ++b) {
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < m; ++j) t += 0.5 * (A[i * m + j] + A[j * m + i]) * sc[i] * sc[j] * Z[j][b];
+        s += Z[i][a] * t;
+      }
+      C[a][b] = s;
+    }
+  if (!jacobi_sym(r, C, U)) { *info = 2; return; }
+  int ord[MODAL_MAX];
+  for (int i = 0; i < r; ++i) ord[i] = i;
+  for (int i = 0; i < r; ++i)
+    for (int j = i + 1; j < r; ++j)
+      if (C[ord[j]][ord[j]] < C[ord[i]][ord[i]]) {
+        const int t = ord[i];
+        ord[i] = ord[j];
+        ord[j] = t;
+      }
+  for (int c = 0; c < k; ++c) {
+    const int oc = ord[c];
+    lam[c] = C[oc][oc];
+    for (int i = 0; i < m; ++i) {
+      double s = 0.0;
+      for (int a = 0; a < r; ++a) s += Z[i][a] * U[a][oc];
+      V[i * k + c] = sc[i] * s;
+    }
+  }
+}
+
+// X[r] = sum_j Y[j] V[j][r] for r < kout, Y with kin rows, V kin x kout
+// row-major (the Ritz vectors of a block).
+__global__ void k_block_combine(int ndof, int vs, int kin, int kout, const double* __restrict__ Y,
+                                const double* __restrict__ V, double* __restrict__ X) {
+  __shared__ double sv[MODAL_MAX * MODAL_MAX];
+  for (int q = threadIdx.x; q < kin * kout; q += blockDim.x) sv[q] = V[q];
+  __syncthreads();
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
+    double y[MODAL_MAX];
+#pragma unroll
+    for (int j = 0; j < MODAL_MAX; ++j) y[j] = j < kin ? Y[(size_t)j * vs + d] : 0.0;
+    for (int r = 0; r < kout; ++r) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < MODAL_MAX; ++j)
+        if (j < kin) s = fma(y[j], sv[j * kout + r], s);
+      X[(size_t)r * vs + d] = s;
+    }
+  }
+}
+
+// R[r] = G X[r] - theta[r] K X[r] (the LOBPCG residual block), zero where
+// mask <= 0, and the partials of |R[r]|^2 and |K X[r]|^2 as k_pair_residual.
+__global__ void __launch_bounds__(RED_THREADS)
+k_lobpcg_residual(int ndof, int vs, const double* __restrict__ GX, const double* __restrict__ KX,
+                  const double* __restrict__ mask, const double* __restrict__ theta, double* __restrict__ R,
+                  double* __restrict__ parts) {
+  __shared__ double red[32 * 2];
+  const int r = blockIdx.y;
+  const size_t off = (size_t)r * vs;
+  const double t = theta[r];
+  double s[2] = {0.0, 0.0};
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
+    const double kx = KX[off + d];
+    const double e = mask[d] > 0.0 ? GX[off + d] - t * kx : 0.0;
+    R[off + d] = e;
+    s[0] = fma(e, e, s[0]);
+    s[1] = mask[d] > 0.0 ? fma(kx, kx, s[1]) : s[1];
+  }
+  double o[2];
+  block_sum_to_f64<2>(s, red, o);
+  if (threadIdx.x == 0) {
+    parts[((size_t)r * gridDim.x + blockIdx.x) * 2] = o[0];
+    parts[((size_t)r * gridDim.x + blockIdx.x) * 2 + 1] = o[1];
+  }
+}
+
 // X[r] = sum_j Y[j] V[j][r] for r < kp (the Ritz vectors of span(Y)).
 __global__ void k_ritz_combine(int ndof, int vs, int kp, const double* __restrict__ Y, const double* __restrict__ V,
                                double* __restrict__ X) {
@@ -343,39 +493,6 @@ k_geo_apply(Grid gr, const double* __restrict__ S6, const uint8_t* __restrict__ 
 #pragma unroll
     for (int c = 0; c < 3; ++c) Y[off + 3 * (size_t)n + c] = ((fb >> c) & 1) ? 0.0 : sign * acc[c];
   }
-}
-
-// Residual partials of the first n pairs with a general second operator:
-// parts[(r * gridDim.x + b) * 2] = sum (A x_r - c_r B x_r)^2 over DOFs with
-// mass/mask > 0, [.. + 1] = sum (A x_r)^2.
-__global__ void __launch_bounds__(RED_THREADS)
-k_pair_residual(int ndof, int vs, const double* __restrict__ AX, const double* __restrict__ BX,
-                const double* __restrict__ mask, const double* __restrict__ coef, double* __restrict__ parts) {
-  __shared__ double red[32 * 2];
-  const int r = blockIdx.y;
-  const size_t off = (size_t)r * vs;
-  const double c = coef[r];
-  double s[2] = {0.0, 0.0};
-  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
-    if (!(mask[d] > 0.0)) continue;
-    const double ax = AX[off + d];
-    const double e = ax - c * BX[off + d];
-    s[0] = fma(e, e, s[0]);
-    s[1] = fma(ax, ax, s[1]);
-  }
-  double o[2];
-  block_sum_to_f64<2>(s, red, o);
-  if (threadIdx.x == 0) {
-    parts[((size_t)r * gridDim.x + blockIdx.x) * 2] = o[0];
-    parts[((size_t)r * gridDim.x + blockIdx.x) * 2 + 1] = o[1];
-  }
-}
-
-// coef[r] = 1 / vals[r]: with the Ritz values nu = -mu of the buckling
-// pencil, K x + lambda K_G x = K x - coef K_G x (lambda = 1/mu).
-__global__ void k_invert_vals(int kp, const double* __restrict__ vals, double* __restrict__ coef) {
-  const int r = threadIdx.x;
-  if (r < kp) coef[r] = 1.0 / vals[r];
 }
 
 // Eq. 3.5 per element for mode r (phi[r], lam[r]), with the paper's K_sigma
