@@ -184,7 +184,7 @@ int afd_eigen_sensitivity(afd_mesh* m, float* out, int out_on_device);
  * stiffness K_G^e[(a,i),(b,j)] = delta_ij int grad N_a . S_e grad N_b (exact
  * cube integrals).  Block LOBPCG for the smallest eigenvalues theta of
  * K_G phi = theta K phi (lambda = -1/theta), block n_modes + 2, with
- * K^-1 by the mesh's solver (relative tolerance 1e-5) as the preconditioner
+ * K^-1 by the mesh's solver (relative tolerance 1e-3) as the preconditioner
  * and Rayleigh-Ritz on [X, W, P] (FP64 Gram matrices, directions scaled and
  * truncated against dependence on the device).  It targets the smallest
  * positive factors even when the reversed load buckles first.

@@ -1516,7 +1516,7 @@ static int subspace_eigs(afd_mesh* m, int n_modes, int kp, double tol, int max_i
 // positive load factor.  Subspace iteration would follow the largest |theta|,
 // and under many loads the reversed load's factors (theta > 0) are the larger
 // ones.  Each step: the residual block R = G X - K X Theta, W = K^-1 R by the
-// mesh's solver (the preconditioner; relative tolerance 1e-5), K W and G W,
+// mesh's solver (the preconditioner; relative tolerance 1e-3), K W and G W,
 // then Rayleigh-Ritz on span[X, W, P] (rows contiguous in lS) with FP64 Gram
 // matrices and the truncating small eigensolver; X and the new direction P
 // (the W, P part of the Ritz coefficients) are rebuilt with their K and G
@@ -1614,7 +1614,7 @@ static int lobpcg_buckling(afd_mesh* m, int n_modes, int kp, double tol, int max
     m->fnorm.assign(kp, 0.0);
     for (int r = 0; r < kp; ++r) m->fnorm[r] = std::sqrt(rn[r]);
     std::vector<afd_stats> st(kp);
-    const int src = afd_solve(m, 1e-5, 0, st.data(), nullptr, 0);
+    const int src = afd_solve(m, 1e-3, 0, st.data(), nullptr, 0);
     if (src != AFD_OK && src != AFD_ERR_NOT_CONVERGED) return src;
     int mx = 0;
     for (int r = 0; r < kp; ++r) mx = std::max(mx, st[r].iters);
