@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <atomic>
 #include <cmath>
 #include <limits>
 #include <cstdarg>
@@ -276,6 +277,23 @@ static int stencil_blocks(const afd_mesh* m, bool f64) {
   return (int)(g.x * g.y);
 }
 
+// Kernels that need more than the default 48 KB of dynamic shared memory get
+// their attribute raised once per device (the attribute is per device; meshes
+// of one process may live on several, and server workers launch from several
+// threads).  bit: which kernel.
+static std::atomic<unsigned> g_optin[64];
+template <typename F>
+static int opt_in_once(int bit, F&& set) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(AFD_ERR_INVALID_ARG, "device index %d out of range", dev);
+  const unsigned mask = 1u << bit;
+  if (g_optin[dev].load(std::memory_order_acquire) & mask) return AFD_OK;
+  CK(set());
+  g_optin[dev].fetch_or(mask, std::memory_order_acq_rel);
+  return AFD_OK;
+}
+
 template <typename T, int MODE, typename TF>
 static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f, float* y32, double* partials,
                           const int* done, int nrhs, const ElemConsts<T>& K, CGState* st = nullptr,
@@ -312,17 +330,14 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
     if ((MODE == ST_APPLY_DOT) != (z != nullptr)) return fail(AFD_ERR_INVALID_ARG, "stencil mode / z mismatch");
     // the asynchronous staging ring lives in dynamic shared memory
     if (m->async32) {
-      static bool opted[2] = {false, false};
       const int ti = m->ty32 == 8 ? 0 : 1;
       const size_t dyn =
           (m->ty32 == 8 ? stencil2_ring_floats<8, MODE>() : stencil2_ring_floats<16, MODE>()) * sizeof(float);
-      if (!opted[ti]) {
-        if (m->ty32 == 8)
-          CK(cudaFuncSetAttribute(stencil2_kernel<8, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-        else
-          CK(cudaFuncSetAttribute(stencil2_kernel<16, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-        opted[ti] = true;
-      }
+      TRY(opt_in_once(2 * MODE + ti, [&]() {
+        return m->ty32 == 8
+                   ? cudaFuncSetAttribute(stencil2_kernel<8, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)
+                   : cudaFuncSetAttribute(stencil2_kernel<16, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      }));
       if (m->ty32 == 8)
         CK(launch_ex(m->pdl_now, stencil2_kernel<8, MODE, true>, grid, dim3(ST_TX * 8), dyn, m->s, a));
       else
@@ -516,11 +531,10 @@ static int coarse_step_smem(const afd_mesh* m, size_t& bytes) {
   if (bytes > kMax)
     return fail(AFD_ERR_INVALID_ARG, "coarse problem too large for the dense inverse (6 x groups above 25600 for FP64, "
                                      "51200 for mixed): use a larger group");
-  static bool opted = false;
-  if (bytes > 40 * 1024 && !opted) {
-    CK(cudaFuncSetAttribute(k_coarse_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax));
-    opted = true;
-  }
+  if (bytes > 40 * 1024)
+    TRY(opt_in_once(16 + (sizeof(T) == 8 ? 1 : 0), [&]() {
+      return cudaFuncSetAttribute(k_coarse_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax);
+    }));
   return AFD_OK;
 }
 
@@ -1400,13 +1414,15 @@ static int modal_gram(afd_mesh* m, int kp, const double* Y, const double* Z, dou
   return AFD_OK;
 }
 
-// The geometric element table c_geo[q][a][b] for the cube of edge h: the
-// integrals of d_k N_a d_l N_b, in closed form per axis (1D integrals of the
-// linear shape functions: int phi_p phi_q = 1/3 or 1/6, int phi_p' phi_q =
-// (2p - 1)/2, int phi_p' phi_q' = (2p - 1)(2q - 1)), summed over (k, l) and
-// (l, k) for the off-diagonal stress components q = xy, yz, zx.
+// The geometric element table c_geo[q][a][b] for the unit cube: the integrals
+// of d_k N_a d_l N_b, in closed form per axis (1D integrals of the linear
+// shape functions: int phi_p phi_q = 1/3 or 1/6, int phi_p' phi_q = (2p - 1)/2,
+// int phi_p' phi_q' = (2p - 1)(2q - 1)), summed over (k, l) and (l, k) for the
+// off-diagonal stress components q = xy, yz, zx.  A cube of edge h scales
+// them by h, which the state stress carries (k_state_stress), so the table is
+// the same for every mesh and concurrent uploads cannot disagree.
 static int upload_geo_table(afd_mesh* m) {
-  const double h = m->opt.h;
+  const double h = 1.0;
   static const int kk[6] = {0, 1, 2, 0, 1, 2}, ll[6] = {0, 1, 2, 1, 2, 0};
   double t[6][8][8];
   auto bit = [](int a, int d) { return (a >> d) & 1; };
@@ -1760,7 +1776,8 @@ int afd_buckling(afd_mesh* m, int n_modes, double tol, int max_iter, double* lam
   F.mu = 1.0 / (2.0 * (1.0 + nu));
   F.nu = nu;
   F.inv4h = 1.0 / (4.0 * m->opt.h);
-  k_state_stress<<<grid_blocks(g.nelem, 256, 8 * RED_BLOCKS), 256, 0, m->s>>>(g, m->u64, m->E64, F, m->bS6);
+  k_state_stress<<<grid_blocks(g.nelem, 256, 8 * RED_BLOCKS), 256, 0, m->s>>>(g, m->u64, m->E64, F, m->opt.h,
+                                                                              m->bS6);
   m->launches++;
   TRY(upload_geo_table(m));
   const int rc = with_saved_loads(m, [&]() -> int {

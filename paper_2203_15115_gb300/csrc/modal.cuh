@@ -435,9 +435,10 @@ k_eigen_topo(Grid gr, const double* __restrict__ phi, const double* __restrict__
 // ---------------------------------------------------------------------------
 
 // Stress of the pre-buckling state u0 at each element centroid (xx, yy, zz,
-// xy, yz, zx), held constant over the element.
+// xy, yz, zx), held constant over the element, times `scale` (the element
+// edge h, by which the unit-cube geometric integrals of c_geo scale).
 __global__ void __launch_bounds__(256)
-k_state_stress(Grid gr, const double* __restrict__ u0, const double* __restrict__ Emod, FieldConsts F,
+k_state_stress(Grid gr, const double* __restrict__ u0, const double* __restrict__ Emod, FieldConsts F, double scale,
                double* __restrict__ S6) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < gr.nelem; e += gridDim.x * blockDim.x) {
     const int i = e % gr.nx, j = (e / gr.nx) % gr.ny, k = e / (gr.nx * gr.ny);
@@ -445,7 +446,7 @@ k_state_stress(Grid gr, const double* __restrict__ u0, const double* __restrict_
     centroid_strain64(gr, u0, i, j, k, F.inv4h, eps);
     const double E = Emod[e];
     const double tre = eps[0] + eps[1] + eps[2];
-    const double la = F.lam * E, mu2 = 2.0 * F.mu * E;
+    const double la = F.lam * E * scale, mu2 = 2.0 * F.mu * E * scale;
 #pragma unroll
     for (int q = 0; q < 3; ++q) S6[(size_t)q * gr.nelem + e] = la * tre + mu2 * eps[q];
 #pragma unroll
@@ -454,8 +455,9 @@ k_state_stress(Grid gr, const double* __restrict__ u0, const double* __restrict_
 }
 
 // Element geometric matrix G_e[a][b] = sum_q S_e[q] GEO[q][a][b]: GEO[q] the
-// integrals of grad N_a (.) grad N_b over the cube for the stress components
-// q = xx, yy, zz, xy, yz, zx (off-diagonal pairs summed), set by the host.
+// integrals of grad N_a (.) grad N_b over the unit cube for the stress
+// components q = xx, yy, zz, xy, yz, zx (off-diagonal pairs summed), set by
+// the host; S_e carries the factor h of a cube of edge h.
 __constant__ double c_geo[6][8][8];
 
 // Y[r] = sign * K_G X[r], gathered per node over its (up to) eight elements;

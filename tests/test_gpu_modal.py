@@ -128,14 +128,14 @@ def _column():
     return nx, ny, nz, E, axial_face_load(nx, ny, nz, -1.0), clamp_face_x0(nx, ny, nz)
 
 
-@pytest.mark.parametrize("precision", [afd.AFD_FP64, afd.AFD_MIXED])
-def test_buckling_matches_oracle(precision):
+@pytest.mark.parametrize("precision,h", [(afd.AFD_FP64, 1.0), (afd.AFD_MIXED, 1.0), (afd.AFD_FP64, 0.5)])
+def test_buckling_matches_oracle(precision, h):
     from oracle import buckling
 
     nx, ny, nz, E, f, fixed = _column()
     n, tol = 3, 1e-8
-    lam_o, phi_o, S = buckling.buckling(nx, ny, nz, E, f, fixed, n)
-    m = afd.Mesh(nx, ny, nz, precision=precision, group=2)
+    lam_o, phi_o, S = buckling.buckling(nx, ny, nz, E, f, fixed, n, h=h)
+    m = afd.Mesh(nx, ny, nz, precision=precision, group=2, h=h)
     m.set_element_moduli(E)
     m.set_loads_bcs(f[None], fixed)
     with pytest.raises(afd.AFDError) as e:
@@ -146,8 +146,8 @@ def test_buckling_matches_oracle(precision):
     lam, info = m.buckling(n, tol=tol, modes_out=phi)
     assert info["steps"] >= 1
     assert np.allclose(lam, lam_o, rtol=1e-8)
-    K = fe.assemble(nx, ny, nz, E)
-    Kg = buckling.assemble_geometric(nx, ny, nz, S)
+    K = fe.assemble(nx, ny, nz, E, h=h)
+    Kg = buckling.assemble_geometric(nx, ny, nz, S, h)
     assert np.allclose(phi @ (K @ phi.T), np.eye(n), atol=1e-9)     # K-orthonormal
     assert np.all(phi[:, fixed == 1] == 0.0)
     fr = fe.free_dofs(fixed)
@@ -158,7 +158,7 @@ def test_buckling_matches_oracle(precision):
     T = np.zeros((n, m.nelem), np.float32)
     m.buckling_sensitivity(T)
     for i in range(n):
-        ref = buckling.buckling_sensitivity(nx, ny, nz, E, S, phi[i], lam[i])
+        ref = buckling.buckling_sensitivity(nx, ny, nz, E, S, phi[i], lam[i], h=h)
         assert np.linalg.norm(T[i] - ref) <= 1e-6 * np.linalg.norm(ref)
         assert abs(float(T[i].astype(np.float64).sum())) <= 1e-5 * float(np.abs(T[i]).sum())
     # the modes of a modal analysis replace the buckling modes
