@@ -50,9 +50,9 @@ sys.path.insert(0, ROOT)
 METRIC = "dCG solve ms & GDOF/s matvec at rel-res 1e-6, mixed vs FP64 on GB300; serve p50/p99"
 VOLUME_FRACTION = 0.9
 UNIT = "ms per topology step (dCG solve to rel-res 1e-6 + coarse setup + J + sensitivity + level-set)"
-# DRAM bytes (read + write) per launch of the FP32 apply kernel, each from one ncu capture
-# (profiles/stencil_fp32_128x64x64_dram.md, profiles/stencil_fp32_384x192x192_async_dram.md), keyed by mesh
-# and CTA shape (warps, planes, async staging); any other shape reports null.
+# DRAM bytes (read + write) per launch of the FP32 apply kernel, each from one ncu capture of the kernel at that
+# size (summarised under profiles/), keyed by mesh and CTA shape (warps, planes, async staging); any other shape
+# reports null.
 # FP32 operations of the modal hex8 apply per element (x/y butterflies 18, z butterfly 21, modal forces 42,
 # transposed z 30, y 12 and x 15 stages: 138 operations, 9 of them FMAs counted twice), and the FP32 peak from the
 # unit counts: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2070 MHz.

@@ -1,7 +1,8 @@
 """GPU parity of the CUDA path against the CPU oracle, through the C ABI.
 
-Tolerances (written here, derived in the design doc): stencil FP64 1e-13 and FP32
-2e-6 relative (max-norm against max |y|); coarse matrix 1e-12; FP64 solve
+Tolerances (written here, derived from the arithmetic of each kernel):
+stencil FP64 1e-13 and FP32 2e-6 relative (max-norm against max |y|);
+coarse matrix 1e-12; FP64 solve
 relative L2(u) <= 1e-9 and J <= 1e-10; mixed solve L2(u) <= 1e-5 and
 J <= 1e-6; sensitivities 1e-5 (mixed) and 2e-7 (FP64, float32 output);
 selection bit exact.
