@@ -1,0 +1,178 @@
+"""Host logic of the Sec. 3.8 driver (run_constrained_topology) on the CPU:
+the mesh's device calls are answered by the oracle, the AL scalars come from
+the library's host routines (Eqs. 3.11, 3.12, 3.18), and the level-set cut is
+the oracle's.  Checks steps 4 and 7-9 of Sec. 3.8 and the hard / soft split of
+Sec. 3.6 without a GPU."""
+import numpy as np
+import pytest
+
+from oracle import buckling, fe, levelset, modal, sensitivity
+from synthetic import axial_face_load, clamp_face_x0, edge_load
+
+
+@pytest.fixture(scope="module")
+def afd():
+    from paper_2203_15115_gb300 import build
+
+    build.build()
+    import paper_2203_15115_gb300 as afd
+
+    afd.lib()
+    return afd
+
+
+_MESHES = {}
+
+
+class OracleMesh:
+    """The subset of Mesh that the driver calls, computed by the oracle.  Like
+    the library's level-set update, the cut writes the new moduli into the
+    mesh (kept 1, the rest e_void)."""
+
+    class _Opt:
+        e_void = 1e-3
+
+    def __init__(self, nx, ny, nz, f, fixed):
+        self.nx, self.ny, self.nz, self.f, self.fixed = nx, ny, nz, f, fixed
+        self.nelem = nx * ny * nz
+        self.options = self._Opt()
+        self.h = len(_MESHES) + 1
+        _MESHES[self.h] = self
+        self.E = None
+        self.u = None
+        self.calls = {"solve": 0, "modal": 0, "buckling": 0}
+
+    def set_element_moduli(self, E):
+        self.E = np.asarray(E, dtype=np.float64).copy()
+        self.u = None
+
+    def solve(self, tol, warm_start=False):
+        self.calls["solve"] += 1
+        self.u = fe.solve_direct(fe.assemble(self.nx, self.ny, self.nz, self.E), self.f, self.fixed)
+        return [{"iters": 1, "rel_residual": 0.0}]
+
+    def compliance(self):
+        assert self.u is not None, "the static solution was discarded"
+        return np.array([fe.compliance(self.f, self.u)])
+
+    def pnorm_stress(self, p):
+        return np.array([sensitivity.pnorm(sensitivity.element_von_mises(self.nx, self.ny, self.nz, self.E, self.u), p)])
+
+    def sensitivity(self, kind, out):
+        out[0] = sensitivity.strain_energy(self.nx, self.ny, self.nz, self.E, self.u)
+
+    def stress_sensitivity(self, p, tol, out):
+        raise AssertionError("no stress constraint in these tests")
+
+    def modal(self, n, rho=1.0, tol=1e-6):
+        self.calls["modal"] += 1
+        lam, phi = modal.modes(self.nx, self.ny, self.nz, self.E, self.fixed, n, rho=rho)
+        self._modes = (lam, phi, rho)
+        self.u = None
+        return lam, {"steps": 1}
+
+    def eigen_sensitivity(self, out):
+        lam, phi, rho = self._modes
+        out[0] = modal.eigen_sensitivity(self.nx, self.ny, self.nz, self.E, phi[0], lam[0], rho)
+
+    def buckling(self, n, tol=1e-6):
+        assert self.u is not None, "buckling needs the static state"
+        self.calls["buckling"] += 1
+        lam, phi, S = buckling.buckling(self.nx, self.ny, self.nz, self.E, self.f, self.fixed, n)
+        self._buck = (lam, phi, S)
+        self.u = None
+        return lam, {"steps": 1}
+
+    def buckling_sensitivity(self, out):
+        lam, phi, S = self._buck
+        out[0] = buckling.buckling_sensitivity(self.nx, self.ny, self.nz, self.E, S, phi[0], lam[0])
+
+
+@pytest.fixture
+def oracle_cut(afd, monkeypatch):
+    def cut(h, fields, weights, v, casting, kept):
+        T = levelset.combine(np.asarray(fields, dtype=np.float32), np.asarray(weights, dtype=np.float64))
+        sel, tau = levelset.select_top(T, levelset.keep_count(v, T.size))
+        kept[:] = sel
+        m = _MESHES[h]
+        m.set_element_moduli(levelset.apply_topology(sel, m.options.e_void))
+        return float(tau)
+
+    monkeypatch.setattr(afd, "afd_levelset_update_fields", cut)
+
+
+def _check_steps(hist, conv=0.01):
+    """Steps 4 and 7-9 of Sec. 3.8 on the records: after a violated hard
+    constraint the step halves and the next design is the last feasible one
+    minus the new step; the target drops only when the previous analysis was
+    feasible too and J moved by at most `conv` since it."""
+    feasible_v = 1.0
+    for i in range(len(hist) - 1):
+        a, b = hist[i], hist[i + 1]
+        assert b["v"] == b["target"]
+        if a["violated"]:
+            assert b["dv"] == a["dv"] / 2
+            assert b["v"] == pytest.approx(feasible_v - b["dv"], abs=1e-12)
+        else:
+            feasible_v = a["v"]
+            if b["target"] < a["target"]:
+                assert i > 0 and not hist[i - 1]["violated"]
+                assert abs(a["J"] - hist[i - 1]["J"]) <= conv * abs(hist[i - 1]["J"])
+                assert b["target"] == pytest.approx(a["target"] - a["dv"], abs=1e-12)
+            else:
+                assert b["target"] == a["target"]
+
+
+def _replay_al(hist, name):
+    mu, gamma, g_prev = levelset.MU0, levelset.GAMMA0, 0.0
+    for k, h in enumerate(hist, start=1):
+        g = h["g"][name]
+        mu = levelset.multiplier_update(mu, gamma, g)
+        gamma = levelset.penalty_update(gamma, g, g_prev, k)
+        g_prev = g
+        assert h["mu"][name] == pytest.approx(mu, rel=1e-12, abs=1e-12)
+        assert h["gamma"][name] == pytest.approx(gamma, rel=1e-12)
+
+
+def test_hard_compliance_and_eigenvalue_steps(afd, oracle_cut):
+    nx, ny, nz = 10, 4, 3
+    f, fixed = edge_load(nx, ny, nz), clamp_face_x0(nx, ny, nz)
+    m = OracleMesh(nx, ny, nz, f, fixed)
+    res = afd.run_constrained_topology(m, np.ones(nx * ny * nz), compliance=1.6, eigen=0.9, dv0=0.1, v_min=0.3,
+                                       max_fea=25)
+    hist = res["history"]
+    assert res["stop"] in ("dv_min", "v_min", "max_fea")
+    for h in hist:
+        assert h["violated"] == (h["g"]["J"] > 0 or h["g"]["lambda"] > 0)
+    _replay_al(hist, "J")
+    _replay_al(hist, "lambda")
+    assert any(h["violated"] for h in hist) and any(b["target"] < a["target"] for a, b in zip(hist, hist[1:]))
+    _check_steps(hist)
+    # the final design is feasible for both hard constraints under the oracle
+    E = res["E"]
+    J0 = res["reference"]["J"]
+    lam0 = res["reference"]["lambda"]
+    u = fe.solve_direct(fe.assemble(nx, ny, nz, E), f, fixed)
+    assert fe.compliance(f, u) <= 1.6 * J0 * (1 + 1e-12)
+    assert modal.modes(nx, ny, nz, E, fixed, 1)[0][0] >= 0.9 * lam0 * (1 - 1e-9)
+    assert int(res["kept"].sum()) == levelset.keep_count(res["volume_fraction"], E.size)
+    # the modal analysis discards the static solution: the static fields come first, every analysis
+    assert m.calls["modal"] == m.calls["solve"] == res["fea"]
+
+
+def test_soft_buckling_never_rejects_and_unconverged_targets_stay(afd, oracle_cut):
+    nx, ny, nz = 10, 3, 2
+    f, fixed = axial_face_load(nx, ny, nz, -1.0), clamp_face_x0(nx, ny, nz)
+    m = OracleMesh(nx, ny, nz, f, fixed)
+    res = afd.run_constrained_topology(m, np.ones(nx * ny * nz), compliance=1.5, buckling=2.0, soft=("P",),
+                                       dv0=0.1, v_min=0.4, max_fea=12)
+    hist = res["history"]
+    assert all(h["g"]["P"] > 0 for h in hist)          # P >= 2 P_0 is never met ...
+    for h in hist:
+        assert h["violated"] == (h["g"]["J"] > 0)       # ... and never counts
+    _replay_al(hist, "P")
+    assert m.calls["buckling"] == res["fea"]
+    assert any(h["violated"] for h in hist)
+    _check_steps(hist)
+    with pytest.raises(ValueError):
+        afd.run_constrained_topology(m, np.ones(nx * ny * nz), compliance=1.5, soft=("J",))
