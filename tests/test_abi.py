@@ -64,3 +64,33 @@ def test_mesh_bytes_estimate_grows_with_the_mesh(afd):
     assert 0 < a < b < c
     assert b > ndof * (3 * 8 + 8 * 4)       # at least the FP64 and FP32 vectors
     assert afd.afd_mesh_bytes(0, 1, 1) == 0
+
+
+def test_product_path_fails_loudly_without_its_library(afd, monkeypatch):
+    """No CPU fallback: without the built library every call raises."""
+    monkeypatch.setattr(afd, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libafdcg.so"))
+    monkeypatch.setattr(afd, "_lib", None)
+    with pytest.raises(RuntimeError):
+        afd.lib()
+    with pytest.raises(RuntimeError):
+        afd.Mesh(4, 2, 2)
+
+
+def test_options_are_validated_before_any_device_call(afd):
+    """Bad options are refused with AFD_ERR_INVALID_ARG on any machine, GPU or
+    not; the device is touched only by a valid request."""
+    for bad in ({"stencil_warps": 12}, {"stencil_planes": -1}, {"inner_aim": 1.5}, {"nu": 0.5},
+                {"max_iter": 0}, {"e_void": 0.0}, {"precision": 7}):
+        with pytest.raises(afd.AFDError) as e:
+            afd.Mesh(4, 2, 2, **bad)
+        assert e.value.code == afd.AFD_ERR_INVALID_ARG, bad
+
+
+def test_a_valid_request_without_a_gpu_is_an_error_not_a_crash(afd):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(afd.AFDError) as e:
+        afd.Mesh(4, 2, 2)
+    assert e.value.code == afd.AFD_ERR_CUDA
