@@ -518,10 +518,10 @@ def next_rows_leg(afd, torch, dev, mesh, w, peak, peak_kind):
             "stress_sensitivity_128x64x64": {"p": 8.0, "ms": round(adj_ms, 3), "adjoint_iters": st[0]["iters"],
                                              "adjoint_rel_residual": st[0]["rel_residual"]},
             "modal_128x64x64": {"n_modes": n_modes, "tol": 1e-6, "ms": round(modal_ms, 1),
-                                "subspace_steps": info["steps"], "inner_iters": info["solve_iters"],
+                                "lobpcg_steps": info["steps"], "inner_iters": info["solve_iters"],
                                 "lambda": [float(x) for x in lam]},
             "buckling_128x64x64": {"n_modes": 2, "tol": 1e-6, "ms": round(buck_ms, 1),
-                                   "subspace_steps": binfo["steps"], "inner_iters": binfo["solve_iters"],
+                                   "lobpcg_steps": binfo["steps"], "inner_iters": binfo["solve_iters"],
                                    "load_factors": [float(x) for x in blam]}}
 
 

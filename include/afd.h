@@ -150,17 +150,20 @@ int afd_stress_sensitivity(afd_mesh* m, double p, double rel_tol, float* out, in
  * (lambda = omega^2) on the mesh's moduli and supports.  The paper gives no
  * mass matrix; M is lumped, every node of element e receiving
  * rho_e h^3 / 8 per direction with rho_e = rho * E_e (density follows the
- * modulus).  Subspace iteration on a block of n_modes + max(2, ceil(n_modes/2))
- * vectors: each step solves K Y = M X with the mesh's solver (its precision
- * and options, to min(1e-6, max(1e-10, tol/10)), started from X / lambda)
- * and takes the Rayleigh-Ritz pairs of span(Y) (FP64 Gram matrices, a small
- * generalised eigenproblem on the device).  Stops when every requested pair
- * has ||K phi - lambda M phi|| <= tol ||K phi|| (free DOFs), else after
- * max_iter steps with AFD_ERR_NOT_CONVERGED (outputs still written).
+ * modulus).  Block LOBPCG on a block of n_modes + 2 vectors, preconditioned
+ * by K^-1 from the mesh's solver (its precision and options, relative
+ * tolerance 1e-3): each step forms the residuals K phi - lambda M phi, solves
+ * for the new directions W and takes the Rayleigh-Ritz pairs of span[X, W, P]
+ * (FP64 Gram matrices; a small generalised eigenproblem on the device,
+ * directions scaled and truncated against dependence).  Stops when every
+ * requested pair has ||K phi - lambda M phi|| <= tol lambda ||M phi|| (free
+ * DOFs), else after max_iter steps with AFD_ERR_NOT_CONVERGED (outputs still
+ * written).  AFD_ERR_NAN if an eigenvalue is not positive (supports that
+ * leave a rigid-body mode).
  * n_modes in [1, 10]; rho > 0.
  * lam_out: n_modes doubles (host), ascending.  modes_out (nullable):
  * n_modes*ndof, M-orthonormal, zero on fixed DOFs, sign arbitrary.
- * iters_out / solve_iters_out (nullable): subspace steps; inner DPCG
+ * iters_out / solve_iters_out (nullable): LOBPCG steps; inner DPCG
  * iterations summed over the steps (the largest per step).
  * The load cases are kept; the static solution is discarded (afd_solve
  * again before afd_compliance or afd_sensitivity).  The modes stay in the
@@ -188,11 +191,11 @@ int afd_eigen_sensitivity(afd_mesh* m, float* out, int out_on_device);
  * and Rayleigh-Ritz on [X, W, P] (FP64 Gram matrices, directions scaled and
  * truncated against dependence on the device).  It targets the smallest
  * positive factors even when the reversed load buckles first.
- * Stops when every requested pair has ||K phi + lambda K_G phi|| <= tol ||K phi||,
+ * Stops when every requested pair has ||K_G phi - theta K phi|| <= tol |theta| ||K phi||,
  * else after max_iter steps with AFD_ERR_NOT_CONVERGED (outputs written).
  * AFD_ERR_NAN if the load gives fewer than n_modes positive factors.
  * lam_out: n_modes doubles ascending; modes_out (nullable): n_modes*ndof,
- * K-orthonormal, zero on fixed DOFs, sign arbitrary.  n_modes in [1, 3].
+ * K-orthonormal, zero on fixed DOFs, sign arbitrary.  n_modes in [1, 10].
  * The load cases are kept; the static solution is discarded.  The modes
  * stay in the mesh for afd_buckling_sensitivity (a later afd_modal replaces
  * them, and the other way round). */

@@ -156,19 +156,19 @@ struct afd_mesh {
   float* lsbuf = nullptr;      // caller fields of afd_levelset_update_fields
   size_t lsbuf_cap = 0;
   int adj_cap = 0;
-  // modal analysis: Ritz block X, K Y, K X (or M Y), lumped mass, Gram partials,
-  // small matrices; the last result (modes = first modal_n rows of mX)
-  double *mX = nullptr, *mKY = nullptr, *mKX = nullptr, *mmass = nullptr, *mparts = nullptr;
+  // eigen analyses: the modes (first modal_n rows of mX), the lumped mass (or
+  // free-DOF mask), Gram partials, small matrices, Ritz values
+  double *mX = nullptr, *mmass = nullptr, *mparts = nullptr;
   double *mA = nullptr, *mB = nullptr, *mV = nullptr, *mlam = nullptr;
   int* minfo = nullptr;
   int modal_cap = 0, modal_n = 0;
   double modal_rho = 1.0;
   bool modal_valid = false;
-  // buckling: the state stress (6 x nelem), Ritz values / load factors
+  // buckling: the state stress (6 x nelem); the load factors
   double *bS6 = nullptr, *bcoef = nullptr;
   bool buckling_valid = false;
-  // LOBPCG blocks [X | W | P] and their K and K_G images, double-buffered (3 kp rows each)
-  double *lS[2] = {nullptr, nullptr}, *lKS[2] = {nullptr, nullptr}, *lGS[2] = {nullptr, nullptr};
+  // LOBPCG blocks [X | W | P] and their A and B images, double-buffered (3 kp rows each)
+  double *lS[2] = {nullptr, nullptr}, *lBS[2] = {nullptr, nullptr}, *lAS[2] = {nullptr, nullptr};
   int lobpcg_cap = 0;
   int nsplit_aw = 1;
   bool coarse_valid = false;
@@ -1002,10 +1002,10 @@ void afd_destroy(afd_mesh* m) {
   dfree(m->grec); dfree(m->gcount); dfree(m->upart);
   dfree(m->ppart); dfree(m->prec); dfree(m->gbar); dfree(m->ptime);
   dfree(m->lam64); dfree(m->gadj); dfree(m->dsig); dfree(m->pn_d); dfree(m->lsbuf);
-  dfree(m->mX); dfree(m->mKY); dfree(m->mKX); dfree(m->mmass); dfree(m->mparts);
+  dfree(m->mX); dfree(m->mmass); dfree(m->mparts);
   dfree(m->mA); dfree(m->mB); dfree(m->mV); dfree(m->mlam); dfree(m->minfo);
   dfree(m->bS6); dfree(m->bcoef);
-  for (int q = 0; q < 2; ++q) { dfree(m->lS[q]); dfree(m->lKS[q]); dfree(m->lGS[q]); }
+  for (int q = 0; q < 2; ++q) { dfree(m->lS[q]); dfree(m->lBS[q]); dfree(m->lAS[q]); }
   if (m->ev) cudaEventDestroy(m->ev);
   if (m->s) cudaStreamDestroy(m->s);
   delete m;
@@ -1402,7 +1402,7 @@ int afd_stress_sensitivity(afd_mesh* m, double p, double rel_tol, float* out, in
 
 // ---------------------------------------------------------------------------
 // Modal analysis (the eigenvalue constraint of Sec. 3.8; Eq. 3.4 needs its
-// modes): subspace iteration with Rayleigh-Ritz on the mesh's own solver.
+// modes) and linear buckling (Eq. 3.5): block LOBPCG on the mesh's own solver.
 // ---------------------------------------------------------------------------
 constexpr int MODAL_GRAM_BLOCKS = 304;
 
@@ -1445,100 +1445,23 @@ static int upload_geo_table(afd_mesh* m) {
   return AFD_OK;
 }
 
-// The subspace iteration of afd_modal (K phi = lambda M phi, M the lumped
-// mass in mmass).  Each step: the right-hand sides M X into the solver's load
-// buffer, Y = K^-1 M X by the mesh's solver (started from X / lambda), the
-// Rayleigh-Ritz pairs of span(Y) from FP64 Gram matrices Y^T K Y and Y^T M Y,
-// the Ritz vectors and their residuals.  vals: the kp Ritz values (ascending).
-// The caller keeps the load cases.
-static int subspace_eigs(afd_mesh* m, int n_modes, int kp, double tol, int max_iter, std::vector<double>& vals,
-                         bool& converged, int& steps, int& solve_iters) {
-  const Grid& g = m->gr;
-  const dim3 vgrid(grid_blocks(g.ndof, 256, 2048), kp);
-  k_modal_start<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, 0x2203151150ull, m->mmass, m->mX); m->launches++;
-  CK(cudaGetLastError());
-  const double solve_tol = std::min(1e-6, std::max(1e-10, 0.1 * tol));
-  vals.assign(kp, 0.0);
-  std::vector<double> sc(kp, 0.0);
-  steps = solve_iters = 0;
-  converged = false;
-  TRY(ensure_partials(m, (size_t)kp * 2 * RED_BLOCKS));
-  for (int it = 0; it < max_iter && !converged; ++it) {
-    // right-hand sides M X in the solver's load buffer, their norms
-    k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->mX, m->f64); m->launches++;
-    TRY(ensure_partials(m, (size_t)kp * 2 * RED_BLOCKS));
-    k_dot<double, double><<<dim3(RED_BLOCKS, kp), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->f64, m->f64, m->partials);
-    m->launches++;
-    CK(cudaGetLastError());
-    std::vector<double> bb;
-    TRY(reduce_partials_host(m, kp, RED_BLOCKS, bb));
-    m->nrhs = kp;
-    m->fnorm.assign(kp, 0.0);
-    for (int r = 0; r < kp; ++r) m->fnorm[r] = std::sqrt(bb[r]);
-    // Y = K^-1 M X, started from X / lambda once Ritz values exist
-    int warm = 0;
-    if (it > 0) {
-      for (int r = 0; r < kp; ++r) sc[r] = vals[r] > 0.0 ? 1.0 / vals[r] : 0.0;
-      CK(cudaMemcpyAsync(m->mlam, sc.data(), kp * sizeof(double), cudaMemcpyHostToDevice, m->s));
-      k_scale_rhs<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mlam, m->mX, m->u64); m->launches++;
-      m->has_solution = true;
-      warm = 1;
-    }
-    std::vector<afd_stats> st(kp);
-    const int src = afd_solve(m, solve_tol, warm, st.data(), nullptr, 0);
-    if (src != AFD_OK && src != AFD_ERR_NOT_CONVERGED) return src;
-    int mx = 0;
-    for (int r = 0; r < kp; ++r) mx = std::max(mx, st[r].iters);
-    solve_iters += mx;
-    // Rayleigh-Ritz on span(Y) (K Y by the FP64 stencil)
-    TRY((launch_stencil<double, ST_APPLY, double>(m, m->u64, m->mKY, m->w64.E, nullptr, nullptr, nullptr, nullptr,
-                                                    kp, m->w64.K)));
-    TRY(modal_gram(m, kp, m->u64, m->mKY, m->mA));
-    k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, m->u64, m->mKX); m->launches++;
-    TRY(modal_gram(m, kp, m->u64, m->mKX, m->mB));
-    k_small_geig<<<1, 32, 0, m->s>>>(kp, m->mA, m->mB, m->mlam, m->mV, m->minfo); m->launches++;
-    const unsigned cb = grid_blocks(g.ndof, 256, 2048);
-    k_ritz_combine<<<cb, 256, 0, m->s>>>(g.ndof, g.vs, kp, m->u64, m->mV, m->mX); m->launches++;
-    k_ritz_combine<<<cb, 256, 0, m->s>>>(g.ndof, g.vs, kp, m->mKY, m->mV, m->mKX); m->launches++;
-    k_modal_residual<<<dim3(RED_BLOCKS, n_modes), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->mKX, m->mX, m->mmass,
-                                                                        m->mlam, m->partials); m->launches++;
-    CK(cudaGetLastError());
-    int info = 0;
-    CK(cudaMemcpyAsync(vals.data(), m->mlam, kp * sizeof(double), cudaMemcpyDeviceToHost, m->s));
-    CK(cudaMemcpyAsync(&info, m->minfo, sizeof(int), cudaMemcpyDeviceToHost, m->s));
-    std::vector<double> hp((size_t)n_modes * RED_BLOCKS * 2);
-    CK(cudaMemcpyAsync(hp.data(), m->partials, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, m->s));
-    CK(cudaStreamSynchronize(m->s));
-    if (info != 0)
-      return fail(AFD_ERR_NAN, "Rayleigh-Ritz step failed (%s)",
-                  info == 1 ? "the Gram matrix is not positive definite" : "Jacobi sweeps did not converge");
-    steps = it + 1;
-    converged = true;
-    for (int r = 0; r < n_modes; ++r) {
-      double e2 = 0.0, k2 = 0.0;
-      for (int b = 0; b < RED_BLOCKS; ++b) {
-        e2 += hp[((size_t)r * RED_BLOCKS + b) * 2];
-        k2 += hp[((size_t)r * RED_BLOCKS + b) * 2 + 1];
-      }
-      if (!std::isfinite(e2) || !std::isfinite(vals[r])) return fail(AFD_ERR_NAN, "eigen iteration is not finite");
-      if (!(std::sqrt(e2) <= tol * std::sqrt(k2))) converged = false;
-    }
-  }
-  return AFD_OK;
-}
-
-// Buckling by block LOBPCG on G phi = theta K phi (G = K_G, theta = -mu =
-// -1/lambda), for the smallest theta: the most negative theta is the smallest
-// positive load factor.  Subspace iteration would follow the largest |theta|,
-// and under many loads the reversed load's factors (theta > 0) are the larger
-// ones.  Each step: the residual block R = G X - K X Theta, W = K^-1 R by the
-// mesh's solver (the preconditioner; relative tolerance 1e-3), K W and G W,
-// then Rayleigh-Ritz on span[X, W, P] (rows contiguous in lS) with FP64 Gram
-// matrices and the truncating small eigensolver; X and the new direction P
-// (the W, P part of the Ritz coefficients) are rebuilt with their K and G
-// images into the other buffer.  vals: the kp Ritz values theta.
-static int lobpcg_buckling(afd_mesh* m, int n_modes, int kp, double tol, int max_iter, std::vector<double>& vals,
-                           bool& converged, int& steps, int& solve_iters) {
+// Block LOBPCG for the kp smallest theta of A phi = theta B phi on the free
+// DOFs, preconditioned by K^-1 (the mesh's solver, relative tolerance 1e-3).
+//   EIG_MODAL:    A = K, B = M (lumped mass in mmass), theta = lambda.
+//   EIG_BUCKLING: A = K_G, B = K, theta = -1/lambda, so the most negative
+//                 theta is the smallest positive load factor.  (Subspace
+//                 iteration would follow the largest |theta|, and under many
+//                 loads the reversed load's factors, theta > 0, are larger.)
+// Each step: the residual block R = A X - B X Theta, W = K^-1 R, the images
+// A W and B W, then Rayleigh-Ritz on span[X, W, P] (rows contiguous in lS,
+// images in lAS / lBS) with FP64 Gram matrices and the truncating small
+// eigensolver; X and the new direction P (the W, P part of the Ritz
+// coefficients) are rebuilt with their images into the other buffer.
+// Converged when |R_r| <= tol |theta_r| |B X_r| for the first n_modes.
+// vals: the kp Ritz values theta; the B-normalised Ritz vectors end in mX.
+enum EigKind { EIG_MODAL = 0, EIG_BUCKLING = 1 };
+static int lobpcg(afd_mesh* m, EigKind kind, int n_modes, int kp, double tol, int max_iter, std::vector<double>& vals,
+                  bool& converged, int& steps, int& solve_iters) {
   const Grid& g = m->gr;
   const size_t blk = (size_t)kp * g.vs;
   const dim3 vgrid(grid_blocks(g.ndof, 256, 2048), kp);
@@ -1549,16 +1472,21 @@ static int lobpcg_buckling(afd_mesh* m, int n_modes, int kp, double tol, int max
   converged = false;
   vals.assign(kp, 0.0);
   std::vector<double> V;
-  auto images = [&](const double* Xs, double* KXs, double* GXs) -> int {   // K and G of kp rows
+  auto images = [&](const double* Xs, double* AXs, double* BXs) -> int {   // A and B of kp rows
+    double* KXs = kind == EIG_MODAL ? AXs : BXs;
     TRY((launch_stencil<double, ST_APPLY, double>(m, Xs, KXs, m->w64.E, nullptr, nullptr, nullptr, nullptr, kp,
                                                     m->w64.K)));
-    k_geo_apply<<<ngrid, 256, 0, m->s>>>(g, m->bS6, m->fixed, 1.0, Xs, GXs); m->launches++;
+    if (kind == EIG_MODAL) {
+      k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, Xs, BXs); m->launches++;
+    } else {
+      k_geo_apply<<<ngrid, 256, 0, m->s>>>(g, m->bS6, m->fixed, 1.0, Xs, AXs); m->launches++;
+    }
     CK(cudaGetLastError());
     return AFD_OK;
   };
   auto rayleigh_ritz = [&](int mrows, std::vector<double>& th, std::vector<double>& Vh) -> int {
-    TRY(modal_gram(m, mrows, m->lS[cur], m->lGS[cur], m->mA));
-    TRY(modal_gram(m, mrows, m->lS[cur], m->lKS[cur], m->mB));
+    TRY(modal_gram(m, mrows, m->lS[cur], m->lAS[cur], m->mA));
+    TRY(modal_gram(m, mrows, m->lS[cur], m->lBS[cur], m->mB));
     k_small_geig_robust<<<1, 32, 0, m->s>>>(mrows, kp, m->mA, m->mB, m->mlam, m->mV, m->minfo); m->launches++;
     int info = 0;
     th.assign(kp, 0.0);
@@ -1571,14 +1499,14 @@ static int lobpcg_buckling(afd_mesh* m, int n_modes, int kp, double tol, int max
       return fail(AFD_ERR_NAN, "Rayleigh-Ritz step failed (%s)",
                   info == 3 ? "the block lost rank" : "Jacobi sweeps did not converge");
     for (double t : th)
-      if (!std::isfinite(t)) return fail(AFD_ERR_NAN, "buckling iteration is not finite");
+      if (!std::isfinite(t)) return fail(AFD_ERR_NAN, "eigen iteration is not finite");
     return AFD_OK;
   };
   // X and P (with_p) of the next buffer from the coefficients of span[X, W, P]
   auto rebuild = [&](int mrows, const std::vector<double>& Vh, bool with_p) -> int {
     const int nxt = 1 - cur;
-    const double* src[3] = {m->lS[cur], m->lKS[cur], m->lGS[cur]};
-    double* dst[3] = {m->lS[nxt], m->lKS[nxt], m->lGS[nxt]};
+    const double* src[3] = {m->lS[cur], m->lAS[cur], m->lBS[cur]};
+    double* dst[3] = {m->lS[nxt], m->lAS[nxt], m->lBS[nxt]};
     CK(cudaMemcpyAsync(m->mV, Vh.data(), Vh.size() * sizeof(double), cudaMemcpyHostToDevice, m->s));
     for (int q = 0; q < 3; ++q) {
       k_block_combine<<<cb, 256, 0, m->s>>>(g.ndof, g.vs, mrows, kp, src[q], m->mV, dst[q]); m->launches++;
@@ -1599,7 +1527,7 @@ static int lobpcg_buckling(afd_mesh* m, int n_modes, int kp, double tol, int max
   };
   // start: random X, Rayleigh-Ritz on X alone
   k_modal_start<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, 0x2203151150ull, m->mmass, m->lS[cur]); m->launches++;
-  TRY(images(m->lS[cur], m->lKS[cur], m->lGS[cur]));
+  TRY(images(m->lS[cur], m->lAS[cur], m->lBS[cur]));
   TRY(rayleigh_ritz(kp, vals, V));
   TRY(rebuild(kp, V, false));
   bool have_p = false;
@@ -1608,7 +1536,7 @@ static int lobpcg_buckling(afd_mesh* m, int n_modes, int kp, double tol, int max
     // residual block into the solver's load buffer, its norms, the convergence test
     CK(cudaMemcpyAsync(m->bcoef, vals.data(), kp * sizeof(double), cudaMemcpyHostToDevice, m->s));
     TRY(ensure_partials(m, (size_t)kp * 2 * RED_BLOCKS));
-    k_lobpcg_residual<<<dim3(RED_BLOCKS, kp), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->lGS[cur], m->lKS[cur],
+    k_lobpcg_residual<<<dim3(RED_BLOCKS, kp), RED_THREADS, 0, m->s>>>(g.ndof, g.vs, m->lAS[cur], m->lBS[cur],
                                                                      m->mmass, m->bcoef, m->f64, m->partials);
     m->launches++;
     CK(cudaGetLastError());
@@ -1636,7 +1564,7 @@ static int lobpcg_buckling(afd_mesh* m, int n_modes, int kp, double tol, int max
     for (int r = 0; r < kp; ++r) mx = std::max(mx, st[r].iters);
     solve_iters += mx;
     CK(cudaMemcpyAsync(m->lS[cur] + blk, m->u64, blk * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
-    TRY(images(m->lS[cur] + blk, m->lKS[cur] + blk, m->lGS[cur] + blk));
+    TRY(images(m->lS[cur] + blk, m->lAS[cur] + blk, m->lBS[cur] + blk));
     const int mrows = have_p ? 3 * kp : 2 * kp;
     TRY(rayleigh_ritz(mrows, vals, V));
     TRY(rebuild(mrows, V, true));
@@ -1648,17 +1576,17 @@ static int lobpcg_buckling(afd_mesh* m, int n_modes, int kp, double tol, int max
   return AFD_OK;
 }
 
-// Buffers of the eigensolvers for a block of kp vectors (buckling adds the
-// state stress, the Ritz values / load factors and the LOBPCG blocks).
+// Buffers of the eigensolvers for a block of kp vectors: the modes, the mass
+// (or free-DOF mask), the small matrices, the LOBPCG blocks [X, W, P] with
+// their A and B images (two of each), and for buckling the state stress and
+// the load factors.
 static int ensure_eig_buffers(afd_mesh* m, int kp, bool buckling) {
   const Grid& g = m->gr;
   if (m->modal_cap < kp) {
-    dfree(m->mX); dfree(m->mKY); dfree(m->mKX); dfree(m->mmass); dfree(m->mparts);
+    dfree(m->mX); dfree(m->mmass); dfree(m->mparts);
     dfree(m->mA); dfree(m->mB); dfree(m->mV); dfree(m->mlam); dfree(m->minfo);
     m->modal_cap = 0;
     TRY(dalloc(&m->mX, (size_t)kp * g.vs));
-    TRY(dalloc(&m->mKY, (size_t)kp * g.vs));
-    TRY(dalloc(&m->mKX, (size_t)kp * g.vs));
     TRY(dalloc(&m->mmass, (size_t)g.vs));
     TRY(dalloc(&m->mparts, (size_t)MODAL_GRAM_BLOCKS * MODAL_MAX * MODAL_MAX));
     TRY(dalloc(&m->mA, (size_t)MODAL_MAX * MODAL_MAX));
@@ -1668,15 +1596,15 @@ static int ensure_eig_buffers(afd_mesh* m, int kp, bool buckling) {
     TRY(dalloc(&m->minfo, 1));
     m->modal_cap = kp;
   }
-  if (buckling) {
-    if (!m->bS6) TRY(dalloc(&m->bS6, (size_t)6 * g.nelem));
-    if (!m->bcoef) TRY(dalloc(&m->bcoef, (size_t)MODAL_MAX));
+  if (!m->bcoef) TRY(dalloc(&m->bcoef, (size_t)MODAL_MAX));
+  if (buckling && !m->bS6) TRY(dalloc(&m->bS6, (size_t)6 * g.nelem));
+  {
     if (m->lobpcg_cap < kp) {
       for (int q = 0; q < 2; ++q) {
-        dfree(m->lS[q]); dfree(m->lKS[q]); dfree(m->lGS[q]);
+        dfree(m->lS[q]); dfree(m->lBS[q]); dfree(m->lAS[q]);
         TRY(dalloc(&m->lS[q], (size_t)3 * kp * g.vs));
-        TRY(dalloc(&m->lKS[q], (size_t)3 * kp * g.vs));
-        TRY(dalloc(&m->lGS[q], (size_t)3 * kp * g.vs));
+        TRY(dalloc(&m->lBS[q], (size_t)3 * kp * g.vs));
+        TRY(dalloc(&m->lAS[q], (size_t)3 * kp * g.vs));
       }
       m->lobpcg_cap = kp;
     }
@@ -1708,10 +1636,13 @@ static int with_saved_loads(afd_mesh* m, F&& body) {
   return rc;
 }
 
+// The LOBPCG block: the requested modes and two guard vectors; the
+// Rayleigh-Ritz basis [X, W, P] holds 3 kp <= MODAL_MAX vectors.
+constexpr int EIG_MAX_MODES = MODAL_MAX / 3 - 2;
 static int eig_block(int n_modes, int& kp) {
-  kp = n_modes + std::max(2, (n_modes + 1) / 2);
-  if (n_modes < 1 || kp > MODAL_MAX)
-    return fail(AFD_ERR_INVALID_ARG, "n_modes must be in [1, %d]", MODAL_MAX - 2 - (MODAL_MAX - 2) / 3);
+  kp = n_modes + 2;
+  if (n_modes < 1 || n_modes > EIG_MAX_MODES)
+    return fail(AFD_ERR_INVALID_ARG, "n_modes must be in [1, %d]", EIG_MAX_MODES);
   return AFD_OK;
 }
 
@@ -1739,7 +1670,9 @@ int afd_modal(afd_mesh* m, int n_modes, double rho, double tol, int max_iter, do
                                                                       m->mmass); m->launches++;
     std::vector<double> vals;
     int steps = 0, solve_iters = 0;
-    TRY(subspace_eigs(m, n_modes, kp, tol, max_iter, vals, converged, steps, solve_iters));
+    TRY(lobpcg(m, EIG_MODAL, n_modes, kp, tol, max_iter, vals, converged, steps, solve_iters));
+    for (int r = 0; r < n_modes; ++r)
+      if (!(vals[r] > 0.0)) return fail(AFD_ERR_NAN, "a non-positive eigenvalue: the supports leave a rigid mode");
     for (int r = 0; r < n_modes; ++r) lam_out[r] = vals[r];
     if (modes_out)
       CK(cudaMemcpy2DAsync(modes_out, (size_t)g.ndof * sizeof(double), m->mX, (size_t)g.vs * sizeof(double),
@@ -1760,8 +1693,8 @@ int afd_modal(afd_mesh* m, int n_modes, double rho, double tol, int max_iter, do
 int afd_buckling(afd_mesh* m, int n_modes, double tol, int max_iter, double* lam_out, double* modes_out,
                  int modes_on_device, int* iters_out, int* solve_iters_out) {
   if (!m || !lam_out) return fail(AFD_ERR_INVALID_ARG, "null argument");
-  const int kp = n_modes + 2;
-  if (n_modes < 1 || 3 * kp > MODAL_MAX) return fail(AFD_ERR_INVALID_ARG, "n_modes must be in [1, 3]");
+  int kp = 0;
+  TRY(eig_block(n_modes, kp));
   if (!(tol > 0.0) || !std::isfinite(tol) || max_iter < 1) return fail(AFD_ERR_INVALID_ARG, "bad tol / max_iter");
   if (!m->has_solution) return fail(AFD_ERR_STATE, "no static solution: afd_solve first (load case 0 is the state)");
   DeviceGuard dg(m->device);
@@ -1792,7 +1725,7 @@ int afd_buckling(afd_mesh* m, int n_modes, double tol, int max_iter, double* lam
     m->launches++;
     std::vector<double> vals;
     int steps = 0, solve_iters = 0;
-    TRY(lobpcg_buckling(m, n_modes, kp, tol, max_iter, vals, converged, steps, solve_iters));
+    TRY(lobpcg(m, EIG_BUCKLING, n_modes, kp, tol, max_iter, vals, converged, steps, solve_iters));
     for (int r = 0; r < n_modes; ++r)
       if (!(vals[r] < 0.0)) return fail(AFD_ERR_NAN, "fewer than %d positive buckling factors for this load", n_modes);
     std::vector<double> lam(n_modes);

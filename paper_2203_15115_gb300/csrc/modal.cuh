@@ -1,8 +1,8 @@
-// Modal analysis on the deflated solver (the eigenvalue constraint of Sec. 3.8
-// and its topological sensitivity, Eq. 3.4): the lowest eigenpairs of
-// K_ff phi = lambda M_ff phi with a lumped mass, by subspace iteration -- each
-// step solves K Y = M X for a block of vectors with the batched solver and
-// takes the Rayleigh-Ritz pairs of span(Y).
+// Modal analysis (the eigenvalue constraint of Sec. 3.8 and its topological
+// sensitivity, Eq. 3.4: K_ff phi = lambda M_ff phi with a lumped mass) and
+// linear buckling (Eq. 3.5: (K + lambda K_G) phi = 0) on the deflated solver:
+// block LOBPCG for the smallest eigenvalues of a pencil (A, B), with K^-1 by
+// the batched solver as the preconditioner.
 //
 // Mass model (the paper gives none): every node of element e receives
 // rho_e h^3 / 8 per direction with rho_e = rho E_e (density follows the
@@ -15,7 +15,7 @@
 
 namespace afd {
 
-constexpr int MODAL_MAX = 16;   // largest block of the subspace iteration
+constexpr int MODAL_MAX = 36;   // largest Rayleigh-Ritz basis (3 blocks [X, W, P] of up to 12 vectors)
 
 // Lumped mass per DOF (zero on fixed DOFs): m_n = (rho h^3 / 8) sum_{e at n} E_e.
 __global__ void k_lumped_mass(Grid gr, const double* __restrict__ Emod, double rho_h3_8,
@@ -53,8 +53,7 @@ __global__ void k_modal_start(int ndof, int vs, uint64_t seed, const double* __r
     X[(size_t)r * vs + d] = mass[d] > 0.0 ? splitmix_unit(seed, (uint64_t)r * ndof + d) : 0.0;
 }
 
-// B[r] = M X[r] (diagonal mass); with inv = true, B[r] = X[r] * s[r] (the warm
-// start X / lambda of the next solve).
+// B[r] = M X[r] (diagonal mass).
 __global__ void k_mass_apply(int ndof, int vs, const double* __restrict__ mass, const double* __restrict__ X,
                              double* __restrict__ B) {
   const int r = blockIdx.y;
@@ -62,26 +61,19 @@ __global__ void k_mass_apply(int ndof, int vs, const double* __restrict__ mass, 
   for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x)
     B[off + d] = mass[d] * X[off + d];
 }
-__global__ void k_scale_rhs(int ndof, int vs, const double* __restrict__ s, const double* __restrict__ X,
-                            double* __restrict__ Y) {
-  const int r = blockIdx.y;
-  const size_t off = (size_t)r * vs;
-  const double sr = s[r];
-  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x)
-    Y[off + d] = sr * X[off + d];
-}
-
 // Gram matrix partials: parts[b][i kp + j] = sum over this block's DOFs of
-// Y[i] Z[j], in a fixed order (tiles of GRAM_T DOFs through shared memory,
-// thread i kp + j accumulating its pair).  Reduced by k_gram_final.
+// Y[i] Z[j], in a fixed order (tiles of GRAM_T DOFs through shared memory;
+// thread t accumulates the pairs t, t + 256, ...).  Reduced by k_gram_final.
 constexpr int GRAM_T = 64;
+constexpr int GRAM_PAIRS = (MODAL_MAX * MODAL_MAX + 255) / 256;   // pairs per thread
 __global__ void __launch_bounds__(256) k_gram(int ndof, int vs, int kp, const double* __restrict__ Y,
                                               const double* __restrict__ Z, double* __restrict__ parts) {
   __shared__ double ys[MODAL_MAX][GRAM_T + 1];
   __shared__ double zs[MODAL_MAX][GRAM_T + 1];
   const int t = threadIdx.x, np = kp * kp;
-  const int pi = t / kp, pj = t % kp;
-  double acc = 0.0;
+  double acc[GRAM_PAIRS];
+#pragma unroll
+  for (int u = 0; u < GRAM_PAIRS; ++u) acc[u] = 0.0;
   for (int base = blockIdx.x * GRAM_T; base < ndof; base += gridDim.x * GRAM_T) {
     for (int q = t; q < kp * GRAM_T; q += blockDim.x) {
       const int r = q / GRAM_T, c = q % GRAM_T, d = base + c;
@@ -89,147 +81,72 @@ __global__ void __launch_bounds__(256) k_gram(int ndof, int vs, int kp, const do
       zs[r][c] = d < ndof ? Z[(size_t)r * vs + d] : 0.0;
     }
     __syncthreads();
-    if (t < np)
-      for (int c = 0; c < GRAM_T; ++c) acc = fma(ys[pi][c], zs[pj][c], acc);
+#pragma unroll
+    for (int u = 0; u < GRAM_PAIRS; ++u) {
+      const int pr = t + 256 * u;
+      if (pr < np) {
+        const int pi = pr / kp, pj = pr % kp;
+        double a = acc[u];
+        for (int c = 0; c < GRAM_T; ++c) a = fma(ys[pi][c], zs[pj][c], a);
+        acc[u] = a;
+      }
+    }
     __syncthreads();
   }
-  if (t < np) parts[(size_t)blockIdx.x * np + t] = acc;
+#pragma unroll
+  for (int u = 0; u < GRAM_PAIRS; ++u) {
+    const int pr = t + 256 * u;
+    if (pr < np) parts[(size_t)blockIdx.x * np + pr] = acc[u];
+  }
 }
 __global__ void k_gram_final(int nparts, int np, const double* __restrict__ parts, double* __restrict__ out) {
-  const int t = threadIdx.x;
-  if (t >= np) return;
-  double s = 0.0;
-  for (int b = 0; b < nparts; ++b) s += parts[(size_t)b * np + t];
-  out[t] = s;
-}
-
-// The small generalised symmetric eigenproblem A v = lambda B v (kp x kp,
-// row-major, B SPD) of the Rayleigh-Ritz step, by one thread: Cholesky
-// B = L L^T, C = L^-1 A L^-T, cyclic Jacobi rotations on C until every
-// off-diagonal entry is below 1e-15 of the diagonal scale (at most 64 sweeps),
-// then V = L^-T Q, eigenvalues ascending.  V^T B V = I.  info: 0 ok, 1 B not
-// positive definite, 2 no convergence.
-__global__ void k_small_geig(int kp, const double* __restrict__ A, const double* __restrict__ Bm,
-                             double* __restrict__ lam, double* __restrict__ V, int* info) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double L[MODAL_MAX][MODAL_MAX], C[MODAL_MAX][MODAL_MAX], Q[MODAL_MAX][MODAL_MAX];
-  const int n = kp;
-  *info = 0;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) L[i][j] = 0.0;
-  for (int j = 0; j < n; ++j) {                        // Cholesky, lower
-    double d = Bm[j * n + j];
-    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-    if (!(d > 0.0)) { *info = 1; return; }
-    L[j][j] = sqrt(d);
-    for (int i = j + 1; i < n; ++i) {
-      double s = Bm[i * n + j];
-      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-      L[i][j] = s / L[j][j];
-    }
-  }
-  // W = L^-1 A (forward substitution per column), then C = W L^-T (per row)
-  for (int c = 0; c < n; ++c)
-    for (int i = 0; i < n; ++i) {
-      double s = A[i * n + c];
-      for (int k = 0; k < i; ++k) s -= L[i][k] * C[k][c];
-      C[i][c] = s / L[i][i];
-    }
-  for (int r = 0; r < n; ++r)
-    for (int i = 0; i < n; ++i) {
-      double s = C[r][i];
-      for (int k = 0; k < i; ++k) s -= L[i][k] * Q[r][k];
-      Q[r][i] = s / L[i][i];
-    }
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) C[i][j] = 0.5 * (Q[i][j] + Q[j][i]);   // symmetric to rounding
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) Q[i][j] = i == j ? 1.0 : 0.0;
-  bool conv = false;
-  for (int sweep = 0; sweep < 64 && !conv; ++sweep) {
-    double scale = 0.0;
-    for (int i = 0; i < n; ++i) scale = fmax(scale, fabs(C[i][i]));
-    conv = true;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        if (fabs(C[p][q]) <= 1e-15 * scale) continue;
-        conv = false;
-        // rotation that zeroes C[p][q] (Rutishauser's form)
-        const double theta = (C[q][q] - C[p][p]) / (2.0 * C[p][q]);
-        const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double cs = 1.0 / sqrt(tt * tt + 1.0), sn = tt * cs;
-        for (int k = 0; k < n; ++k) {                  // C <- C J (columns p, q)
-          const double a = C[k][p], b = C[k][q];
-          C[k][p] = cs * a - sn * b;
-          C[k][q] = sn * a + cs * b;
-        }
-        for (int k = 0; k < n; ++k) {                  // C <- J^T C (rows p, q)
-          const double a = C[p][k], b = C[q][k];
-          C[p][k] = cs * a - sn * b;
-          C[q][k] = sn * a + cs * b;
-        }
-        for (int k = 0; k < n; ++k) {                  // Q <- Q J
-          const double a = Q[k][p], b = Q[k][q];
-          Q[k][p] = cs * a - sn * b;
-          Q[k][q] = sn * a + cs * b;
-        }
-      }
-  }
-  if (!conv) *info = 2;
-  // ascending order (selection sort on the diagonal, columns of Q follow)
-  int ord[MODAL_MAX];
-  for (int i = 0; i < n; ++i) ord[i] = i;
-  for (int i = 0; i < n; ++i)
-    for (int j = i + 1; j < n; ++j)
-      if (C[ord[j]][ord[j]] < C[ord[i]][ord[i]]) {
-        const int t = ord[i];
-        ord[i] = ord[j];
-        ord[j] = t;
-      }
-  // V = L^-T Q (back substitution per column)
-  for (int c = 0; c < n; ++c) {
-    const int oc = ord[c];
-    lam[c] = C[oc][oc];
-    for (int i = n - 1; i >= 0; --i) {
-      double s = Q[i][oc];
-      for (int k = i + 1; k < n; ++k) s -= L[k][i] * V[k * n + c];
-      V[i * n + c] = s / L[i][i];
-    }
+  for (int t = threadIdx.x; t < np; t += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += parts[(size_t)b * np + t];
+    out[t] = s;
   }
 }
 
-// Cyclic Jacobi on a symmetric n x n matrix C (n <= MODAL_MAX) in place:
-// eigenvalues on the diagonal, eigenvectors in the columns of Q.  At most 64
-// sweeps; returns false without convergence.
+// Cyclic Jacobi on a symmetric n x n matrix C (n <= MODAL_MAX) in place,
+// run by one warp on shared-memory matrices: every lane takes the same
+// rotation (p, q) and applies it to the columns / rows k = lane, lane + 32.
+// Eigenvalues end on the diagonal, eigenvectors in the columns of Q.  At most
+// 64 sweeps; returns false (in every lane) without convergence.
 __device__ bool jacobi_sym(int n, double (&C)[MODAL_MAX][MODAL_MAX], double (&Q)[MODAL_MAX][MODAL_MAX]) {
+  const int l = threadIdx.x & 31;
   for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) Q[i][j] = i == j ? 1.0 : 0.0;
+    for (int k = l; k < n; k += 32) Q[i][k] = i == k ? 1.0 : 0.0;
+  __syncwarp();
   for (int sweep = 0; sweep < 64; ++sweep) {
     double scale = 0.0;
     for (int i = 0; i < n; ++i) scale = fmax(scale, fabs(C[i][i]));
     bool conv = true;
     for (int p = 0; p < n - 1; ++p)
       for (int q = p + 1; q < n; ++q) {
-        if (fabs(C[p][q]) <= 1e-15 * scale) continue;
+        const double cpq = C[p][q];
+        if (fabs(cpq) <= 1e-15 * scale) continue;   // the same decision in every lane
         conv = false;
-        const double theta = (C[q][q] - C[p][p]) / (2.0 * C[p][q]);
+        const double theta = (C[q][q] - C[p][p]) / (2.0 * cpq);
         const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
         const double cs = 1.0 / sqrt(tt * tt + 1.0), sn = tt * cs;
-        for (int k = 0; k < n; ++k) {
+        __syncwarp();   // every lane has read C[p][p], C[p][q], C[q][q]
+        for (int k = l; k < n; k += 32) {
           const double a = C[k][p], b = C[k][q];
           C[k][p] = cs * a - sn * b;
           C[k][q] = sn * a + cs * b;
         }
-        for (int k = 0; k < n; ++k) {
+        __syncwarp();
+        for (int k = l; k < n; k += 32) {
           const double a = C[p][k], b = C[q][k];
           C[p][k] = cs * a - sn * b;
           C[q][k] = sn * a + cs * b;
         }
-        for (int k = 0; k < n; ++k) {
+        for (int k = l; k < n; k += 32) {
           const double a = Q[k][p], b = Q[k][q];
           Q[k][p] = cs * a - sn * b;
           Q[k][q] = sn * a + cs * b;
         }
+        __syncwarp();
       }
     if (conv) return true;
   }
@@ -238,26 +155,34 @@ __device__ bool jacobi_sym(int n, double (&C)[MODAL_MAX][MODAL_MAX], double (&Q)
 
 // Rayleigh-Ritz of A v = theta B v (m x m, row-major) when B may be nearly
 // singular (the blocks of LOBPCG grow nearly dependent as it converges): with
-// the columns scaled to unit B-norm, B = U diag(d) U^T by Jacobi, the directions with d > 1e-12 max d kept,
-// Z = U_keep diag(d_keep)^-1/2, C = Z^T A Z by Jacobi, V = Z Q.  The k
-// smallest theta (ascending) and their m x k coefficients (row-major, V^T B V
-// = I) are written.  info: 0 ok, 2 no convergence, 3 fewer than k directions.
-__global__ void k_small_geig_robust(int m, int k, const double* __restrict__ A, const double* __restrict__ Bm,
-                                    double* __restrict__ lam, double* __restrict__ V, int* info) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double C[MODAL_MAX][MODAL_MAX], U[MODAL_MAX][MODAL_MAX], Z[MODAL_MAX][MODAL_MAX];
-  double sc[MODAL_MAX];
-  *info = 0;
+// the columns scaled to unit B-norm, B = U diag(d) U^T by Jacobi, the
+// directions with d > 1e-12 max d kept, Z = U_keep diag(d_keep)^-1/2,
+// C = Z^T A Z by Jacobi, V = Z Q.  The k smallest theta (ascending) and their
+// m x k coefficients (row-major, V^T B V = I) are written.  info: 0 ok, 2 no
+// convergence, 3 fewer than k directions.  One warp (launch <<<1, 32>>>).
+__global__ void __launch_bounds__(32)
+k_small_geig_robust(int m, int k, const double* __restrict__ A, const double* __restrict__ Bm,
+                    double* __restrict__ lam, double* __restrict__ V, int* info) {
+  __shared__ double C[MODAL_MAX][MODAL_MAX], U[MODAL_MAX][MODAL_MAX], Z[MODAL_MAX][MODAL_MAX];
+  __shared__ double sc[MODAL_MAX];
+  __shared__ int ord[MODAL_MAX];
+  const int l = threadIdx.x;
+  if (blockIdx.x != 0 || l >= 32) return;
+  if (l == 0) *info = 0;
   // columns scaled to unit B-norm first (W and P shrink with the residual; a
   // zero column is dropped), so that the truncation below sees only true
   // dependence, not scale
-  for (int i = 0; i < m; ++i) {
+  for (int i = l; i < m; i += 32) {
     const double d = Bm[i * m + i];
     sc[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
   }
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) C[i][j] = 0.5 * (Bm[i * m + j] + Bm[j * m + i]) * sc[i] * sc[j];
-  if (!jacobi_sym(m, C, U)) { *info = 2; return; }
+  __syncwarp();
+  for (int t = l; t < m * m; t += 32) {
+    const int i = t / m, j = t % m;
+    C[i][j] = 0.5 * (Bm[i * m + j] + Bm[j * m + i]) * sc[i] * sc[j];
+  }
+  __syncwarp();
+  if (!jacobi_sym(m, C, U)) { if (l == 0) *info = 2; return; }
   double dmax = 0.0;
   for (int i = 0; i < m; ++i) dmax = fmax(dmax, C[i][i]);
   int r = 0;
@@ -265,39 +190,53 @@ __global__ void k_small_geig_robust(int m, int k, const double* __restrict__ A, 
     const double d = C[j][j];
     if (!(d > 1e-12 * dmax)) continue;
     const double s = 1.0 / sqrt(d);
-    for (int i = 0; i < m; ++i) Z[i][r] = U[i][j] * s;
+    for (int i = l; i < m; i += 32) Z[i][r] = U[i][j] * s;
     ++r;
   }
-  if (r < k) { *info = 3; return; }
-  // C = Z^T A' Z (r x r) with A' the scaled A, symmetrised
-  for (int a = 0; a < r; ++a)
-    for (int b = 0; b < r; ++b) {
-      double s = 0.0;
-      for (int i = 0; i < m; ++i) {
-        double t = 0.0;
-        for (int j = 0; j < m; ++j) t += 0.5 * (A[i * m + j] + A[j * m + i]) * sc[i] * sc[j] * Z[j][b];
-        s += Z[i][a] * t;
-      }
+  if (r < k) { if (l == 0) *info = 3; return; }
+  __syncwarp();
+  // T = A' Z (m x r, into U) with A' the scaled, symmetrised A; C = Z^T T
+  for (int t = l; t < m * r; t += 32) {
+    const int i = t / r, b = t % r;
+    double s = 0.0;
+    for (int j = 0; j < m; ++j) s = fma(0.5 * (A[i * m + j] + A[j * m + i]) * sc[i] * sc[j], Z[j][b], s);
+    U[i][b] = s;
+  }
+  __syncwarp();
+  for (int t = l; t < r * r; t += 32) {
+    const int a = t / r, b = t % r;
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s = fma(Z[i][a], U[i][b], s);
+    C[a][b] = s;
+  }
+  __syncwarp();
+  for (int t = l; t < r * r; t += 32) {   // symmetrise (each pair once)
+    const int a = t / r, b = t % r;
+    if (a < b) {
+      const double s = 0.5 * (C[a][b] + C[b][a]);
       C[a][b] = s;
+      C[b][a] = s;
     }
-  if (!jacobi_sym(r, C, U)) { *info = 2; return; }
-  int ord[MODAL_MAX];
-  for (int i = 0; i < r; ++i) ord[i] = i;
-  for (int i = 0; i < r; ++i)
-    for (int j = i + 1; j < r; ++j)
-      if (C[ord[j]][ord[j]] < C[ord[i]][ord[i]]) {
-        const int t = ord[i];
-        ord[i] = ord[j];
-        ord[j] = t;
-      }
-  for (int c = 0; c < k; ++c) {
-    const int oc = ord[c];
-    lam[c] = C[oc][oc];
-    for (int i = 0; i < m; ++i) {
-      double s = 0.0;
-      for (int a = 0; a < r; ++a) s += Z[i][a] * U[a][oc];
-      V[i * k + c] = sc[i] * s;
-    }
+  }
+  __syncwarp();
+  if (!jacobi_sym(r, C, U)) { if (l == 0) *info = 2; return; }
+  if (l == 0) {
+    for (int i = 0; i < r; ++i) ord[i] = i;
+    for (int i = 0; i < r; ++i)
+      for (int j = i + 1; j < r; ++j)
+        if (C[ord[j]][ord[j]] < C[ord[i]][ord[i]]) {
+          const int t = ord[i];
+          ord[i] = ord[j];
+          ord[j] = t;
+        }
+    for (int c = 0; c < k; ++c) lam[c] = C[ord[c]][ord[c]];
+  }
+  __syncwarp();
+  for (int t = l; t < m * k; t += 32) {
+    const int i = t / k, c = t % k, oc = ord[c];
+    double s = 0.0;
+    for (int a = 0; a < r; ++a) s = fma(Z[i][a], U[a][oc], s);
+    V[i * k + c] = sc[i] * s;
   }
 }
 
@@ -322,8 +261,9 @@ __global__ void k_block_combine(int ndof, int vs, int kin, int kout, const doubl
   }
 }
 
-// R[r] = G X[r] - theta[r] K X[r] (the LOBPCG residual block), zero where
-// mask <= 0, and the partials of |R[r]|^2 and |K X[r]|^2 as k_pair_residual.
+// R[r] = A X[r] - theta[r] B X[r] (the LOBPCG residual block), zero where
+// mask <= 0, and the partials parts[(r * gridDim.x + b) * 2 + {0, 1}] of
+// |R[r]|^2 and |B X[r]|^2.
 __global__ void __launch_bounds__(RED_THREADS)
 k_lobpcg_residual(int ndof, int vs, const double* __restrict__ GX, const double* __restrict__ KX,
                   const double* __restrict__ mask, const double* __restrict__ theta, double* __restrict__ R,
@@ -339,50 +279,6 @@ k_lobpcg_residual(int ndof, int vs, const double* __restrict__ GX, const double*
     R[off + d] = e;
     s[0] = fma(e, e, s[0]);
     s[1] = mask[d] > 0.0 ? fma(kx, kx, s[1]) : s[1];
-  }
-  double o[2];
-  block_sum_to_f64<2>(s, red, o);
-  if (threadIdx.x == 0) {
-    parts[((size_t)r * gridDim.x + blockIdx.x) * 2] = o[0];
-    parts[((size_t)r * gridDim.x + blockIdx.x) * 2 + 1] = o[1];
-  }
-}
-
-// X[r] = sum_j Y[j] V[j][r] for r < kp (the Ritz vectors of span(Y)).
-__global__ void k_ritz_combine(int ndof, int vs, int kp, const double* __restrict__ Y, const double* __restrict__ V,
-                               double* __restrict__ X) {
-  __shared__ double sv[MODAL_MAX * MODAL_MAX];
-  for (int q = threadIdx.x; q < kp * kp; q += blockDim.x) sv[q] = V[q];
-  __syncthreads();
-  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
-    double y[MODAL_MAX];
-#pragma unroll
-    for (int j = 0; j < MODAL_MAX; ++j) y[j] = j < kp ? Y[(size_t)j * vs + d] : 0.0;
-    for (int r = 0; r < kp; ++r) {
-      double s = 0.0;
-#pragma unroll
-      for (int j = 0; j < MODAL_MAX; ++j)
-        if (j < kp) s = fma(y[j], sv[j * kp + r], s);
-      X[(size_t)r * vs + d] = s;
-    }
-  }
-}
-
-// Residual partials of the first n Ritz pairs: parts[(r * gridDim.x + b) * 2]
-// = sum (K x_r - lambda_r M x_r)^2, [.. + 1] = sum (K x_r)^2.
-__global__ void __launch_bounds__(RED_THREADS)
-k_modal_residual(int ndof, int vs, const double* __restrict__ KX, const double* __restrict__ X,
-                 const double* __restrict__ mass, const double* __restrict__ lam, double* __restrict__ parts) {
-  __shared__ double red[32 * 2];
-  const int r = blockIdx.y;
-  const size_t off = (size_t)r * vs;
-  const double l = lam[r];
-  double s[2] = {0.0, 0.0};
-  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndof; d += gridDim.x * blockDim.x) {
-    const double kx = KX[off + d];
-    const double e = mass[d] > 0.0 ? kx - l * mass[d] * X[off + d] : 0.0;
-    s[0] = fma(e, e, s[0]);
-    s[1] = mass[d] > 0.0 ? fma(kx, kx, s[1]) : s[1];
   }
   double o[2];
   block_sum_to_f64<2>(s, red, o);
