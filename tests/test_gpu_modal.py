@@ -224,3 +224,36 @@ def test_buckling_when_the_reversed_load_buckles_first():
     for i in range(n):
         assert abs(abs(phi[i] @ (K @ phi_o[i])) - 1.0) < 1e-6
     m.close()
+
+
+def test_eigen_block_limit():
+    """Ten modes (the largest block: [X, W, P] of 12 vectors each fills the
+    36-vector Rayleigh-Ritz basis) for both analyses against the oracle;
+    eleven are refused before any work."""
+    from oracle import buckling
+
+    w = _case(seed=9)
+    n, rho, tol = 10, 1.0, 1e-9
+    lam_o, _ = modal.modes(w.nx, w.ny, w.nz, w.E, w.fixed, n, rho=rho)
+    m = afd.Mesh(w.nx, w.ny, w.nz, group=w.group)
+    m.set_element_moduli(w.E)
+    m.set_loads_bcs(w.f, w.fixed)
+    for call in (lambda: m.modal(n + 1), lambda: m.buckling(n + 1)):
+        with pytest.raises(afd.AFDError) as e:
+            call()
+        assert e.value.code == afd.AFD_ERR_INVALID_ARG
+    phi = np.zeros((n, m.ndof))
+    lam, _ = m.modal(n, rho=rho, tol=tol, modes_out=phi, max_iter=300)
+    assert np.allclose(lam, lam_o, rtol=1e-8)
+    mass = modal.lumped_mass(w.nx, w.ny, w.nz, w.E, rho)
+    assert np.allclose(phi @ (mass[:, None] * phi.T), np.eye(n), atol=1e-9)
+    m.close()
+    nx, ny, nz, E, f, fixed = _column()
+    lam_o, _, _ = buckling.buckling(nx, ny, nz, E, f, fixed, n)
+    m = afd.Mesh(nx, ny, nz, group=2)
+    m.set_element_moduli(E)
+    m.set_loads_bcs(f[None], fixed)
+    m.solve(1e-11)
+    lam, _ = m.buckling(n, tol=tol, max_iter=300)
+    assert np.allclose(lam, lam_o, rtol=1e-7)
+    m.close()
