@@ -71,6 +71,8 @@ def alu_roofline(n_elements: int, ms: float) -> dict:
 
 
 STENCIL_DRAM_BYTES = {(128, 64, 64, 8, 6, 0): 9198592, (384, 192, 192, 8, 12, 1): 378244608}
+# The same for the stencil of the inner DPCG iteration (ST_APPLY_DOT), captured inside a mixed solve.
+STENCIL_DOT_DRAM_BYTES = {(128, 64, 64, 8, 6, 0): 15795456}
 
 
 def rank_info():
@@ -224,6 +226,16 @@ def run_ours(args):
     achieved = bytes32 / (mv_ms * 1e-3) / 1e9
     shape = (afd.afd_stencil_warps(mesh.h), afd.afd_stencil_depth(mesh.h), afd.afd_stencil_async(mesh.h))
     traffic = STENCIL_DRAM_BYTES.get((w.nx, w.ny, w.nz) + shape)
+    # the step's dominant kernel: the FP32 stencil of the inner DPCG iteration (beta and the stopping test from
+    # the partials, p = z + W mu + beta p formed on load, q = K p, p.q), each launch bracketed by CUDA events on
+    # the mesh's stream, over 200 iterations continuing a solve of the step's design
+    mesh.set_element_moduli(E_d)
+    mesh.solve(w.tol)
+    kt = afd.afd_time_dpcg_kernels(mesh.h, 200)
+    it_ms = kt["stencil_us"] * 1e-3
+    bytes_dot = 4 * 3 * nn * 4 + 4 * ne + nn        # read p_old, z, E, fixed bits; write p, q
+    achieved_dot = bytes_dot / (it_ms * 1e-3) / 1e9
+    traffic_dot = STENCIL_DOT_DRAM_BYTES.get((w.nx, w.ny, w.nz) + shape)
 
     # HBM roofline on the largest mesh of the method (384x192x192, 43 M DOFs): the
     # same FP32 apply, 400 MB of algorithmic traffic per launch, well above L2
@@ -302,11 +314,20 @@ def run_ours(args):
                   "speedup_mixed_vs_fp64": round(float(np.median(fp64)) / float(np.median(solve_ms)), 3)},
         "matvec": {"f32_ms": round(mv_ms, 5), "f32_gdofs": round(3 * nn / (mv_ms * 1e-3) / 1e9, 3),
                    "f64_ms": round(mv64_ms, 5), "f64_gdofs": round(3 * nn / (mv64_ms * 1e-3) / 1e9, 3)},
-        "roofline": {"kernel": "stencil2_kernel<TY,ST_APPLY> (K u, FP32, packed float2)", "bound": "hbm",
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "peak_source": peak_kind, "bytes_per_launch": bytes32,
-                     "alu": alu_roofline(ne, mv_ms)},
+        "roofline": {"kernel": "stencil2_kernel<TY,ST_APPLY_DOT> (inner DPCG iteration: p formed on load, q = K p, "
+                               "p.q; FP32, packed float2)", "bound": "hbm",
+                     "achieved": round(achieved_dot, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved_dot / peak, 4), "traffic": traffic_dot,
+                     "peak_source": peak_kind, "bytes_per_launch": bytes_dot,
+                     "launch_us": round(kt["stencil_us"], 3),
+                     "alu": alu_roofline(ne, it_ms),
+                     "other_iteration_kernels_us": {k: round(kt[k], 3) for k in
+                                                    ("update_us", "coarse_rhs_us", "coarse_step_us")}},
+        "roofline_apply": {"kernel": "stencil2_kernel<TY,ST_APPLY> (K u alone, FP32, packed float2)", "bound": "hbm",
+                           "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                           "frac": round(achieved / peak, 4), "traffic": traffic,
+                           "peak_source": peak_kind, "bytes_per_launch": bytes32,
+                           "alu": alu_roofline(ne, mv_ms)},
         "roofline_384x192x192": roofline_large,
         "e2e": {"value": round(float(np.median(e2e)), 3), "unit": "ms per topology step, host buffers",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

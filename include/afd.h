@@ -324,7 +324,8 @@ int afd_stencil_async(const afd_mesh* m);
 /* Measurement aid for the CUDA-graph inner solver: continues the last FP32
  * inner DPCG iteration of a completed AFD_MIXED solve for `iters` iterations
  * (no stopping test; the solution u is not touched), launching its kernels
- * one by one with CUDA events between them on the mesh's stream.  us_out5 =
+ * one by one with CUDA events between them on the mesh's stream (every
+ * iteration enqueued before one synchronisation; iters in [1, 4096]).  us_out5 =
  * mean microseconds per iteration of the stencil, the vector update, the
  * coarse right-hand side, the coarse step, and (variant 1) the separate
  * search-direction kernel.  variant 0: the stencil forms p = z + W mu +

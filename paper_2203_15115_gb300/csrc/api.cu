@@ -2082,7 +2082,7 @@ int afd_set_stencil_shape(afd_mesh* m, int warps, int planes, int async_staging)
 }
 
 int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, double* us_out5) {
-  if (!m || !us_out5 || iters < 1 || nsplit < 0 || nsplit > 64 || variant < 0 || variant > 1)
+  if (!m || !us_out5 || iters < 1 || iters > 4096 || nsplit < 0 || nsplit > 64 || variant < 0 || variant > 1)
     return fail(AFD_ERR_INVALID_ARG, "bad argument");
   if (!m->has_solution || m->opt.precision != AFD_MIXED || !m->w32.x || !m->coarse_valid)
     return fail(AFD_ERR_STATE, "needs a completed AFD_MIXED solve on this mesh");
@@ -2119,13 +2119,16 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
   unsigned int* cnt_co = m->counters + MAX_RHS;
   float* P[2] = {w.p, w.t};
   const dim3 pg(grid_blocks(gr.nnodes, 256, 4 * RED_BLOCKS), R);
-  cudaEvent_t ev[6];
-  for (auto& e : ev) CK(cudaEventCreate(&e));
+  // six events per iteration, all enqueued before one synchronisation, so that
+  // the stream stays ahead of the GPU and each pair brackets its kernel only
+  std::vector<cudaEvent_t> evs((size_t)iters * 6);
+  for (auto& e : evs) CK(cudaEventCreate(&e));
   double acc[5] = {0, 0, 0, 0, 0};
   int rc = AFD_OK;
   for (int it = 0; it < iters && rc == AFD_OK; ++it) {
     float* pold = P[it & 1];
     float* pnew = P[(it + 1) & 1];
+    cudaEvent_t* ev = evs.data() + (size_t)it * 6;
     cudaEventRecord(ev[5], m->s);
     if (variant == 1) {  // p = beta p + z + W mu in place, then the plain p.Kp stencil
       k_prolong<float><<<pg, 256, 0, m->s>>>(0, gr, m->gp, P[0], w.z, m->mu, m->fixed, m->st);
@@ -2151,19 +2154,21 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
                                                      cnt_co, m->upart, RED_BLOCKS);
     cudaEventRecord(ev[4], m->s);
     m->launches += 4;
-    if (cudaEventSynchronize(ev[4]) != cudaSuccess) rc = fail(AFD_ERR_CUDA, "timing run failed");
-    for (int q = 0; q < 4 && rc == AFD_OK; ++q) {
+  }
+  if (rc == AFD_OK && cudaEventSynchronize(evs[(size_t)iters * 6 - 2]) != cudaSuccess)
+    rc = fail(AFD_ERR_CUDA, "timing run failed");
+  for (int it = 0; it < iters && rc == AFD_OK; ++it) {
+    cudaEvent_t* ev = evs.data() + (size_t)it * 6;
+    for (int q = 0; q < 4; ++q) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
       acc[q] += ms;
     }
-    if (rc == AFD_OK) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[5], ev[0]);
-      acc[4] += ms;
-    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[5], ev[0]);
+    acc[4] += ms;
   }
-  for (auto& e : ev) cudaEventDestroy(e);
+  for (auto& e : evs) cudaEventDestroy(e);
   for (int r = 0; r < R; ++r) hd[r] = 1;
   CK(cudaMemcpyAsync(m->done, hd.data(), R * sizeof(int), cudaMemcpyHostToDevice, m->s));
   m->nsplit = keep_split;

@@ -427,3 +427,25 @@ def test_iteration_budget_stops_the_solve_with_not_converged(precision):
         m.solve(1e-10)
     assert e.value.code == afd.AFD_ERR_NOT_CONVERGED
     m.close()
+
+
+def test_iteration_kernel_timing_leaves_the_solution_and_the_solver_intact():
+    """The measurement hook behind the bench's roofline: it runs the inner
+    iteration's kernels after a mixed solve, reports a positive time for each,
+    leaves u and J untouched, refuses a bad count, and the next solve (graphs
+    recaptured) still meets its tolerance."""
+    w = small_cantilever(20, 10, 10, seed=5, n_spheres=4, rmin=1.5, rmax=3.0, group=4)
+    m, u, _ = _solve(w, afd.AFD_MIXED, 1e-8)
+    J = m.compliance()[0]
+    t = afd.afd_time_dpcg_kernels(m.h, 64)
+    for k in ("stencil_us", "update_us", "coarse_rhs_us", "coarse_step_us"):
+        assert np.isfinite(t[k]) and t[k] > 0.0
+    with pytest.raises(afd.AFDError) as e:
+        afd.afd_time_dpcg_kernels(m.h, 4097)
+    assert e.value.code == afd.AFD_ERR_INVALID_ARG
+    assert m.compliance()[0] == J
+    u2 = np.zeros_like(w.f)
+    stats = m.solve(1e-8, u_out=u2)
+    assert stats[0]["rel_residual"] <= 1e-8
+    assert np.linalg.norm(u2 - u) <= 1e-6 * np.linalg.norm(u)
+    m.close()
