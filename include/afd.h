@@ -160,6 +160,8 @@ int afd_stress_sensitivity(afd_mesh* m, double p, double rel_tol, float* out, in
  * DOFs), else after max_iter steps with AFD_ERR_NOT_CONVERGED (outputs still
  * written).  AFD_ERR_NAN if an eigenvalue is not positive (supports that
  * leave a rigid-body mode).
+ * Relative residuals much below 1e-8 are not reliably reached for large
+ * blocks (the Rayleigh-Ritz basis grows nearly dependent first).
  * n_modes in [1, 10]; rho > 0.
  * lam_out: n_modes doubles (host), ascending.  modes_out (nullable):
  * n_modes*ndof, M-orthonormal, zero on fixed DOFs, sign arbitrary.

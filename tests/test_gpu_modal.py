@@ -229,11 +229,14 @@ def test_buckling_when_the_reversed_load_buckles_first():
 def test_eigen_block_limit():
     """Ten modes (the largest block: [X, W, P] of 12 vectors each fills the
     36-vector Rayleigh-Ritz basis) for both analyses against the oracle;
-    eleven are refused before any work."""
+    eleven are refused before any work.  tol = 1e-8: a relative residual of
+    1e-9 for all ten is LOBPCG's stagnation floor here (a CPU replica with an
+    exact K^-1 perturbed by 1e-3 needed 46 to over 400 steps for it, and 13 to
+    51 for 1e-8)."""
     from oracle import buckling
 
     w = _case(seed=9)
-    n, rho, tol = 10, 1.0, 1e-9
+    n, rho, tol = 10, 1.0, 1e-8
     lam_o, _ = modal.modes(w.nx, w.ny, w.nz, w.E, w.fixed, n, rho=rho)
     m = afd.Mesh(w.nx, w.ny, w.nz, group=w.group)
     m.set_element_moduli(w.E)
