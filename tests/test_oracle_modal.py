@@ -114,3 +114,30 @@ def test_eigen_sensitivity_closed_forms():
     ut = np.tile(t, X.shape[0])
     assert np.allclose(modal.eigen_sensitivity(nx, ny, nz, E, ut, lam, rho, nu), -lam * rho * E * (t @ t),
                        rtol=1e-12)
+
+
+def test_slender_cantilever_approaches_euler_bernoulli_frequencies():
+    """A clamped-free beam of length L = 20 and unit square section (E = 1,
+    rho = 1, lumped mass), refined through the thickness (h = 1/n): the first
+    bending eigenvalue omega^2 falls monotonically onto Euler-Bernoulli's
+    beta_1^4 E I / (rho A L^4) with the trilinear element's O(h^2) error
+    (Richardson on n = 3, 4 within 1 %); bending pairs are equal (square
+    section); the second bending eigenvalue extrapolates to within 3 % below
+    its Euler-Bernoulli value (shear and rotary inertia lower it)."""
+    L = 20
+    b1, b2 = 1.8751040687119611, 4.6940911329741745          # roots of cos b cosh b = -1
+    lam_eb1 = b1 ** 4 * (1.0 / 12.0) / L ** 4
+    lam_eb2 = b2 ** 4 * (1.0 / 12.0) / L ** 4
+    r1, r2 = [], []
+    for n in (1, 2, 3, 4):
+        nx = L * n
+        lam, _ = modal.modes(nx, n, n, np.ones(nx * n * n), clamp_face_x0(nx, n, n), 4, rho=1.0, h=1.0 / n)
+        assert abs(lam[1] - lam[0]) <= 1e-8 * lam[0] and abs(lam[3] - lam[2]) <= 1e-8 * lam[2]
+        r1.append(lam[0] / lam_eb1)
+        r2.append(lam[2] / lam_eb2)
+    assert all(a > b > 1.0 for a, b in zip(r1, r1[1:]))
+    e = [r - 1.0 for r in r1]
+    assert 3.5 < e[0] / e[1] < 4.5 and 1.9 < e[1] / e[2] < 2.6
+    assert abs((16.0 * r1[3] - 9.0 * r1[2]) / 7.0 - 1.0) < 1e-2
+    x2 = (16.0 * r2[3] - 9.0 * r2[2]) / 7.0
+    assert 0.97 < x2 < 1.0
