@@ -152,16 +152,15 @@ int afd_stress_sensitivity(afd_mesh* m, double p, double rel_tol, float* out, in
  * rho_e h^3 / 8 per direction with rho_e = rho * E_e (density follows the
  * modulus).  Block LOBPCG on a block of n_modes + 2 vectors, preconditioned
  * by K^-1 from the mesh's solver (its precision and options, relative
- * tolerance 1e-3): each step forms the residuals K phi - lambda M phi, solves
- * for the new directions W and takes the Rayleigh-Ritz pairs of span[X, W, P]
+ * tolerance 3e-2): each step forms the residuals K phi - lambda M phi, solves
+ * for the new directions W of the vectors not yet converged (soft locking)
+ * and takes the Rayleigh-Ritz pairs of span[X, W, P]
  * (FP64 Gram matrices; a small generalised eigenproblem on the device,
  * directions scaled and truncated against dependence).  Stops when every
  * requested pair has ||K phi - lambda M phi|| <= tol lambda ||M phi|| (free
  * DOFs), else after max_iter steps with AFD_ERR_NOT_CONVERGED (outputs still
  * written).  AFD_ERR_NAN if an eigenvalue is not positive (supports that
  * leave a rigid-body mode).
- * Relative residuals much below 1e-8 are not reliably reached for large
- * blocks (the Rayleigh-Ritz basis grows nearly dependent first).
  * n_modes in [1, 10]; rho > 0.
  * lam_out: n_modes doubles (host), ascending.  modes_out (nullable):
  * n_modes*ndof, M-orthonormal, zero on fixed DOFs, sign arbitrary.
@@ -189,7 +188,8 @@ int afd_eigen_sensitivity(afd_mesh* m, float* out, int out_on_device);
  * stiffness K_G^e[(a,i),(b,j)] = delta_ij int grad N_a . S_e grad N_b (exact
  * cube integrals).  Block LOBPCG for the smallest eigenvalues theta of
  * K_G phi = theta K phi (lambda = -1/theta), block n_modes + 2, with
- * K^-1 by the mesh's solver (relative tolerance 1e-3) as the preconditioner
+ * K^-1 by the mesh's solver (relative tolerance 3e-2) as the preconditioner,
+ * soft locking of converged vectors
  * and Rayleigh-Ritz on [X, W, P] (FP64 Gram matrices, directions scaled and
  * truncated against dependence on the device).  It targets the smallest
  * positive factors even when the reversed load buckles first.

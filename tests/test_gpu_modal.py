@@ -229,10 +229,10 @@ def test_buckling_when_the_reversed_load_buckles_first():
 def test_eigen_block_limit():
     """Ten modes (the largest block: [X, W, P] of 12 vectors each fills the
     36-vector Rayleigh-Ritz basis) for both analyses against the oracle;
-    eleven are refused before any work.  tol = 1e-8: a relative residual of
-    1e-9 for all ten is LOBPCG's stagnation floor here (a CPU replica with an
-    exact K^-1 perturbed by 1e-3 needed 46 to over 400 steps for it, and 13 to
-    51 for 1e-8)."""
+    eleven are refused before any work.  Soft locking keeps the basis
+    independent: without it, ten modes of such a mesh stalled near a relative
+    residual of 1e-9 (a CPU replica needed 249 steps for 1e-8 on one of these
+    cases, 12 with locking)."""
     from oracle import buckling
 
     w = _case(seed=9)
