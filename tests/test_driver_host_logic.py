@@ -62,7 +62,11 @@ class OracleMesh:
         out[0] = sensitivity.strain_energy(self.nx, self.ny, self.nz, self.E, self.u)
 
     def stress_sensitivity(self, p, tol, out):
-        raise AssertionError("no stress constraint in these tests")
+        # Eq. 3.3 with its adjoint: K lambda = -d sigma_PN / d u on the free DOFs
+        assert self.u is not None, "the stress field needs the static solution"
+        g = sensitivity.pnorm_stress_gradient(self.nx, self.ny, self.nz, self.E, self.u, p)
+        lam = fe.solve_direct(fe.assemble(self.nx, self.ny, self.nz, self.E), -g, self.fixed)
+        out[0] = sensitivity.stress_topological_sensitivity(self.nx, self.ny, self.nz, self.E, self.u, lam)
 
     def modal(self, n, rho=1.0, tol=1e-6):
         self.calls["modal"] += 1
@@ -176,3 +180,27 @@ def test_soft_buckling_never_rejects_and_unconverged_targets_stay(afd, oracle_cu
     _check_steps(hist)
     with pytest.raises(ValueError):
         afd.run_constrained_topology(m, np.ones(nx * ny * nz), compliance=1.5, soft=("J",))
+
+
+def test_hard_compliance_and_stress_steps(afd, oracle_cut):
+    """Both constraints of the paper's static problem hard: J <= 1.5 J_0 and
+    sigma_PN(p = 8) <= 1.3 sigma_0.  Every record's violation flag follows the
+    two g values, both multipliers follow Eqs. 3.11-3.12, steps 4 and 7-9 hold,
+    and the final design meets both constraints under the oracle."""
+    nx, ny, nz = 12, 4, 3
+    f, fixed = edge_load(nx, ny, nz), clamp_face_x0(nx, ny, nz)
+    m = OracleMesh(nx, ny, nz, f, fixed)
+    res = afd.run_constrained_topology(m, np.ones(nx * ny * nz), compliance=1.5, stress=1.3, p=8.0, dv0=0.1,
+                                       v_min=0.3, max_fea=25)
+    hist = res["history"]
+    for h in hist:
+        assert h["violated"] == (h["g"]["J"] > 0 or h["g"]["sigma"] > 0)
+    _replay_al(hist, "J")
+    _replay_al(hist, "sigma")
+    _check_steps(hist)
+    assert any(h["violated"] for h in hist)
+    E = res["E"]
+    u = fe.solve_direct(fe.assemble(nx, ny, nz, E), f, fixed)
+    assert fe.compliance(f, u) <= 1.5 * res["reference"]["J"] * (1 + 1e-12)
+    vm = sensitivity.element_von_mises(nx, ny, nz, E, u)
+    assert sensitivity.pnorm(vm, 8.0) <= 1.3 * res["reference"]["sigma"] * (1 + 1e-12)
