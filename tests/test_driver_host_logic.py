@@ -95,10 +95,12 @@ class OracleMesh:
 @pytest.fixture
 def oracle_cut(afd, monkeypatch):
     def cut(h, fields, weights, v, casting, kept):
+        m = _MESHES[h]
         T = levelset.combine(np.asarray(fields, dtype=np.float32), np.asarray(weights, dtype=np.float64))
+        if casting is not None:
+            T = levelset.casting_scan(T, m.nx, m.ny, m.nz, *casting)
         sel, tau = levelset.select_top(T, levelset.keep_count(v, T.size))
         kept[:] = sel
-        m = _MESHES[h]
         m.set_element_moduli(levelset.apply_topology(sel, m.options.e_void))
         return float(tau)
 
@@ -204,3 +206,28 @@ def test_hard_compliance_and_stress_steps(afd, oracle_cut):
     assert fe.compliance(f, u) <= 1.5 * res["reference"]["J"] * (1 + 1e-12)
     vm = sensitivity.element_von_mises(nx, ny, nz, E, u)
     assert sensitivity.pnorm(vm, 8.0) <= 1.3 * res["reference"]["sigma"] * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("axis,parting", [(2, 0), (1, 2)])
+def test_casting_designs_have_no_undercut(afd, oracle_cut, axis, parting):
+    """Sec. 3.7 inside the Sec. 3.8 loop: with a casting direction every design
+    the driver cuts, and the final feasible one, keeps on each line along the
+    axis and on each side of the parting plane a run of elements that starts
+    at the plane (the part can be drawn from its mould)."""
+    nx, ny, nz = 10, 4, 4
+    f, fixed = edge_load(nx, ny, nz), clamp_face_x0(nx, ny, nz)
+    m = OracleMesh(nx, ny, nz, f, fixed)
+    designs = []
+    res = afd.run_constrained_topology(m, np.ones(nx * ny * nz), compliance=2.0, dv0=0.1, v_min=0.4, max_fea=12,
+                                       casting=(axis, parting), on_step=lambda rec: designs.append(m.E.copy()))
+    designs.append(res["E"])
+    _check_steps(res["history"])
+    for E in designs[1:]:
+        a = np.moveaxis((E == 1.0).reshape(nz, ny, nx), {0: 2, 1: 1, 2: 0}[axis], 0)
+        n = a.shape[0]
+        for half in (a[parting:], a[:parting][::-1]):       # each half ordered away from the plane
+            if half.shape[0] == 0:
+                continue
+            run = np.cumprod(half, axis=0)                   # kept and every element before it kept
+            assert np.array_equal(run, half), "undercut"
+    assert any(not np.all(E == 1.0) for E in designs)
