@@ -791,6 +791,31 @@ def profile_solve(warps: int, planes: int, solves: int, staging: int = 0):
     mesh.close()
 
 
+def profile_eigen(kind: str, calls: int):
+    """`calls` eigen analyses of the 128x64x64 voided cantilever after one
+    mixed solve (modal: 4 modes; buckling: 2 factors of the solved state; both
+    to 1e-6), for ncu launch lists of the LOBPCG steps."""
+    import torch
+
+    import paper_2203_15115_gb300 as afd
+    from synthetic import cantilever_128x64x64_voids
+
+    w = cantilever_128x64x64_voids()
+    mesh = afd.Mesh(w.nx, w.ny, w.nz, group=w.group)
+    mesh.set_loads_bcs(w.f, w.fixed)
+    mesh.set_element_moduli(w.E)
+    out = []
+    for _ in range(calls):
+        mesh.solve(w.tol)
+        t0 = time.perf_counter()
+        lam, info = mesh.modal(4, tol=1e-6, max_iter=200) if kind == "modal" else mesh.buckling(2, tol=1e-6, max_iter=200)
+        torch.cuda.synchronize()
+        out.append({"ms": round((time.perf_counter() - t0) * 1e3, 1), "steps": info["steps"],
+                    "inner_iters": info["solve_iters"], "values": [float(x) for x in lam]})
+    print(json.dumps({"workload": w.name, "analysis": kind, "calls": out}))
+    mesh.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -807,6 +832,8 @@ def main():
     ap.add_argument("--launch-summary", metavar="CSV", help="summarise an ncu launch list of one timed step")
     ap.add_argument("--profile-solve", action="store_true",
                     help="only run --steps mixed solves of the 128x64x64 workload in a pinned stencil shape (for ncu)")
+    ap.add_argument("--profile-eigen", choices=("modal", "buckling"),
+                    help="only run --steps eigen analyses of the 128x64x64 workload (for ncu)")
     ap.add_argument("--stencil-warps", type=int, default=0, help="pinned FP32 stencil warps per CTA (profile modes)")
     ap.add_argument("--stencil-planes", type=int, default=0, help="pinned FP32 stencil planes per CTA (profile modes)")
     ap.add_argument("--stencil-async", type=int, default=0, choices=(0, 1),
@@ -818,6 +845,8 @@ def main():
         profile_stencil(args.profile_stencil, max(1, args.steps), args.stencil_warps, args.stencil_planes, args.stencil_async)
     elif args.profile_solve:
         profile_solve(args.stencil_warps, args.stencil_planes, max(1, args.steps), args.stencil_async)
+    elif args.profile_eigen:
+        profile_eigen(args.profile_eigen, max(1, args.steps))
     elif args.impl == "reference":
         run_reference(args)
     else:
