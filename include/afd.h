@@ -349,7 +349,14 @@ int afd_solver_phase_times(afd_mesh* m, double* out10, int reset);
 int64_t afd_ndof(const afd_mesh* m);
 int64_t afd_nelem(const afd_mesh* m);
 
+/* Frees every device buffer, stream, event and graph the mesh owns and the
+ * handle itself (null is allowed).  Waits for the mesh's stream first; the
+ * handle must not be used afterwards, nor by another thread during the call. */
 void afd_destroy(afd_mesh* m);
+
+/* The message of the calling thread's most recent failure (thread-local,
+ * owned by the library; the pointer stays valid until that thread's next
+ * failing call); "" if none of its calls has failed. */
 const char* afd_last_error(void);
 
 /* ---- serving: solve requests of different mesh sizes concurrently ---- */
