@@ -289,7 +289,10 @@ int afd_select_topk(const float* keys, int64_t n, int64_t k, uint8_t* kept, floa
  * current); make that first call before any stream capture.  Every call
  * shares the one array and re-initialises it; calls that overlap on the GPU
  * (e.g. on two streams at once) race and give undefined results.  Returns
- * after cuda_stream has finished, like afd_select_topk. */
+ * after cuda_stream has finished, like afd_select_topk.  keys and kept must be
+ * device memory of one device; the call runs with that device current and
+ * uses that device's array.  The looked-up address is cached for the life of
+ * the process: do not keep using the library across a cudaDeviceReset. */
 int afd_select_topk_noalloc(const float* keys, int64_t n, int64_t k, uint8_t* kept, float* tau_out,
                             void* cuda_stream);
 

@@ -386,13 +386,27 @@ def afd_coarse_matrix(mesh) -> np.ndarray:
     return out
 
 
-def afd_select_topk(keys, k: int, kept, stream=None) -> float:
+def _select_args(keys, kept):
+    """Device pointers and the key count of a top-k selection; both arrays must
+    be CUDA tensors, kept at least as long as keys."""
+    for name, x in (("keys", keys), ("kept", kept)):
+        if not (hasattr(x, "data_ptr") and x.is_cuda):
+            raise TypeError(f"{name} must be a CUDA tensor")
+    if keys.device != kept.device:
+        raise ValueError("keys and kept must be on the same device")
+    n = int(keys.numel())
+    if int(kept.numel()) < n:
+        raise ValueError(f"kept holds {kept.numel()} bytes for {n} keys")
     pk, _, _k1 = _arr(keys, np.float32)
     po, _, _k2 = _arr(kept, np.uint8)
+    return pk, po, n, (_k1, _k2)
+
+
+def afd_select_topk(keys, k: int, kept, stream=None) -> float:
+    pk, po, n, _keep = _select_args(keys, kept)
     tau = ctypes.c_float()
     s = stream if stream is not None else current_stream()
-    _check(lib().afd_select_topk(pk, int(keys.numel() if hasattr(keys, "numel") else len(keys)), int(k), po,
-                                 ctypes.byref(tau), s))
+    _check(lib().afd_select_topk(pk, n, int(k), po, ctypes.byref(tau), s))
     return tau.value
 
 
@@ -441,15 +455,13 @@ def afd_kernel_launches(mesh) -> int:
     return int(lib().afd_kernel_launches(mesh))
 
 
-def afd_select_topk_noalloc(keys, k: int, kept, stream=None, n: Optional[int] = None) -> float:
+def afd_select_topk_noalloc(keys, k: int, kept, stream=None) -> float:
     """afd_select_topk without device allocation (file-scope device scratch,
     at most 16,777,216 keys; see include/afd.h)."""
-    pk, _, _k1 = _arr(keys, np.float32)
-    po, _, _k2 = _arr(kept, np.uint8)
+    pk, po, n, _keep = _select_args(keys, kept)
     tau = ctypes.c_float()
     s = stream if stream is not None else current_stream()
-    count = n if n is not None else int(keys.numel() if hasattr(keys, "numel") else len(keys))
-    _check(lib().afd_select_topk_noalloc(pk, count, int(k), po, ctypes.byref(tau), s))
+    _check(lib().afd_select_topk_noalloc(pk, n, int(k), po, ctypes.byref(tau), s))
     return tau.value
 
 

@@ -1896,6 +1896,20 @@ static int noalloc_scratch(void** out) {
   return AFD_OK;
 }
 
+// Device that holds a device (or managed) pointer; refuses host memory.
+static int device_of(const void* p, const char* what, int* dev) {
+  cudaPointerAttributes at;
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AFD_ERR_INVALID_ARG, "%s: not a CUDA pointer (%s)", what, cudaGetErrorString(e));
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(AFD_ERR_INVALID_ARG, "%s must be device memory", what);
+  *dev = at.device;
+  return AFD_OK;
+}
+
 int afd_select_topk_noalloc(const float* keys, int64_t n, int64_t k, uint8_t* kept, float* tau_out,
                             void* cuda_stream) {
   if (n < 0 || k < 0 || k > n) return fail(AFD_ERR_INVALID_ARG, "need 0 <= k <= n");
@@ -1907,6 +1921,13 @@ int afd_select_topk_noalloc(const float* keys, int64_t n, int64_t k, uint8_t* ke
     if (tau_out) *tau_out = NAN;
     return AFD_OK;
   }
+  // The scratch looked up below is the one of the keys' device: switch to it
+  // for the call, and refuse `kept` on another device.
+  int dk = 0, dm = 0;
+  TRY(device_of(keys, "keys", &dk));
+  TRY(device_of(kept, "kept", &dm));
+  if (dk != dm) return fail(AFD_ERR_INVALID_ARG, "keys (device %d) and kept (device %d) on different devices", dk, dm);
+  DeviceGuard guard(dk);
   void* base = nullptr;
   TRY(noalloc_scratch(&base));
   SelectState* st = (SelectState*)base;

@@ -49,6 +49,13 @@ def test_alu_roofline_arithmetic():
     r = bench.alu_roofline(1_000_000, 0.01)             # 147 MFLOP in 10 us
     assert r["flops_per_launch"] == 147_000_000
     assert abs(r["achieved"] - 14.7) < 1e-9
-    assert abs(r["peak"] - 80.5) < 0.05
-    assert abs(r["frac"] - 14.7 / bench.FP32_PEAK_TFLOPS) < 1e-4
+    peak = bench.fp32_peak_tflops(r["sm_count"], bench.sm_max_mhz())
+    assert abs(r["peak"] - round(peak, 1)) < 1e-9
+    assert abs(r["frac"] - 14.7 / peak) < 1e-4
     assert r["unit"] == "TFLOP/s" and r["bound"] == "alu"
+
+
+def test_fp32_peak_from_unit_counts():
+    # 152 SMs x 128 lanes x 2 flops x 2070 MHz
+    assert abs(bench.fp32_peak_tflops(152, 2070.0) - 80.54) < 0.01
+    assert abs(bench.fp32_peak_tflops(76, 2070.0) - 40.27) < 0.01
