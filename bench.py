@@ -730,7 +730,7 @@ def cpu_baseline(w, budget_s: float = 8.0):
     v, note = oracle_step_sample(w, budget_s)
     return {"value": None if v is None else round(v, 1), "unit": UNIT, "cores": ORACLE_THREADS,
             "affinity_cores": len(os.sched_getaffinity(0)),
-            "kind": "oracle (extrapolated: measured set-up + sampled Jacobi-PCG iterations x stored iteration count)",
+            "kind": "oracle", "extrapolated": "measured set-up + sampled Jacobi-PCG iterations x stored iteration count",
             "sample": note}
 
 
@@ -758,8 +758,8 @@ def run_reference(args):
                       "config": {"workload": w.name},
                       "cpu_baseline": {"value": v, "unit": UNIT, "cores": ORACLE_THREADS,
                                        "affinity_cores": len(os.sched_getaffinity(0)),
-                                       "kind": "oracle (extrapolated: measured set-up + sampled Jacobi-PCG "
-                                               "iterations x stored iteration count)", "sample": note},
+                                       "kind": "oracle", "extrapolated": "measured set-up + sampled Jacobi-PCG "
+                                       "iterations x stored iteration count", "sample": note},
                       "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
           flush=True)
 

@@ -89,6 +89,8 @@ def test_reference_arm_line_on_rank_zero(monkeypatch):
     assert line["impl"] == "reference" and line["value"] == 1234.5
     assert line["unit"] == bench.UNIT and line["higher_is_better"] is False
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["unit"] == bench.UNIT and line["cpu_baseline"]["cores"] == bench.ORACLE_THREADS
+    assert "extrapolated" in line["cpu_baseline"]
 
 
 def test_oracle_step_sample_runs_on_a_small_mesh():
