@@ -258,6 +258,20 @@ int afd_casting_scan(float* keys, int nx, int ny, int nz, int axis, int parting,
  * of ndof values, RHS-major.  Device pointers only. */
 int afd_apply_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y);
 
+/* One search-direction step of the inner FP32 deflated PCG iteration (Sec.
+ * 3.5), as the solver runs it: for each of n_rhs load cases
+ *   p = z + W mu + beta p_old   on the free DOFs (0 on fixed DOFs),
+ *   q = K p                     (rows of fixed DOFs 0),
+ * formed by the solver's fused FP32 stencil in the mesh's current CTA shape
+ * (afd_set_stencil_shape pins it), and *pq_out = p.q per case (host, nullable).
+ * z, p_old, p_out, q_out: device float, RHS-major with stride ndof; mu: device
+ * double, n_rhs x n_c coarse coefficients (6 rigid modes per group, the order
+ * of afd_deflation_w); beta: host, n_rhs values.  Needs moduli and loads
+ * (the supports); builds the coarse problem if it is stale.  Used by the tests
+ * to check every stencil variant element by element. */
+int afd_apply_search_direction(afd_mesh* m, int n_rhs, const float* z, const float* p_old, const double* mu,
+                               const double* beta, float* p_out, float* q_out, double* pq_out);
+
 /* Deflation operators (Sec. 3.5): out = W^T v (n_rhs*6*N_g) and
  * out = W y (n_rhs*ndof), FP64, device pointers.  Group G's 6 values are
  * (T_x, T_y, T_z, R_x, R_y, R_z): force sums and moments about the group's

@@ -76,3 +76,19 @@ def coarse_matrix(K, W: np.ndarray, fixed: np.ndarray) -> np.ndarray:
     Kff = K[fr][:, fr]
     Wf = W[fr]
     return Wf.T @ (Kff @ Wf)
+
+
+def apply_w(nx, ny, nz, g, fixed: np.ndarray, mu: np.ndarray) -> np.ndarray:
+    """W mu without forming W: at node n of group G the rigid motion
+    t_G + omega_G x (x_n - c_G), with mu = (t_x, t_y, t_z, omega_x, omega_y,
+    omega_z) per group in the column order of ``deflation_matrix``; zero at
+    fixed DOFs."""
+    X = fe.node_coordinates(nx, ny, nz)
+    gid = node_groups(nx, ny, nz, g)
+    c = group_centroids(nx, ny, nz, g)
+    m6 = np.asarray(mu, dtype=np.float64).reshape(-1, 6)
+    rel = X - c[gid]
+    out = m6[gid, :3] + np.cross(m6[gid, 3:], rel)
+    out = out.reshape(-1)
+    out[np.asarray(fixed) != 0] = 0.0
+    return out

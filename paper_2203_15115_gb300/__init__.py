@@ -46,7 +46,7 @@ EXPORTS = [
     "afd_mesh_bytes", "afd_server_create", "afd_server_submit", "afd_server_wait", "afd_server_destroy",
     "afd_server_submit_session", "afd_server_end_session", "afd_server_resident", "afd_levelset_update_cast",
     "afd_casting_scan", "afd_stress_sensitivity", "afd_levelset_update_fields", "afd_modal",
-    "afd_eigen_sensitivity", "afd_buckling", "afd_buckling_sensitivity",
+    "afd_eigen_sensitivity", "afd_buckling", "afd_buckling_sensitivity", "afd_apply_search_direction",
 ]
 
 
@@ -140,6 +140,7 @@ def lib() -> ctypes.CDLL:
             "afd_buckling": (i, [vp, i, d, i, ctypes.POINTER(d), vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
             "afd_buckling_sensitivity": (i, [vp, vp, i]),
             "afd_levelset_update_fields": (i, [vp, vp, i, i, ctypes.POINTER(d), d, i, i, ctypes.POINTER(d), vp]),
+            "afd_apply_search_direction": (i, [vp, i, vp, vp, vp, ctypes.POINTER(d), vp, vp, ctypes.POINTER(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -361,6 +362,23 @@ def afd_apply_stiffness(mesh, arith: int, n_rhs: int, u, y) -> None:
     pu, _, _k1 = _arr(u, dt)
     py, _, _k2 = _arr(y, dt)
     _check(lib().afd_apply_stiffness(mesh, arith, n_rhs, pu, py))
+
+
+def afd_apply_search_direction(mesh, n_rhs: int, z, p_old, mu, beta, p_out, q_out) -> np.ndarray:
+    """p = z + W mu + beta p_old (free DOFs) and q = K p by the solver's fused
+    FP32 stencil; returns p.q per load case.  Device tensors only."""
+    for name, x in (("z", z), ("p_old", p_old), ("mu", mu), ("p_out", p_out), ("q_out", q_out)):
+        if not (hasattr(x, "data_ptr") and x.is_cuda):
+            raise TypeError(f"{name} must be a CUDA tensor")
+    pz, _, _k1 = _arr(z, np.float32)
+    pp, _, _k2 = _arr(p_old, np.float32)
+    pm, _, _k3 = _arr(mu, np.float64)
+    po, _, _k4 = _arr(p_out, np.float32)
+    pq, _, _k5 = _arr(q_out, np.float32)
+    b = (ctypes.c_double * n_rhs)(*[float(x) for x in beta])
+    out = (ctypes.c_double * n_rhs)()
+    _check(lib().afd_apply_search_direction(mesh, n_rhs, pz, pp, pm, b, po, pq, out))
+    return np.array(out[:])
 
 
 def afd_deflation_wt(mesh, n_rhs: int, v, out) -> None:

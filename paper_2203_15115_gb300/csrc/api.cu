@@ -2072,6 +2072,39 @@ int afd_apply_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* 
   return finish(m);
 }
 
+int afd_apply_search_direction(afd_mesh* m, int n_rhs, const float* z, const float* p_old, const double* mu,
+                               const double* beta, float* p_out, float* q_out, double* pq_out) {
+  if (!m || !z || !p_old || !mu || !beta || !p_out || !q_out) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "n_rhs must be >= 1");
+  if (!m->has_moduli || !m->has_loads) return fail(AFD_ERR_STATE, "set moduli and loads first");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  TRY(build_coarse(m));
+  const size_t nd = (size_t)m->gr.ndof;
+  const int nsb = stencil_blocks(m, false);
+  TRY(ensure_partials(m, (size_t)nsb));
+  std::vector<double> parts(nsb);
+  for (int r = 0; r < n_rhs; ++r) {
+    // beta reaches the kernel through the solver state of RHS 0 (the kernel
+    // is launched for one RHS at a time on caller arrays of stride ndof)
+    CGState h;
+    memset(&h, 0, sizeof(h));
+    h.beta = beta[r];
+    CK(cudaMemcpyAsync(m->st, &h, sizeof(h), cudaMemcpyHostToDevice, m->s));
+    TRY((launch_stencil<float, ST_APPLY_DOT, float>(m, p_old + r * nd, q_out + r * nd, m->w32.E, nullptr, nullptr,
+                                                     m->partials, nullptr, 1, m->w32.K, m->st, nullptr, z + r * nd,
+                                                     mu + (size_t)r * m->nc, p_out + r * nd, nullptr)));
+    if (pq_out) {
+      CK(cudaMemcpyAsync(parts.data(), m->partials, nsb * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+      CK(cudaStreamSynchronize(m->s));
+      double sum = 0.0;
+      for (int b = 0; b < nsb; ++b) sum += parts[b];
+      pq_out[r] = sum;
+    }
+  }
+  return finish(m);
+}
+
 int afd_deflation_wt(afd_mesh* m, int n_rhs, const double* v, double* out) {
   if (!m || !v || !out || n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "bad argument");
   DeviceGuard dg(m->device);

@@ -1,0 +1,120 @@
+"""Every CTA shape and plane staging the FP32 stencil's autotuner can pick,
+checked element by element against the oracle (Sec. 3.5: K u without
+assembling K), through the C ABI:
+
+* K u alone (afd_apply_stiffness) against the oracle's assembled K with the
+  fixed rows and columns removed;
+* the fused step of the inner deflated PCG iteration
+  (afd_apply_search_direction): p = z + W mu + beta p_old on the free DOFs
+  against the oracle's W mu, q = K p against the assembled K applied to the
+  kernel's own p, and p.q against the float64 dot of the returned vectors.
+
+The shape is pinned with afd_set_stencil_shape, so the variant the autotuner
+would take on a large mesh (e.g. the cp.async ring, 16 warps, 24 planes) is
+the one that runs here.  Meshes: several x and y tiles with ragged edges and
+several z chunks at every depth, scattered supports, moduli spanning 1e-3..1.
+
+Tolerances (max-norm relative to the largest entry, derived from FP32
+rounding): K u 2e-6 (a sum of <= 27 x 24 products, about 10 ulp of the
+cancelling sum); p 2e-6 of max(|z| + |W mu| + |beta p_old|) (three roundings
+of terms of that size); p.q 1e-5 relative (per-thread FP32 partial sums).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import paper_2203_15115_gb300 as afd  # noqa: E402
+from oracle import deflation, fe  # noqa: E402
+
+PLANES = [2, 3, 4, 5, 6, 8, 12, 16, 24, 32]
+WARPS = [8, 16]
+STAGING = [0, 1]
+MESHES = {"70x40x30": (70, 40, 30, 10), "3x2x50": (3, 2, 50, 2), "33x31x9": (33, 31, 9, 4)}
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def masked_matvec(K, u, fixed):
+    uu = u.copy()
+    uu[fixed != 0] = 0.0
+    y = K @ uu
+    y[fixed != 0] = 0.0
+    return y
+
+
+class Case:
+    def __init__(self, nx, ny, nz, g):
+        rng = np.random.default_rng(nx * 10000 + ny * 100 + nz)
+        self.nx, self.ny, self.nz, self.g = nx, ny, nz, g
+        self.E = rng.uniform(1e-3, 1.0, nx * ny * nz)
+        ndof = 3 * (nx + 1) * (ny + 1) * (nz + 1)
+        self.fixed = (rng.random(ndof) < 0.08).astype(np.uint8)
+        self.fixed[: 3 * (nx + 1)] = 1   # a fully clamped first node row as well
+        self.K = fe.assemble(nx, ny, nz, self.E)
+        self.m = afd.Mesh(nx, ny, nz, group=g, precision=afd.AFD_MIXED)
+        self.m.set_element_moduli(self.E)
+        self.m.set_loads_bcs(np.zeros((1, ndof)), self.fixed)
+        self.nc = afd.afd_coarse_size(self.m.h)
+        R = 2
+        self.u = rng.standard_normal((R, ndof)).astype(np.float32)
+        self.y_ref = np.stack([masked_matvec(self.K, self.u[r].astype(np.float64), self.fixed) for r in range(R)])
+        self.z = rng.standard_normal((R, ndof)).astype(np.float32)
+        self.p_old = rng.standard_normal((R, ndof)).astype(np.float32)
+        self.mu = 0.3 * rng.standard_normal((R, self.nc))
+        self.beta = [0.7, -1.3]
+        self.p_ref, self.p_scale = [], []
+        for r in range(R):
+            wmu = deflation.apply_w(nx, ny, nz, g, self.fixed, self.mu[r])
+            z64, p64 = self.z[r].astype(np.float64), self.p_old[r].astype(np.float64)
+            p = z64 + wmu + self.beta[r] * p64
+            p[self.fixed != 0] = 0.0
+            self.p_ref.append(p)
+            self.p_scale.append(np.max(np.abs(z64) + np.abs(wmu) + abs(self.beta[r]) * np.abs(p64)))
+
+
+@pytest.fixture(scope="module")
+def cases():
+    assert torch.cuda.is_available()
+    afd.lib()
+    out = {k: Case(*v) for k, v in MESHES.items()}
+    yield out
+    for c in out.values():
+        c.m.close()
+
+
+@pytest.mark.parametrize("staging", STAGING)
+@pytest.mark.parametrize("warps", WARPS)
+@pytest.mark.parametrize("mesh", list(MESHES))
+def test_every_stencil_shape_matches_the_oracle(cases, mesh, warps, staging):
+    c = cases[mesh]
+    R = c.u.shape[0]
+    ndof = c.u.shape[1]
+    u = cuda(c.u)
+    for planes in PLANES:
+        afd.afd_set_stencil_shape(c.m.h, warps, planes, staging)
+        shape = (warps, planes, staging)
+        y = torch.zeros((R, ndof), dtype=torch.float32, device="cuda")
+        afd.afd_apply_stiffness(c.m.h, afd.AFD_F32, R, u, y)
+        y = y.cpu().numpy().astype(np.float64)
+        err = np.max(np.abs(y - c.y_ref)) / np.max(np.abs(c.y_ref))
+        assert err <= 2e-6, ("K u", shape, err)
+
+        p = torch.full((R, ndof), np.nan, dtype=torch.float32, device="cuda")
+        q = torch.full((R, ndof), np.nan, dtype=torch.float32, device="cuda")
+        pq = afd.afd_apply_search_direction(c.m.h, R, cuda(c.z), cuda(c.p_old), cuda(c.mu), c.beta, p, q)
+        p = p.cpu().numpy().astype(np.float64)
+        q = q.cpu().numpy().astype(np.float64)
+        for r in range(R):
+            ep = np.max(np.abs(p[r] - c.p_ref[r])) / c.p_scale[r]
+            assert ep <= 2e-6, ("p", shape, r, ep)
+            assert np.all(p[r][c.fixed != 0] == 0.0)
+            qref = masked_matvec(c.K, p[r], c.fixed)
+            eq = np.max(np.abs(q[r] - qref)) / np.max(np.abs(qref))
+            assert eq <= 2e-6, ("q", shape, r, eq)
+            dot = float(p[r] @ q[r])
+            assert abs(pq[r] - dot) <= 1e-5 * abs(dot), ("p.q", shape, r, pq[r], dot)

@@ -51,3 +51,19 @@ def test_coarse_matrix_spd_with_clamp_and_six_zero_modes_without():
     W0 = deflation.deflation_matrix(nx, ny, nz, g, free)
     w = np.linalg.eigvalsh(deflation.coarse_matrix(K, W0, free))
     assert np.sum(np.abs(w) < 1e-10 * w.max()) == 6
+
+
+def test_apply_w_equals_the_dense_deflation_matrix():
+    """W mu without forming W agrees with the explicit columns (ragged group
+    grid, last planes folded, scattered supports), and it is rigid on one
+    unsupported group: K (W mu) = 0."""
+    rng = np.random.default_rng(21)
+    for (nx, ny, nz, g) in ((5, 3, 4, 2), (7, 4, 3, 3), (3, 3, 3, 3)):
+        nn = (nx + 1) * (ny + 1) * (nz + 1)
+        fixed = (rng.random(3 * nn) < 0.1).astype(np.uint8)
+        W = deflation.deflation_matrix(nx, ny, nz, g, fixed)
+        mu = rng.standard_normal(W.shape[1])
+        assert np.max(np.abs(deflation.apply_w(nx, ny, nz, g, fixed, mu) - W @ mu)) < 1e-13
+    K = fe.assemble(3, 3, 3, np.ones(27))
+    v = deflation.apply_w(3, 3, 3, 3, np.zeros(3 * 64, np.uint8), rng.standard_normal(6))
+    assert np.max(np.abs(K @ v)) < 1e-12 * np.max(np.abs(v))
