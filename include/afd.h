@@ -447,6 +447,122 @@ void afd_al_update(afd_al_state* s, double g_new);
 /* Eq. 3.18 weight: mu + gamma g when positive, else 0. */
 double afd_al_weight(const afd_al_state* s);
 
+/* ---- the algorithm of Sec. 3.8 (steps 2-9) with Eq. 3.21's constraints ----
+ *
+ * min |Omega| subject to up to four constraints, each against its value at
+ * the initial design (Sec. 3.8 step 1):
+ *   AFD_CON_COMPLIANCE  J <= bound J_0          g = J / (bound J_0) - 1
+ *   AFD_CON_STRESS      sigma_PN <= bound s_0   g = sigma_PN / (bound s_0) - 1
+ *   AFD_CON_EIGEN       lambda_1 >= bound l_0   g = 1 - lambda_1 / (bound l_0)
+ *   AFD_CON_BUCKLING    P >= bound P_0          g = 1 - P / (bound P_0)
+ * (J and sigma_PN of load case 0, Eqs. 1.3-1.4 and the p-norm of Eq. 3.3;
+ * lambda_1 the fundamental eigenvalue of the lumped-mass modal problem; P the
+ * smallest positive buckling factor of load case 0).  Every analysis updates
+ * each constraint's (mu, gamma) by Eqs. 3.11-3.12; a hard constraint with
+ * g > 0 makes the design infeasible.  Steps: a violated hard constraint sends
+ * the run back to the last feasible design with the volume step halved (stop
+ * when it falls below dv_min); a feasible analysis whose J moved by at most
+ * conv since the previous analysis at the same target lowers the target by the
+ * volume step (stop when it would fall below v_min); otherwise the target
+ * stays.  Each new design is the level set (Eq. 3.17) of the constraints'
+ * fields -- strain energy (compliance), the adjoint T_sigma (stress, Eq. 3.3),
+ * T_lambda (Eq. 3.4), Eq. 3.5's field (buckling) -- weighted by their Eq. 3.18
+ * weights, optionally with the casting scan (Sec. 3.7), cut at the target
+ * volume (Eq. 3.6).  The volume objective's sensitivity is constant and does
+ * not change the ranking. */
+enum { AFD_CON_COMPLIANCE = 0, AFD_CON_STRESS = 1, AFD_CON_EIGEN = 2, AFD_CON_BUCKLING = 3, AFD_CON_COUNT = 4 };
+enum { AFD_STOP_MAX_FEA = 0, AFD_STOP_DV_MIN = 1, AFD_STOP_V_MIN = 2 };
+
+typedef struct {
+  double bound[AFD_CON_COUNT];  /* alpha per constraint; a constraint is active when bound > 0 */
+  int soft[AFD_CON_COUNT];      /* 1: soft (Sec. 3.6: eigenvalue and buckling only) -- steers, never violated */
+  double p;                     /* p-norm exponent of the stress constraint */
+  double dv0;                   /* first volume step */
+  double dv_min;                /* stop when the halved step falls below it (<= 0: 0.1 dv0) */
+  double v_min;                 /* lowest target volume fraction */
+  double conv;                  /* relative change of J that counts as converged (e.g. 0.01) */
+  int max_fea;                  /* cap on analyses */
+  double tol;                   /* relative residual of every solve */
+  double eig_tol;               /* relative residual of the eigen analyses */
+  double rho;                   /* density of the modal analysis */
+  int casting_axis;             /* -1: no casting constraint; else 0/1/2 with casting_parting */
+  int casting_parting;
+} afd_topology_spec;
+
+/* One analysis of the run.  g[c]/mu[c]/gamma[c] are NaN for inactive c, and
+ * so is value[c] except J (value[AFD_CON_COMPLIANCE]), analysed every time. */
+typedef struct {
+  int fea;                          /* analyses so far (1 = the initial design) */
+  double v;                         /* volume fraction of the analysed design */
+  double target;                    /* target volume fraction after this analysis' decision */
+  double dv;                        /* volume step */
+  double value[AFD_CON_COUNT];      /* J, sigma_PN, lambda_1, P */
+  double g[AFD_CON_COUNT];          /* normalised constraint values */
+  int violated;                     /* a hard constraint has g > 0 */
+  int iters;                        /* inner iterations of the static solve */
+  double rel_residual;              /* its final relative residual */
+  double mu[AFD_CON_COUNT], gamma[AFD_CON_COUNT];  /* AL scalars after this analysis' update */
+} afd_topology_record;
+
+typedef struct {
+  int stop;                         /* AFD_STOP_* */
+  int fea;                          /* analyses run */
+  int n_records;                    /* records produced (those beyond hist_cap are not stored) */
+  double volume_fraction;           /* of the final (last feasible) design */
+  double reference[AFD_CON_COUNT];  /* values at the initial design */
+} afd_topology_result;
+
+/* The steps above with caller-supplied analyses (the same loop that
+ * afd_constrained_topology runs on a mesh; lets any analysis drive it).  Each
+ * callback returns AFD_OK or an error code that ends the run with that code.
+ *   analyse: analyse the current design (warm: start the solve from the last
+ *            solution), fill value[4] for the active constraints, keep their
+ *            fields for the next cut, and report the static solve's stats;
+ *   save_feasible / restore_feasible: remember / reinstate the current design;
+ *   cut:     make the level set of the kept fields with weight[c] (0 for
+ *            inactive c) at volume fraction v_target the current design. */
+typedef struct {
+  int (*analyse)(void* ctx, int warm, double* value, int* iters, double* rel_residual);
+  int (*save_feasible)(void* ctx);
+  int (*restore_feasible)(void* ctx);
+  int (*cut)(void* ctx, const double* weight, double v_target);
+} afd_topology_ops;
+
+int afd_topology_run(const afd_topology_spec* spec, const afd_topology_ops* ops, void* ctx,
+                     afd_topology_record* hist, int hist_cap, afd_topology_result* res);
+
+/* The Sec. 3.8 algorithm on a mesh, from its current moduli, loads (one load
+ * case) and supports: every analysis, field, snapshot and cut stays on the
+ * device (afd_solve warm-started, afd_compliance, afd_pnorm_stress,
+ * afd_sensitivity, afd_stress_sensitivity, afd_buckling(+_sensitivity),
+ * afd_modal + afd_eigen_sensitivity, the level-set cut).  kept_out (host,
+ * N_e bytes) and E_out (host, N_e doubles), nullable, receive the final
+ * feasible design; the mesh ends holding the last analysed design. */
+int afd_constrained_topology(afd_mesh* m, const afd_topology_spec* spec, afd_topology_record* hist, int hist_cap,
+                             afd_topology_result* res, uint8_t* kept_out, double* E_out);
+
+/* The compliance-constrained volume minimisation with fixed volume steps
+ * (Sec. 3.8 with the Delta-v control replaced by v_k = 1 - k dv): solve for
+ * J_0 (J_all = j_factor J_0), then `steps` times take the level set of the
+ * AL-weighted field `kind` (AFD_SENS_*) at v_k, solve it warm-started from the
+ * previous solution, and update (mu, gamma) with g = J / J_all - 1.  One
+ * record per solve (record 0: the initial design), hist holds steps + 1. */
+typedef struct {
+  int step;
+  double volume_fraction;
+  double J, J_over_J0, g;
+  int iters;
+  double rel_residual;
+  double ms;                /* wall time of the step (level set + solve + J) */
+  double tau;               /* level-set threshold (NaN for step 0) */
+  double al_weight;         /* Eq. 3.18 weight used for the cut (before this step's update) */
+  double mu, gamma;         /* AL scalars after the step's update */
+  long long kept;           /* elements kept by the cut (N_e for step 0) */
+} afd_volmin_record;
+
+int afd_volume_minimisation(afd_mesh* m, int steps, double dv, double j_factor, double tol, int kind,
+                            afd_volmin_record* hist, uint8_t* kept_out, double* u_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,7 @@ EXPORTS = [
     "afd_server_submit_session", "afd_server_end_session", "afd_server_resident", "afd_levelset_update_cast",
     "afd_casting_scan", "afd_stress_sensitivity", "afd_levelset_update_fields", "afd_modal",
     "afd_eigen_sensitivity", "afd_buckling", "afd_buckling_sensitivity", "afd_apply_search_direction",
+    "afd_topology_run", "afd_constrained_topology", "afd_volume_minimisation",
 ]
 
 
@@ -141,6 +142,9 @@ def lib() -> ctypes.CDLL:
             "afd_buckling_sensitivity": (i, [vp, vp, i]),
             "afd_levelset_update_fields": (i, [vp, vp, i, i, ctypes.POINTER(d), d, i, i, ctypes.POINTER(d), vp]),
             "afd_apply_search_direction": (i, [vp, i, vp, vp, vp, ctypes.POINTER(d), vp, vp, ctypes.POINTER(d)]),
+            "afd_topology_run": (i, [vp, vp, vp, vp, i, vp]),
+            "afd_constrained_topology": (i, [vp, vp, vp, i, vp, vp, vp]),
+            "afd_volume_minimisation": (i, [vp, i, d, d, d, i, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -559,50 +563,163 @@ def afd_al_weight(s: afd_al_state) -> float:
     return float(lib().afd_al_weight(ctypes.byref(s)))
 
 
+class afd_topology_spec(ctypes.Structure):
+    _fields_ = [("bound", ctypes.c_double * 4), ("soft", ctypes.c_int * 4), ("p", ctypes.c_double),
+                ("dv0", ctypes.c_double), ("dv_min", ctypes.c_double), ("v_min", ctypes.c_double),
+                ("conv", ctypes.c_double), ("max_fea", ctypes.c_int), ("tol", ctypes.c_double),
+                ("eig_tol", ctypes.c_double), ("rho", ctypes.c_double), ("casting_axis", ctypes.c_int),
+                ("casting_parting", ctypes.c_int)]
+
+
+class afd_topology_record(ctypes.Structure):
+    _fields_ = [("fea", ctypes.c_int), ("v", ctypes.c_double), ("target", ctypes.c_double), ("dv", ctypes.c_double),
+                ("value", ctypes.c_double * 4), ("g", ctypes.c_double * 4), ("violated", ctypes.c_int),
+                ("iters", ctypes.c_int), ("rel_residual", ctypes.c_double), ("mu", ctypes.c_double * 4),
+                ("gamma", ctypes.c_double * 4)]
+
+
+class afd_topology_result(ctypes.Structure):
+    _fields_ = [("stop", ctypes.c_int), ("fea", ctypes.c_int), ("n_records", ctypes.c_int),
+                ("volume_fraction", ctypes.c_double), ("reference", ctypes.c_double * 4)]
+
+
+TOPO_ANALYSE = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double))
+TOPO_STEP = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p)
+TOPO_CUT = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_double)
+
+
+class afd_topology_ops(ctypes.Structure):
+    _fields_ = [("analyse", TOPO_ANALYSE), ("save_feasible", TOPO_STEP), ("restore_feasible", TOPO_STEP),
+                ("cut", TOPO_CUT)]
+
+
+class afd_volmin_record(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int), ("volume_fraction", ctypes.c_double), ("J", ctypes.c_double),
+                ("J_over_J0", ctypes.c_double), ("g", ctypes.c_double), ("iters", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("ms", ctypes.c_double), ("tau", ctypes.c_double),
+                ("al_weight", ctypes.c_double), ("mu", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("kept", ctypes.c_longlong)]
+
+
+# constraint names in the order of AFD_CON_COMPLIANCE .. AFD_CON_BUCKLING
+CONSTRAINTS = ("J", "sigma", "lambda", "P")
+_STOPS = {0: "max_fea", 1: "dv_min", 2: "v_min"}
+
+
+def topology_spec(compliance=None, stress=None, eigen=None, buckling=None, soft=(), p: float = 8.0,
+                  dv0: float = 0.05, dv_min: Optional[float] = None, v_min: float = 0.05, conv: float = 0.01,
+                  max_fea: int = 200, tol: float = 1e-6, eig_tol: float = 1e-6, rho: float = 1.0,
+                  casting=None) -> afd_topology_spec:
+    """The afd_topology_spec of the keyword arguments (None: constraint absent;
+    soft names among "lambda", "P"; casting (axis, parting) or None)."""
+    sp = afd_topology_spec()
+    for c, b in enumerate((compliance, stress, eigen, buckling)):
+        sp.bound[c] = 0.0 if b is None else float(b)
+        sp.soft[c] = int(CONSTRAINTS[c] in set(soft))
+    sp.p, sp.dv0, sp.dv_min, sp.v_min, sp.conv = p, dv0, (0.0 if dv_min is None else dv_min), v_min, conv
+    sp.max_fea, sp.tol, sp.eig_tol, sp.rho = max_fea, tol, eig_tol, rho
+    sp.casting_axis, sp.casting_parting = (-1, 0) if casting is None else (int(casting[0]), int(casting[1]))
+    return sp
+
+
+def _topology_output(sp, hist, res) -> dict:
+    """Records and result of a Sec. 3.8 run as Python dicts (values of absent
+    constraints are None)."""
+    act = [sp.bound[c] > 0 for c in range(4)]
+
+    def opt(x):
+        return None if x != x else float(x)
+
+    out = []
+    for r in hist[:min(res.n_records, len(hist))]:
+        rec = {"fea": r.fea, "v": r.v, "target": r.target, "dv": r.dv, "violated": bool(r.violated),
+               "iters": r.iters, "rel_residual": r.rel_residual}
+        for c, name in enumerate(CONSTRAINTS):
+            rec[name] = opt(r.value[c])
+        rec["g"] = {name: r.g[c] for c, name in enumerate(CONSTRAINTS) if act[c]}
+        rec["mu"] = {name: r.mu[c] for c, name in enumerate(CONSTRAINTS) if act[c]}
+        rec["gamma"] = {name: r.gamma[c] for c, name in enumerate(CONSTRAINTS) if act[c]}
+        out.append(rec)
+    return {"history": out, "volume_fraction": res.volume_fraction, "stop": _STOPS[res.stop], "fea": res.fea,
+            "reference": {name: opt(res.reference[c]) for c, name in enumerate(CONSTRAINTS)}}
+
+
+def afd_topology_run(spec: afd_topology_spec, analyse, save_feasible, restore_feasible, cut,
+                     hist_cap: int = 1000) -> dict:
+    """The Sec. 3.8 loop of the library (afd_topology_run) over Python
+    analyses: analyse(warm) -> (values[4], iters, rel_residual) with None for
+    constraints it does not evaluate; save_feasible(); restore_feasible();
+    cut(weights[4], v_target).  An exception in a callback ends the run with
+    AFD_ERR_STATE and is re-raised."""
+    err = []
+
+    def guard(fn):
+        def wrapped(*a):
+            try:
+                return fn(*a)
+            except BaseException as e:  # noqa: BLE001 - re-raised after the C call returns
+                err.append(e)
+                return AFD_ERR_STATE
+        return wrapped
+
+    @guard
+    def _analyse(ctx, warm, val, it, rel):
+        v, iters, r = analyse(bool(warm))
+        for c in range(4):
+            val[c] = float("nan") if v[c] is None else float(v[c])
+        it[0], rel[0] = int(iters), float(r)
+        return AFD_OK
+
+    @guard
+    def _save(ctx):
+        save_feasible()
+        return AFD_OK
+
+    @guard
+    def _restore(ctx):
+        restore_feasible()
+        return AFD_OK
+
+    @guard
+    def _cut(ctx, w, v):
+        cut([w[c] for c in range(4)], float(v))
+        return AFD_OK
+
+    ops = afd_topology_ops(TOPO_ANALYSE(_analyse), TOPO_STEP(_save), TOPO_STEP(_restore), TOPO_CUT(_cut))
+    hist = (afd_topology_record * hist_cap)()
+    res = afd_topology_result()
+    rc = lib().afd_topology_run(ctypes.byref(spec), ctypes.byref(ops), None, hist, hist_cap, ctypes.byref(res))
+    if err:
+        raise err[0]
+    _check(rc)
+    return _topology_output(spec, hist, res)
+
+
 def run_volume_minimisation(mesh: "Mesh", steps: int = 20, dv: float = 0.02, j_factor: float = 1.6,
                             tol: float = 1e-6, kind: int = AFD_SENS_STRAIN_ENERGY, on_step=None,
                             kept_out=None, u_out=None) -> list:
-    """Compliance-constrained volume minimisation by the topological level set
-    with the augmented-Lagrangian weight (Sec. 3.8 with fixed volume steps;
-    Eqs. 3.6, 3.11, 3.12, 3.17, 3.18): starting from the mesh's current moduli
-    and loads, solve once for J_0 (the constraint is J <= j_factor * J_0), then
-    `steps` times: take the level set of the AL-weighted field at volume
-    fraction 1 - k dv (the mesh's moduli are rewritten on the device), solve
-    from the previous solution (warm start), and update the AL scalars with
-    g = J / (j_factor J_0) - 1.  Every step runs in the library's kernels; this
-    loop only moves the scalars.  Returns one dict per solve (step 0 is the
-    initial design).  kept_out (host uint8, nelem) receives the last kept mask
-    and each step records its kept count; u_out (host float64, ndof) receives
-    the last displacement."""
-    hist = []
-    t0 = time.perf_counter()
-    st = mesh.solve(tol)
-    J = float(mesh.compliance()[0])
-    J0, J_all = J, j_factor * J
-    al = afd_al_init()
-    hist.append({"step": 0, "volume_fraction": 1.0, "J": J, "g": J / J_all - 1.0, "iters": st[0]["iters"],
-                 "rel_residual": st[0]["rel_residual"], "ms": (time.perf_counter() - t0) * 1e3, "tau": None,
-                 "al_weight": afd_al_weight(al)})
-    if on_step:
-        on_step(hist[-1])
-    for k in range(1, steps + 1):
-        t0 = time.perf_counter()
-        v = 1.0 - k * dv
-        wgt = afd_al_weight(al)
-        mask = kept_out if kept_out is not None else None
-        tau = mesh.levelset_update(kind, [wgt], v, mask)
-        last = k == steps
-        st = mesh.solve(tol, warm_start=True, u_out=u_out if (last and u_out is not None) else None)
-        J = float(mesh.compliance()[0])
-        g = J / J_all - 1.0
-        afd_al_update(al, g)
-        hist.append({"step": k, "volume_fraction": v, "J": J, "J_over_J0": J / J0, "g": g, "iters": st[0]["iters"],
-                     "rel_residual": st[0]["rel_residual"], "ms": (time.perf_counter() - t0) * 1e3, "tau": tau,
-                     "al_weight": wgt, "mu": al.mu, "gamma": al.gamma,
-                     "kept": int(np.count_nonzero(mask)) if mask is not None else None})
+    """Compliance-constrained volume minimisation with fixed volume steps
+    (afd_volume_minimisation: Sec. 3.8 with v_k = 1 - k dv; Eqs. 3.6, 3.11,
+    3.12, 3.17, 3.18), run by the library from the mesh's current moduli and
+    loads.  Returns one dict per solve (step 0 is the initial design); on_step
+    is called with each afterwards.  kept_out (host uint8, nelem) receives the
+    last kept mask; u_out (host float64, ndof) the last displacement."""
+    hist = (afd_volmin_record * (steps + 1))()
+    pk, _, _k1 = _arr(kept_out, np.uint8) if kept_out is not None else (None, 0, None)
+    pu, _, _k2 = _arr(u_out, np.float64) if u_out is not None else (None, 0, None)
+    if kept_out is not None and not isinstance(kept_out, np.ndarray):
+        raise TypeError("kept_out must be a host numpy array")
+    _check(lib().afd_volume_minimisation(mesh.h, steps, dv, j_factor, tol, kind, hist, pk, pu))
+    out = []
+    for r in hist:
+        rec = {k: getattr(r, k) for k, _ in afd_volmin_record._fields_}
+        if r.step == 0:
+            rec["tau"] = None
+        out.append(rec)
         if on_step:
-            on_step(hist[-1])
-    return hist
+            on_step(rec)
+    return out
 
 
 def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] = None, stress: Optional[float] = None,
@@ -610,132 +727,33 @@ def run_constrained_topology(mesh: "Mesh", E_init, compliance: Optional[float] =
                              max_fea: int = 200, conv: float = 0.01, tol: float = 1e-6, casting=None,
                              on_step=None, eigen: Optional[float] = None, rho: float = 1.0,
                              eig_tol: float = 1e-6, buckling: Optional[float] = None, soft=()) -> dict:
-    """The algorithm of Sec. 3.8 (with Eq. 3.21's four constraints) for
-    min |Omega| subject to J <= compliance * J_0, sigma_PN <= stress * sigma_0,
-    lambda_1 >= eigen * lambda_1,0 (the fundamental eigenvalue of the
-    lumped-mass modal problem, afd_modal) and P >= buckling * P_0 (the
-    smallest positive buckling load factor of load case 0, afd_buckling); any
-    may be None.  Constraints named in `soft` ("lambda", "P"; Sec. 3.6) steer
-    the level set through their AL weights but never count as violated.  Over
-    the library's calls (each step runs in its kernels):
-      2. analysis: solve (warm start), J, sigma_PN (p-norm of Eq. 3.3), their
-         fields (strain energy, adjoint T_sigma); with `buckling` the buckling
-         analysis of that state (1 factor to eig_tol) and Eq. 3.5's field; with
-         `eigen` the modal analysis (1 mode to eig_tol, density rho) and
-         T_lambda (Eq. 3.4);
-      3. g_i = value / (alpha_i value_0) - 1 for the upper bounds (J, sigma),
-         g = 1 - value / (alpha value_0) for the lower bounds (lambda, P), and
-         the AL update (Eqs. 3.11-3.12);
-      4./9. a violated hard constraint returns to the last feasible design with
-         the volume step halved (stop when it falls below dv_min, default 0.1 dv0);
-         soft constraints are not checked;
-      5./6. the augmented level set (Eq. 3.17): strain-energy field weighted by
-         the compliance constraint's (mu + gamma g)+, the adjoint stress field
-         T_sigma by the stress constraint's, T_lambda and T_P by the eigenvalue
-         and buckling constraints', optional casting, cut at the target volume;
-      7./8. when J changed by less than `conv` since the previous analysis at
-         the same target, the target drops by the volume step (stop below
-         v_min).
-    The volume objective's sensitivity is constant and does not change the
-    ranking.  Returns the history, the final feasible design's kept mask and
-    volume fraction, and why it stopped."""
-    ne = mesh.nelem
-    dv_min = 0.1 * dv0 if dv_min is None else dv_min
-    cons = [c for c in (("J", compliance), ("sigma", stress), ("lambda", eigen), ("P", buckling)) if c[1] is not None]
-    soft = set(soft)
-    if not soft <= {"lambda", "P"}:
+    """The algorithm of Sec. 3.8 with Eq. 3.21's constraints, run by the library
+    on the mesh (afd_constrained_topology; every analysis, field and cut stays
+    on the device): min |Omega| subject to J <= compliance J_0,
+    sigma_PN <= stress sigma_0, lambda_1 >= eigen lambda_1,0 and
+    P >= buckling P_0 (any may be None; "lambda" and "P" may be soft).  Starts
+    from E_init.  Returns the history (one dict per analysis; on_step is called
+    with each afterwards), the final feasible design's kept mask, moduli and
+    volume fraction, why it stopped, the number of analyses and the reference
+    values."""
+    if not set(soft) <= {"lambda", "P"}:
         raise ValueError("only the eigenvalue and buckling constraints can be soft")
-    hard = [name for name, _ in cons if name not in soft]
-    al = {name: afd_al_init() for name, _ in cons}
-    E_cur = np.asarray(E_init, dtype=np.float64).copy()
-    mesh.set_element_moduli(E_cur)
-    e_void = mesh.options.e_void
-
-    def analyse(warm):
-        # the static fields first: the modal analysis discards the static solution
-        st = mesh.solve(tol, warm_start=warm)
-        J = float(mesh.compliance()[0])
-        sig = float(mesh.pnorm_stress(p)[0]) if stress is not None else None
-        flds = {}
-        if compliance is not None:
-            f = np.zeros((1, ne), np.float32)
-            mesh.sensitivity(AFD_SENS_STRAIN_ENERGY, f)
-            flds["J"] = f[0]
-        if stress is not None:
-            f = np.zeros((1, ne), np.float32)
-            mesh.stress_sensitivity(p, tol, f)
-            flds["sigma"] = f[0]
-        P1 = None
-        if buckling is not None:   # the state is the solution just computed
-            lamb, _ = mesh.buckling(1, tol=eig_tol)
-            P1 = float(lamb[0])
-            f = np.zeros((1, ne), np.float32)
-            mesh.buckling_sensitivity(f)
-            flds["P"] = f[0]
-        lam1 = None
-        if eigen is not None:
-            lam, _ = mesh.modal(1, rho=rho, tol=eig_tol)
-            lam1 = float(lam[0])
-            f = np.zeros((1, ne), np.float32)
-            mesh.eigen_sensitivity(f)
-            flds["lambda"] = f[0]
-        return st[0], {"J": J, "sigma": sig, "lambda": lam1, "P": P1}, flds
-
-    def gval(name, alpha, v, r):
-        return 1.0 - v / (alpha * r) if name in ("lambda", "P") else v / (alpha * r) - 1.0
-
-    st, val, flds = analyse(False)
-    fea = 1
-    ref = dict(val)
-    feasible = {"E": E_cur.copy(), "v": 1.0, "kept": np.ones(ne, np.uint8)}
-    v_design, dv = 1.0, dv0
-    v_target = 1.0 - dv
-    J_prev = None
-    kept = np.ones(ne, np.uint8)
-    hist = []
-    reason = "max_fea"
-    while True:
-        g = {name: gval(name, alpha, val[name], ref[name]) for name, alpha in cons}
-        for name, _ in cons:
-            afd_al_update(al[name], g[name])
-        violated = any(g[name] > 0.0 for name in hard)
-        rec = {"fea": fea, "v": v_design, "target": v_target, "dv": dv, "J": val["J"], "sigma": val["sigma"],
-               "lambda": val["lambda"], "P": val["P"],
-               "g": dict(g), "violated": violated, "iters": st["iters"], "rel_residual": st["rel_residual"],
-               "mu": {n: al[n].mu for n, _ in cons}, "gamma": {n: al[n].gamma for n, _ in cons}}
-        hist.append(rec)
-        if on_step:
+    sp = topology_spec(compliance, stress, eigen, buckling, soft, p, dv0, dv_min, v_min, conv, max_fea, tol,
+                       eig_tol, rho, casting)
+    mesh.set_element_moduli(np.asarray(E_init, dtype=np.float64))
+    ne = mesh.nelem
+    hist = (afd_topology_record * max(1, max_fea))()
+    res = afd_topology_result()
+    kept = np.zeros(ne, np.uint8)
+    E = np.zeros(ne)
+    _check(lib().afd_constrained_topology(mesh.h, ctypes.byref(sp), hist, max(1, max_fea), ctypes.byref(res),
+                                          ctypes.c_void_p(kept.ctypes.data), ctypes.c_void_p(E.ctypes.data)))
+    out = _topology_output(sp, hist, res)
+    out["kept"], out["E"] = kept, E
+    if on_step:
+        for rec in out["history"]:
             on_step(rec)
-        if fea >= max_fea:
-            break
-        if violated:
-            dv *= 0.5
-            if dv < dv_min:
-                reason = "dv_min"
-                break
-            E_cur = feasible["E"].copy()
-            mesh.set_element_moduli(E_cur)
-            v_design, v_target = feasible["v"], feasible["v"] - dv
-            st, val, flds = analyse(True)
-            fea += 1
-            J_prev = None
-        else:
-            feasible = {"E": E_cur.copy(), "v": v_design, "kept": kept.copy()}
-            if J_prev is not None and abs(val["J"] - J_prev) <= conv * abs(J_prev):
-                if v_target - dv < v_min:
-                    reason = "v_min"
-                    break
-                v_target -= dv
-            J_prev = val["J"]
-        fields = [flds[name] for name, _ in cons]
-        weights = [afd_al_weight(al[name]) for name, _ in cons]
-        afd_levelset_update_fields(mesh.h, np.stack(fields), weights, v_target, casting, kept)
-        E_cur = np.where(kept != 0, 1.0, e_void)
-        v_design = v_target
-        st, val, flds = analyse(True)
-        fea += 1
-    return {"history": hist, "kept": feasible["kept"], "E": feasible["E"], "volume_fraction": feasible["v"],
-            "stop": reason, "fea": fea, "reference": ref}
+    return out
 
 
 class Mesh:

@@ -30,6 +30,7 @@
 #include "stencil2.cuh"
 #include "dpcg_persistent.cuh"
 #include "modal.cuh"
+#include "topology.h"
 
 using namespace afd;
 
@@ -1996,7 +1997,7 @@ static int ensure_select(afd_mesh* m) {
 // (Eq. 3.17), the casting scan (axis >= 0), the cut at round(v N_e) (Eq. 3.6)
 // and the new moduli.
 static int levelset_cut(afd_mesh* m, const float* fields, int nf, const double* weights, double volume_fraction,
-                        int axis, int parting, double* tau_out, uint8_t* kept_out) {
+                        int axis, int parting, double* tau_out, uint8_t* kept_out, int64_t* k_out = nullptr) {
   const int64_t n = m->gr.nelem;
   TRY(ensure_select(m));
   float* dmaxv = m->fsmall + FS_MAXV;
@@ -2015,6 +2016,7 @@ static int levelset_cut(afd_mesh* m, const float* fields, int nf, const double* 
   TRY(refresh_moduli(m));
   if (kept_out) CK(cudaMemcpyAsync(kept_out, m->kept, (size_t)n, cudaMemcpyDeviceToHost, m->s));
   if (tau_out) *tau_out = (double)tau;
+  if (k_out) *k_out = k;
   return finish(m);
 }
 
@@ -2348,3 +2350,164 @@ double afd_al_weight(const afd_al_state* s) {
   return w > 0.0 ? w : 0.0;
 }
 
+
+// ---- the algorithm of Sec. 3.8 (topology.h) ----
+int afd_topology_run(const afd_topology_spec* spec, const afd_topology_ops* ops, void* ctx,
+                     afd_topology_record* hist, int hist_cap, afd_topology_result* res) {
+  if (!spec || !ops || !ops->analyse || !ops->save_feasible || !ops->restore_feasible || !ops->cut)
+    return fail(AFD_ERR_INVALID_ARG, "null spec or callback");
+  if (const char* why = topo_check(*spec)) return fail(AFD_ERR_INVALID_ARG, "%s", why);
+  if (hist_cap < 0) return fail(AFD_ERR_INVALID_ARG, "hist_cap must be >= 0");
+  auto call = [](int rc, const char* what) {
+    if (rc != AFD_OK) fail(rc, "topology callback %s returned %d", what, rc);
+    return rc;
+  };
+  return topology_loop(
+      *spec,
+      [&](int warm, double* v, int* it, double* rel) { return call(ops->analyse(ctx, warm, v, it, rel), "analyse"); },
+      [&]() { return call(ops->save_feasible(ctx), "save_feasible"); },
+      [&]() { return call(ops->restore_feasible(ctx), "restore_feasible"); },
+      [&](const double* w, double v) { return call(ops->cut(ctx, w, v), "cut"); }, hist, hist_cap, res);
+}
+
+namespace {
+// Device state of one run on a mesh: the fields of the active constraints
+// (field-major, one slot each), and the last feasible design.
+struct TopoMesh {
+  afd_mesh* m = nullptr;
+  int slot[AFD_CON_COUNT] = {-1, -1, -1, -1};
+  int nf = 0;
+  float* fields = nullptr;
+  double* feasE = nullptr;
+  uint8_t* feasKept = nullptr;
+  bool cut_done = false;   // m->kept describes the current design
+  ~TopoMesh() {
+    dfree(fields);
+    dfree(feasE);
+    dfree(feasKept);
+  }
+};
+}  // namespace
+
+static int topo_mesh_analyse(TopoMesh& t, const afd_topology_spec& s, int warm, double* val, int* iters,
+                             double* rel) {
+  afd_mesh* m = t.m;
+  const size_t ne = (size_t)m->gr.nelem;
+  afd_stats st;
+  TRY(afd_solve(m, s.tol, warm, &st, nullptr, 0));
+  *iters = st.iters;
+  *rel = st.rel_residual;
+  TRY(afd_compliance(m, &val[AFD_CON_COMPLIANCE]));
+  // the static fields first: the modal analysis discards the static solution
+  if (t.slot[AFD_CON_COMPLIANCE] >= 0)
+    TRY(afd_sensitivity(m, AFD_SENS_STRAIN_ENERGY, t.fields + t.slot[AFD_CON_COMPLIANCE] * ne, 1));
+  if (t.slot[AFD_CON_STRESS] >= 0) {
+    TRY(afd_pnorm_stress(m, s.p, &val[AFD_CON_STRESS]));
+    afd_stats ast;
+    TRY(afd_stress_sensitivity(m, s.p, s.tol, t.fields + t.slot[AFD_CON_STRESS] * ne, 1, &ast, nullptr, 0));
+  }
+  int it = 0, sit = 0;
+  if (t.slot[AFD_CON_BUCKLING] >= 0) {   // the state is the solution just computed
+    TRY(afd_buckling(m, 1, s.eig_tol, 100, &val[AFD_CON_BUCKLING], nullptr, 0, &it, &sit));
+    TRY(afd_buckling_sensitivity(m, t.fields + t.slot[AFD_CON_BUCKLING] * ne, 1));
+  }
+  if (t.slot[AFD_CON_EIGEN] >= 0) {
+    TRY(afd_modal(m, 1, s.rho, s.eig_tol, 100, &val[AFD_CON_EIGEN], nullptr, 0, &it, &sit));
+    TRY(afd_eigen_sensitivity(m, t.fields + t.slot[AFD_CON_EIGEN] * ne, 1));
+  }
+  return AFD_OK;
+}
+
+int afd_constrained_topology(afd_mesh* m, const afd_topology_spec* spec, afd_topology_record* hist, int hist_cap,
+                             afd_topology_result* res, uint8_t* kept_out, double* E_out) {
+  if (!m || !spec) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (const char* why = topo_check(*spec)) return fail(AFD_ERR_INVALID_ARG, "%s", why);
+  if (hist_cap < 0) return fail(AFD_ERR_INVALID_ARG, "hist_cap must be >= 0");
+  if (!m->has_moduli || !m->has_loads) return fail(AFD_ERR_STATE, "set moduli and loads before the topology run");
+  if (m->nrhs != 1) return fail(AFD_ERR_INVALID_ARG, "the topology run takes one load case (the mesh has %d)", m->nrhs);
+  if (spec->casting_axis >= 0)
+    TRY(casting_args_ok(m->gr.nx, m->gr.ny, m->gr.nz, spec->casting_axis, spec->casting_parting));
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  const afd_topology_spec& s = *spec;
+  const size_t ne = (size_t)m->gr.nelem;
+  TopoMesh t;
+  t.m = m;
+  for (int c = 0; c < AFD_CON_COUNT; ++c)
+    if (topo_active(s, c)) t.slot[c] = t.nf++;
+  TRY(dalloc(&t.fields, (size_t)t.nf * ne));
+  TRY(dalloc(&t.feasE, ne));
+  TRY(dalloc(&t.feasKept, ne));
+  TRY(ensure_select(m));
+  auto analyse = [&](int warm, double* v, int* it, double* rel) { return topo_mesh_analyse(t, s, warm, v, it, rel); };
+  auto save = [&]() -> int {
+    CK(cudaMemcpyAsync(t.feasE, m->E64, ne * sizeof(double), cudaMemcpyDeviceToDevice, m->s));
+    if (t.cut_done)
+      CK(cudaMemcpyAsync(t.feasKept, m->kept, ne, cudaMemcpyDeviceToDevice, m->s));
+    else
+      CK(cudaMemsetAsync(t.feasKept, 1, ne, m->s));
+    return AFD_OK;
+  };
+  auto restore = [&]() -> int {
+    TRY(afd_set_element_moduli(m, t.feasE, 1));
+    CK(cudaMemcpyAsync(m->kept, t.feasKept, ne, cudaMemcpyDeviceToDevice, m->s));
+    t.cut_done = true;
+    return AFD_OK;
+  };
+  auto cut = [&](const double* w, double v) -> int {
+    double wc[AFD_CON_COUNT];
+    for (int c = 0; c < AFD_CON_COUNT; ++c)
+      if (t.slot[c] >= 0) wc[t.slot[c]] = w[c];
+    double tau;
+    TRY(levelset_cut(m, t.fields, t.nf, wc, v, s.casting_axis, s.casting_parting, &tau, nullptr));
+    t.cut_done = true;
+    return AFD_OK;
+  };
+  TRY(topology_loop(s, analyse, save, restore, cut, hist, hist_cap, res));
+  if (kept_out) CK(cudaMemcpyAsync(kept_out, t.feasKept, ne, cudaMemcpyDeviceToHost, m->s));
+  if (E_out) CK(cudaMemcpyAsync(E_out, t.feasE, ne * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+  return finish(m);
+}
+
+int afd_volume_minimisation(afd_mesh* m, int steps, double dv, double j_factor, double tol, int kind,
+                            afd_volmin_record* hist, uint8_t* kept_out, double* u_out) {
+  if (!m || !hist) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  if (steps < 0 || !(dv > 0.0) || !(steps * dv < 1.0)) return fail(AFD_ERR_INVALID_ARG, "need steps >= 0 and 0 < steps dv < 1");
+  if (!(j_factor > 0.0) || !(tol > 0.0)) return fail(AFD_ERR_INVALID_ARG, "j_factor and tol must be > 0");
+  if (kind < 0 || kind > 2) return fail(AFD_ERR_INVALID_ARG, "unknown field kind %d", kind);
+  if (!m->has_moduli || !m->has_loads) return fail(AFD_ERR_STATE, "set moduli and loads first");
+  if (m->nrhs != 1) return fail(AFD_ERR_INVALID_ARG, "the volume minimisation takes one load case");
+  DeviceGuard dg(m->device);
+  using clk = std::chrono::steady_clock;
+  auto t0 = clk::now();
+  afd_stats st;
+  TRY(afd_solve(m, tol, 0, &st, steps == 0 ? u_out : nullptr, 0));
+  double J = 0.0;
+  TRY(afd_compliance(m, &J));
+  const double J0 = J, J_all = j_factor * J;
+  afd_al_state al;
+  afd_al_init(&al);
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  hist[0] = afd_volmin_record{0, 1.0, J, 1.0, J / J_all - 1.0, st.iters, st.rel_residual,
+                              std::chrono::duration<double, std::milli>(clk::now() - t0).count(), nan,
+                              afd_al_weight(&al), al.mu, al.gamma, (long long)m->gr.nelem};
+  for (int k = 1; k <= steps; ++k) {
+    t0 = clk::now();
+    const double v = 1.0 - k * dv;
+    const double w = afd_al_weight(&al);
+    const bool last = k == steps;
+    double tau = nan;
+    int64_t kept = 0;
+    TRY(enter(m));
+    TRY(fields_to(m, kind, m->fbuf));
+    TRY(levelset_cut(m, m->fbuf, 1, &w, v, -1, 0, &tau, last ? kept_out : nullptr, &kept));
+    TRY(afd_solve(m, tol, 1, &st, last ? u_out : nullptr, 0));
+    TRY(afd_compliance(m, &J));
+    const double g = J / J_all - 1.0;
+    afd_al_update(&al, g);
+    hist[k] = afd_volmin_record{k, v, J, J / J0, g, st.iters, st.rel_residual,
+                                std::chrono::duration<double, std::milli>(clk::now() - t0).count(), tau, w, al.mu,
+                                al.gamma, (long long)kept};
+  }
+  return AFD_OK;
+}
