@@ -395,7 +395,7 @@ def large_mesh_roofline(afd, torch, dev, peak, peak_kind, n=384):
     u = torch.randn((1, mesh.ndof), dtype=torch.float32, device=dev)
     y = torch.empty_like(u)
     best = None
-    for staging in (0, 1):
+    for staging in (0, 1, 2):
         for warps, planes in ((8, 4), (8, 6), (8, 8), (8, 12), (16, 8), (16, 16)):
             afd.afd_set_stencil_shape(mesh.h, warps, planes, staging)
             afd.afd_time_stiffness(mesh.h, afd.AFD_F32, 1, u, y, 5)
@@ -889,8 +889,9 @@ def main():
                     help="only run --steps eigen analyses of the 128x64x64 workload (for ncu)")
     ap.add_argument("--stencil-warps", type=int, default=0, help="pinned FP32 stencil warps per CTA (profile modes)")
     ap.add_argument("--stencil-planes", type=int, default=0, help="pinned FP32 stencil planes per CTA (profile modes)")
-    ap.add_argument("--stencil-async", type=int, default=0, choices=(0, 1),
-                    help="pinned FP32 stencil plane staging, 1 = cp.async (profile modes)")
+    ap.add_argument("--stencil-async", type=int, default=0, choices=(0, 1, 2),
+                    help="pinned FP32 stencil variant: 0 register prefetch, 1 cp.async ring, 2 packed bands "
+                         "(profile modes)")
     args = ap.parse_args()
     if args.launch_summary:
         launch_summary(args.launch_summary)

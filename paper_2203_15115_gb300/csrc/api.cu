@@ -28,6 +28,7 @@
 #include "sens.cuh"
 #include "stencil.cuh"
 #include "stencil2.cuh"
+#include "stencil3.cuh"
 #include "dpcg_persistent.cuh"
 #include "modal.cuh"
 #include "topology.h"
@@ -103,7 +104,11 @@ struct afd_mesh {
   cudaEvent_t ev = nullptr;
   int kz = 8;                  // node planes per CTA of the FP64 stencil
   int kz32 = 8, ty32 = 16;     // planes per CTA and warps per CTA of the FP32 stencil
-  int async32 = 0;             // 1: the FP32 stencil stages planes with cp.async
+  int async32 = 0;             // FP32 stencil variant: 0 register prefetch, 1 cp.async ring (stencil2.cuh),
+                               // 2 packed bands (stencil3.cuh)
+  uint8_t* tflags = nullptr;   // per-tile "has a fixed node" flags of the packed-band stencil
+  int tflags_ty = 0;           // CTA height they were computed for (0: stale)
+  size_t tflags_cap = 0;
   bool tuned = false;          // autotuner has chosen kz32 / ty32 for this mesh
   bool pdl_now = false;        // launches being captured use programmatic dependent launch
   // state
@@ -264,12 +269,47 @@ static void geom32(const Grid& g, int ty, int kz, int& tiles_x, dim3& grid) {
     StencilGeom2<16>::get(g, kz, tiles_x, grid);
 }
 
+static void geom3(const Grid& g, int ty, int kz, int& tiles_x, dim3& grid) {
+  int tiles_y;
+  if (ty == 8)
+    St3Geom<8>::get(g, kz, tiles_x, tiles_y, grid);
+  else
+    St3Geom<16>::get(g, kz, tiles_x, tiles_y, grid);
+}
+
 static void stencil_geom(const afd_mesh* m, bool f64, int& tiles_x, dim3& grid) {
   if (f64)
     StencilGeom<TY64>::get(m->gr, m->kz, tiles_x, grid);
+  else if (m->async32 == 2)
+    geom3(m->gr, m->ty32, m->kz32, tiles_x, grid);
   else
     geom32(m->gr, m->ty32, m->kz32, tiles_x, grid);
 }
+
+// Per-tile flags of the packed-band stencil for the current supports and CTA
+// height (recomputed when either changes).
+static int ensure_tile_flags(afd_mesh* m) {
+  if (m->tflags_ty == m->ty32 && m->tflags) return AFD_OK;
+  int tx;
+  dim3 grid;
+  geom3(m->gr, m->ty32, 1, tx, grid);
+  const size_t nt = grid.x;
+  if (nt > m->tflags_cap) {
+    dfree(m->tflags);
+    m->tflags_cap = 0;
+    TRY(dalloc(&m->tflags, nt));
+    m->tflags_cap = nt;
+  }
+  if (m->ty32 == 8)
+    k_st3_tile_flags<8><<<(unsigned)nt, 256, 0, m->s>>>(m->gr, m->fixed, tx, m->tflags);
+  else
+    k_st3_tile_flags<16><<<(unsigned)nt, 256, 0, m->s>>>(m->gr, m->fixed, tx, m->tflags);
+  m->launches++;
+  CK(cudaGetLastError());
+  m->tflags_ty = m->ty32;
+  return AFD_OK;
+}
+
 
 static int stencil_blocks(const afd_mesh* m, bool f64) {
   int tx;
@@ -292,6 +332,17 @@ static int opt_in_once(int bit, F&& set) {
   if (g_optin[dev].load(std::memory_order_acquire) & mask) return AFD_OK;
   CK(set());
   g_optin[dev].fetch_or(mask, std::memory_order_acq_rel);
+  return AFD_OK;
+}
+
+template <int TY, int MODE>
+static int launch_st3(afd_mesh* m, const StencilArgs<float, float>& a, dim3 grid) {
+  const size_t dyn = st3_smem_bytes<TY, MODE>();
+  TRY(opt_in_once(24 + 2 * MODE + (TY == 8 ? 0 : 1), [&]() {
+    return cudaFuncSetAttribute(st3_kernel<TY, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  }));
+  CK(launch_ex(m->pdl_now, st3_kernel<TY, MODE, false>, grid, dim3(ST_TX * TY), dyn, m->s, a,
+               (const uint8_t*)m->tflags));
   return AFD_OK;
 }
 
@@ -329,8 +380,13 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
     static_assert(std::is_same<TF, float>::value, "the FP32 stencil takes FP32 right-hand sides");
     // the packed FP32 kernel forms p in ST_APPLY_DOT only, and always there
     if ((MODE == ST_APPLY_DOT) != (z != nullptr)) return fail(AFD_ERR_INVALID_ARG, "stencil mode / z mismatch");
-    // the asynchronous staging ring lives in dynamic shared memory
-    if (m->async32) {
+    if (m->async32 == 2) {
+      TRY(ensure_tile_flags(m));
+      if (m->ty32 == 8)
+        TRY((launch_st3<8, MODE>(m, a, grid)));
+      else
+        TRY((launch_st3<16, MODE>(m, a, grid)));
+    } else if (m->async32) {   // the asynchronous staging ring lives in dynamic shared memory
       const int ti = m->ty32 == 8 ? 0 : 1;
       const size_t dyn =
           (m->ty32 == 8 ? stencil2_ring_floats<8, MODE>() : stencil2_ring_floats<16, MODE>()) * sizeof(float);
@@ -561,6 +617,8 @@ static int autotune_stencil(afd_mesh* m) {
       dim3 gr;
       geom32(g, ty, kz, tx, gr);
       maxp = std::max(maxp, (size_t)gr.x * gr.y);
+      geom3(g, ty, kz, tx, gr);
+      maxp = std::max(maxp, (size_t)gr.x * gr.y);
     }
   TRY(ensure_partials(m, (size_t)std::max(m->cap, 1) * std::max(maxp, (size_t)2 * RED_BLOCKS)));
   CK(cudaMemsetAsync(m->w32.p, 0, (size_t)g.vs * sizeof(float), m->s));
@@ -569,7 +627,7 @@ static int autotune_stencil(afd_mesh* m) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_kz = m->kz32, best_ty = m->ty32, best_as = m->async32;
-  for (int as = 0; as < 2; ++as)
+  for (int as = 0; as < 3; ++as)
   for (int ty : cand_ty)
     for (int kz : cand_kz) {
       if (kz > g.nnz && kz != cand_kz.front()) continue;
@@ -985,6 +1043,7 @@ void afd_destroy(afd_mesh* m) {
     dfree(wp->x); dfree(wp->r); dfree(wp->z); dfree(wp->p); dfree(wp->q); dfree(wp->t); dfree(wp->b);
     dfree(wp->r2); dfree(wp->AW); dfree(wp->invd);
     dfree(wp->invdiag); dfree(wp->E);
+    dfree(m->tflags);
     if (wp->graph) cudaGraphExecDestroy(wp->graph);
   }
   {
@@ -1108,6 +1167,7 @@ int afd_set_loads_bcs(afd_mesh* m, int n_rhs, const double* f, int f_on_device, 
     CK(cudaMemcpyAsync(dmask, mask, g.ndof, cudaMemcpyHostToDevice, m->s));
   }
   k_pack_fixed<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g.nnodes, dmask, m->fixed); m->launches++;
+  m->tflags_ty = 0;   // the packed-band stencil's tile flags follow the supports
   k_group_box_init<<<grid_blocks((size_t)6 * m->gp.ng, 256, 256), 256, 0, m->s>>>(m->gp.ng, m->gbox); m->launches++;
   k_group_fixed<<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->gp, m->fixed, m->gbox); m->launches++;
   m->gbox_h.assign((size_t)6 * m->gp.ng, 0);
@@ -2142,8 +2202,8 @@ int afd_stencil_warps(const afd_mesh* m) { return m ? m->ty32 : 0; }
 int afd_stencil_async(const afd_mesh* m) { return m ? m->async32 : 0; }
 
 int afd_set_stencil_shape(afd_mesh* m, int warps, int planes, int async_staging) {
-  if (!m || (warps != 8 && warps != 16) || planes < 1 || async_staging < 0 || async_staging > 1)
-    return fail(AFD_ERR_INVALID_ARG, "warps must be 8 or 16, planes >= 1, async_staging 0 or 1");
+  if (!m || (warps != 8 && warps != 16) || planes < 1 || async_staging < 0 || async_staging > 2)
+    return fail(AFD_ERR_INVALID_ARG, "warps must be 8 or 16, planes >= 1, async_staging 0, 1 or 2");
   m->ty32 = warps;
   m->async32 = async_staging;
   m->kz32 = std::min(planes, m->gr.nnz);

@@ -28,11 +28,15 @@ torch = pytest.importorskip("torch")
 
 import paper_2203_15115_gb300 as afd  # noqa: E402
 from oracle import deflation, fe  # noqa: E402
+from synthetic import clamp_face_x0  # noqa: E402
 
 PLANES = [2, 3, 4, 5, 6, 8, 12, 16, 24, 32]
 WARPS = [8, 16]
-STAGING = [0, 1]
-MESHES = {"70x40x30": (70, 40, 30, 10), "3x2x50": (3, 2, 50, 2), "33x31x9": (33, 31, 9, 4)}
+STAGING = [0, 1, 2]
+# (nx, ny, nz, group, supports): "scattered" fixes random DOFs everywhere (every tile takes the fixed-DOF
+# path); "clamp" fixes the face x = 0 only, so most tiles take the path without fixed DOFs
+MESHES = {"70x40x30": (70, 40, 30, 10, "scattered"), "3x2x50": (3, 2, 50, 2, "scattered"),
+          "33x31x9": (33, 31, 9, 4, "clamp"), "95x33x21": (95, 33, 21, 8, "clamp")}
 
 
 def cuda(x):
@@ -48,13 +52,16 @@ def masked_matvec(K, u, fixed):
 
 
 class Case:
-    def __init__(self, nx, ny, nz, g):
+    def __init__(self, nx, ny, nz, g, supports):
         rng = np.random.default_rng(nx * 10000 + ny * 100 + nz)
         self.nx, self.ny, self.nz, self.g = nx, ny, nz, g
         self.E = rng.uniform(1e-3, 1.0, nx * ny * nz)
         ndof = 3 * (nx + 1) * (ny + 1) * (nz + 1)
-        self.fixed = (rng.random(ndof) < 0.08).astype(np.uint8)
-        self.fixed[: 3 * (nx + 1)] = 1   # a fully clamped first node row as well
+        if supports == "scattered":
+            self.fixed = (rng.random(ndof) < 0.08).astype(np.uint8)
+            self.fixed[: 3 * (nx + 1)] = 1   # a fully clamped first node row as well
+        else:
+            self.fixed = clamp_face_x0(nx, ny, nz)
         self.K = fe.assemble(nx, ny, nz, self.E)
         self.m = afd.Mesh(nx, ny, nz, group=g, precision=afd.AFD_MIXED)
         self.m.set_element_moduli(self.E)
