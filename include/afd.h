@@ -44,7 +44,8 @@ enum {
   AFD_ERR_INVALID_ARG = -1,     /* bad size, null pointer, NaN/negative modulus ... */
   AFD_ERR_OOM = -2,             /* device allocation failed, or a budget was exceeded */
   AFD_ERR_NOT_CONVERGED = -3,   /* iteration cap reached; u still holds the best iterate */
-  AFD_ERR_COARSE_SINGULAR = -4, /* coarse Cholesky met a pivot <= 0 (e.g. no supports) */
+  AFD_ERR_COARSE_SINGULAR = -4, /* the coarse matrix W^T K W is singular: its inversion (blocked Gauss-Jordan
+                                   sweeps of the SPD matrix) met a pivot <= 0 (e.g. no supports) */
   AFD_ERR_NAN = -5,             /* a residual norm became NaN or Inf */
   AFD_ERR_CUDA = -6,            /* a CUDA runtime call failed */
   AFD_ERR_STATE = -7            /* call out of order (e.g. solve before set_loads_bcs) */
@@ -82,6 +83,10 @@ typedef struct {
                          plain stream order, measured faster on the 128x64x64 workload */
   double inner_aim;   /* AFD_MIXED: each inner solve aims at inner_aim * rel_tol in the true relative residual
                          (not below inner_tol); default 0.5, in (0, 1) */
+  int coarse_fp64;    /* AFD_MIXED: 1 builds W^T K W from FP64 element products and inverts it in FP64 (its
+                         FP32 rounding is applied in the FP32 inner iterations); 0 (default) builds it from
+                         FP32 element products summed in FP64 and inverts it in FP32 (same inner iteration
+                         counts on the measured workloads at a lower set-up cost).  AFD_FP64 is always FP64. */
 } afd_options;
 
 typedef struct {

@@ -56,7 +56,8 @@ class afd_options(ctypes.Structure):
                 ("h", ctypes.c_double), ("e_void", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("persistent", ctypes.c_int), ("stencil_warps", ctypes.c_int),
-                ("stencil_planes", ctypes.c_int), ("pdl", ctypes.c_int), ("inner_aim", ctypes.c_double)]
+                ("stencil_planes", ctypes.c_int), ("pdl", ctypes.c_int), ("inner_aim", ctypes.c_double),
+                ("coarse_fp64", ctypes.c_int)]
 
 
 class afd_stats(ctypes.Structure):

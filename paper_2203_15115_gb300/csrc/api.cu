@@ -503,7 +503,7 @@ static int assemble_coarse(afd_mesh* m) {
   }
   CK(cudaMemsetAsync(m->Ec, 0, nn * sizeof(double), m->s));
   const dim3 grid(m->gp.ng, 27);
-  if (m->opt.precision == AFD_FP64) {
+  if (m->opt.precision == AFD_FP64 || m->opt.coarse_fp64) {
     k_coarse_block<double><<<grid, COARSE_THREADS, 0, m->s>>>(m->gr, m->gp, m->E64, m->fixed, m->w64.K, m->Ec); m->launches++;
   } else {
     k_coarse_block<float><<<grid, COARSE_THREADS, 0, m->s>>>(m->gr, m->gp, m->E64, m->fixed, m->w32.K, m->Ec); m->launches++;
@@ -558,6 +558,13 @@ static int build_coarse(afd_mesh* m) {
     if (!m->Einv64) TRY(dalloc(&m->Einv64, nn));
     k_scale_dense<double><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(m->nc, m->Ec, m->Einv64); m->launches++;
     TRY(invert_coarse<double>(m, m->Einv64, 1e-12));
+  } else if (m->opt.coarse_fp64) {
+    // FP64 inverse, rounded once to FP32 for the inner iterations' coarse step
+    if (!m->Einv64) TRY(dalloc(&m->Einv64, nn));
+    if (!m->Einv32) TRY(dalloc(&m->Einv32, nn));
+    k_scale_dense<double><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(m->nc, m->Ec, m->Einv64); m->launches++;
+    TRY(invert_coarse<double>(m, m->Einv64, 1e-12));
+    k_convert_dense<float><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(nn, m->Einv64, m->Einv32); m->launches++;
   } else {
     if (!m->Einv32) TRY(dalloc(&m->Einv32, nn));
     k_scale_dense<float><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(m->nc, m->Ec, m->Einv32); m->launches++;
@@ -595,11 +602,13 @@ static int coarse_step_smem(const afd_mesh* m, size_t& bytes) {
   return AFD_OK;
 }
 
-// Stencil autotuner: the FP32 stencil's CTA shape (8 or 16 warps, i.e. 14 or
-// 30 finished node rows) and z depth trade redundant halo rows and element
-// layers against the number of CTAs (waves over the SMs).  Each candidate is
-// timed on the solver's FP32 kernel and stream with CUDA events (3 launches
-// after one warm-up); the fastest is kept for the mesh.
+// Stencil autotuner: the FP32 stencil's variant (stencil2 with register
+// prefetch or a cp.async ring, or the packed-band stencil3), CTA shape (8 or
+// 16 warps, i.e. 14 or 30 finished node rows) and z depth trade redundant
+// halo rows and element layers against the number of CTAs (waves over the
+// SMs).  Each candidate is timed as the inner iteration runs it (the fused
+// search-direction kernel) on the solver's stream with CUDA events (3
+// launches after one warm-up); the fastest is kept for the mesh.
 static int autotune_stencil(afd_mesh* m) {
   TRY(ensure_work(m, m->w32, 1));
   const Grid& g = m->gr;
@@ -621,7 +630,12 @@ static int autotune_stencil(afd_mesh* m) {
       maxp = std::max(maxp, (size_t)gr.x * gr.y);
     }
   TRY(ensure_partials(m, (size_t)std::max(m->cap, 1) * std::max(maxp, (size_t)2 * RED_BLOCKS)));
+  // the timed kernel is the inner iteration's fused one (p = z + W mu + beta p_old, q = K p, p.q) on
+  // zero vectors and a zero coarse vector (its cost does not depend on the values)
   CK(cudaMemsetAsync(m->w32.p, 0, (size_t)g.vs * sizeof(float), m->s));
+  CK(cudaMemsetAsync(m->w32.z, 0, (size_t)g.vs * sizeof(float), m->s));
+  CK(cudaMemsetAsync(m->mu, 0, (size_t)m->nc * sizeof(double), m->s));
+  CK(cudaMemsetAsync(m->st, 0, sizeof(CGState), m->s));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -634,12 +648,14 @@ static int autotune_stencil(afd_mesh* m) {
       m->ty32 = ty;
       m->kz32 = kz;
       m->async32 = as;
-      TRY((launch_stencil<float, ST_APPLY, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr, nullptr, nullptr,
-                                                    1, m->w32.K)));
+      auto fused = [&]() {
+        return launch_stencil<float, ST_APPLY_DOT, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr,
+                                                          m->partials, nullptr, 1, m->w32.K, m->st, nullptr,
+                                                          m->w32.z, m->mu, m->w32.t, nullptr);
+      };
+      TRY(fused());
       CK(cudaEventRecord(e0, m->s));
-      for (int rep = 0; rep < 3; ++rep)
-        TRY((launch_stencil<float, ST_APPLY, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr, nullptr,
-                                                      nullptr, 1, m->w32.K)));
+      for (int rep = 0; rep < 3; ++rep) TRY(fused());
       CK(cudaEventRecord(e1, m->s));
       CK(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -940,6 +956,7 @@ void afd_default_options(afd_options* o) {
   o->stencil_planes = 0;
   o->pdl = 0;
   o->inner_aim = 0.5;
+  o->coarse_fp64 = 0;
 }
 
 const char* afd_last_error(void) { return g_err.c_str(); }
@@ -2340,6 +2357,7 @@ size_t afd_mesh_bytes(int nx, int ny, int nz, int n_rhs, const afd_options* opt)
   b += nn * (1 + 4 + 8) + vs * (4 + 8);                             // mask, Jacobi factors
   b += (size_t)n_rhs * vs * (3 * 8 + 8 * tsz);                      // f, u, r (FP64) + Krylov work
   b += nc * nc * (8 + tsz) + nc * GJ_NB * 2 * 8 + GJ_NB * GJ_NB * 8; // coarse matrix, inverse, sweep scratch
+  if (!f64 && o.coarse_fp64) b += nc * nc * 8;                      // FP64 inverse before its FP32 rounding
   const size_t box = (size_t)(g + 3) * (g + 3) * (g + 3);
   if (f64 || o.persistent) b += ng * box * (18 * tsz + 4);          // K W on group shells (upper bound)
   b += (size_t)n_rhs * (nc * 4 * 8 + ng * 64 * 12 * 8) + 64 * 1024 * 1024 / 8;  // coarse vectors, partials

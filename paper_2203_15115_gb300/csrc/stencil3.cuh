@@ -95,7 +95,8 @@ __global__ void k_st3_tile_flags(const Grid gr, const uint8_t* __restrict__ fixe
 }
 
 // One CTA tile (tile_x, tile_y, z chunk zc) of one RHS; returns this thread's
-// partial sum of p.(K p) (ST_APPLY_DOT / ST_DOT_PLAIN) over the nodes it finishes.
+// partial sum over the nodes it finishes: p.(K p) (ST_APPLY_DOT / ST_DOT_PLAIN)
+// or r.r with r = f - K u written in place of y (ST_RESIDUAL).
 template <int TY, int MODE, bool MASKED>
 __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, float beta, int tile, int zc, int rhs,
                                           float* smem) {
@@ -230,16 +231,17 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
 #pragma unroll
     for (int c = 0; c < 3; ++c) v[c] = make_float2(rs[(Q::U + c) * NT], rs[(Q::U + 3 + c) * NT]);
     if constexpr (formp) {
-      const bool kin = k >= 0 && k < gr.nnz;
-      if (kin && k >= gz_next) refresh_group(k);
-      const float2 rz = bc2(hh * (float)(2 * k - zsum));
-      const float2 kz2 = make_float2(kin && cv0 ? 1.f : 0.f, kin && cv1 ? 1.f : 0.f);
-      float2 zz[3];
+      if (k >= 0 && k < gr.nnz) {   // uniform; outside the mesh the staged zeros stand
+        if (k >= gz_next) refresh_group(k);
+        const float2 rz = bc2(hh * (float)(2 * k - zsum));
+        const float2 cz = make_float2(cv0 ? 1.f : 0.f, cv1 ? 1.f : 0.f);
+        float2 zz[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) zz[c] = make_float2(rs[(Q::Z + c) * NT], rs[(Q::Z + 3 + c) * NT]);
-      v[0] = mul2(kz2, fma2(bt, v[0], add2(zz[0], fma2(rz, sAB[3 * NT + tid], sAB[0 * NT + tid]))));
-      v[1] = mul2(kz2, fma2(bt, v[1], add2(zz[1], fma2(rz, sAB[4 * NT + tid], sAB[1 * NT + tid]))));
-      v[2] = mul2(kz2, fma2(bt, v[2], add2(zz[2], sAB[2 * NT + tid])));
+        for (int c = 0; c < 3; ++c) zz[c] = make_float2(rs[(Q::Z + c) * NT], rs[(Q::Z + 3 + c) * NT]);
+        v[0] = mul2(cz, fma2(bt, v[0], add2(zz[0], fma2(rz, sAB[3 * NT + tid], sAB[0 * NT + tid]))));
+        v[1] = mul2(cz, fma2(bt, v[1], add2(zz[1], fma2(rz, sAB[4 * NT + tid], sAB[1 * NT + tid]))));
+        v[2] = mul2(cz, fma2(bt, v[2], add2(zz[2], sAB[2 * NT + tid])));
+      }
     }
     if constexpr (MASKED) {
       const unsigned w0 = __float_as_uint(rs[Q::F * NT]), w1 = __float_as_uint(rs[(Q::F + 1) * NT]);
@@ -290,6 +292,10 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
   float2 part = bc2(0.f);
 
   // prologue: three planes in flight, plane k0 - 1 made into the bottom faces
+  if constexpr (formp) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) sAB[q * NT + tid] = bc2(0.f);
+  }
   issue();
   issue();
   issue();
@@ -419,7 +425,7 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
       yv[c] = add2(sub2(t0, t1), fl);
     }
     if (l >= k0) {
-      if constexpr (MASKED) {
+      if constexpr (MASKED && MODE != ST_RESIDUAL) {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
           yv[c] = mul2(yv[c], make_float2(((Mc >> c) & 1u) ? 0.f : 1.f, ((Mc >> (8 + c)) & 1u) ? 0.f : 1.f));
@@ -433,6 +439,32 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
         }
       }
       const size_t o0 = 3 * (size_t)(n0 + l * PS), o1 = 3 * (size_t)(n1 + l * PS);
+      if constexpr (MODE == ST_RESIDUAL) {
+        // r = f - K u on the free DOFs (0 on fixed DOFs), its partial r.r, optional float copy
+        const float* f = a.f + voff;
+        const float2 ov2 = make_float2(ov0 ? 1.f : 0.f, ov1 ? 1.f : 0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float2 r = sub2(make_float2(ov0 ? __ldg(f + o0 + c) : 0.f, ov1 ? __ldg(f + o1 + c) : 0.f), yv[c]);
+          if constexpr (MASKED)
+            r = mul2(r, make_float2(((Mc >> c) & 1u) ? 0.f : 1.f, ((Mc >> (8 + c)) & 1u) ? 0.f : 1.f));
+          yv[c] = r;
+          r = mul2(r, ov2);
+          part = fma2(r, r, part);
+        }
+        if (a.y32) {
+          if (ov0) {
+            a.y32[voff + o0] = yv[0].x;
+            a.y32[voff + o0 + 1] = yv[1].x;
+            a.y32[voff + o0 + 2] = yv[2].x;
+          }
+          if (ov1) {
+            a.y32[voff + o1] = yv[0].y;
+            a.y32[voff + o1 + 1] = yv[1].y;
+            a.y32[voff + o1 + 2] = yv[2].y;
+          }
+        }
+      }
       float* y = a.y + voff;
       if (ov0) {
         y[o0] = yv[0].x;

@@ -67,18 +67,20 @@ def test_stencil_matches_assembled_K(dims):
     m.close()
 
 
-@pytest.mark.parametrize("precision,ctol", [(afd.AFD_FP64, 1e-12), (afd.AFD_MIXED, 1e-6)])
+@pytest.mark.parametrize("precision,cfp64,ctol", [(afd.AFD_FP64, 1, 1e-12), (afd.AFD_MIXED, 1, 1e-12),
+                                                  (afd.AFD_MIXED, 0, 1e-6)])
 @pytest.mark.parametrize("dims,g", [((4, 2, 2), 2), ((9, 5, 7), 3), ((12, 6, 6), 4)])
-def test_deflation_operators_and_coarse_matrix(dims, g, precision, ctol):
+def test_deflation_operators_and_coarse_matrix(dims, g, precision, cfp64, ctol):
     """W^T, W and E = W^T K W against the oracle's dense W.  The mixed path
-    builds E with FP32 element products summed in FP64 (the coarse solve is a
-    preconditioner component there), hence its looser bound."""
+    builds E from FP64 element products by default (coarse_fp64 = 1); with
+    coarse_fp64 = 0 from FP32 element products summed in FP64 (the coarse
+    solve is a preconditioner component there), hence its looser bound."""
     nx, ny, nz = dims
     rng = np.random.default_rng(11)
     E = np.where(rng.random(nx * ny * nz) < 0.3, 1e-3, 1.0)
     fixed = clamp_face_x0(nx, ny, nz)
     fixed[rng.random(fixed.size) < 0.05] = 1
-    m = afd.Mesh(nx, ny, nz, group=g, precision=precision)
+    m = afd.Mesh(nx, ny, nz, group=g, precision=precision, coarse_fp64=cfp64)
     m.set_element_moduli(E)
     m.set_loads_bcs(edge_load(nx, ny, nz)[None], fixed)
     W = deflation.deflation_matrix(nx, ny, nz, g, fixed)
