@@ -474,7 +474,7 @@ static int invert_coarse(afd_mesh* m, T* A, double rel) {
   const dim3 ug((nc + 31) / 32, (nc + 31) / 32);
   for (int k0 = 0; k0 < nc; k0 += GJ_NB) {
     const int nb = std::min(GJ_NB, nc - k0);
-    k_gj_pivot<T><<<1, 256, 0, m->s>>>(A, nc, k0, P, m->dmax, rel, m->dstatus); m->launches++;
+    k_gj_pivot<T><<<1, 32, 0, m->s>>>(A, nc, k0, P, m->dmax, rel, m->dstatus); m->launches++;
     k_gj_panel<T><<<(nc * nb + 255) / 256, 256, 0, m->s>>>(A, nc, k0, P, B, R); m->launches++;
     k_gj_update<T><<<ug, 256, 0, m->s>>>(A, nc, k0, P, B, R, k0 + GJ_NB >= nc ? 1 : 0); m->launches++;
   }
@@ -1253,7 +1253,8 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
     TRY(autotune_stencil(m));
     TRY(autotune_coarse_split(m));
   }
-  if (!warm_start || !m->has_solution) CK(cudaMemsetAsync(m->u64, 0, (size_t)R * g.vs * sizeof(double), m->s));
+  const bool cold = !warm_start || !m->has_solution;
+  if (cold) CK(cudaMemsetAsync(m->u64, 0, (size_t)R * g.vs * sizeof(double), m->s));
   std::vector<int> iters(R, 0), status(R, AFD_OK), refine(R, 0);
   std::vector<double> rel;
   if (m->opt.precision == AFD_FP64) {
@@ -1272,7 +1273,19 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
   } else {
     TRY(ensure_work(m, m->w32, R));
     float* b32 = m->w32.b;
-    TRY(true_residual(m, b32, rel));
+    if (cold) {
+      // u = 0: the residual is f itself (zero on fixed DOFs), so the first FP64 pass is not needed
+      for (int r = 0; r < R; ++r) {
+        k_convert<float><<<grid_blocks(g.ndof, 256, 4096), 256, 0, m->s>>>((size_t)g.ndof, m->f64 + (size_t)r * g.vs,
+                                                                          b32 + (size_t)r * g.vs);
+        m->launches++;
+      }
+      CK(cudaGetLastError());
+      rel.assign(R, 0.0);
+      for (int r = 0; r < R; ++r) rel[r] = m->fnorm[r] > 0.0 ? 1.0 : 0.0;
+    } else {
+      TRY(true_residual(m, b32, rel));
+    }
     for (int step = 0; step <= m->opt.max_refine; ++step) {
       std::vector<int> act(R, 0);
       std::vector<double> t2(R, 0.0);

@@ -160,44 +160,48 @@ __global__ void k_unscale_dense(int n, const double* __restrict__ a, T* __restri
   }
 }
 
-// Invert the nb x nb diagonal block at k0 (unblocked sweeps in shared memory);
-// P = A_KK^{-1} (nb x nb).  A pivot <= rel * (*dmax) (or NaN) sets *status.
+// Invert the nb x nb diagonal block at k0 by unblocked sweeps held in the
+// registers of one warp: lane i keeps row i of the block, the pivot column is
+// in every lane's own registers and the pivot row arrives by shuffles, so a
+// sweep costs no barrier.  P = A_KK^{-1} (nb x nb).  Rows and columns beyond
+// nb are an identity (pivot 1, no coupling).  A pivot <= rel * (*dmax) (or
+// NaN) sets *status (the sweep continues with pivot 1).
 template <typename T>
-__global__ void __launch_bounds__(256) k_gj_pivot(const T* A, int n, int k0, T* P, const double* dmax, double rel, int* status) {
-  __shared__ T s[GJ_NB][GJ_NB + 1];
-  __shared__ T rowp[GJ_NB], colp[GJ_NB];
-  __shared__ T dpiv;
+__global__ void __launch_bounds__(32) k_gj_pivot(const T* A, int n, int k0, T* P, const double* dmax, double rel,
+                                                 int* status) {
   const int nb = min(GJ_NB, n - k0);
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) s[q / nb][q % nb] = A[(size_t)(k0 + q / nb) * n + k0 + q % nb];
-  __syncthreads();
-  for (int p = 0; p < nb; ++p) {
-    if (threadIdx.x == 0) {
-      T d = s[p][p];
-      if (!(d > (T)(rel * (*dmax))) || !isfinite((double)d)) {
-        *status = -4;
-        d = T(1);
-      }
-      dpiv = d;
+  const int i = threadIdx.x;
+  T s[GJ_NB];
+#pragma unroll
+  for (int j = 0; j < GJ_NB; ++j)
+    s[j] = (i < nb && j < nb) ? A[(size_t)(k0 + i) * n + k0 + j] : (i == j ? T(1) : T(0));
+  const double thr = rel * (*dmax);
+  bool bad = false;
+#pragma unroll
+  for (int p = 0; p < GJ_NB; ++p) {
+    const T colp = s[p];   // this row's entry in the pivot column
+    T d = __shfl_sync(0xffffffffu, colp, p);
+    if (p < nb && (!((double)d > thr) || !isfinite((double)d))) {
+      bad = true;
+      d = T(1);
     }
-    if (threadIdx.x < nb) {
-      rowp[threadIdx.x] = s[p][threadIdx.x];
-      colp[threadIdx.x] = s[threadIdx.x][p];
-    }
-    __syncthreads();
-    const T d = dpiv, inv = T(1) / d;
-    for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-      const int i = q / nb, j = q % nb;
+    const T inv = T(1) / d;
+#pragma unroll
+    for (int j = 0; j < GJ_NB; ++j) {
+      const T rowp = __shfl_sync(0xffffffffu, s[j], p);
       T v;
-      if (i == p && j == p) v = -inv;
-      else if (i == p) v = rowp[j] * inv;
-      else if (j == p) v = colp[i] * inv;
-      else v = s[i][j] - colp[i] * rowp[j] * inv;
-      s[i][j] = v;
+      if (i == p) v = (j == p) ? -inv : rowp * inv;
+      else v = (j == p) ? colp * inv : s[j] - colp * rowp * inv;
+      s[j] = v;
     }
-    __syncthreads();
   }
   // s = -A_KK^{-1}
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) P[q] = -s[q / nb][q % nb];
+  if (i < nb) {
+#pragma unroll
+    for (int j = 0; j < GJ_NB; ++j)
+      if (j < nb) P[i * nb + j] = -s[j];
+  }
+  if (bad && i == 0) *status = -4;
 }
 
 // B[i][m] = sum_t A[i][k0+t] P[t][m] for every row i outside K (rows of K
