@@ -148,6 +148,8 @@ struct afd_mesh {
   int* aw_node = nullptr;      // [aw_total / 18] node index of every shell slot
   double* grec = nullptr;      // [rhs][N_g][12] per-group records of the coarse right-hand side
   double* upart = nullptr;     // [rhs][RED_BLOCKS][2] partials of the vector update
+  double* updred = nullptr;    // [rhs][coarse-step blocks][2] the same, summed in one slice per coarse-step block
+  size_t updred_cap = 0;
   unsigned int* gcount = nullptr;  // [rhs][N_g] split counters
   size_t aw_total = 0;         // elements of AW
   // persistent inner solver: per-CTA partials, coarse records, grid barrier
@@ -851,8 +853,16 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
   k_update<T><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, x, w.r, w.z, P[0], w.q, w.invd, m->upart, m->st, nullptr,
                                             0, m->done); m->launches++;
   TRY(launch_coarse_rhs<T>(m, w, m->nsplit, nrhs, false));
+  const size_t ured = (size_t)nrhs * crows * 2;
+  if (ured > m->updred_cap) {
+    invalidate_graphs(m);
+    dfree(m->updred);
+    m->updred_cap = 0;
+    TRY(dalloc(&m->updred, ured));
+    m->updred_cap = ured;
+  }
   k_coarse_step<T><<<crows, CSTEP_THREADS, csmem, m->s>>>(m->nc, nrhs, Einv, m->mu, m->st, m->grec, m->wr, 2, m->done, cnt_co,
-                                               m->upart, RED_BLOCKS); m->launches++;
+                                               m->upart, RED_BLOCKS, m->updred); m->launches++;
   CK(cudaGetLastError());
 
   if constexpr (!F64) {
@@ -881,7 +891,7 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
     for (int it = 0; it < m->opt.check_every; ++it) {
       T* pold = P[it & 1];
       T* pnew = P[(it + 1) & 1];
-      const IterPartials ip{m->upart, RED_BLOCKS, m->wr, crows, it & 1};
+      const IterPartials ip{m->updred, crows, m->wr, crows, it & 1};
       TRY((launch_stencil<T, ST_APPLY_DOT, TB>(m, pold, w.q, w.E, nullptr, nullptr, m->partials, m->done, nrhs, w.K,
                                                 m->st, nullptr, w.z, m->mu, pnew, &ip)));
       const bool pdl = m->pdl_now;
@@ -890,7 +900,8 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
       m->launches++;
       TRY(launch_coarse_rhs<T>(m, w, m->nsplit, nrhs, pdl));
       CK(launch_ex(pdl, k_coarse_step<T>, dim3(crows), dim3(CSTEP_THREADS), csmem, m->s, m->nc, nrhs, (const T*)Einv, m->mu,
-                   m->st, (const double*)m->grec, m->wr, 1, m->done, cnt_co, (const double*)m->upart, (int)RED_BLOCKS));
+                   m->st, (const double*)m->grec, m->wr, 1, m->done, cnt_co, (const double*)m->upart, (int)RED_BLOCKS,
+                   m->updred));
       m->launches++;
     }
     CK(cudaGetLastError());
@@ -1076,7 +1087,7 @@ void afd_destroy(afd_mesh* m) {
   dfree(m->selcnt); dfree(m->fsmall);
   dfree(m->Ec); dfree(m->Einv64); dfree(m->Einv32); dfree(m->gjP); dfree(m->gjB); dfree(m->gjR);
   dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gbox); dfree(m->aw_off); dfree(m->aw_node);
-  dfree(m->grec); dfree(m->gcount); dfree(m->upart);
+  dfree(m->grec); dfree(m->gcount); dfree(m->upart); dfree(m->updred);
   dfree(m->ppart); dfree(m->prec); dfree(m->gbar); dfree(m->ptime);
   dfree(m->lam64); dfree(m->gadj); dfree(m->dsig); dfree(m->pn_d); dfree(m->lsbuf);
   dfree(m->mX); dfree(m->mmass); dfree(m->mparts);
@@ -2301,7 +2312,7 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
       rc = launch_stencil<float, ST_DOT_PLAIN, float>(m, pnew, w.q, w.E, nullptr, nullptr, m->partials, m->done, R,
                                                      w.K, m->st, nullptr);
     else {
-      const IterPartials ip{m->upart, RED_BLOCKS, m->wr, crows, it & 1};
+      const IterPartials ip{m->updred, crows, m->wr, crows, it & 1};
       rc = launch_stencil<float, ST_APPLY_DOT, float>(m, pold, w.q, w.E, nullptr, nullptr, m->partials, m->done, R,
                                                      w.K, m->st, nullptr, w.z, m->mu, pnew, &ip);
     }
@@ -2312,7 +2323,7 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
     rc = launch_coarse_rhs<float>(m, w, m->nsplit, R, false);
     cudaEventRecord(ev[3], m->s);
     k_coarse_step<float><<<crows, CSTEP_THREADS, csmem, m->s>>>(m->nc, R, m->Einv32, m->mu, m->st, m->grec, m->wr, 1, m->done,
-                                                     cnt_co, m->upart, RED_BLOCKS);
+                                                     cnt_co, m->upart, RED_BLOCKS, m->updred);
     cudaEventRecord(ev[4], m->s);
     m->launches += 4;
   }

@@ -943,7 +943,8 @@ template <typename TE>
 __global__ void __launch_bounds__(256)
 k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict__ mu, CGState* st,
               const double* __restrict__ rec, double* __restrict__ cd_parts, int fin, int* done_flags,
-              unsigned int* counter, const double* __restrict__ upd_partials, int upd_nparts) {
+              unsigned int* counter, const double* __restrict__ upd_partials, int upd_nparts,
+              double* __restrict__ upd_red) {
   using VT = typename Vec16<TE>::T;
   constexpr int V = Vec16<TE>::N, U = 8;
   extern __shared__ __align__(16) double vs[];   // nc values of v for the current RHS (as TE)
@@ -959,6 +960,19 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
   // issued first, so that they overlap the loads of v and of the state (the
   // kernel is a chain of memory latencies, not bandwidth).  Rows that fit in
   // one batch of U vectors per lane stay in registers for every RHS.
+  // The vector update's (r.z, r.r) partials are summed here in slices, one per
+  // block in block order (each slice in index order), so that the next
+  // stencil's every CTA sums gridDim.x slices instead of all of them.  This
+  // block is latency-bound: the few extra loads overlap its GEMV.
+  if (upd_red && threadIdx.x < 2 * nrhs) {
+    const int r = threadIdx.x >> 1, comp = threadIdx.x & 1;
+    const int per = (upd_nparts + gridDim.x - 1) / gridDim.x;
+    const int i0 = blockIdx.x * per, i1 = min(i0 + per, upd_nparts);
+    const double* up = upd_partials + (size_t)r * upd_nparts * 2;
+    double sum = 0.0;
+    for (int i = i0; i < i1; ++i) sum += up[2 * i + comp];
+    upd_red[((size_t)r * gridDim.x + blockIdx.x) * 2 + comp] = sum;
+  }
   const int nv = nc / V;
   const bool in_regs = nc % V == 0 && nv <= 32 * U;
   VT e[U];
