@@ -331,18 +331,20 @@ int64_t afd_kernel_launches(const afd_mesh* m);
  * the first mixed solve when opt.autotune is set, else by a size heuristic). */
 int afd_stencil_depth(const afd_mesh* m);
 
-/* Warps per CTA of the FP32 stiffness kernel (8 or 16; each warp owns two node
- * rows, a CTA finishes 2 * warps - 2 of them); chosen with the depth. */
+/* Warps per CTA of the FP32 stiffness kernel (8 or 16); chosen with the depth. */
 int afd_stencil_warps(const afd_mesh* m);
 
-/* Pin the FP32 stencil's CTA shape (8 or 16 warps, planes >= 1, clipped to the
- * mesh) and its plane staging (async_staging = 1: each thread stages the next
- * planes' node values in shared memory with cp.async, two planes ahead; 0:
- * register prefetch one plane ahead) on an existing mesh; the autotuner then
- * leaves this mesh alone. */
+/* Pin the FP32 stencil's variant and CTA shape (8 or 16 warps, planes >= 1,
+ * clipped to the mesh) on an existing mesh; the autotuner then leaves this mesh
+ * alone.  Variant (async_staging): 0 two node rows per thread, the next plane
+ * prefetched into registers; 1 the same with a cp.async ring two planes ahead
+ * in shared memory; 2 two row bands per CTA packed into the lanes of every
+ * float2, cp.async ring; 3 variant 2 with two load cases in the lanes instead
+ * of two bands, for solves of two or more load cases (one load case runs
+ * variant 2). */
 int afd_set_stencil_shape(afd_mesh* m, int warps, int planes, int async_staging);
 
-/* 1 when the FP32 stencil stages planes with cp.async (chosen with the shape). */
+/* The FP32 stencil variant in use (the async_staging values above). */
 int afd_stencil_async(const afd_mesh* m);
 
 /* Measurement aid for the CUDA-graph inner solver: continues the last FP32

@@ -107,7 +107,8 @@ struct afd_mesh {
   int async32 = 0;             // FP32 stencil variant: 0 register prefetch, 1 cp.async ring (stencil2.cuh),
                                // 2 packed bands (stencil3.cuh)
   uint8_t* tflags = nullptr;   // per-tile "has a fixed node" flags of the packed-band stencil
-  int tflags_ty = 0;           // CTA height they were computed for (0: stale)
+  int tflags_ty = 0;           // 2 x CTA height + pair mode they were computed for (0: stale)
+  int rp32 = 0;                // 1: the packed-band stencil takes load cases in pairs (two or more cases)
   size_t tflags_cap = 0;
   bool tuned = false;          // autotuner has chosen kz32 / ty32 for this mesh
   bool pdl_now = false;        // launches being captured use programmatic dependent launch
@@ -271,30 +272,35 @@ static void geom32(const Grid& g, int ty, int kz, int& tiles_x, dim3& grid) {
     StencilGeom2<16>::get(g, kz, tiles_x, grid);
 }
 
-static void geom3(const Grid& g, int ty, int kz, int& tiles_x, dim3& grid) {
+static void geom3(const Grid& g, int ty, int kz, bool rp, int& tiles_x, dim3& grid) {
   int tiles_y;
   if (ty == 8)
-    St3Geom<8>::get(g, kz, tiles_x, tiles_y, grid);
+    rp ? St3Geom<8, true>::get(g, kz, tiles_x, tiles_y, grid) : St3Geom<8>::get(g, kz, tiles_x, tiles_y, grid);
   else
-    St3Geom<16>::get(g, kz, tiles_x, tiles_y, grid);
+    rp ? St3Geom<16, true>::get(g, kz, tiles_x, tiles_y, grid) : St3Geom<16>::get(g, kz, tiles_x, tiles_y, grid);
 }
 
-static void stencil_geom(const afd_mesh* m, bool f64, int& tiles_x, dim3& grid) {
+// The FP32 stencil runs load cases in pairs (packed-band kernel, pair mode)
+// when the autotuner chose it for this mesh and there are at least two.
+static bool use_rp(const afd_mesh* m, int nrhs) { return m->rp32 && m->async32 == 2 && nrhs >= 2; }
+
+static void stencil_geom(const afd_mesh* m, bool f64, int& tiles_x, dim3& grid, int nrhs = 1) {
   if (f64)
     StencilGeom<TY64>::get(m->gr, m->kz, tiles_x, grid);
   else if (m->async32 == 2)
-    geom3(m->gr, m->ty32, m->kz32, tiles_x, grid);
+    geom3(m->gr, m->ty32, m->kz32, use_rp(m, nrhs), tiles_x, grid);
   else
     geom32(m->gr, m->ty32, m->kz32, tiles_x, grid);
 }
 
-// Per-tile flags of the packed-band stencil for the current supports and CTA
-// height (recomputed when either changes).
-static int ensure_tile_flags(afd_mesh* m) {
-  if (m->tflags_ty == m->ty32 && m->tflags) return AFD_OK;
+// Per-tile flags of the packed-band stencil for the current supports, CTA
+// height and mode (recomputed when any changes).
+static int ensure_tile_flags(afd_mesh* m, bool rp) {
+  const int key = 2 * m->ty32 + (rp ? 1 : 0);
+  if (m->tflags_ty == key && m->tflags) return AFD_OK;
   int tx;
   dim3 grid;
-  geom3(m->gr, m->ty32, 1, tx, grid);
+  geom3(m->gr, m->ty32, 1, rp, tx, grid);
   const size_t nt = grid.x;
   if (nt > m->tflags_cap) {
     dfree(m->tflags);
@@ -303,20 +309,22 @@ static int ensure_tile_flags(afd_mesh* m) {
     m->tflags_cap = nt;
   }
   if (m->ty32 == 8)
-    k_st3_tile_flags<8><<<(unsigned)nt, 256, 0, m->s>>>(m->gr, m->fixed, tx, m->tflags);
+    rp ? k_st3_tile_flags<8, true><<<(unsigned)nt, 256, 0, m->s>>>(m->gr, m->fixed, tx, m->tflags)
+       : k_st3_tile_flags<8, false><<<(unsigned)nt, 256, 0, m->s>>>(m->gr, m->fixed, tx, m->tflags);
   else
-    k_st3_tile_flags<16><<<(unsigned)nt, 256, 0, m->s>>>(m->gr, m->fixed, tx, m->tflags);
+    rp ? k_st3_tile_flags<16, true><<<(unsigned)nt, 256, 0, m->s>>>(m->gr, m->fixed, tx, m->tflags)
+       : k_st3_tile_flags<16, false><<<(unsigned)nt, 256, 0, m->s>>>(m->gr, m->fixed, tx, m->tflags);
   m->launches++;
   CK(cudaGetLastError());
-  m->tflags_ty = m->ty32;
+  m->tflags_ty = key;
   return AFD_OK;
 }
 
 
-static int stencil_blocks(const afd_mesh* m, bool f64) {
+static int stencil_blocks(const afd_mesh* m, bool f64, int nrhs = 1) {
   int tx;
   dim3 g;
-  stencil_geom(m, f64, tx, g);
+  stencil_geom(m, f64, tx, g, nrhs);
   return (int)(g.x * g.y);
 }
 
@@ -324,13 +332,13 @@ static int stencil_blocks(const afd_mesh* m, bool f64) {
 // their attribute raised once per device (the attribute is per device; meshes
 // of one process may live on several, and server workers launch from several
 // threads).  bit: which kernel.
-static std::atomic<unsigned> g_optin[64];
+static std::atomic<unsigned long long> g_optin[64];
 template <typename F>
 static int opt_in_once(int bit, F&& set) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(AFD_ERR_INVALID_ARG, "device index %d out of range", dev);
-  const unsigned mask = 1u << bit;
+  const unsigned long long mask = 1ull << bit;
   if (g_optin[dev].load(std::memory_order_acquire) & mask) return AFD_OK;
   CK(set());
   g_optin[dev].fetch_or(mask, std::memory_order_acq_rel);
@@ -338,13 +346,23 @@ static int opt_in_once(int bit, F&& set) {
 }
 
 template <int TY, int MODE>
-static int launch_st3(afd_mesh* m, const StencilArgs<float, float>& a, dim3 grid) {
+static int launch_st3(afd_mesh* m, const StencilArgs<float, float>& a, dim3 grid, int nrhs) {
   const size_t dyn = st3_smem_bytes<TY, MODE>();
+  if (use_rp(m, nrhs)) {
+    if (a.counter) return fail(AFD_ERR_INVALID_ARG, "load-case pairs take no last-CTA step length");
+    TRY(opt_in_once(32 + 2 * MODE + (TY == 8 ? 0 : 1), [&]() {
+      return cudaFuncSetAttribute(st3_kernel<TY, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    }));
+    grid.z = (nrhs + 1) / 2;
+    CK(launch_ex(m->pdl_now, st3_kernel<TY, MODE, true>, grid, dim3(ST_TX * TY), dyn, m->s, a,
+                 (const uint8_t*)m->tflags, nrhs));
+    return AFD_OK;
+  }
   TRY(opt_in_once(24 + 2 * MODE + (TY == 8 ? 0 : 1), [&]() {
     return cudaFuncSetAttribute(st3_kernel<TY, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   }));
   CK(launch_ex(m->pdl_now, st3_kernel<TY, MODE, false>, grid, dim3(ST_TX * TY), dyn, m->s, a,
-               (const uint8_t*)m->tflags));
+               (const uint8_t*)m->tflags, nrhs));
   return AFD_OK;
 }
 
@@ -374,7 +392,7 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
   a.gp = m->gp;
   a.ip = ip ? *ip : IterPartials{nullptr, 0, nullptr, 0, 0};
   dim3 grid;
-  stencil_geom(m, F64, a.tiles_x, grid);
+  stencil_geom(m, F64, a.tiles_x, grid, nrhs);
   grid.z = nrhs;
   if constexpr (F64) {
     CK(launch_ex(m->pdl_now, stencil_kernel<T, TY64, MODE, TF>, grid, dim3(ST_TX * TY64), 0, m->s, a));
@@ -383,11 +401,11 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
     // the packed FP32 kernel forms p in ST_APPLY_DOT only, and always there
     if ((MODE == ST_APPLY_DOT) != (z != nullptr)) return fail(AFD_ERR_INVALID_ARG, "stencil mode / z mismatch");
     if (m->async32 == 2) {
-      TRY(ensure_tile_flags(m));
+      TRY(ensure_tile_flags(m, use_rp(m, nrhs)));
       if (m->ty32 == 8)
-        TRY((launch_st3<8, MODE>(m, a, grid)));
+        TRY((launch_st3<8, MODE>(m, a, grid, nrhs)));
       else
-        TRY((launch_st3<16, MODE>(m, a, grid)));
+        TRY((launch_st3<16, MODE>(m, a, grid, nrhs)));
     } else if (m->async32) {   // the asynchronous staging ring lives in dynamic shared memory
       const int ti = m->ty32 == 8 ? 0 : 1;
       const size_t dyn =
@@ -611,8 +629,17 @@ static int coarse_step_smem(const afd_mesh* m, size_t& bytes) {
 // SMs).  Each candidate is timed as the inner iteration runs it (the fused
 // search-direction kernel) on the solver's stream with CUDA events (3
 // launches after one warm-up); the fastest is kept for the mesh.
+// One fused in-iteration stencil launch for R load cases on zero vectors (the
+// autotuner's timed kernel; its cost does not depend on the values).
+static int fused_for_tuning(afd_mesh* m, int R) {
+  return launch_stencil<float, ST_APPLY_DOT, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr, m->partials,
+                                                    nullptr, R, m->w32.K, m->st, nullptr, m->w32.z, m->mu, m->w32.t,
+                                                    nullptr);
+}
+
 static int autotune_stencil(afd_mesh* m) {
-  TRY(ensure_work(m, m->w32, 1));
+  const int R = std::max(1, m->nrhs);
+  TRY(ensure_work(m, m->w32, R));
   const Grid& g = m->gr;
   static const int all_kz[] = {2, 3, 4, 5, 6, 8, 12, 16, 24, 32};
   static const int all_ty[] = {8, 16};
@@ -628,16 +655,19 @@ static int autotune_stencil(afd_mesh* m) {
       dim3 gr;
       geom32(g, ty, kz, tx, gr);
       maxp = std::max(maxp, (size_t)gr.x * gr.y);
-      geom3(g, ty, kz, tx, gr);
+      geom3(g, ty, kz, false, tx, gr);
+      maxp = std::max(maxp, (size_t)gr.x * gr.y);
+      geom3(g, ty, kz, true, tx, gr);
       maxp = std::max(maxp, (size_t)gr.x * gr.y);
     }
   TRY(ensure_partials(m, (size_t)std::max(m->cap, 1) * std::max(maxp, (size_t)2 * RED_BLOCKS)));
   // the timed kernel is the inner iteration's fused one (p = z + W mu + beta p_old, q = K p, p.q) on
   // zero vectors and a zero coarse vector (its cost does not depend on the values)
-  CK(cudaMemsetAsync(m->w32.p, 0, (size_t)g.vs * sizeof(float), m->s));
-  CK(cudaMemsetAsync(m->w32.z, 0, (size_t)g.vs * sizeof(float), m->s));
-  CK(cudaMemsetAsync(m->mu, 0, (size_t)m->nc * sizeof(double), m->s));
-  CK(cudaMemsetAsync(m->st, 0, sizeof(CGState), m->s));
+  CK(cudaMemsetAsync(m->w32.p, 0, (size_t)R * g.vs * sizeof(float), m->s));
+  CK(cudaMemsetAsync(m->w32.z, 0, (size_t)R * g.vs * sizeof(float), m->s));
+  CK(cudaMemsetAsync(m->mu, 0, (size_t)R * m->nc * sizeof(double), m->s));
+  CK(cudaMemsetAsync(m->st, 0, (size_t)R * sizeof(CGState), m->s));
+  m->rp32 = 0;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -650,11 +680,7 @@ static int autotune_stencil(afd_mesh* m) {
       m->ty32 = ty;
       m->kz32 = kz;
       m->async32 = as;
-      auto fused = [&]() {
-        return launch_stencil<float, ST_APPLY_DOT, float>(m, m->w32.p, m->w32.q, m->w32.E, nullptr, nullptr,
-                                                          m->partials, nullptr, 1, m->w32.K, m->st, nullptr,
-                                                          m->w32.z, m->mu, m->w32.t, nullptr);
-      };
+      auto fused = [&]() { return fused_for_tuning(m, 1); };
       TRY(fused());
       CK(cudaEventRecord(e0, m->s));
       for (int rep = 0; rep < 3; ++rep) TRY(fused());
@@ -669,11 +695,53 @@ static int autotune_stencil(afd_mesh* m) {
         best_as = as;
       }
     }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   m->kz32 = best_kz;
   m->ty32 = best_ty;
   m->async32 = best_as;
+  if (R >= 2) {
+    // several load cases: the packed-band kernel with the cases in pairs against the best single-case
+    // variant launched for all of them (both for the R cases of this mesh)
+    auto time_r = [&](float& ms) -> int {
+      TRY(fused_for_tuning(m, R));
+      CK(cudaEventRecord(e0, m->s));
+      for (int rep = 0; rep < 3; ++rep) TRY(fused_for_tuning(m, R));
+      CK(cudaEventRecord(e1, m->s));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      return AFD_OK;
+    };
+    float best_r = 0.f;
+    TRY(time_r(best_r));
+    int rp_ty = 0, rp_kz = 0;
+    for (int ty : cand_ty)
+      for (int kz : cand_kz) {
+        if (kz > g.nnz && kz != cand_kz.front()) continue;
+        m->ty32 = ty;
+        m->kz32 = kz;
+        m->async32 = 2;
+        m->rp32 = 1;
+        float ms = 0.f;
+        TRY(time_r(ms));
+        if (ms < best_r) {
+          best_r = ms;
+          rp_ty = ty;
+          rp_kz = kz;
+        }
+      }
+    if (rp_ty) {
+      m->ty32 = rp_ty;
+      m->kz32 = rp_kz;
+      m->async32 = 2;
+      m->rp32 = 1;
+    } else {
+      m->kz32 = best_kz;
+      m->ty32 = best_ty;
+      m->async32 = best_as;
+      m->rp32 = 0;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   m->tuned = true;
   invalidate_graphs(m);  // captured launches bake in the grid
   return AFD_OK;
@@ -814,7 +882,7 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
                 const std::vector<int>& active, int max_iters, std::vector<CGState>& out) {
   constexpr bool F64 = sizeof(T) == 8;
   const Grid& gr = m->gr;
-  const int nsb = stencil_blocks(m, F64);
+  const int nsb = stencil_blocks(m, F64, nrhs);
   TRY(ensure_partials(m, (size_t)nrhs * std::max(nsb, 2 * RED_BLOCKS)));
   // state init
   std::vector<CGState> h(nrhs);
@@ -2240,13 +2308,14 @@ int afd_stencil_depth(const afd_mesh* m) { return m ? m->kz32 : 0; }
 
 int afd_stencil_warps(const afd_mesh* m) { return m ? m->ty32 : 0; }
 
-int afd_stencil_async(const afd_mesh* m) { return m ? m->async32 : 0; }
+int afd_stencil_async(const afd_mesh* m) { return m ? (m->async32 == 2 && m->rp32 ? 3 : m->async32) : 0; }
 
 int afd_set_stencil_shape(afd_mesh* m, int warps, int planes, int async_staging) {
-  if (!m || (warps != 8 && warps != 16) || planes < 1 || async_staging < 0 || async_staging > 2)
-    return fail(AFD_ERR_INVALID_ARG, "warps must be 8 or 16, planes >= 1, async_staging 0, 1 or 2");
+  if (!m || (warps != 8 && warps != 16) || planes < 1 || async_staging < 0 || async_staging > 3)
+    return fail(AFD_ERR_INVALID_ARG, "warps must be 8 or 16, planes >= 1, async_staging 0, 1, 2 or 3");
   m->ty32 = warps;
-  m->async32 = async_staging;
+  m->async32 = async_staging == 3 ? 2 : async_staging;
+  m->rp32 = async_staging == 3 ? 1 : 0;
   m->kz32 = std::min(planes, m->gr.nnz);
   m->tuned = true;
   invalidate_graphs(m);
@@ -2318,7 +2387,7 @@ int afd_time_dpcg_kernels(afd_mesh* m, int iters, int nsplit, int variant, doubl
     }
     cudaEventRecord(ev[1], m->s);
     k_update<float><<<vg, RED_THREADS, 0, m->s>>>(gr.ndof, gr.vs, w.x, w.r, w.z, pnew, w.q, w.invd, m->upart, m->st,
-                                                 m->partials, stencil_blocks(m, false), m->done);
+                                                 m->partials, stencil_blocks(m, false, R), m->done);
     cudaEventRecord(ev[2], m->s);
     rc = launch_coarse_rhs<float>(m, w, m->nsplit, R, false);
     cudaEventRecord(ev[3], m->s);

@@ -38,9 +38,12 @@ namespace afd {
 constexpr int ST3_RING = 3;   // planes per thread in the staging ring (2 in flight while one is used)
 constexpr int ST3_COLS = ST_TX - 2;
 
-template <int TY>
+// RP = false: two row bands per CTA (2 TY - 2 finished rows); RP = true: one
+// band of TY rows and two load cases in the lanes of every float2 (TY - 2
+// finished rows).
+template <int TY, bool RP = false>
 struct St3Geom {
-  static constexpr int ROWS = 2 * TY - 2;
+  static constexpr int ROWS = RP ? TY - 2 : 2 * TY - 2;
   static void get(const Grid& gr, int kz, int& tiles_x, int& tiles_y, dim3& grid) {
     tiles_x = (gr.nnx + ST3_COLS - 1) / ST3_COLS;
     tiles_y = (gr.nny + ROWS - 1) / ROWS;
@@ -48,9 +51,10 @@ struct St3Geom {
   }
 };
 
-// Ring values per thread and plane: u (3 per band), z (3 per band, formed
-// search direction only), the modulus of the element layer below the plane
-// (per band), the 4-byte word holding the node's fixed bits (per band).
+// Ring values per thread and plane: u (3 per band or load case), z (3 per
+// band or load case, formed search direction only), the modulus of the
+// element layer below the plane (per band; the pair mode uses the first), the
+// 4-byte word holding the node's fixed bits (likewise).
 template <int MODE>
 struct St3Q {
   static constexpr bool FORMP = MODE == ST_APPLY_DOT;
@@ -69,15 +73,16 @@ constexpr size_t st3_smem_bytes() {
          (St3Q<MODE>::FORMP ? (size_t)5 * ST_TX * TY * 8 : 0) + (size_t)6 * ST_TX * TY * 8;   // + sP
 }
 
-// Tiles whose loaded window (30 x (2 TY - 2) output nodes plus a one-node
-// halo on each side in x and y) holds a node with a fixed DOF, over all
-// planes.  One CTA per tile.
-template <int TY>
+// Tiles whose loaded window (30 x ROWS output nodes plus a one-node halo on
+// each side in x and y) holds a node with a fixed DOF, over all planes.  One
+// CTA per tile.
+template <int TY, bool RP>
 __global__ void k_st3_tile_flags(const Grid gr, const uint8_t* __restrict__ fixed, int tiles_x, uint8_t* flags) {
+  constexpr int ROWS = St3Geom<TY, RP>::ROWS;
   const int tile = blockIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int i0 = max(tx * ST3_COLS - 1, 0), i1 = min(tx * ST3_COLS + ST3_COLS + 1, gr.nnx);
-  const int j0 = max(ty * St3Geom<TY>::ROWS - 1, 0), j1 = min(ty * St3Geom<TY>::ROWS + St3Geom<TY>::ROWS + 1, gr.nny);
+  const int j0 = max(ty * ROWS - 1, 0), j1 = min(ty * ROWS + ROWS + 1, gr.nny);
   const int ni = i1 - i0, nj = j1 - j0;
   int any = 0;
   if (fixed && ni > 0 && nj > 0) {
@@ -94,12 +99,14 @@ __global__ void k_st3_tile_flags(const Grid gr, const uint8_t* __restrict__ fixe
   if (threadIdx.x == 0) flags[tile] = (uint8_t)any;
 }
 
-// One CTA tile (tile_x, tile_y, z chunk zc) of one RHS; returns this thread's
-// partial sum over the nodes it finishes: p.(K p) (ST_APPLY_DOT / ST_DOT_PLAIN)
-// or r.r with r = f - K u written in place of y (ST_RESIDUAL).
-template <int TY, int MODE, bool MASKED>
-__device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, float beta, int tile, int zc, int rhs,
-                                          float* smem) {
+// One CTA tile (tile_x, tile_y, z chunk zc) of one RHS (RP: of the load
+// cases rhs0 in the .x lanes and rhs1 in the .y lanes, each only where act0 /
+// act1); returns this thread's partial sums (.x band 0 or rhs0, .y band 1 or
+// rhs1) over the nodes it finishes: p.(K p) (ST_APPLY_DOT / ST_DOT_PLAIN) or
+// r.r with r = f - K u written in place of y (ST_RESIDUAL).
+template <int TY, int MODE, bool MASKED, bool RP>
+__device__ __forceinline__ float2 st3_tile(const StencilArgs<float, float>& a, float2 beta, int tile, int zc, int rhs0,
+                                           int rhs1, bool act0, bool act1, float* smem) {
   using Q = St3Q<MODE>;
   constexpr bool formp = Q::FORMP;
   constexpr bool dot = MODE == ST_APPLY_DOT || MODE == ST_DOT_PLAIN;
@@ -108,9 +115,10 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int tile_x = tile % a.tiles_x, tile_y = tile / a.tiles_x;
   const int i = tile_x * ST3_COLS - 1 + lane;
-  const int j0 = tile_y * St3Geom<TY>::ROWS - 1 + w, j1 = j0 + TY;   // rows of band 0 and band 1
+  // rows of band 0 and band 1 (one row for both load cases in the pair mode)
+  const int j0 = tile_y * St3Geom<TY, RP>::ROWS - 1 + w, j1 = RP ? j0 : j0 + TY;
   const int k0 = zc * a.kz, k1 = min(k0 + a.kz, gr.nnz);
-  const size_t voff = (size_t)rhs * gr.vs;
+  const size_t voff0 = (size_t)rhs0 * gr.vs, voff1 = (size_t)(RP ? rhs1 : rhs0) * gr.vs;
   const int PS = gr.nnx * gr.nny, ES = gr.nx * gr.ny;
 
   float* ring = smem;
@@ -125,12 +133,15 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
   const bool ei = i >= 0 && i < gr.nx;
   const bool ev0 = ei && j0 >= 0 && j0 < gr.ny, ev1 = ei && j1 >= 0 && j1 < gr.ny;
   const bool oi = lane >= 1 && lane <= ST3_COLS && i < gr.nnx;
-  const bool ov0 = oi && w >= 1 && cv0, ov1 = oi && w <= TY - 2 && cv1;
+  const bool ov0 = RP ? act0 && oi && w >= 1 && w <= TY - 2 && cv0 : oi && w >= 1 && cv0;
+  const bool ov1 = RP ? act1 && oi && w >= 1 && w <= TY - 2 && cv1 : oi && w <= TY - 2 && cv1;
   // node offsets of plane 0 (the element below-left of node (i, j) has offset n - j)
   const int n0 = cv0 ? i + gr.nnx * j0 : 0, n1 = cv1 ? i + gr.nnx * j1 : 0;
 
-  const float* u = a.u + voff;
-  const float* zv = formp ? a.z + voff : nullptr;
+  const float* u0 = a.u + voff0;
+  const float* u1 = a.u + voff1;
+  const float* zv0 = formp ? a.z + voff0 : nullptr;
+  const float* zv1 = formp ? a.z + voff1 : nullptr;
   // producer state: the next plane to stage and its ring slot
   int pk = k0 - 1, pslot = 0;
   auto issue = [&]() {
@@ -141,8 +152,8 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
     const int pn0 = kin && cv0 ? n0 + pk * PS : 0, pn1 = kin && cv1 ? n1 + pk * PS : 0;
     const int pe0 = lin && ev0 ? n0 - j0 + (pk - 1) * ES : 0, pe1 = lin && ev1 ? n1 - j1 + (pk - 1) * ES : 0;
     const int sz0 = kin && cv0 ? 4 : 0, sz1 = kin && cv1 ? 4 : 0;
-    const float* a0 = u + 3 * (size_t)pn0;
-    const float* a1 = u + 3 * (size_t)pn1;
+    const float* a0 = u0 + 3 * (size_t)pn0;
+    const float* a1 = u1 + 3 * (size_t)pn1;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sbase + (Q::U + c) * NT * 4),
@@ -151,8 +162,8 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
                    "l"(a1 + c), "r"(sz1) : "memory");
     }
     if constexpr (formp) {
-      const float* b0 = zv + 3 * (size_t)pn0;
-      const float* b1 = zv + 3 * (size_t)pn1;
+      const float* b0 = zv0 + 3 * (size_t)pn0;
+      const float* b1 = zv1 + 3 * (size_t)pn1;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sbase + (Q::Z + c) * NT * 4),
@@ -164,16 +175,18 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
     {
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sbase + Q::E * NT * 4), "l"(a.E + pe0),
                    "r"(lin && ev0 ? 4 : 0) : "memory");
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sbase + (Q::E + 1) * NT * 4), "l"(a.E + pe1),
-                   "r"(lin && ev1 ? 4 : 0) : "memory");
+      if constexpr (!RP)   // the pair's load cases share the element row
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sbase + (Q::E + 1) * NT * 4),
+                     "l"(a.E + pe1), "r"(lin && ev1 ? 4 : 0) : "memory");
     }
     if constexpr (MASKED) {
       const uint8_t* f0 = a.fixed + ((size_t)pn0 & ~(size_t)3);
       const uint8_t* f1 = a.fixed + ((size_t)pn1 & ~(size_t)3);
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sbase + Q::F * NT * 4), "l"(f0),
                    "r"(sz0) : "memory");
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sbase + (Q::F + 1) * NT * 4), "l"(f1),
-                   "r"(sz1) : "memory");
+      if constexpr (!RP)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sbase + (Q::F + 1) * NT * 4), "l"(f1),
+                     "r"(sz1) : "memory");
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     ++pk;
@@ -186,7 +199,8 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
   const Groups gp = a.gp;
   const float hh = (float)(0.5 * gp.h);
   int gz_next = -(1 << 30), zsum = 0;
-  const double* murhs = formp ? a.mu + (size_t)rhs * 6 * gp.ng : nullptr;
+  const double* murhs0 = formp ? a.mu + (size_t)rhs0 * 6 * gp.ng : nullptr;
+  const double* murhs1 = formp ? a.mu + (size_t)(RP ? rhs1 : rhs0) * 6 * gp.ng : nullptr;
   auto refresh_group = [&](int k) {
     const int gz = group_of_axis(k, gp.g, gp.ngz);
     int zlo, zhi, lo, hi;
@@ -204,8 +218,8 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
     group_range(Gy1, gp.g, gp.ngy, gr.ny, lo, hi);
     const float ry1 = hh * (float)(2 * jc1 - lo - hi);
     const int gzo = gp.ngx * gp.ngy * gz;
-    const double* m0 = murhs + 6 * (Gx + gp.ngx * Gy0 + gzo);
-    const double* m1 = murhs + 6 * (Gx + gp.ngx * Gy1 + gzo);
+    const double* m0 = murhs0 + 6 * (Gx + gp.ngx * Gy0 + gzo);
+    const double* m1 = murhs1 + 6 * (Gx + gp.ngx * Gy1 + gzo);
     const float tx0 = (float)__ldg(m0), ty0 = (float)__ldg(m0 + 1), tz0 = (float)__ldg(m0 + 2);
     const float ox0 = (float)__ldg(m0 + 3), oy0 = (float)__ldg(m0 + 4), oz0 = (float)__ldg(m0 + 5);
     const float tx1 = (float)__ldg(m1), ty1 = (float)__ldg(m1 + 1), tz1 = (float)__ldg(m1 + 2);
@@ -219,7 +233,7 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
 
   // consumer state
   int cslot = 0;
-  const float2 bt = bc2(beta);
+  const float2 bt = beta;
   // The values of plane k from the ring: the applied vector v (u, or the
   // formed p), with its fixed DOFs (MASKED) and invalid columns zeroed; the
   // fixed bits of both bands (bits 0-2 band 0, 8-10 band 1, MASKED only) and
@@ -227,7 +241,7 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
   auto consume = [&](int k, float2 (&v)[3], unsigned& fb, float2& E) {
     const float* rs = ring + cslot * (Q::N * NT) + tid;
     cslot = cslot + 1 == ST3_RING ? 0 : cslot + 1;
-    E = make_float2(rs[Q::E * NT], rs[(Q::E + 1) * NT]);
+    E = RP ? bc2(rs[Q::E * NT]) : make_float2(rs[Q::E * NT], rs[(Q::E + 1) * NT]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) v[c] = make_float2(rs[(Q::U + c) * NT], rs[(Q::U + 3 + c) * NT]);
     if constexpr (formp) {
@@ -244,7 +258,7 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
       }
     }
     if constexpr (MASKED) {
-      const unsigned w0 = __float_as_uint(rs[Q::F * NT]), w1 = __float_as_uint(rs[(Q::F + 1) * NT]);
+      const unsigned w0 = __float_as_uint(rs[Q::F * NT]), w1 = RP ? w0 : __float_as_uint(rs[(Q::F + 1) * NT]);
       fb = ((w0 >> (8 * ((n0 + k * PS) & 3))) & 7u) | (((w1 >> (8 * ((n1 + k * PS) & 3))) & 7u) << 8);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -265,7 +279,7 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
       D[c] = sub2(right, v[c]);
       xe[(c * (TY + 1) + w) * ST_TX + lane] = make_float4(S[c].x, S[c].y, D[c].x, D[c].y);
     }
-    if (w == 0) {
+    if (!RP && w == 0) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) xe[(c * (TY + 1) + TY) * ST_TX + lane] = make_float4(S[c].y, 0.f, D[c].y, 0.f);
     }
@@ -292,6 +306,17 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
   float2 part = bc2(0.f);
 
   // prologue: three planes in flight, plane k0 - 1 made into the bottom faces
+  if constexpr (RP) {
+    // the slot above the last warp (x-edges) and below the first (y forces)
+    // belong to no warp in the pair mode: zeros, for rows that are not finished
+    if (w == 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        xe[(c * (TY + 1) + TY) * ST_TX + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ye[(c * (TY + 1)) * ST_TX + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
   if constexpr (formp) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) sAB[q * NT + tid] = bc2(0.f);
@@ -407,7 +432,7 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
       }
       ye[(c * (TY + 1) + w + 1) * ST_TX + lane] = make_float4(e1[c][0].x, e1[c][0].y, e1[c][1].x, e1[c][1].y);
     }
-    if (w == TY - 1) {
+    if (!RP && w == TY - 1) {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         ye[(c * (TY + 1)) * ST_TX + lane] = make_float4(0.f, e1[c][0].x, 0.f, e1[c][1].x);
@@ -438,10 +463,10 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
           part = fma2(mul2(Pl[c], make_float2(ov0 ? 1.f : 0.f, ov1 ? 1.f : 0.f)), yv[c], part);
         }
       }
-      const size_t o0 = 3 * (size_t)(n0 + l * PS), o1 = 3 * (size_t)(n1 + l * PS);
+      const size_t o0 = voff0 + 3 * (size_t)(n0 + l * PS), o1 = voff1 + 3 * (size_t)(n1 + l * PS);
       if constexpr (MODE == ST_RESIDUAL) {
         // r = f - K u on the free DOFs (0 on fixed DOFs), its partial r.r, optional float copy
-        const float* f = a.f + voff;
+        const float* f = a.f;
         const float2 ov2 = make_float2(ov0 ? 1.f : 0.f, ov1 ? 1.f : 0.f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -454,18 +479,18 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
         }
         if (a.y32) {
           if (ov0) {
-            a.y32[voff + o0] = yv[0].x;
-            a.y32[voff + o0 + 1] = yv[1].x;
-            a.y32[voff + o0 + 2] = yv[2].x;
+            a.y32[o0] = yv[0].x;
+            a.y32[o0 + 1] = yv[1].x;
+            a.y32[o0 + 2] = yv[2].x;
           }
           if (ov1) {
-            a.y32[voff + o1] = yv[0].y;
-            a.y32[voff + o1 + 1] = yv[1].y;
-            a.y32[voff + o1 + 2] = yv[2].y;
+            a.y32[o1] = yv[0].y;
+            a.y32[o1 + 1] = yv[1].y;
+            a.y32[o1 + 2] = yv[2].y;
           }
         }
       }
-      float* y = a.y + voff;
+      float* y = a.y;
       if (ov0) {
         y[o0] = yv[0].x;
         y[o0 + 1] = yv[1].x;
@@ -477,7 +502,7 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
         y[o1 + 2] = yv[2].y;
       }
       if constexpr (formp) {
-        float* p = a.pout + voff;
+        float* p = a.pout;
         if (ov0) {
           p[o0] = Pl[0].x;
           p[o0 + 1] = Pl[1].x;
@@ -501,45 +526,74 @@ __device__ __forceinline__ float st3_tile(const StencilArgs<float, float>& a, fl
     MA = MB;
   }
   cp_async_wait<0>();   // no copy may land after the tile
-  return part.x + part.y;
+  return part;
 }
 
-template <int TY, int MODE, bool MASKED_ONLY>
+// RP = false: blockIdx.z is the RHS.  RP = true: blockIdx.z is the pair of
+// load cases (2 z, 2 z + 1) of the nrhs (the last pair of an odd count has one).
+template <int TY, int MODE, bool RP>
 __global__ void __launch_bounds__(ST_TX * TY, 16 / TY)
-st3_kernel(const StencilArgs<float, float> a, const uint8_t* __restrict__ tflags) {
-  __shared__ double red[32];
+st3_kernel(const StencilArgs<float, float> a, const uint8_t* __restrict__ tflags, int nrhs) {
+  __shared__ double red[64];
   pdl_acquire();
-  const int rhs = blockIdx.z;
-  if (a.done && a.done[rhs]) return;
-  __shared__ float s_beta;
+  const int rhs0 = RP ? 2 * (int)blockIdx.z : (int)blockIdx.z;
+  const int rhs1 = RP && rhs0 + 1 < nrhs ? rhs0 + 1 : rhs0;
+  bool act0 = !(a.done && a.done[rhs0]);
+  bool act1 = RP ? rhs1 != rhs0 && !(a.done && a.done[rhs1]) : act0;
+  if (!act0 && !act1) return;
+  __shared__ float s_beta[2];
   if (MODE == ST_APPLY_DOT) {
     if (a.ip.upd) {
+      // the iteration start of each load case (every CTA sums the same partials and takes the same decision)
       double b;
-      if (!dpcg_iteration_start(a.st, rhs, const_cast<int*>(a.done), a.ip, b)) return;
-      if (threadIdx.x == 0) s_beta = (float)b;
+      if (act0) {
+        act0 = dpcg_iteration_start(a.st, rhs0, const_cast<int*>(a.done), a.ip, b);
+        if (threadIdx.x == 0) s_beta[0] = (float)b;
+      }
+      if (RP && act1) {
+        act1 = dpcg_iteration_start(a.st, rhs1, const_cast<int*>(a.done), a.ip, b);
+        if (threadIdx.x == 0) s_beta[1] = (float)b;
+      }
+      if (!RP) act1 = act0;
+      if (!act0 && !act1) return;
     } else {
-      if (threadIdx.x == 0) s_beta = (float)a.st[rhs].beta;
+      if (threadIdx.x == 0) {
+        s_beta[0] = (float)a.st[rhs0].beta;
+        s_beta[1] = (float)a.st[rhs1].beta;
+      }
     }
     __syncthreads();
   }
-  const float beta = MODE == ST_APPLY_DOT ? s_beta : 0.f;
+  const float2 beta = MODE == ST_APPLY_DOT ? make_float2(s_beta[0], RP ? s_beta[1] : s_beta[0]) : bc2(0.f);
   extern __shared__ float4 st3_smem4[];
   float* smem = reinterpret_cast<float*>(st3_smem4);
   // tiles without a fixed node skip the fixed-DOF factors (uniform per CTA)
   const bool masked = a.fixed && (!tflags || tflags[blockIdx.x]);
-  float part;
+  float2 part;
   if (masked)
-    part = st3_tile<TY, MODE, true>(a, beta, blockIdx.x, blockIdx.y, rhs, smem);
+    part = st3_tile<TY, MODE, true, RP>(a, beta, blockIdx.x, blockIdx.y, rhs0, rhs1, act0, act1, smem);
   else
-    part = st3_tile<TY, MODE, false>(a, beta, blockIdx.x, blockIdx.y, rhs, smem);
+    part = st3_tile<TY, MODE, false, RP>(a, beta, blockIdx.x, blockIdx.y, rhs0, rhs1, act0, act1, smem);
   pdl_release();
   if (MODE != ST_APPLY) {
-    float pv[1] = {part};
+    const int nparts = gridDim.x * gridDim.y;
+    const int slot = blockIdx.y * gridDim.x + blockIdx.x;
+    if constexpr (RP) {
+      float pv[2] = {part.x, part.y};
+      double o[2];
+      block_sum_to_f64<2>(pv, red, o);
+      if (threadIdx.x == 0) {
+        if (act0) a.partials[(size_t)rhs0 * nparts + slot] = o[0];
+        if (act1) a.partials[(size_t)rhs1 * nparts + slot] = o[1];
+      }
+      return;   // the last-CTA step length is not used with load-case pairs
+    }
+    float pv[1] = {part.x + part.y};
     double o[1];
     block_sum_to_f64<1>(pv, red, o);
-    const int nparts = gridDim.x * gridDim.y;
+    const int rhs = rhs0;
     double* parts = a.partials + (size_t)rhs * nparts;
-    if (threadIdx.x == 0) parts[blockIdx.y * gridDim.x + blockIdx.x] = o[0];
+    if (threadIdx.x == 0) parts[slot] = o[0];
     if ((MODE == ST_APPLY_DOT || MODE == ST_DOT_PLAIN) && a.st && a.counter) {
       __shared__ bool s_last;
       __threadfence();

@@ -157,3 +157,32 @@ def test_mixed_solve_with_every_stencil_variant_pinned(voided_case, staging, war
     m.close()
     assert np.linalg.norm(u[0] - uref) <= 1e-5 * np.linalg.norm(uref), st
     assert abs(J - Jref) <= 1e-6 * abs(Jref)
+
+
+@pytest.mark.parametrize("staging", [2, 3])
+def test_batched_solve_with_load_case_pairs(staging):
+    """Three load cases solved at once with the packed-band stencil, its load
+    cases in pairs (variant 3: the second pair holds one case, and the cases
+    converge at different iterations, so a pair runs with one lane finished)
+    or one case per launch lane set (variant 2): every displacement matches the
+    oracle's direct solution to 1e-5 and J to 1e-6 (Eq. 1.1; Sec. 4.5's
+    multiple loads)."""
+    from synthetic import small_cantilever
+
+    w = small_cantilever(32, 14, 10, seed=12, n_spheres=5, rmin=1.5, rmax=3.5, group=4, n_rhs=3)
+    m = afd.Mesh(w.nx, w.ny, w.nz, group=w.group, stencil_warps=8, stencil_planes=4)
+    m.set_element_moduli(w.E)
+    m.set_loads_bcs(w.f, w.fixed)
+    afd.afd_set_stencil_shape(m.h, 8, 4, staging)
+    u = np.zeros_like(w.f)
+    st = m.solve(1e-8, u_out=u)
+    J = m.compliance()
+    assert afd.afd_stencil_async(m.h) == staging
+    m.close()
+    K = fe.assemble(w.nx, w.ny, w.nz, w.E)
+    for r in range(3):
+        uref = fe.solve_direct(K, w.f[r], w.fixed)
+        assert np.linalg.norm(u[r] - uref) <= 1e-5 * np.linalg.norm(uref), (r, st[r])
+        Jref = fe.compliance(w.f[r], uref)
+        assert abs(J[r] - Jref) <= 1e-6 * abs(Jref), r
+    assert len({s["iters"] for s in st}) > 1   # the cases stop at different iterations
