@@ -103,7 +103,8 @@ def alu_roofline(n_elements: int, ms: float) -> dict:
 # The FP32 stencil variants the autotuner chooses from (afd_stencil_async).
 STENCIL_NAMES = {0: "stencil2_kernel<TY,{mode},register prefetch>", 1: "stencil2_kernel<TY,{mode},cp.async ring>",
                  2: "st3_kernel<TY,{mode}> (packed bands)"}
-STENCIL_DRAM_BYTES = {(128, 64, 64, 8, 6, 0): 9198592, (384, 192, 192, 8, 12, 1): 378244608}
+STENCIL_DRAM_BYTES = {(128, 64, 64, 8, 6, 0): 9198592, (384, 192, 192, 8, 12, 1): 378244608,
+                      (384, 192, 192, 8, 12, 2): 363241984}
 # The same for the stencil of the inner DPCG iteration (ST_APPLY_DOT), captured inside a mixed solve.
 STENCIL_DOT_DRAM_BYTES = {(128, 64, 64, 8, 6, 0): 15795456}
 
