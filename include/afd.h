@@ -52,7 +52,9 @@ enum {
 };
 
 enum { AFD_FP64 = 0, AFD_MIXED = 1 };        /* solver precision */
-enum { AFD_F32 = 0, AFD_F64 = 1 };           /* arithmetic type of a stencil call */
+/* arithmetic type of a stencil call: FP32 on float data, FP64 on double data, or double-float on double data
+ * (each value an unevaluated sum of two floats, about 44 significant bits, on the FP32 pipes) */
+enum { AFD_F32 = 0, AFD_F64 = 1, AFD_F64_DF = 2 };
 enum {
   AFD_SENS_STRAIN_ENERGY = 0,  /* s_e = u_e^T (E_e K0) u_e; sums to J (Sec. 3.1 fallback) */
   AFD_SENS_TJ = 1,             /* Eq. 3.2 at the element centroid, as printed */
@@ -87,6 +89,12 @@ typedef struct {
                          FP32 rounding is applied in the FP32 inner iterations); 0 (default) builds it from
                          FP32 element products summed in FP64 and inverts it in FP32 (same inner iteration
                          counts on the measured workloads at a lower set-up cost).  AFD_FP64 is always FP64. */
+  int residual_fp64;  /* AFD_MIXED: 0 (default) evaluates the refinement residual f - K u from the FP64 u and f
+                         in double-float arithmetic (AFD_F64_DF) when rel_tol >= 1e-10 and every nonzero
+                         ||f|| lies in [1e-20, 1e20], else in FP64 (and again in FP64 if its norm is not
+                         finite); 1 always in FP64.  The double-float residual's rounding is a few 2^-44 of
+                         the element forces, far below the tolerances it serves, at a fraction of FP64's
+                         cost on GB300. */
 } afd_options;
 
 typedef struct {
@@ -259,8 +267,9 @@ int afd_casting_scan(float* keys, int nx, int ny, int nz, int axis, int parting,
 /* ---- lower-level entry points (the pieces of the path, used by the tests) ---- */
 
 /* y = K u on the free DOFs (rows and columns of fixed DOFs act as zero), in
- * FP32 (arith = AFD_F32: u, y float) or FP64 (AFD_F64: double); n_rhs vectors
- * of ndof values, RHS-major.  Device pointers only. */
+ * FP32 (arith = AFD_F32: u, y float), FP64 (AFD_F64: double) or double-float
+ * arithmetic on double data (AFD_F64_DF: u, y double); n_rhs vectors of ndof
+ * values, RHS-major.  Device pointers only. */
 int afd_apply_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y);
 
 /* One search-direction step of the inner FP32 deflated PCG iteration (Sec.
@@ -316,7 +325,7 @@ int afd_select_topk_noalloc(const float* keys, int64_t n, int64_t k, uint8_t* ke
                             void* cuda_stream);
 
 /* Time `launches` back-to-back stiffness applies y = K u (the solver's
- * kernel and launch geometry, arith AFD_F32 or AFD_F64, n_rhs vectors, device
+ * kernel and launch geometry, arith AFD_F32, AFD_F64 or AFD_F64_DF, n_rhs vectors, device
  * pointers, one launch per vector) on the mesh's stream with CUDA events
  * recorded on that stream; *ms_out = mean device time per round of n_rhs
  * launches.  Measurement aid (Sec. 3.5 names

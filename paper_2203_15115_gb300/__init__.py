@@ -30,6 +30,7 @@ AFD_FP64 = 0
 AFD_MIXED = 1
 AFD_F32 = 0
 AFD_F64 = 1
+AFD_F64_DF = 2   # double data, double-float arithmetic
 AFD_SENS_STRAIN_ENERGY = 0
 AFD_SENS_TJ = 1
 AFD_SENS_VON_MISES = 2
@@ -57,7 +58,8 @@ class afd_options(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("persistent", ctypes.c_int), ("stencil_warps", ctypes.c_int),
                 ("stencil_planes", ctypes.c_int), ("pdl", ctypes.c_int), ("inner_aim", ctypes.c_double),
-                ("coarse_fp64", ctypes.c_int)]
+                ("coarse_fp64", ctypes.c_int),
+                ("residual_fp64", ctypes.c_int)]
 
 
 class afd_stats(ctypes.Structure):
@@ -363,7 +365,7 @@ def afd_casting_scan(keys, nx: int, ny: int, nz: int, axis: int, parting: int, s
 
 
 def afd_apply_stiffness(mesh, arith: int, n_rhs: int, u, y) -> None:
-    dt = np.float64 if arith == AFD_F64 else np.float32
+    dt = np.float32 if arith == AFD_F32 else np.float64
     pu, _, _k1 = _arr(u, dt)
     py, _, _k2 = _arr(y, dt)
     _check(lib().afd_apply_stiffness(mesh, arith, n_rhs, pu, py))
@@ -435,7 +437,7 @@ def afd_select_topk(keys, k: int, kept, stream=None) -> float:
 
 def afd_time_stiffness(mesh, arith: int, n_rhs: int, u, y, launches: int) -> float:
     """Mean device ms per stiffness apply, timed with CUDA events on the mesh's stream."""
-    dt = np.float64 if arith == AFD_F64 else np.float32
+    dt = np.float32 if arith == AFD_F32 else np.float64
     pu, _, _k1 = _arr(u, dt)
     py, _, _k2 = _arr(y, dt)
     ms = ctypes.c_double()

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include "dfloat.cuh"
 
 namespace afd {
 

@@ -116,7 +116,7 @@ struct afd_mesh {
   double* E64 = nullptr;
   uint8_t* fixed = nullptr;   // per node bits
   int nrhs = 0, cap = 0;
-  double *f64 = nullptr, *u64 = nullptr, *r64 = nullptr;
+  double *f64 = nullptr, *u64 = nullptr;
   std::vector<double> fnorm;
   bool has_moduli = false, has_loads = false, has_solution = false;
   // shared scratch
@@ -264,6 +264,9 @@ static int ensure_partials(afd_mesh* m, size_t n) {
 }
 
 constexpr int TY64 = 8;  // warps per FP64 stencil CTA; the FP32 stencil takes m->ty32 (8 or 16)
+// Smallest relative tolerance whose refinement residual is evaluated in double-float arithmetic: its
+// rounding, a few 2^-44 of the largest element forces, stays about 1e-12 of ||f|| on voided meshes.
+constexpr double RESIDUAL_DF_MIN_TOL = 1e-10;
 
 static void geom32(const Grid& g, int ty, int kz, int& tiles_x, dim3& grid) {
   if (ty == 8)
@@ -366,7 +369,7 @@ static int launch_st3(afd_mesh* m, const StencilArgs<float, float>& a, dim3 grid
   return AFD_OK;
 }
 
-template <typename T, int MODE, typename TF>
+template <typename T, int MODE, typename TF, typename C = T>
 static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f, float* y32, double* partials,
                           const int* done, int nrhs, const ElemConsts<T>& K, CGState* st = nullptr,
                           unsigned int* counter = nullptr, const T* z = nullptr, const double* mu = nullptr,
@@ -395,7 +398,7 @@ static int launch_stencil(afd_mesh* m, const T* u, T* y, const T* E, const TF* f
   stencil_geom(m, F64, a.tiles_x, grid, nrhs);
   grid.z = nrhs;
   if constexpr (F64) {
-    CK(launch_ex(m->pdl_now, stencil_kernel<T, TY64, MODE, TF>, grid, dim3(ST_TX * TY64), 0, m->s, a));
+    CK(launch_ex(m->pdl_now, stencil_kernel<T, TY64, MODE, TF, C>, grid, dim3(ST_TX * TY64), 0, m->s, a));
   } else {
     static_assert(std::is_same<TF, float>::value, "the FP32 stencil takes FP32 right-hand sides");
     // the packed FP32 kernel forms p in ST_APPLY_DOT only, and always there
@@ -456,10 +459,10 @@ static int ensure_work(afd_mesh* m, Work<T>& w, int nrhs) {
 static int ensure_rhs(afd_mesh* m, int nrhs) {
   if (m->cap >= nrhs) return AFD_OK;
   invalidate_graphs(m);
-  dfree(m->f64); dfree(m->u64); dfree(m->r64); dfree(m->st); dfree(m->done); dfree(m->v); dfree(m->mu); dfree(m->wr);
+  dfree(m->f64); dfree(m->u64); dfree(m->st); dfree(m->done); dfree(m->v); dfree(m->mu); dfree(m->wr);
   dfree(m->fbuf);
   const size_t n = (size_t)nrhs * m->gr.vs;
-  TRY(dalloc(&m->f64, n)); TRY(dalloc(&m->u64, n)); TRY(dalloc(&m->r64, n));
+  TRY(dalloc(&m->f64, n)); TRY(dalloc(&m->u64, n));
   TRY(dalloc(&m->st, (size_t)nrhs)); TRY(dalloc(&m->done, (size_t)nrhs));
   TRY(dalloc(&m->v, (size_t)nrhs * m->nc)); TRY(dalloc(&m->mu, (size_t)nrhs * m->nc));
   TRY(dalloc(&m->wr, (size_t)nrhs * m->nc));
@@ -1036,6 +1039,7 @@ void afd_default_options(afd_options* o) {
   o->pdl = 0;
   o->inner_aim = 0.5;
   o->coarse_fp64 = 0;
+  o->residual_fp64 = 0;
 }
 
 const char* afd_last_error(void) { return g_err.c_str(); }
@@ -1149,7 +1153,7 @@ void afd_destroy(afd_mesh* m) {
     dfree(wp->invdiag); dfree(wp->E);
     if (wp->graph) cudaGraphExecDestroy(wp->graph);
   }
-  dfree(m->E64); dfree(m->fixed); dfree(m->f64); dfree(m->u64); dfree(m->r64); dfree(m->partials);
+  dfree(m->E64); dfree(m->fixed); dfree(m->f64); dfree(m->u64); dfree(m->partials);
   dfree(m->st); dfree(m->done); dfree(m->v); dfree(m->mu); dfree(m->wr); dfree(m->cpart); dfree(m->fbuf); dfree(m->fkeys); dfree(m->kept);
   if (m->sel) cudaFree(m->sel);
   dfree(m->selcnt); dfree(m->fsmall);
@@ -1305,14 +1309,23 @@ int afd_set_loads_bcs(afd_mesh* m, int n_rhs, const double* f, int f_on_device, 
   return finish(m);
 }
 
-// r64 = f - K u64 (FP64), optional float copy into b32; returns ||r||/||f|| per RHS.
-static int true_residual(afd_mesh* m, float* b32, std::vector<double>& rel) {
+// r = f - K u64 from FP64 data into its float copy b32 (nullable: the norm
+// only); returns ||r||/||f|| per RHS.  dfl: the arithmetic is double-float
+// (FP32 pairs, about 44 bits) instead of FP64.
+static int true_residual(afd_mesh* m, float* b32, std::vector<double>& rel, bool dfl = false) {
   const int nsb = stencil_blocks(m, true);
   TRY(ensure_partials(m, (size_t)m->nrhs * std::max(nsb, 2 * RED_BLOCKS)));
-  TRY((launch_stencil<double, ST_RESIDUAL, double>(m, m->u64, m->r64, m->w64.E, m->f64, b32, m->partials, nullptr,
-                                                     m->nrhs, m->w64.K)));
+  if (dfl)
+    TRY((launch_stencil<double, ST_RESIDUAL, double, dfloat>(m, m->u64, nullptr, m->w64.E, m->f64, b32, m->partials,
+                                                               nullptr, m->nrhs, m->w64.K)));
+  else
+    TRY((launch_stencil<double, ST_RESIDUAL, double>(m, m->u64, nullptr, m->w64.E, m->f64, b32, m->partials, nullptr,
+                                                       m->nrhs, m->w64.K)));
   std::vector<double> rr;
   TRY(reduce_partials_host(m, m->nrhs, nsb, rr));
+  if (dfl)
+    for (int r = 0; r < m->nrhs; ++r)
+      if (!std::isfinite(rr[r])) return true_residual(m, b32, rel, false);   // beyond FP32's exponent range
   rel.resize(m->nrhs);
   for (int r = 0; r < m->nrhs; ++r) rel[r] = m->fnorm[r] > 0 ? std::sqrt(rr[r]) / m->fnorm[r] : std::sqrt(rr[r]);
   return AFD_OK;
@@ -1352,6 +1365,11 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
   } else {
     TRY(ensure_work(m, m->w32, R));
     float* b32 = m->w32.b;
+    // the refinement residual in double-float unless the tolerance nears its rounding (about 1e-12 of
+    // ||f||) or the loads are far from unit scale (the pairs have FP32's exponent range)
+    bool dfl = !m->opt.residual_fp64 && rel_tol >= RESIDUAL_DF_MIN_TOL;
+    for (int r = 0; r < R; ++r)
+      if (m->fnorm[r] != 0.0 && !(m->fnorm[r] >= 1e-20 && m->fnorm[r] <= 1e20)) dfl = false;
     if (cold) {
       // u = 0: the residual is f itself (zero on fixed DOFs), so the first FP64 pass is not needed
       for (int r = 0; r < R; ++r) {
@@ -1363,7 +1381,7 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
       rel.assign(R, 0.0);
       for (int r = 0; r < R; ++r) rel[r] = m->fnorm[r] > 0.0 ? 1.0 : 0.0;
     } else {
-      TRY(true_residual(m, b32, rel));
+      TRY(true_residual(m, b32, rel, dfl));
     }
     for (int step = 0; step <= m->opt.max_refine; ++step) {
       std::vector<int> act(R, 0);
@@ -1398,7 +1416,7 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
       CK(cudaMemcpyAsync(dskip, skip.data(), R * sizeof(int), cudaMemcpyHostToDevice, m->s));
       k_accumulate<<<dim3(grid_blocks(g.ndof, 256, 2048), R), 256, 0, m->s>>>(g.ndof, g.vs, m->u64, m->w32.x, dskip); m->launches++;
       CK(cudaGetLastError());
-      TRY(true_residual(m, b32, rel));
+      TRY(true_residual(m, b32, rel, dfl));
     }
     for (int r = 0; r < R; ++r)
       if (status[r] == AFD_OK && !(rel[r] <= rel_tol)) status[r] = AFD_ERR_NOT_CONVERGED;
@@ -2223,23 +2241,32 @@ int afd_levelset_update_fields(afd_mesh* m, const float* fields, int fields_on_d
   return levelset_cut(m, m->lsbuf, nfields, weights, volume_fraction, axis, parting, tau_out, kept_out);
 }
 
+// One y = K u launch for one vector in arithmetic `arith` (AFD_F32, AFD_F64 or AFD_F64_DF).
+static int apply_one(afd_mesh* m, int arith, const void* u, void* y) {
+  if (arith == AFD_F64)
+    return launch_stencil<double, ST_APPLY, double>(m, (const double*)u, (double*)y, m->w64.E, nullptr, nullptr,
+                                                    nullptr, nullptr, 1, m->w64.K);
+  if (arith == AFD_F64_DF)
+    return launch_stencil<double, ST_APPLY, double, dfloat>(m, (const double*)u, (double*)y, m->w64.E, nullptr,
+                                                            nullptr, nullptr, nullptr, 1, m->w64.K);
+  return launch_stencil<float, ST_APPLY, float>(m, (const float*)u, (float*)y, m->w32.E, nullptr, nullptr, nullptr,
+                                                nullptr, 1, m->w32.K);
+}
+
+static bool valid_arith(int arith) { return arith == AFD_F32 || arith == AFD_F64 || arith == AFD_F64_DF; }
+
 int afd_apply_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y) {
   if (!m || !u || !y) return fail(AFD_ERR_INVALID_ARG, "null argument");
   if (n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "n_rhs must be >= 1");
   if (!m->has_moduli) return fail(AFD_ERR_STATE, "moduli not set");
   DeviceGuard dg(m->device);
   TRY(enter(m));
-  if (arith != AFD_F32 && arith != AFD_F64) return fail(AFD_ERR_INVALID_ARG, "arith must be AFD_F32 or AFD_F64");
+  if (!valid_arith(arith)) return fail(AFD_ERR_INVALID_ARG, "arith must be AFD_F32, AFD_F64 or AFD_F64_DF");
   // caller arrays are RHS-major with stride ndof: one launch per RHS
   const size_t nd = (size_t)m->gr.ndof;
-  for (int r = 0; r < n_rhs; ++r) {
-    if (arith == AFD_F64)
-      TRY((launch_stencil<double, ST_APPLY, double>(m, (const double*)u + r * nd, (double*)y + r * nd, m->w64.E, nullptr,
-                                                      nullptr, nullptr, nullptr, 1, m->w64.K)));
-    else
-      TRY((launch_stencil<float, ST_APPLY, float>(m, (const float*)u + r * nd, (float*)y + r * nd, m->w32.E, nullptr,
-                                                    nullptr, nullptr, nullptr, 1, m->w32.K)));
-  }
+  const size_t es = arith == AFD_F32 ? sizeof(float) : sizeof(double);
+  for (int r = 0; r < n_rhs; ++r)
+    TRY(apply_one(m, arith, (const char*)u + r * nd * es, (char*)y + r * nd * es));
   return finish(m);
 }
 
@@ -2448,7 +2475,7 @@ size_t afd_mesh_bytes(int nx, int ny, int nz, int n_rhs, const afd_options* opt)
   size_t b = 0;
   b += ne * (8 + 4 + 8) + ne * (4 * (size_t)n_rhs + 4 + 1);        // moduli, fields, keys, kept
   b += nn * (1 + 4 + 8) + vs * (4 + 8);                             // mask, Jacobi factors
-  b += (size_t)n_rhs * vs * (3 * 8 + 8 * tsz);                      // f, u, r (FP64) + Krylov work
+  b += (size_t)n_rhs * vs * (2 * 8 + 8 * tsz);                      // f, u (FP64) + Krylov work
   b += nc * nc * (8 + tsz) + nc * GJ_NB * 2 * 8 + GJ_NB * GJ_NB * 8; // coarse matrix, inverse, sweep scratch
   if (!f64 && o.coarse_fp64) b += nc * nc * 8;                      // FP64 inverse before its FP32 rounding
   const size_t box = (size_t)(g + 3) * (g + 3) * (g + 3);
@@ -2460,7 +2487,7 @@ size_t afd_mesh_bytes(int nx, int ny, int nz, int n_rhs, const afd_options* opt)
 int afd_time_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y, int launches, double* ms_out) {
   if (!m || !u || !y || !ms_out || launches < 1 || n_rhs < 1) return fail(AFD_ERR_INVALID_ARG, "bad argument");
   if (!m->has_moduli) return fail(AFD_ERR_STATE, "moduli not set");
-  if (arith != AFD_F32 && arith != AFD_F64) return fail(AFD_ERR_INVALID_ARG, "arith must be AFD_F32 or AFD_F64");
+  if (!valid_arith(arith)) return fail(AFD_ERR_INVALID_ARG, "arith must be AFD_F32, AFD_F64 or AFD_F64_DF");
   DeviceGuard dg(m->device);
   TRY(enter(m));
   cudaEvent_t e0, e1;
@@ -2468,16 +2495,9 @@ int afd_time_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, m->s));
   const size_t nd = (size_t)m->gr.ndof;
-  for (int i = 0; i < launches; ++i) {
-    for (int r = 0; r < n_rhs; ++r) {
-      if (arith == AFD_F64)
-        TRY((launch_stencil<double, ST_APPLY, double>(m, (const double*)u + r * nd, (double*)y + r * nd, m->w64.E,
-                                                        nullptr, nullptr, nullptr, nullptr, 1, m->w64.K)));
-      else
-        TRY((launch_stencil<float, ST_APPLY, float>(m, (const float*)u + r * nd, (float*)y + r * nd, m->w32.E, nullptr,
-                                                      nullptr, nullptr, nullptr, 1, m->w32.K)));
-    }
-  }
+  const size_t es = arith == AFD_F32 ? sizeof(float) : sizeof(double);
+  for (int i = 0; i < launches; ++i)
+    for (int r = 0; r < n_rhs; ++r) TRY(apply_one(m, arith, (const char*)u + r * nd * es, (char*)y + r * nd * es));
   CK(cudaEventRecord(e1, m->s));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;

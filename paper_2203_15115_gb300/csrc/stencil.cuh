@@ -16,6 +16,7 @@
 // every node is finished by exactly one thread.
 #pragma once
 
+#include <type_traits>
 #include "afd_common.cuh"
 #include "dpcg_kernels.cuh"
 
@@ -32,7 +33,7 @@ template <typename T, typename TF>
 struct StencilArgs {
   Grid gr;
   const T* u;             // [rhs][ndof]
-  T* y;                   // [rhs][ndof]
+  T* y;                   // [rhs][ndof] (ST_RESIDUAL: nullable, then only the norm and y32 are formed)
   const T* E;             // [nelem] element moduli in the working type
   const uint8_t* fixed;   // [nnodes] bit c set = DOF c fixed (nullable: none fixed)
   ElemConsts<T> K;
@@ -74,16 +75,36 @@ struct StencilGeom {
   }
 };
 
-template <typename T, int TY, int MODE, typename TF>
-__global__ void __launch_bounds__(ST_TX * TY)
+// Element constants in the kernel's arithmetic type (a no-op copy when it is
+// the storage type).
+template <typename C, typename T>
+__device__ __forceinline__ ElemConsts<C> elem_consts_as(const ElemConsts<T>& k) {
+  using A = Arith<C, T>;
+  ElemConsts<C> c;
+  c.l16 = A::in(k.l16);
+  c.m16 = A::in(k.m16);
+  c.m8 = A::in(k.m8);
+  c.l48 = A::in(k.l48);
+  c.m48 = A::in(k.m48);
+  c.m3_48 = A::in(k.m3_48);
+  c.t144 = A::in(k.t144);
+  return c;
+}
+
+// T: the type of u, y, z, p and E in memory; C: the arithmetic type (T, or
+// dfloat for an FP64-accurate residual computed on the FP32 pipes).
+template <typename T, int TY, int MODE, typename TF, typename C = T>
+__global__ void __launch_bounds__(ST_TX * TY, std::is_same<C, dfloat>::value ? 2 : 1)
 stencil_kernel(const StencilArgs<T, TF> a) {
+  using AT = Arith<C, T>;
+  const ElemConsts<C> K = elem_consts_as<C>(a.K);
   pdl_acquire();
   // TY warps: warps 0..TY-2 own element rows, the last warp only supplies the
   // x-edges of the row above the tile.  Exchange buffers: each is written,
   // then read after a barrier; the other exchange's barrier separates that
   // read from the next write.
-  __shared__ T xe[6][TY][ST_TX];   // x-edge (S, D) x 3 components
-  __shared__ T ye[6][TY][ST_TX];   // edge contributions sent to the row above
+  __shared__ C xe[6][TY][ST_TX];   // x-edge (S, D) x 3 components
+  __shared__ C ye[6][TY][ST_TX];   // edge contributions sent to the row above
   __shared__ double red[32];
 
   const int rhs = blockIdx.z;
@@ -108,30 +129,30 @@ stencil_kernel(const StencilArgs<T, TF> a) {
   // A_G = t + omega x (r_x, r_y, 0), B_G = (omega_y, -omega_x, 0); A, B are
   // refreshed when the plane index enters the next group along z.
   const bool formp = a.z != nullptr;
-  T beta = T(0);
+  C beta = C(0);
   if (formp) {
     if (a.ip.upd) {
       double b;
       if (!dpcg_iteration_start(a.st, rhs, const_cast<int*>(a.done), a.ip, b)) return;
-      beta = (T)b;
+      beta = (C)b;
     } else {
-      beta = (T)a.st[rhs].beta;
+      beta = (C)a.st[rhs].beta;
     }
   }
   const Groups gp = a.gp;
-  const T hh = (T)(0.5 * gp.h);
-  T rx = T(0), ry = T(0);
+  const C hh = (C)(0.5 * gp.h);
+  C rx = C(0), ry = C(0);
   int gxy = 0;            // Gx + ngx * Gy
   int gz = -1, gz_next = 0, zlo = 0, zhi = 0;
-  T A0 = T(0), A1 = T(0), A2 = T(0), B0 = T(0), B1 = T(0);
+  C A0 = C(0), A1 = C(0), A2 = C(0), B0 = C(0), B1 = C(0);
   const double* murhs = formp ? a.mu + (size_t)rhs * 6 * gp.ng : nullptr;
   if (formp && col_ok) {
     int lo, hi;
     const int Gx = group_of_axis(i, gp.g, gp.ngx), Gy = group_of_axis(j, gp.g, gp.ngy);
     group_range(Gx, gp.g, gp.ngx, gr.nx, lo, hi);
-    rx = hh * (T)(2 * i - lo - hi);
+    rx = hh * (C)(2 * i - lo - hi);
     group_range(Gy, gp.g, gp.ngy, gr.ny, lo, hi);
-    ry = hh * (T)(2 * j - lo - hi);
+    ry = hh * (C)(2 * j - lo - hi);
     gxy = Gx + gp.ngx * Gy;
   }
   auto refresh_group = [&](int k) {
@@ -139,7 +160,7 @@ stencil_kernel(const StencilArgs<T, TF> a) {
     group_range(gz, gp.g, gp.ngz, gr.nz, zlo, zhi);
     gz_next = (gz == gp.ngz - 1) ? (1 << 30) : zhi + 1;
     const double* m6 = murhs + 6 * (gxy + gp.ngx * gp.ngy * gz);
-    const T tx = (T)m6[0], ty = (T)m6[1], tz = (T)m6[2], ox = (T)m6[3], oy = (T)m6[4], oz = (T)m6[5];
+    const C tx = (C)m6[0], ty = (C)m6[1], tz = (C)m6[2], ox = (C)m6[3], oy = (C)m6[4], oz = (C)m6[5];
     A0 = tx - oz * ry;
     A1 = ty + oz * rx;
     A2 = tz + (ox * ry - oy * rx);
@@ -147,7 +168,7 @@ stencil_kernel(const StencilArgs<T, TF> a) {
     B1 = -ox;
   };
 
-  auto load_node = [&](int k, T (&v)[3]) {
+  auto load_node = [&](int k, C (&v)[3]) {
     if (col_ok && k >= 0 && k < gr.nnz) {
       const int n = i + gr.nnx * (j + gr.nny * k);
       const uint8_t fb = a.fixed ? a.fixed[n] : 0;
@@ -155,27 +176,27 @@ stencil_kernel(const StencilArgs<T, TF> a) {
       if (formp) {
         if (k >= gz_next || gz < 0) refresh_group(k);
         const T* zz = a.z + voff + 3 * (size_t)n;
-        const T rz = hh * (T)(2 * k - zlo - zhi);
-        v[0] = (fb & 1) ? T(0) : fma(beta, p[0], zz[0] + fma(rz, B0, A0));
-        v[1] = (fb & 2) ? T(0) : fma(beta, p[1], zz[1] + fma(rz, B1, A1));
-        v[2] = (fb & 4) ? T(0) : fma(beta, p[2], zz[2] + A2);
+        const C rz = hh * (C)(2 * k - zlo - zhi);
+        v[0] = (fb & 1) ? C(0) : fma(beta, AT::in(p[0]), AT::in(zz[0]) + fma(rz, B0, A0));
+        v[1] = (fb & 2) ? C(0) : fma(beta, AT::in(p[1]), AT::in(zz[1]) + fma(rz, B1, A1));
+        v[2] = (fb & 4) ? C(0) : fma(beta, AT::in(p[2]), AT::in(zz[2]) + A2);
       } else {
-        v[0] = (fb & 1) ? T(0) : p[0];
-        v[1] = (fb & 2) ? T(0) : p[1];
-        v[2] = (fb & 4) ? T(0) : p[2];
+        v[0] = (fb & 1) ? C(0) : AT::in(p[0]);
+        v[1] = (fb & 2) ? C(0) : AT::in(p[1]);
+        v[2] = (fb & 4) ? C(0) : AT::in(p[2]);
       }
     } else {
-      v[0] = v[1] = v[2] = T(0);
+      v[0] = v[1] = v[2] = C(0);
     }
   };
 
   // face values (x-edge stage then y stage) of a node plane for element column (i, j):
   // F[c][q], q = mx + 2 my (mx: x-difference, my: y-difference)
-  auto face_values = [&](const T (&un)[3], T (&F)[3][4]) {
-    T S[3], D[3];
+  auto face_values = [&](const C (&un)[3], C (&F)[3][4]) {
+    C S[3], D[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const T right = __shfl_down_sync(0xffffffffu, un[c], 1);  // lane 31: unused
+      const C right = __shfl_down_sync(0xffffffffu, un[c], 1);  // lane 31: unused
       S[c] = right + un[c];
       D[c] = right - un[c];
       xe[c][w][lane] = S[c];
@@ -185,7 +206,7 @@ stencil_kernel(const StencilArgs<T, TF> a) {
     if (w < TY - 1) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const T S1 = xe[c][w + 1][lane], D1 = xe[3 + c][w + 1][lane];
+        const C S1 = xe[c][w + 1][lane], D1 = xe[3 + c][w + 1][lane];
         F[c][0] = S1 + S[c];
         F[c][1] = D1 + D[c];
         F[c][2] = S1 - S[c];
@@ -193,39 +214,39 @@ stencil_kernel(const StencilArgs<T, TF> a) {
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) F[c][0] = F[c][1] = F[c][2] = F[c][3] = T(0);
+      for (int c = 0; c < 3; ++c) F[c][0] = F[c][1] = F[c][2] = F[c][3] = C(0);
     }
   };
 
-  T Fb[3][4];      // face values of the plane below the current element layer
-  T Tprev[3][4];   // top-face forces of the element layer below the current plane
+  C Fb[3][4];      // face values of the plane below the current element layer
+  C Tprev[3][4];   // top-face forces of the element layer below the current plane
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Fb[c][q] = Tprev[c][q] = T(0);
+    for (int q = 0; q < 4; ++q) Fb[c][q] = Tprev[c][q] = C(0);
 
   {
-    T un0[3];
+    C un0[3];
     load_node(k0 - 1, un0);
     face_values(un0, Fb);
     __syncthreads();  // the loop's first x-edge write follows this read
   }
-  T ucur[3] = {T(0), T(0), T(0)};   // (formed) u at (i, j, l) for the dot epilogue and p write
-  T part = T(0);
-  T un[3];
+  C ucur[3] = {C(0), C(0), C(0)};   // (formed) u at (i, j, l) for the dot epilogue and p write
+  C part = C(0);
+  C un[3];
   load_node(k0, un);   // prefetch of the next plane
 
   for (int l = k0 - 1; l < k1; ++l) {
     // element layer l lies between node planes l and l+1; finish plane l
-    T Ft[3][4];
+    C Ft[3][4];
     face_values(un, Ft);
-    const T u_l1[3] = {un[0], un[1], un[2]};  // plane l+1
-    T E = T(0);
-    if (elem_xy && l >= 0 && l < gr.nz) E = a.E[i + gr.nx * (j + gr.ny * l)];
+    const C u_l1[3] = {un[0], un[1], un[2]};  // plane l+1
+    C E = C(0);
+    if (elem_xy && l >= 0 && l < gr.nz) E = AT::in(a.E[i + gr.nx * (j + gr.ny * l)]);
     if (l + 2 <= k1) load_node(l + 2, un);  // prefetch plane l+2
-    T Bf[3][4];  // bottom-face forces of element layer l (plane l)
-    if (E != T(0)) {
-      T h[3][8];
+    C Bf[3][4];  // bottom-face forces of element layer l (plane l)
+    if (E != C(0)) {
+      C h[3][8];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -233,14 +254,14 @@ stencil_kernel(const StencilArgs<T, TF> a) {
           h[c][q] = Ft[c][q] + Fb[c][q];
           h[c][q + 4] = Ft[c][q] - Fb[c][q];
         }
-      modal_forces(h, E, a.K);
+      modal_forces(h, E, K);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const T g0 = h[c][q], g1 = h[c][q + 4];
+          const C g0 = h[c][q], g1 = h[c][q + 4];
           Bf[c][q] = g0 - g1;
-          const T tf = g0 + g1;
+          const C tf = g0 + g1;
           h[c][q] = tf;   // keep the top-face force
         }
       // plane l total face force: this layer's bottom + the layer below's top
@@ -257,7 +278,7 @@ stencil_kernel(const StencilArgs<T, TF> a) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           Bf[c][q] = Tprev[c][q];
-          Tprev[c][q] = T(0);
+          Tprev[c][q] = C(0);
         }
     }
 #pragma unroll
@@ -266,7 +287,7 @@ stencil_kernel(const StencilArgs<T, TF> a) {
       for (int q = 0; q < 4; ++q) Fb[c][q] = Ft[c][q];
 
     // transposed y stage: face (i, j) -> x-edges of rows j and j+1
-    T e0[3][2], e1[3][2];
+    C e0[3][2], e1[3][2];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -288,36 +309,36 @@ stencil_kernel(const StencilArgs<T, TF> a) {
       }
     }
     // transposed x stage: edge (i, i+1) -> node i gets s - d, node i+1 gets s + d
-    T yv[3];
+    C yv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const T sp = e0[c][0] + e0[c][1];
-      const T from_left = __shfl_up_sync(0xffffffffu, sp, 1);
-      yv[c] = (e0[c][0] - e0[c][1]) + (lane >= 1 ? from_left : T(0));
+      const C sp = e0[c][0] + e0[c][1];
+      const C from_left = __shfl_up_sync(0xffffffffu, sp, 1);
+      yv[c] = (e0[c][0] - e0[c][1]) + (lane >= 1 ? from_left : C(0));
     }
     if (l >= k0 && out_xy) {
       const int n = i + gr.nnx * (j + gr.nny * l);
       const uint8_t fb = a.fixed ? a.fixed[n] : 0;
-      T* yp = a.y + voff + 3 * (size_t)n;
+      T* yp = a.y ? a.y + voff + 3 * (size_t)n : nullptr;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const bool fx = (fb >> c) & 1;
-        T out;
+        C out;
         if (MODE == ST_RESIDUAL) {
-          out = fx ? T(0) : (T)a.f[voff + 3 * (size_t)n + c] - yv[c];
+          out = fx ? C(0) : Arith<C, TF>::in(a.f[voff + 3 * (size_t)n + c]) - yv[c];
           part += out * out;
           if (a.y32) a.y32[voff + 3 * (size_t)n + c] = (float)out;
         } else {
-          out = fx ? T(0) : yv[c];
+          out = fx ? C(0) : yv[c];
           if (MODE == ST_APPLY_DOT) part += ucur[c] * out;
         }
-        yp[c] = out;
+        if (MODE != ST_RESIDUAL || yp) yp[c] = AT::out(out);
       }
       if (formp) {
         T* pp = a.pout + voff + 3 * (size_t)n;
-        pp[0] = ucur[0];
-        pp[1] = ucur[1];
-        pp[2] = ucur[2];
+        pp[0] = AT::out(ucur[0]);
+        pp[1] = AT::out(ucur[1]);
+        pp[2] = AT::out(ucur[2]);
       }
     }
     if (MODE == ST_APPLY_DOT) {
@@ -328,7 +349,7 @@ stencil_kernel(const StencilArgs<T, TF> a) {
   }
   pdl_release();
   if (MODE != ST_APPLY) {
-    T pv[1] = {out_xy ? part : T(0)};
+    C pv[1] = {out_xy ? part : C(0)};
     double o[1];
     block_sum_to_f64<1>(pv, red, o);
     const int nparts = gridDim.x * gridDim.y;
