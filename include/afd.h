@@ -293,6 +293,15 @@ int afd_apply_search_direction(afd_mesh* m, int n_rhs, const float* z, const flo
 int afd_deflation_wt(afd_mesh* m, int n_rhs, const double* v, double* out);
 int afd_deflation_w(afd_mesh* m, int n_rhs, const double* y, double* out);
 
+/* The inverse of W^T K W (n_c x n_c, row-major, host doubles) as the solver
+ * forms it: FP32 on AFD_MIXED meshes (FP64 with opt.coarse_fp64 and on
+ * AFD_FP64 meshes), from the unit-diagonal scaled matrix by blocked
+ * Gauss-Jordan sweeps without pivoting (E is SPD).  Rebuilds the coarse
+ * matrix from the current moduli and supports and leaves the solver's coarse
+ * data stale.  AFD_ERR_COARSE_SINGULAR when a pivot of the scaled matrix is
+ * <= 1e-6 (FP32) / 1e-12 (FP64) or not finite.  Used by the tests. */
+int afd_coarse_inverse(afd_mesh* m, double* out_host);
+
 /* Number of coarse unknowns 6*N_g, and the dense coarse matrix W^T K W
  * (n_c*n_c FP64, host) built from the current moduli and supports. */
 int afd_coarse_size(afd_mesh* m);

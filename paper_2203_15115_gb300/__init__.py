@@ -39,7 +39,8 @@ AFD_SENS_VON_MISES = 2
 EXPORTS = [
     "afd_default_options", "afd_create_mesh", "afd_set_element_moduli", "afd_set_loads_bcs", "afd_solve",
     "afd_compliance", "afd_sensitivity", "afd_pnorm_stress", "afd_levelset_update", "afd_apply_stiffness",
-    "afd_deflation_wt", "afd_deflation_w", "afd_coarse_size", "afd_coarse_matrix", "afd_select_topk",
+    "afd_deflation_wt", "afd_deflation_w", "afd_coarse_size", "afd_coarse_matrix", "afd_coarse_inverse",
+    "afd_select_topk",
     "afd_ndof", "afd_nelem", "afd_destroy", "afd_last_error", "afd_al_init", "afd_al_update", "afd_al_weight",
     "afd_time_stiffness", "afd_kernel_launches", "afd_select_topk_noalloc", "afd_stencil_depth",
     "afd_stencil_warps", "afd_solver_phase_times", "afd_time_dpcg_kernels", "afd_set_stencil_shape",
@@ -110,6 +111,7 @@ def lib() -> ctypes.CDLL:
             "afd_deflation_wt": (i, [vp, i, vp, vp]),
             "afd_deflation_w": (i, [vp, i, vp, vp]),
             "afd_coarse_size": (i, [vp]),
+            "afd_coarse_inverse": (i, [vp, vp]),
             "afd_coarse_matrix": (i, [vp, vp]),
             "afd_select_topk": (i, [vp, i64, i64, vp, ctypes.POINTER(ctypes.c_float), vp]),
             "afd_ndof": (i64, [vp]),
@@ -408,6 +410,14 @@ def afd_coarse_matrix(mesh) -> np.ndarray:
     nc = afd_coarse_size(mesh)
     out = np.zeros((nc, nc))
     _check(lib().afd_coarse_matrix(mesh, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def afd_coarse_inverse(mesh) -> np.ndarray:
+    """The solver's inverse of W^T K W, as FP64 on the host."""
+    nc = afd_coarse_size(mesh)
+    out = np.zeros((nc, nc))
+    _check(lib().afd_coarse_inverse(mesh, ctypes.c_void_p(out.ctypes.data)))
     return out
 
 

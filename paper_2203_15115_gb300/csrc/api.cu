@@ -139,6 +139,7 @@ struct afd_mesh {
   double* Einv64 = nullptr;    // its inverse, FP64 path
   float* Einv32 = nullptr;     // its inverse, mixed path
   double *gjP = nullptr, *gjB = nullptr, *gjR = nullptr;  // Gauss-Jordan scratch
+  cudaGraphExec_t gj_graph[2] = {nullptr, nullptr};       // the inversion's panel sweeps (FP32, FP64), replayed
   double* cpart = nullptr;     // coarse right-hand side partials [rhs][G][split][12]
   unsigned int* counters = nullptr;  // last-block counters: [rhs] stencil, [MAX_RHS] coarse
   double* dmax = nullptr;
@@ -495,20 +496,49 @@ static int invert_coarse(afd_mesh* m, T* A, double rel) {
   T* B = (T*)m->gjB;
   T* R = (T*)m->gjR;
   const dim3 ug((nc + 31) / 32, (nc + 31) / 32);
-  for (int k0 = 0; k0 < nc; k0 += GJ_NB) {
-    const int nb = std::min(GJ_NB, nc - k0);
-    k_gj_pivot<T><<<1, 32, 0, m->s>>>(A, nc, k0, P, m->dmax, rel, m->dstatus); m->launches++;
-    k_gj_panel<T><<<(nc * nb + 255) / 256, 256, 0, m->s>>>(A, nc, k0, P, B, R); m->launches++;
-    k_gj_update<T><<<ug, 256, 0, m->s>>>(A, nc, k0, P, B, R, k0 + GJ_NB >= nc ? 1 : 0); m->launches++;
+  // The 3 launches per panel of GJ_NB columns are a few microseconds each: they
+  // are captured once per mesh and type into a graph (A, the scratch and the
+  // tolerance do not change for the mesh's life) and replayed.
+  const int npanel = (nc + GJ_NB - 1) / GJ_NB;
+  cudaGraphExec_t& gx = m->gj_graph[sizeof(T) == 8 ? 1 : 0];
+  if (!gx) {
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(m->s, cudaStreamCaptureModeThreadLocal));
+    for (int k0 = 0; k0 < nc; k0 += GJ_NB) {
+      const int nb = std::min(GJ_NB, nc - k0);
+      k_gj_pivot<T><<<1, 32, 0, m->s>>>(A, nc, k0, P, m->dmax, rel, m->dstatus);
+      k_gj_panel<T><<<(nc * nb + 255) / 256, 256, 0, m->s>>>(A, nc, k0, P, B, R);
+      k_gj_update<T><<<ug, 256, 0, m->s>>>(A, nc, k0, P, B, R, k0 + GJ_NB >= nc ? 1 : 0);
+    }
+    k_unscale_dense<T><<<grid_blocks((size_t)nc * nc, 256, 4096), 256, 0, m->s>>>(nc, m->Ec, A);
+    const cudaError_t le = cudaGetLastError();
+    const cudaError_t ce = cudaStreamEndCapture(m->s, &graph);
+    if (le != cudaSuccess) return fail(AFD_ERR_CUDA, "coarse inverse capture: %s", cudaGetErrorString(le));
+    if (ce != cudaSuccess) return fail(AFD_ERR_CUDA, "coarse inverse capture: %s", cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&gx, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      gx = nullptr;
+      return fail(AFD_ERR_CUDA, "coarse inverse graph: %s", cudaGetErrorString(ie));
+    }
   }
-  k_unscale_dense<T><<<grid_blocks((size_t)nc * nc, 256, 4096), 256, 0, m->s>>>(nc, m->Ec, A); m->launches++;
-  CK(cudaGetLastError());
+  CK(cudaGraphLaunch(gx, m->s));
+  m->launches += 3 * npanel + 1;
   int status = 0;
   CK(cudaMemcpyAsync(&status, m->dstatus, sizeof(int), cudaMemcpyDeviceToHost, m->s));
   CK(cudaStreamSynchronize(m->s));
   if (status != 0)
     return fail(AFD_ERR_COARSE_SINGULAR, "coarse matrix W^T K W is singular (are there enough supports?)");
   return AFD_OK;
+}
+
+// A = Ec^{-1} in type T: the unit-diagonal scaled matrix, inverted by the
+// blocked Gauss-Jordan sweeps and unscaled.
+template <typename T>
+static int scale_and_invert(afd_mesh* m, T* A, double rel) {
+  const size_t nn = (size_t)m->nc * m->nc;
+  k_scale_dense<T><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(m->nc, m->Ec, A); m->launches++;
+  return invert_coarse<T>(m, A, rel);
 }
 
 // E = W^T K W into m->Ec (FP64 sums; element math in FP32 on the mixed path).
@@ -579,19 +609,16 @@ static int build_coarse(afd_mesh* m) {
   const size_t nn = (size_t)m->nc * m->nc;
   if (m->opt.precision == AFD_FP64) {
     if (!m->Einv64) TRY(dalloc(&m->Einv64, nn));
-    k_scale_dense<double><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(m->nc, m->Ec, m->Einv64); m->launches++;
-    TRY(invert_coarse<double>(m, m->Einv64, 1e-12));
+    TRY(scale_and_invert<double>(m, m->Einv64, 1e-12));
   } else if (m->opt.coarse_fp64) {
     // FP64 inverse, rounded once to FP32 for the inner iterations' coarse step
     if (!m->Einv64) TRY(dalloc(&m->Einv64, nn));
     if (!m->Einv32) TRY(dalloc(&m->Einv32, nn));
-    k_scale_dense<double><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(m->nc, m->Ec, m->Einv64); m->launches++;
-    TRY(invert_coarse<double>(m, m->Einv64, 1e-12));
+    TRY(scale_and_invert<double>(m, m->Einv64, 1e-12));
     k_convert_dense<float><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(nn, m->Einv64, m->Einv32); m->launches++;
   } else {
     if (!m->Einv32) TRY(dalloc(&m->Einv32, nn));
-    k_scale_dense<float><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(m->nc, m->Ec, m->Einv32); m->launches++;
-    TRY(invert_coarse<float>(m, m->Einv32, 1e-6));
+    TRY(scale_and_invert<float>(m, m->Einv32, 1e-6));
   }
   m->coarse_valid = true;
   return AFD_OK;
@@ -1158,6 +1185,8 @@ void afd_destroy(afd_mesh* m) {
   if (m->sel) cudaFree(m->sel);
   dfree(m->selcnt); dfree(m->fsmall);
   dfree(m->Ec); dfree(m->Einv64); dfree(m->Einv32); dfree(m->gjP); dfree(m->gjB); dfree(m->gjR);
+  for (auto& g : m->gj_graph)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gbox); dfree(m->aw_off); dfree(m->aw_node);
   dfree(m->grec); dfree(m->gcount); dfree(m->upart); dfree(m->updred);
   dfree(m->ppart); dfree(m->prec); dfree(m->gbar); dfree(m->ptime);
@@ -2506,6 +2535,29 @@ int afd_time_stiffness(afd_mesh* m, int arith, int n_rhs, const void* u, void* y
   cudaEventDestroy(e1);
   *ms_out = (double)ms / launches;
   return finish(m);
+}
+
+int afd_coarse_inverse(afd_mesh* m, double* out_host) {
+  if (!m || !out_host) return fail(AFD_ERR_INVALID_ARG, "null argument");
+  DeviceGuard dg(m->device);
+  TRY(enter(m));
+  m->coarse_valid = false;
+  TRY(assemble_coarse(m));
+  const size_t nn = (size_t)m->nc * m->nc;
+  if (m->opt.precision == AFD_FP64 || m->opt.coarse_fp64) {
+    if (!m->Einv64) TRY(dalloc(&m->Einv64, nn));
+    TRY(scale_and_invert<double>(m, m->Einv64, 1e-12));
+    CK(cudaMemcpyAsync(out_host, m->Einv64, nn * sizeof(double), cudaMemcpyDeviceToHost, m->s));
+    TRY(finish(m));
+  } else {
+    if (!m->Einv32) TRY(dalloc(&m->Einv32, nn));
+    TRY(scale_and_invert<float>(m, m->Einv32, 1e-6));
+    std::vector<float> h(nn);
+    CK(cudaMemcpyAsync(h.data(), m->Einv32, nn * sizeof(float), cudaMemcpyDeviceToHost, m->s));
+    TRY(finish(m));
+    for (size_t q = 0; q < nn; ++q) out_host[q] = h[q];
+  }
+  return AFD_OK;
 }
 
 int afd_coarse_matrix(afd_mesh* m, double* out_host) {

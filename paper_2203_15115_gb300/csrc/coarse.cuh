@@ -139,12 +139,13 @@ __global__ void k_convert_dense(size_t n, const double* __restrict__ a, T* __res
 // diagonal, so that the inverse does not lose the small rigid modes of groups
 // whose elements are mostly void.  A diagonal <= 0 gives NaN, which the pivot
 // test reports as singular.
+// (n <= 8192, so n * n and the indices fit in 32 bits.)
 template <typename T>
 __global__ void k_scale_dense(int n, const double* __restrict__ a, T* __restrict__ b) {
-  const size_t nn = (size_t)n * n;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = q / n, j = q % n;
-    const double di = a[i * n + i], dj = a[j * n + j];
+  const unsigned nn = (unsigned)n * (unsigned)n;
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < nn; q += gridDim.x * blockDim.x) {
+    const unsigned i = q / (unsigned)n, j = q - i * (unsigned)n;
+    const double di = a[(size_t)i * n + i], dj = a[(size_t)j * n + j];
     b[q] = (di > 0.0 && dj > 0.0) ? (T)(a[q] / sqrt(di * dj)) : (T)NAN;
   }
 }
@@ -153,10 +154,10 @@ __global__ void k_scale_dense(int n, const double* __restrict__ a, T* __restrict
 // inverse of a.
 template <typename T>
 __global__ void k_unscale_dense(int n, const double* __restrict__ a, T* __restrict__ b) {
-  const size_t nn = (size_t)n * n;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = q / n, j = q % n;
-    b[q] = (T)((double)b[q] / sqrt(a[i * n + i] * a[j * n + j]));
+  const unsigned nn = (unsigned)n * (unsigned)n;
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < nn; q += gridDim.x * blockDim.x) {
+    const unsigned i = q / (unsigned)n, j = q - i * (unsigned)n;
+    b[q] = (T)((double)b[q] / sqrt(a[(size_t)i * n + i] * a[(size_t)j * n + j]));
   }
 }
 
@@ -165,23 +166,33 @@ __global__ void k_unscale_dense(int n, const double* __restrict__ a, T* __restri
 // in every lane's own registers and the pivot row arrives by shuffles, so a
 // sweep costs no barrier.  P = A_KK^{-1} (nb x nb).  Rows and columns beyond
 // nb are an identity (pivot 1, no coupling).  A pivot <= rel * (*dmax) (or
-// NaN) sets *status (the sweep continues with pivot 1).
+// NaN) sets *status (the sweep continues with pivot 1).  The block is read
+// row by row (coalesced) through shared memory, and the pivot test runs in
+// the working type, off the FP64 unit.
+template <typename T> struct FiniteMax;
+template <> struct FiniteMax<float> { static constexpr float v = 3.40282347e38f; };
+template <> struct FiniteMax<double> { static constexpr double v = 1.7976931348623157e308; };
+
 template <typename T>
 __global__ void __launch_bounds__(32) k_gj_pivot(const T* A, int n, int k0, T* P, const double* dmax, double rel,
                                                  int* status) {
+  __shared__ T blk[GJ_NB][GJ_NB + 1];
   const int nb = min(GJ_NB, n - k0);
   const int i = threadIdx.x;
+#pragma unroll 8
+  for (int r = 0; r < GJ_NB; ++r)
+    blk[r][i] = (r < nb && i < nb) ? A[(size_t)(k0 + r) * n + k0 + i] : (r == i ? T(1) : T(0));
+  __syncwarp();
   T s[GJ_NB];
 #pragma unroll
-  for (int j = 0; j < GJ_NB; ++j)
-    s[j] = (i < nb && j < nb) ? A[(size_t)(k0 + i) * n + k0 + j] : (i == j ? T(1) : T(0));
-  const double thr = rel * (*dmax);
+  for (int j = 0; j < GJ_NB; ++j) s[j] = blk[i][j];
+  const T thr = (T)(rel * (*dmax));
   bool bad = false;
 #pragma unroll
   for (int p = 0; p < GJ_NB; ++p) {
     const T colp = s[p];   // this row's entry in the pivot column
     T d = __shfl_sync(0xffffffffu, colp, p);
-    if (p < nb && (!((double)d > thr) || !isfinite((double)d))) {
+    if (p < nb && !(d > thr && d <= FiniteMax<T>::v)) {   // too small, NaN or infinite
       bad = true;
       d = T(1);
     }
