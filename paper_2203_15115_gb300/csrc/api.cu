@@ -149,6 +149,9 @@ struct afd_mesh {
   std::vector<int> gbox_h;     // host copy
   long long* aw_off = nullptr; // [N_g + 1] offset of group G's block in AW (last: total)
   int* aw_node = nullptr;      // [aw_total / 18] node index of every shell slot
+  uint4* cut = nullptr;        // records of every group's cut elements (k_build_cut_recs); null: decoded per use
+  long long* cut_off = nullptr;  // [N_g + 1] offset of group G's records
+  size_t cut_cap = 0;
   double* grec = nullptr;      // [rhs][N_g][12] per-group records of the coarse right-hand side
   double* upart = nullptr;     // [rhs][RED_BLOCKS][2] partials of the vector update
   double* updred = nullptr;    // [rhs][coarse-step blocks][2] the same, summed in one slice per coarse-step block
@@ -587,13 +590,54 @@ static int build_aw(afd_mesh* m, Work<T>& w) {
 // the FP64 path and the persistent kernel read K W stored on the node shells.
 static bool uses_stored_aw(const afd_mesh* m) { return m->opt.precision == AFD_FP64 || m->opt.persistent; }
 
+// The cut-element records of the FP32 graph path (k_build_cut_recs), rebuilt
+// with the supports; left null (the kernel decodes each element's position
+// instead) when a group is too wide for their 10-bit coordinates.
+static int build_cut_records(afd_mesh* m) {
+  if (uses_stored_aw(m)) return AFD_OK;
+  const Grid& g = m->gr;
+  const Groups& gp = m->gp;
+  std::vector<long long> off(gp.ng + 1);
+  size_t tot = 0;
+  bool fits = true;
+  for (int G = 0; G < gp.ng; ++G) {
+    int b[12];
+    elem_shell_bounds(g, gp, G, m->gbox_h.data() + 6 * G, b);
+    Shell sh;
+    sh.init(b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], b[8], b[9], b[10], b[11], false);
+    for (int d = 0; d < 3; ++d) fits = fits && b[2 * d + 1] - b[2 * d] + 2 <= 1023;
+    off[G] = (long long)tot;
+    tot += (size_t)sh.count;
+  }
+  off[gp.ng] = (long long)tot;
+  invalidate_graphs(m);
+  if (!fits) {
+    dfree(m->cut);
+    m->cut = nullptr;
+    m->cut_cap = 0;
+    return AFD_OK;
+  }
+  if (!m->cut_off) TRY(dalloc(&m->cut_off, (size_t)gp.ng + 1));
+  if (tot > m->cut_cap || !m->cut) {
+    dfree(m->cut);
+    m->cut = nullptr;
+    m->cut_cap = 0;
+    TRY(dalloc(&m->cut, std::max<size_t>(tot, 1)));
+    m->cut_cap = tot;
+  }
+  CK(cudaMemcpyAsync(m->cut_off, off.data(), (gp.ng + 1) * sizeof(long long), cudaMemcpyHostToDevice, m->s));
+  k_build_cut_recs<<<gp.ng, 256, 0, m->s>>>(g, gp, m->fixed, m->gbox, m->cut_off, m->cut); m->launches++;
+  CK(cudaGetLastError());
+  return AFD_OK;
+}
+
 template <typename T>
 static int launch_coarse_rhs(afd_mesh* m, Work<T>& w, int nsplit, int nrhs, bool pdl) {
   const dim3 ug(m->gp.ng, nsplit, nrhs);
   if (sizeof(T) == 4 && !uses_stored_aw(m))
     CK(launch_ex(pdl, k_coarse_rhs_cut<T>, ug, dim3(256), 0, m->s, m->gr, m->gp, nsplit, (const T*)w.r,
                  (const T*)w.z, (const T*)w.E, (const uint8_t*)m->fixed, (const int*)m->gbox, w.K, m->cpart, m->grec,
-                 m->gcount, (const CGState*)m->st));
+                 m->gcount, (const CGState*)m->st, (const uint4*)m->cut, (const long long*)m->cut_off));
   else
     CK(launch_ex(pdl, k_coarse_rhs<T>, ug, dim3(256), 0, m->s, m->gr, m->gp, nsplit, (const T*)w.r, (const T*)w.z,
                  (const long long*)m->aw_off, (const int*)m->aw_node, (const T*)w.AW, m->cpart, m->grec, m->gcount,
@@ -1213,6 +1257,7 @@ void afd_destroy(afd_mesh* m) {
   for (auto& g : m->gj_graph)
     if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gbox); dfree(m->aw_off); dfree(m->aw_node);
+  dfree(m->cut); dfree(m->cut_off);
   dfree(m->grec); dfree(m->gcount); dfree(m->upart); dfree(m->updred);
   dfree(m->ppart); dfree(m->prec); dfree(m->gbar); dfree(m->ptime);
   dfree(m->lam64); dfree(m->gadj); dfree(m->dsig); dfree(m->pn_d); dfree(m->lsbuf);
@@ -1343,6 +1388,7 @@ int afd_set_loads_bcs(afd_mesh* m, int n_rhs, const double* f, int f_on_device, 
     m->aw_total = tot;
     CK(cudaMemcpyAsync(m->aw_off, off.data(), (m->gp.ng + 1) * sizeof(long long), cudaMemcpyHostToDevice, m->s));
   }
+  TRY(build_cut_records(m));
   k_zero_fixed<<<dim3(grid_blocks(g.nnodes, 256, 4096), n_rhs), 256, 0, m->s>>>(g.nnodes, n_rhs, g.vs, m->fixed, m->f64); m->launches++;
   CK(cudaMemsetAsync(m->u64, 0, n * sizeof(double), m->s));
   CK(cudaGetLastError());
@@ -2534,6 +2580,7 @@ size_t afd_mesh_bytes(int nx, int ny, int nz, int n_rhs, const afd_options* opt)
   if (!f64 && o.coarse_fp64) b += nc * nc * 8;                      // FP64 inverse before its FP32 rounding
   const size_t box = (size_t)(g + 3) * (g + 3) * (g + 3);
   if (f64 || o.persistent) b += ng * box * (18 * tsz + 4);          // K W on group shells (upper bound)
+  else b += ng * (box - (size_t)std::max(g - 3, 0) * std::max(g - 3, 0) * std::max(g - 3, 0)) * 16;  // cut records
   b += (size_t)n_rhs * (nc * 4 * 8 + ng * 64 * 12 * 8) + 64 * 1024 * 1024 / 8;  // coarse vectors, partials
   return b + b / 10;
 }

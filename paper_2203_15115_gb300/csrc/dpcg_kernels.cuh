@@ -207,12 +207,14 @@ struct Shell {
   int x0, y0, z0, IX, IY, IZ;   // inner box origin and extent (all > 0, or none)
   int A, Rg, nlo, nmid;          // layer area, ring area, full layers below, ring layers
   int count;
-  __device__ void init(int X0_, int X1, int Y0_, int Y1, int Z0_, int Z1, int x0_, int x1, int y0_, int y1, int z0_,
-                       int z1, bool full) {
+  __host__ __device__ void init(int X0_, int X1, int Y0_, int Y1, int Z0_, int Z1, int x0_, int x1, int y0_, int y1,
+                                int z0_, int z1, bool full) {
     X0 = X0_; Y0 = Y0_; Z0 = Z0_;
     LX = X1 - X0 + 1; LY = Y1 - Y0 + 1; LZ = Z1 - Z0 + 1;
     x0 = x0_; y0 = y0_; z0 = z0_;
-    IX = max(x1 - x0 + 1, 0); IY = max(y1 - y0 + 1, 0); IZ = max(z1 - z0 + 1, 0);
+    IX = x1 - x0 + 1 > 0 ? x1 - x0 + 1 : 0;
+    IY = y1 - y0 + 1 > 0 ? y1 - y0 + 1 : 0;
+    IZ = z1 - z0 + 1 > 0 ? z1 - z0 + 1 : 0;
     if (full || IX == 0 || IY == 0 || IZ == 0) { IX = IY = IZ = 0; x0 = X0; y0 = Y0; z0 = Z0; }
     A = LX * LY;
     Rg = A - IX * IY;
@@ -705,7 +707,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)   // FP32: 4 bloc
 k_coarse_rhs_cut(Grid gr, Groups gp, int nsplit, const T* __restrict__ r, const T* __restrict__ z,
                  const T* __restrict__ Emod, const uint8_t* __restrict__ fixed, const int* __restrict__ gbox,
                  ElemConsts<T> K, double* __restrict__ part, double* __restrict__ rec,
-                 unsigned int* __restrict__ gcount, const CGState* st) {
+                 unsigned int* __restrict__ gcount, const CGState* st, const uint4* __restrict__ cut,
+                 const long long* __restrict__ cut_off) {
   __shared__ double red[32 * 12];
   __shared__ bool s_last;
   pdl_acquire();
@@ -727,7 +730,49 @@ k_coarse_rhs_cut(Grid gr, Groups gp, int nsplit, const T* __restrict__ r, const 
     const int kb = klo + sp * kper, ke = min(kb + kper, khi + 1);
     group_wtr_planes(gr, r, off, ilo, ihi, jlo, jhi, klo, khi, kb, ke, hh, s, [](const T* p) { return __ldg(p); });
   }
-  {
+  if (cut) {
+    // the group's cut elements from their records (k_build_cut_recs)
+    const long long base = cut_off[G];
+    const int cnt = (int)(cut_off[G + 1] - base);
+    const int per = (cnt + nsplit - 1) / nsplit;
+    const int qb = sp * per, qe = min(qb + per, cnt);
+    const int plane = gr.nnx * gr.nny;
+    const T h2 = hh + hh;
+    const T bx0 = hh * (T)(ilo - ihi - 2), by0 = hh * (T)(jlo - jhi - 2), bz0 = hh * (T)(klo - khi - 2);
+    for (int t = qb + threadIdx.x; t < qe; t += blockDim.x) {
+      const uint4 q = __ldg(cut + base + t);
+      const int n0 = (int)q.x;
+      const unsigned ingrp = q.w >> 24, fbits = q.w & 0xFFFFFFu;
+      T v[3][8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int n = n0 + (a & 1) + ((a >> 1) & 1) * gr.nnx + ((a >> 2) & 1) * plane;
+        const T* zp = z + off + 3 * (size_t)n;
+        v[0][a] = __ldg(zp);
+        v[1][a] = __ldg(zp + 1);
+        v[2][a] = __ldg(zp + 2);
+      }
+      hex8_apply(v, __ldg(Emod + q.y), K);
+      // moment arms about the group centre: hh (2 i - ilo - ihi) with i = ilo - 1 + rel_i + (a & 1)
+      const T bx = bx0 + h2 * (T)(int)(q.z & 1023u), by = by0 + h2 * (T)(int)((q.z >> 10) & 1023u),
+              bz = bz0 + h2 * (T)(int)((q.z >> 20) & 1023u);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        if (!((ingrp >> a) & 1u)) continue;
+        const unsigned fb = (fbits >> (3 * a)) & 7u;
+        const T y0 = (fb & 1) ? T(0) : v[0][a];
+        const T y1 = (fb & 2) ? T(0) : v[1][a];
+        const T y2 = (fb & 4) ? T(0) : v[2][a];
+        const T rx = (a & 1) ? bx + h2 : bx, ry = ((a >> 1) & 1) ? by + h2 : by, rz = ((a >> 2) & 1) ? bz + h2 : bz;
+        s[6] += y0;
+        s[7] += y1;
+        s[8] += y2;
+        s[9] += ry * y2 - rz * y1;
+        s[10] += rz * y0 - rx * y2;
+        s[11] += rx * y1 - ry * y0;
+      }
+    }
+  } else {
     int b[12];
     elem_shell_bounds(gr, gp, G, gbox ? gbox + 6 * G : nullptr, b);
     Shell sh;
@@ -790,6 +835,45 @@ k_coarse_rhs_cut(Grid gr, Groups gp, int nsplit, const T* __restrict__ r, const 
     rec[((size_t)rhs * gp.ng + G) * 12 + threadIdx.x] = v;
   }
   if (threadIdx.x == 0) gcount[(size_t)rhs * gp.ng + G] = 0u;
+}
+
+// Records of the cut elements of every group (the shells of
+// k_coarse_rhs_cut, in the same order), one block per group, written once per
+// set of supports: x = node index of the element's corner (i, j, k),
+// y = element index, z = the element's position relative to the group,
+// (i - ilo + 1) | (j - jlo + 1) << 10 | (k - klo + 1) << 20, w = the fixed-DOF
+// bits of its 8 nodes (3 per node, node a at bit 3a) | the mask of its nodes
+// in the group << 24.  Needs groups at most 1022 elements wide.
+__global__ void k_build_cut_recs(Grid gr, Groups gp, const uint8_t* __restrict__ fixed, const int* __restrict__ gbox,
+                                 const long long* __restrict__ cut_off, uint4* __restrict__ cut) {
+  const int G = blockIdx.x;
+  const int Gx = G % gp.ngx, Gy = (G / gp.ngx) % gp.ngy, Gz = G / (gp.ngx * gp.ngy);
+  int ilo, ihi, jlo, jhi, klo, khi;
+  group_range(Gx, gp.g, gp.ngx, gr.nx, ilo, ihi);
+  group_range(Gy, gp.g, gp.ngy, gr.ny, jlo, jhi);
+  group_range(Gz, gp.g, gp.ngz, gr.nz, klo, khi);
+  int b[12];
+  elem_shell_bounds(gr, gp, G, gbox ? gbox + 6 * G : nullptr, b);
+  Shell sh;
+  sh.init(b[0], b[1], b[2], b[3], b[4], b[5], b[6], b[7], b[8], b[9], b[10], b[11], false);
+  const long long base = cut_off[G];
+  for (int t = threadIdx.x; t < sh.count; t += blockDim.x) {
+    int ei, ej, ek;
+    sh.at(t, ei, ej, ek);
+    unsigned fb = 0, in = 0;
+    for (int a = 0; a < 8; ++a) {
+      const int i = ei + (a & 1), j = ej + ((a >> 1) & 1), k = ek + ((a >> 2) & 1);
+      const int n = i + gr.nnx * (j + gr.nny * k);
+      fb |= (unsigned)(fixed ? fixed[n] & 7 : 0) << (3 * a);
+      if (i >= ilo && i <= ihi && j >= jlo && j <= jhi && k >= klo && k <= khi) in |= 1u << a;
+    }
+    uint4 q;
+    q.x = (unsigned)(ei + gr.nnx * (ej + gr.nny * ek));
+    q.y = (unsigned)(ei + gr.nx * (ej + gr.ny * ek));
+    q.z = (unsigned)(ei - ilo + 1) | (unsigned)(ej - jlo + 1) << 10 | (unsigned)(ek - klo + 1) << 20;
+    q.w = fb | in << 24;
+    cut[base + t] = q;
+  }
 }
 
 // gbox[6G..6G+5] = bounding box (imin, imax, jmin, jmax, kmin, kmax) of the
