@@ -141,8 +141,7 @@ struct afd_mesh {
   double *gjP = nullptr, *gjB = nullptr, *gjR = nullptr;  // Gauss-Jordan scratch
   cudaGraphExec_t gj_graph[2] = {nullptr, nullptr};       // the inversion's panel sweeps (FP32, FP64), replayed
   double* cpart = nullptr;     // coarse right-hand side partials [rhs][G][split][12]
-  unsigned int* counters = nullptr;  // last-block counters: [rhs] stencil, [MAX_RHS] coarse; [MAX_RHS + 1,
-                                     // MAX_RHS + 2] chunks run and chunk budget of the solver graph's loop
+  unsigned int* counters = nullptr;  // last-block counters: [rhs] stencil, [MAX_RHS] coarse
   double* dmax = nullptr;
   int* dstatus = nullptr;
   int* gbox = nullptr;         // [N_g][6] bounding box of the group's fixed nodes (max < min: none)
@@ -1050,66 +1049,42 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
     CK(cudaGetLastError());
     return AFD_OK;
   };
-  // The whole inner solve is one graph launch: a while node whose body is one
-  // chunk and k_chunk_cond, which ends the loop when every RHS is done or the
-  // chunk budget is spent.  The graph bakes in x and b; it is rebuilt when they
-  // or the RHS count change.
+  // the graph bakes in x and b; rebuild it when they or the RHS count change
   static_assert(sizeof(void*) == 8, "64-bit");
-  unsigned int* chunk_ctr = m->counters + MAX_RHS + 1;
   cudaGraphExec_t& gexec = w.graph;
   const bool reuse = gexec && w.graph_nrhs == nrhs;
   if (!reuse) {
     if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
     cudaGraph_t graph;
-    CK(cudaGraphCreate(&graph, 0));
-    cudaGraphConditionalHandle handle;
-    cudaGraphNode_t loop;
-    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess) {
-      cp.conditional.handle = handle;
-      cp.conditional.type = cudaGraphCondTypeWhile;
-      cp.conditional.size = 1;
-      e = cudaGraphAddNode(&loop, graph, nullptr, nullptr, 0, &cp);
-    }
-    if (e == cudaSuccess)
-      e = cudaStreamBeginCaptureToGraph(m->s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                        cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) {
-      cudaGraphDestroy(graph);
-      return fail(AFD_ERR_CUDA, "solver graph: %s", cudaGetErrorString(e));
-    }
     const int64_t before = m->launches;
+    CK(cudaStreamBeginCapture(m->s, cudaStreamCaptureModeThreadLocal));
     m->pdl_now = m->opt.pdl != 0;
     int rc = enqueue_chunk();
     m->pdl_now = false;
-    if (rc == AFD_OK) k_chunk_cond<<<1, 32, 0, m->s>>>(handle, m->done, nrhs, chunk_ctr);
-    w.graph_kernels = m->launches - before + 1;  // per chunk, captured, not run
+    w.graph_kernels = m->launches - before;  // captured, not run
     m->launches = before;
-    cudaGraph_t body;
-    e = cudaStreamEndCapture(m->s, &body);
-    if (rc != AFD_OK || e != cudaSuccess) {
-      cudaGraphDestroy(graph);
-      if (rc != AFD_OK) return rc;
-      return fail(AFD_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-    }
+    cudaError_t e = cudaStreamEndCapture(m->s, &graph);
+    if (rc != AFD_OK) return rc;
+    if (e != cudaSuccess) return fail(AFD_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&gexec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      gexec = nullptr;
-      return fail(AFD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    }
+    if (e != cudaSuccess) return fail(AFD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
     w.graph_nrhs = nrhs;
   }
-  const unsigned int ctr_h[2] = {0u, (unsigned int)(max_iters / std::max(1, m->opt.check_every) + 2)};
-  CK(cudaMemcpyAsync(chunk_ctr, ctr_h, sizeof(ctr_h), cudaMemcpyHostToDevice, m->s));
-  CK(cudaGraphLaunch(gexec, m->s));
-  unsigned int chunks = 0;
-  CK(cudaMemcpyAsync(&chunks, chunk_ctr, sizeof(chunks), cudaMemcpyDeviceToHost, m->s));
+  const int max_chunks = max_iters / std::max(1, m->opt.check_every) + 2;
+  std::vector<int> flags(nrhs);
+  for (int c = 0; c < max_chunks; ++c) {
+    CK(cudaMemcpyAsync(flags.data(), m->done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, m->s));
+    CK(cudaStreamSynchronize(m->s));
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) all &= flags[r] != 0;
+    if (all) break;
+    CK(cudaGraphLaunch(gexec, m->s));
+    m->launches += w.graph_kernels;
+  }
   out.resize(nrhs);
   CK(cudaMemcpyAsync(out.data(), m->st, nrhs * sizeof(CGState), cudaMemcpyDeviceToHost, m->s));
   CK(cudaStreamSynchronize(m->s));
-  m->launches += (int64_t)chunks * w.graph_kernels;
   return AFD_OK;
 }
 
@@ -1215,14 +1190,14 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
       (rc = dalloc(&m->w64.invdiag, (size_t)g.nnodes)) != AFD_OK || (rc = dalloc(&m->fixed, (size_t)(g.nnodes + 3) / 4 * 4)) != AFD_OK ||
       (rc = dalloc(&m->w32.invd, (size_t)g.vs)) != AFD_OK || (rc = dalloc(&m->w64.invd, (size_t)g.vs)) != AFD_OK ||
       (rc = dalloc(&m->fsmall, (size_t)FSMALL_SIZE)) != AFD_OK ||
-      (rc = dalloc(&m->counters, (size_t)MAX_RHS + 3)) != AFD_OK ||
+      (rc = dalloc(&m->counters, (size_t)MAX_RHS + 1)) != AFD_OK ||
       (rc = dalloc(&m->gbox, (size_t)gp.ng * 6)) != AFD_OK ||
       (rc = dalloc(&m->aw_off, (size_t)gp.ng + 1)) != AFD_OK) {
     afd_destroy(m);
     return rc;
   }
   cudaMemsetAsync(m->fixed, 0, (size_t)(g.nnodes + 3) / 4 * 4, m->s);   // padded: read as 4-byte words
-  cudaMemsetAsync(m->counters, 0, (MAX_RHS + 3) * sizeof(unsigned int), m->s);
+  cudaMemsetAsync(m->counters, 0, (MAX_RHS + 1) * sizeof(unsigned int), m->s);
   if (cudaStreamSynchronize(m->s) != cudaSuccess) {
     afd_destroy(m);
     return fail(AFD_ERR_CUDA, "init failed");

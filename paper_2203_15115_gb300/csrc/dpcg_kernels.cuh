@@ -1164,20 +1164,6 @@ k_coarse_step(int nc, int nrhs, const TE* __restrict__ Einv, double* __restrict_
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// End of one captured chunk of inner iterations inside the solver graph's
-// while loop: counts the chunk and keeps the loop going while some RHS is not
-// done and fewer than ctr[1] chunks have run (the loop is bounded by
-// construction).  One thread.
-__global__ void k_chunk_cond(cudaGraphConditionalHandle h, const int* __restrict__ done, int nrhs,
-                             unsigned int* ctr) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  bool any = false;
-  for (int r = 0; r < nrhs; ++r) any |= done[r] == 0;
-  const unsigned int c = ctr[0] + 1u;
-  ctr[0] = c;
-  cudaGraphSetConditional(h, (any && c < ctr[1]) ? 1u : 0u);
-}
-
 // ---------------------------------------------------------------------------
 // Mixed-precision refinement helpers
 // ---------------------------------------------------------------------------
