@@ -103,10 +103,20 @@ def alu_roofline(n_elements: int, ms: float) -> dict:
 # The FP32 stencil variants the autotuner chooses from (afd_stencil_async).
 STENCIL_NAMES = {0: "stencil2_kernel<TY,{mode},register prefetch>", 1: "stencil2_kernel<TY,{mode},cp.async ring>",
                  2: "st3_kernel<TY,{mode}> (packed bands)"}
-STENCIL_DRAM_BYTES = {(128, 64, 64, 8, 6, 0): 9198592, (384, 192, 192, 8, 12, 1): 378244608,
-                      (384, 192, 192, 8, 12, 2): 363241984}
-# The same for the stencil of the inner DPCG iteration (ST_APPLY_DOT), captured inside a mixed solve.
-STENCIL_DOT_DRAM_BYTES = {(128, 64, 64, 8, 6, 0): 15795456}
+STENCIL_DRAM_BYTES = {
+    (128, 64, 64, 8, 4, 0): 9197824, (128, 64, 64, 8, 4, 1): 9204992, (128, 64, 64, 8, 4, 2): 8667392,
+    (128, 64, 64, 8, 6, 0): 9197568, (128, 64, 64, 8, 6, 1): 9205248, (128, 64, 64, 8, 6, 2): 8667392,
+    (128, 64, 64, 8, 8, 0): 9197568, (128, 64, 64, 8, 8, 1): 9205248, (128, 64, 64, 8, 8, 2): 8667648,
+    (128, 64, 64, 8, 12, 0): 9199104, (128, 64, 64, 8, 12, 1): 9205504, (128, 64, 64, 8, 12, 2): 8667648,
+    (384, 192, 192, 8, 12, 1): 378244608, (384, 192, 192, 8, 12, 2): 363241984}
+# The same for the stencil of the inner DPCG iteration (ST_APPLY_DOT), captured inside a mixed solve of the
+# 128x64x64 workload in every shape of 8 warps the autotuner may pick (the reads of p_old, z, E and the mask;
+# the writes of p and q stay in L2 until after the launch).
+STENCIL_DOT_DRAM_BYTES = {
+    (128, 64, 64, 8, 4, 0): 15789568, (128, 64, 64, 8, 4, 1): 15791616, (128, 64, 64, 8, 4, 2): 15809280,
+    (128, 64, 64, 8, 6, 0): 15789312, (128, 64, 64, 8, 6, 1): 15792640, (128, 64, 64, 8, 6, 2): 15806464,
+    (128, 64, 64, 8, 8, 0): 15789824, (128, 64, 64, 8, 8, 1): 15793152, (128, 64, 64, 8, 8, 2): 15812096,
+    (128, 64, 64, 8, 12, 0): 15789056, (128, 64, 64, 8, 12, 1): 15791616, (128, 64, 64, 8, 12, 2): 15804672}
 
 
 def rank_info():
@@ -847,6 +857,29 @@ def profile_stencil(n: int, launches: int, warps: int = 0, planes: int = 0, stag
     mesh.close()
 
 
+def profile_residual(launches: int):
+    """K u on the 128x64x64 voided cantilever from FP64 data, `launches` times
+    in double-float arithmetic (the refinement residual's kernel) and then in
+    FP64: a case for ncu captures of the two (Sec. 3.5's FP64 residual)."""
+    import torch
+
+    import paper_2203_15115_gb300 as afd
+    from synthetic import cantilever_128x64x64_voids
+
+    w = cantilever_128x64x64_voids()
+    mesh = afd.Mesh(w.nx, w.ny, w.nz, group=w.group)
+    mesh.set_element_moduli(w.E)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    u = torch.randn((1, mesh.ndof), dtype=torch.float64, device="cuda", generator=g)
+    y = torch.empty_like(u)
+    out = {"workload": w.name}
+    for name, arith in (("f64_df", afd.AFD_F64_DF), ("f64", afd.AFD_F64)):
+        out[name + "_us"] = round(afd.afd_time_stiffness(mesh.h, arith, 1, u, y, launches) * 1e3, 1)
+    print(json.dumps(out))
+    mesh.close()
+
+
 def profile_solve(warps: int, planes: int, solves: int, staging: int = 0):
     """`solves` mixed solves of the 128x64x64 voided cantilever with the FP32
     stencil in a pinned CTA shape (no autotuning): the solver's kernels in
@@ -908,6 +941,8 @@ def main():
     ap.add_argument("--profile-stencil", type=int, default=0, metavar="NX",
                     help="only time the FP32 stencil on an NX x NX/2 x NX/2 mesh (for ncu)")
     ap.add_argument("--launch-summary", metavar="CSV", help="summarise an ncu launch list of one timed step")
+    ap.add_argument("--profile-residual", action="store_true",
+                    help="time (and let ncu capture) the double-float and FP64 K u of the refinement residual")
     ap.add_argument("--profile-solve", action="store_true",
                     help="only run --steps mixed solves of the 128x64x64 workload in a pinned stencil shape (for ncu)")
     ap.add_argument("--profile-eigen", choices=("modal", "buckling"),
@@ -922,6 +957,8 @@ def main():
         launch_summary(args.launch_summary)
     elif args.profile_stencil:
         profile_stencil(args.profile_stencil, max(1, args.steps), args.stencil_warps, args.stencil_planes, args.stencil_async)
+    elif args.profile_residual:
+        profile_residual(max(1, args.steps))
     elif args.profile_solve:
         profile_solve(args.stencil_warps, args.stencil_planes, max(1, args.steps), args.stencil_async)
     elif args.profile_eigen:
