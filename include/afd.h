@@ -229,7 +229,9 @@ int afd_buckling_sensitivity(afd_mesh* m, float* out, int out_on_device);
  * weights[r] (float32, fixed order), keep the k = round(v * nelem) elements
  * with the largest value (ties keep the lower element index), set their
  * modulus to 1 and the others to opt.e_void.  tau_out (nullable) receives the
- * cut value, kept_out (nullable, host, nelem bytes) the kept mask. */
+ * cut value, kept_out (nullable, host, nelem bytes) the kept mask.  When the
+ * call on this mesh just before was afd_sensitivity of the same kind, its
+ * fields are reused (nothing in between can have changed u or the moduli). */
 int afd_levelset_update(afd_mesh* m, int kind, const double* weights, double volume_fraction,
                         double* tau_out, uint8_t* kept_out);
 

@@ -101,6 +101,7 @@ struct afd_mesh {
   afd_options opt;
   int device = 0;
   cudaStream_t user = nullptr, s = nullptr;
+  int fcache_kind = -1;        // the field kind fbuf holds for the current u and E (-1: none); see enter()
   cudaEvent_t ev = nullptr;
   int kz = 8;                  // node planes per CTA of the FP64 stencil
   int kz32 = 8, ty32 = 16;     // planes per CTA and warps per CTA of the FP32 stencil
@@ -207,7 +208,12 @@ struct DeviceGuard {
 };
 
 // Order the mesh stream after the user's stream (device inputs made there).
+// Start of every call on a mesh.  Any call may change u, the moduli or the
+// load cases, so the cached field in fbuf is dropped here; afd_sensitivity
+// refills it, and a level-set update of the same kind that follows it
+// directly reuses it.
 static int enter(afd_mesh* m) {
+  m->fcache_kind = -1;
   CK(cudaEventRecord(m->ev, m->user));
   CK(cudaStreamWaitEvent(m->s, m->ev, 0));
   return AFD_OK;
@@ -1556,11 +1562,12 @@ int afd_sensitivity(afd_mesh* m, int kind, float* out, int out_on_device) {
   if (!m->has_solution) return fail(AFD_ERR_STATE, "no solution");
   DeviceGuard dg(m->device);
   TRY(enter(m));
-  float* dst = out_on_device ? out : m->fbuf;
-  TRY(fields_to(m, kind, dst));
-  if (!out_on_device)
-    CK(cudaMemcpyAsync(out, m->fbuf, (size_t)m->nrhs * m->gr.nelem * sizeof(float), cudaMemcpyDeviceToHost, m->s));
-  return finish(m);
+  TRY(fields_to(m, kind, m->fbuf));
+  CK(cudaMemcpyAsync(out, m->fbuf, (size_t)m->nrhs * m->gr.nelem * sizeof(float),
+                     out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->s));
+  TRY(finish(m));
+  m->fcache_kind = kind;
+  return AFD_OK;
 }
 
 static int maxabs_per_rhs(afd_mesh* m, const float* x, int nrhs, float* dmax_out) {
@@ -2289,8 +2296,9 @@ static int levelset_update_impl(afd_mesh* m, int kind, const double* weights, do
   if (!std::isfinite(volume_fraction)) return fail(AFD_ERR_INVALID_ARG, "volume fraction must be finite");
   if (!m->has_solution) return fail(AFD_ERR_STATE, "no solution");
   DeviceGuard dg(m->device);
+  const int cached = m->fcache_kind;   // the field of the sensitivity call just before, if any
   TRY(enter(m));
-  TRY(fields_to(m, kind, m->fbuf));
+  if (cached != kind) TRY(fields_to(m, kind, m->fbuf));
   return levelset_cut(m, m->fbuf, m->nrhs, weights, volume_fraction, axis, parting, tau_out, kept_out);
 }
 

@@ -1,8 +1,9 @@
 // Per-element sensitivity fields from the displacement (Sec. 3.1): strain
 // energy s_e = u_e^T (E_e K0) u_e (the element-sensitivity form), Eq. 3.2 at
 // the element centroid as printed, and the centroid von Mises stress (the
-// measure inside Eq. 3.3's p-norm).  The nodal differences are formed in FP64
-// (the Walsh-Hadamard transform of the FP64 displacement), the rest in the
+// measure inside Eq. 3.3's p-norm).  The nodal differences (the
+// Walsh-Hadamard transform of the FP64 displacement) are formed in FP64 for
+// FP64 fields and in double-float arithmetic for float ones, the rest in the
 // compute type TC.
 #pragma once
 
@@ -19,18 +20,30 @@ struct FieldConsts {
 template <typename TC>
 __device__ __forceinline__ void element_fields(const double (&u)[3][8], TC E, const ElemConsts<TC>& K,
                                                const FieldConsts& F, TC& s_out, TC& tj_out, TC& vm_out) {
-  double hd[3][8];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-#pragma unroll
-    for (int a = 0; a < 8; ++a) hd[c][a] = u[c][a];
-    wht8_fwd(hd[c]);
-  }
   TC h[3][8], g[3][8];
+  if constexpr (sizeof(TC) == 4) {
+    // float fields: the transform in double-float arithmetic on the FP32 pipes
+    // (the nodal differences to about 2^-44 of u), then rounded to float
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
+    for (int c = 0; c < 3; ++c) {
+      dfloat hd[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) h[c][a] = g[c][a] = (TC)hd[c][a];
+      for (int a = 0; a < 8; ++a) hd[a] = df_from_double(u[c][a]);
+      wht8_fwd(hd);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) h[c][a] = g[c][a] = (TC)(hd[a].hi + hd[a].lo);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double hd[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) hd[a] = u[c][a];
+      wht8_fwd(hd);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) h[c][a] = g[c][a] = (TC)hd[a];
+    }
+  }
   modal_forces(g, E, K);
   TC s = TC(0);
 #pragma unroll

@@ -257,6 +257,43 @@ def test_levelset_update_keeps_the_oracle_set_up_to_rounding_ties():
     m.close()
 
 
+def test_levelset_update_after_sensitivity_reuses_only_a_current_field():
+    """afd_levelset_update reuses the field of an afd_sensitivity call of the
+    same kind made just before it on the same mesh (Eq. 3.6's cut of Sec.
+    3.1's field): the kept set and the cut value equal those of an update
+    without the sensitivity call, bit for bit; after another call in between
+    (new moduli and a new solve), or for another kind, the field is formed
+    again from the current state."""
+    w = small_cantilever(24, 12, 8, seed=8, n_spheres=4, rmin=1.5, rmax=3.5, group=4, n_rhs=2)
+    weights = [1.0, 0.5]
+    E2 = np.where(np.arange(w.E.size) % 7 == 0, 1e-3, w.E)
+
+    def run(pre_kind, change):
+        m = afd.Mesh(w.nx, w.ny, w.nz, precision=afd.AFD_MIXED, group=w.group, stencil_warps=8, stencil_planes=4)
+        m.set_element_moduli(w.E)
+        m.set_loads_bcs(w.f, w.fixed)
+        m.solve(1e-9)
+        out = np.zeros((2, m.nelem), np.float32)
+        if pre_kind is not None:
+            m.sensitivity(pre_kind, out)
+        if change:
+            m.set_element_moduli(E2)
+            m.solve(1e-9)
+        kept = np.zeros(m.nelem, np.uint8)
+        tau = m.levelset_update(afd.AFD_SENS_STRAIN_ENERGY, weights, 0.8, kept)
+        m.close()
+        return kept, tau
+
+    base = run(None, False)
+    for pre in (afd.AFD_SENS_STRAIN_ENERGY, afd.AFD_SENS_VON_MISES):
+        kept, tau = run(pre, False)
+        assert np.array_equal(kept, base[0]) and tau == base[1], pre
+    changed = run(None, True)
+    kept, tau = run(afd.AFD_SENS_STRAIN_ENERGY, True)
+    assert np.array_equal(kept, changed[0]) and tau == changed[1]
+    assert not np.array_equal(changed[0], base[0])
+
+
 def test_error_paths():
     nx, ny, nz = 6, 3, 3
     m = afd.Mesh(nx, ny, nz, group=2)
