@@ -140,6 +140,7 @@ struct afd_mesh {
   double* Einv64 = nullptr;    // its inverse, FP64 path
   float* Einv32 = nullptr;     // its inverse, mixed path
   double *gjP = nullptr, *gjB = nullptr, *gjR = nullptr;  // Gauss-Jordan scratch
+  double* gjD = nullptr;       // [n_c] 1 / sqrt of the coarse matrix's diagonal
   cudaGraphExec_t gj_graph[2] = {nullptr, nullptr};       // the inversion's panel sweeps (FP32, FP64), replayed
   double* cpart = nullptr;     // coarse right-hand side partials [rhs][G][split][12]
   unsigned int* counters = nullptr;  // last-block counters: [rhs] stencil, [MAX_RHS] coarse
@@ -519,7 +520,7 @@ static int invert_coarse(afd_mesh* m, T* A, double rel) {
       k_gj_panel<T><<<(nc * nb + 255) / 256, 256, 0, m->s>>>(A, nc, k0, P, B, R);
       k_gj_update<T><<<ug, 256, 0, m->s>>>(A, nc, k0, P, B, R, k0 + GJ_NB >= nc ? 1 : 0);
     }
-    k_unscale_dense<T><<<grid_blocks((size_t)nc * nc, 256, 4096), 256, 0, m->s>>>(nc, m->Ec, A);
+    k_unscale_dense<T><<<grid_blocks((size_t)nc * nc, 256, 4096), 256, 0, m->s>>>(nc, m->gjD, A);
     const cudaError_t le = cudaGetLastError();
     const cudaError_t ce = cudaStreamEndCapture(m->s, &graph);
     if (le != cudaSuccess) return fail(AFD_ERR_CUDA, "coarse inverse capture: %s", cudaGetErrorString(le));
@@ -546,7 +547,8 @@ static int invert_coarse(afd_mesh* m, T* A, double rel) {
 template <typename T>
 static int scale_and_invert(afd_mesh* m, T* A, double rel) {
   const size_t nn = (size_t)m->nc * m->nc;
-  k_scale_dense<T><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(m->nc, m->Ec, A); m->launches++;
+  k_diag_rsqrt<<<grid_blocks((size_t)m->nc, 256, 64), 256, 0, m->s>>>(m->nc, m->Ec, m->gjD); m->launches++;
+  k_scale_dense<T><<<grid_blocks(nn, 256, 4096), 256, 0, m->s>>>(m->nc, m->Ec, m->gjD, A); m->launches++;
   return invert_coarse<T>(m, A, rel);
 }
 
@@ -558,6 +560,7 @@ static int assemble_coarse(afd_mesh* m) {
   if (!m->Ec) {
     TRY(dalloc(&m->Ec, nn));
     TRY(dalloc(&m->gjP, (size_t)GJ_NB * GJ_NB));
+    TRY(dalloc(&m->gjD, (size_t)nc));
     TRY(dalloc(&m->gjB, (size_t)nc * GJ_NB));
     TRY(dalloc(&m->gjR, (size_t)nc * GJ_NB));
     TRY(dalloc(&m->dmax, 1));
@@ -1192,9 +1195,11 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
     return fail(AFD_ERR_CUDA, "stream creation failed");
   }
   if ((rc = dalloc(&m->E64, (size_t)g.nelem)) != AFD_OK || (rc = dalloc(&m->w32.E, (size_t)g.nelem)) != AFD_OK ||
-      (rc = dalloc(&m->w64.E, (size_t)g.nelem)) != AFD_OK || (rc = dalloc(&m->w32.invdiag, (size_t)g.nnodes)) != AFD_OK ||
-      (rc = dalloc(&m->w64.invdiag, (size_t)g.nnodes)) != AFD_OK || (rc = dalloc(&m->fixed, (size_t)(g.nnodes + 3) / 4 * 4)) != AFD_OK ||
-      (rc = dalloc(&m->w32.invd, (size_t)g.vs)) != AFD_OK || (rc = dalloc(&m->w64.invd, (size_t)g.vs)) != AFD_OK ||
+      (rc = dalloc(&m->w32.invdiag, (size_t)g.nnodes)) != AFD_OK ||
+      (rc = dalloc(&m->fixed, (size_t)(g.nnodes + 3) / 4 * 4)) != AFD_OK ||
+      (rc = dalloc(&m->w32.invd, (size_t)g.vs)) != AFD_OK ||
+      (o.precision == AFD_FP64 && (rc = dalloc(&m->w64.invdiag, (size_t)g.nnodes)) != AFD_OK) ||
+      (o.precision == AFD_FP64 && (rc = dalloc(&m->w64.invd, (size_t)g.vs)) != AFD_OK) ||
       (rc = dalloc(&m->fsmall, (size_t)FSMALL_SIZE)) != AFD_OK ||
       (rc = dalloc(&m->counters, (size_t)MAX_RHS + 1)) != AFD_OK ||
       (rc = dalloc(&m->gbox, (size_t)gp.ng * 6)) != AFD_OK ||
@@ -1202,6 +1207,7 @@ int afd_create_mesh(int nx, int ny, int nz, const afd_options* opt, void* cuda_s
     afd_destroy(m);
     return rc;
   }
+  m->w64.E = m->E64;   // the FP64 stencils read the FP64 moduli themselves
   cudaMemsetAsync(m->fixed, 0, (size_t)(g.nnodes + 3) / 4 * 4, m->s);   // padded: read as 4-byte words
   cudaMemsetAsync(m->counters, 0, (MAX_RHS + 1) * sizeof(unsigned int), m->s);
   if (cudaStreamSynchronize(m->s) != cudaSuccess) {
@@ -1227,14 +1233,15 @@ void afd_destroy(afd_mesh* m) {
     auto* wp = &m->w64;
     dfree(wp->x); dfree(wp->r); dfree(wp->z); dfree(wp->p); dfree(wp->q); dfree(wp->t); dfree(wp->b);
     dfree(wp->r2); dfree(wp->AW); dfree(wp->invd);
-    dfree(wp->invdiag); dfree(wp->E);
+    dfree(wp->invdiag);
+    wp->E = nullptr;   // the FP64 moduli themselves (E64)
     if (wp->graph) cudaGraphExecDestroy(wp->graph);
   }
   dfree(m->E64); dfree(m->fixed); dfree(m->f64); dfree(m->u64); dfree(m->partials);
   dfree(m->st); dfree(m->done); dfree(m->v); dfree(m->mu); dfree(m->wr); dfree(m->cpart); dfree(m->fbuf); dfree(m->fkeys); dfree(m->kept);
   if (m->sel) cudaFree(m->sel);
   dfree(m->selcnt); dfree(m->fsmall);
-  dfree(m->Ec); dfree(m->Einv64); dfree(m->Einv32); dfree(m->gjP); dfree(m->gjB); dfree(m->gjR);
+  dfree(m->Ec); dfree(m->Einv64); dfree(m->Einv32); dfree(m->gjP); dfree(m->gjB); dfree(m->gjR); dfree(m->gjD);
   for (auto& g : m->gj_graph)
     if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gbox); dfree(m->aw_off); dfree(m->aw_node);
@@ -1271,12 +1278,13 @@ static int refresh_moduli(afd_mesh* m) {
   const Grid& g = m->gr;
   const size_t ne = g.nelem;
   k_convert<float><<<grid_blocks(ne, 256, 4096), 256, 0, m->s>>>(ne, m->E64, m->w32.E); m->launches++;
-  k_convert<double><<<grid_blocks(ne, 256, 4096), 256, 0, m->s>>>(ne, m->E64, m->w64.E); m->launches++;
   const double d0 = elem_diag(m->opt.nu, m->opt.h);
   k_invdiag<float><<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->E64, d0, m->w32.invdiag); m->launches++;
-  k_invdiag<double><<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->E64, d0, m->w64.invdiag); m->launches++;
   k_expand3<float><<<grid_blocks(g.ndof, 256, 4096), 256, 0, m->s>>>(g.ndof, m->w32.invdiag, m->w32.invd); m->launches++;
-  k_expand3<double><<<grid_blocks(g.ndof, 256, 4096), 256, 0, m->s>>>(g.ndof, m->w64.invdiag, m->w64.invd); m->launches++;
+  if (m->opt.precision == AFD_FP64) {   // the FP64 Jacobi factors serve only the FP64 solver
+    k_invdiag<double><<<grid_blocks(g.nnodes, 256, 4096), 256, 0, m->s>>>(g, m->E64, d0, m->w64.invdiag); m->launches++;
+    k_expand3<double><<<grid_blocks(g.ndof, 256, 4096), 256, 0, m->s>>>(g.ndof, m->w64.invdiag, m->w64.invd); m->launches++;
+  }
   CK(cudaGetLastError());
   m->coarse_valid = false;
   m->has_moduli = true;
@@ -2556,8 +2564,8 @@ size_t afd_mesh_bytes(int nx, int ny, int nz, int n_rhs, const afd_options* opt)
   const bool f64 = o.precision == AFD_FP64;
   const size_t tsz = f64 ? 8 : 4;
   size_t b = 0;
-  b += ne * (8 + 4 + 8) + ne * (4 * (size_t)n_rhs + 4 + 1);        // moduli, fields, keys, kept
-  b += nn * (1 + 4 + 8) + vs * (4 + 8);                             // mask, Jacobi factors
+  b += ne * (8 + 4) + ne * (4 * (size_t)n_rhs + 4 + 1);            // moduli, fields, keys, kept
+  b += nn * (1 + 4 + (f64 ? 8 : 0)) + vs * (4 + (f64 ? 8 : 0));   // mask, Jacobi factors
   b += (size_t)n_rhs * vs * (2 * 8 + 8 * tsz);                      // f, u (FP64) + Krylov work
   b += nc * nc * (8 + tsz) + nc * GJ_NB * 2 * 8 + GJ_NB * GJ_NB * 8; // coarse matrix, inverse, sweep scratch
   if (!f64 && o.coarse_fp64) b += nc * nc * 8;                      // FP64 inverse before its FP32 rounding

@@ -135,29 +135,37 @@ __global__ void k_convert_dense(size_t n, const double* __restrict__ a, T* __res
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) b[i] = (T)a[i];
 }
 
-// b = D^{-1/2} a D^{-1/2} (D = diag a) in type T: the coarse matrix with unit
-// diagonal, so that the inverse does not lose the small rigid modes of groups
-// whose elements are mostly void.  A diagonal <= 0 gives NaN, which the pivot
-// test reports as singular.
+// dinv[i] = 1 / sqrt(a_ii) of a dense FP64 matrix (NaN for a diagonal <= 0).
+__global__ void k_diag_rsqrt(int n, const double* __restrict__ a, double* __restrict__ dinv) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double d = a[(size_t)i * n + i];
+    dinv[i] = d > 0.0 ? 1.0 / sqrt(d) : (double)NAN;
+  }
+}
+
+// b = D^{-1/2} a D^{-1/2} (D = diag a, dinv = its inverse square roots) in
+// type T: the coarse matrix with unit diagonal, so that the inverse does not
+// lose the small rigid modes of groups whose elements are mostly void.  A
+// diagonal <= 0 gives NaN, which the pivot test reports as singular.
 // (n <= 8192, so n * n and the indices fit in 32 bits.)
 template <typename T>
-__global__ void k_scale_dense(int n, const double* __restrict__ a, T* __restrict__ b) {
+__global__ void k_scale_dense(int n, const double* __restrict__ a, const double* __restrict__ dinv,
+                              T* __restrict__ b) {
   const unsigned nn = (unsigned)n * (unsigned)n;
   for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < nn; q += gridDim.x * blockDim.x) {
     const unsigned i = q / (unsigned)n, j = q - i * (unsigned)n;
-    const double di = a[(size_t)i * n + i], dj = a[(size_t)j * n + j];
-    b[q] = (di > 0.0 && dj > 0.0) ? (T)(a[q] / sqrt(di * dj)) : (T)NAN;
+    b[q] = (T)(a[q] * dinv[i] * dinv[j]);
   }
 }
 
 // b <- D^{-1/2} b D^{-1/2}: the inverse of the scaled matrix back to the
 // inverse of a.
 template <typename T>
-__global__ void k_unscale_dense(int n, const double* __restrict__ a, T* __restrict__ b) {
+__global__ void k_unscale_dense(int n, const double* __restrict__ dinv, T* __restrict__ b) {
   const unsigned nn = (unsigned)n * (unsigned)n;
   for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < nn; q += gridDim.x * blockDim.x) {
     const unsigned i = q / (unsigned)n, j = q - i * (unsigned)n;
-    b[q] = (T)((double)b[q] / sqrt(a[(size_t)i * n + i] * a[(size_t)j * n + j]));
+    b[q] = (T)((double)b[q] * dinv[i] * dinv[j]);
   }
 }
 
