@@ -84,7 +84,7 @@ typedef struct {
                          (each may be scheduled while its predecessor finishes its reductions); 0 (default):
                          plain stream order, measured faster on the 128x64x64 workload */
   double inner_aim;   /* AFD_MIXED: each inner solve aims at inner_aim * rel_tol in the true relative residual
-                         (not below inner_tol); default 0.5, in (0, 1) */
+                         (not below inner_tol); default 0.7, in (0, 1) */
   int coarse_fp64;    /* AFD_MIXED: 1 builds W^T K W from FP64 element products and inverts it in FP64 (its
                          FP32 rounding is applied in the FP32 inner iterations); 0 (default) builds it from
                          FP32 element products summed in FP64 and inverts it in FP32 (same inner iteration

@@ -1117,7 +1117,7 @@ void afd_default_options(afd_options* o) {
   o->stencil_warps = 0;
   o->stencil_planes = 0;
   o->pdl = 0;
-  o->inner_aim = 0.5;
+  o->inner_aim = 0.7;
   o->coarse_fp64 = 0;
   o->residual_fp64 = 0;
 }
