@@ -151,6 +151,9 @@ struct afd_mesh {
   long long* aw_off = nullptr; // [N_g + 1] offset of group G's block in AW (last: total)
   int* aw_node = nullptr;      // [aw_total / 18] node index of every shell slot
   uint4* cut = nullptr;        // records of every group's cut elements (k_build_cut_recs); null: decoded per use
+  double* cpart_c = nullptr;   // [N_g][shares][36] partial sums of the coarse diagonal blocks (k_coarse_cut)
+  size_t cpart_c_cap = 0;
+  unsigned int* ccount = nullptr;  // [N_g] share counters of k_coarse_cut
   long long* cut_off = nullptr;  // [N_g + 1] offset of group G's records
   size_t cut_cap = 0;
   double* grec = nullptr;      // [rhs][N_g][12] per-group records of the coarse right-hand side
@@ -567,6 +570,31 @@ static int assemble_coarse(afd_mesh* m) {
     TRY(dalloc(&m->dstatus, 1));
   }
   CK(cudaMemsetAsync(m->Ec, 0, nn * sizeof(double), m->s));
+  if (m->cut) {
+    // from the cut-element records: E_GG in nself shares, the 13 neighbours after G with their transposes
+    const int nself = std::max(1, std::min(16, m->gp.g / 2));
+    const size_t need = (size_t)m->gp.ng * nself * 36;
+    if (need > m->cpart_c_cap) {
+      dfree(m->cpart_c);
+      m->cpart_c_cap = 0;
+      TRY(dalloc(&m->cpart_c, need));
+      m->cpart_c_cap = need;
+    }
+    if (!m->ccount) {
+      TRY(dalloc(&m->ccount, (size_t)m->gp.ng));
+      CK(cudaMemsetAsync(m->ccount, 0, (size_t)m->gp.ng * sizeof(unsigned int), m->s));
+    }
+    const dim3 cg(m->gp.ng, nself + 13);
+    if (m->opt.coarse_fp64)
+      k_coarse_cut<double><<<cg, COARSE_THREADS, 0, m->s>>>(m->gr, m->gp, nself, m->cut, m->cut_off, m->E64,
+                                                             m->w64.K, m->Ec, m->cpart_c, m->ccount);
+    else
+      k_coarse_cut<float><<<cg, COARSE_THREADS, 0, m->s>>>(m->gr, m->gp, nself, m->cut, m->cut_off, m->E64,
+                                                            m->w32.K, m->Ec, m->cpart_c, m->ccount);
+    m->launches++;
+    CK(cudaGetLastError());
+    return AFD_OK;
+  }
   const dim3 grid(m->gp.ng, 27);
   if (m->opt.precision == AFD_FP64 || m->opt.coarse_fp64) {
     k_coarse_block<double><<<grid, COARSE_THREADS, 0, m->s>>>(m->gr, m->gp, m->E64, m->fixed, m->w64.K, m->Ec); m->launches++;
@@ -1245,7 +1273,7 @@ void afd_destroy(afd_mesh* m) {
   for (auto& g : m->gj_graph)
     if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   dfree(m->dmax); dfree(m->dstatus); dfree(m->counters); dfree(m->gbox); dfree(m->aw_off); dfree(m->aw_node);
-  dfree(m->cut); dfree(m->cut_off);
+  dfree(m->cut); dfree(m->cut_off); dfree(m->cpart_c); dfree(m->ccount);
   dfree(m->grec); dfree(m->gcount); dfree(m->upart); dfree(m->updred);
   dfree(m->ppart); dfree(m->prec); dfree(m->gbar); dfree(m->ptime);
   dfree(m->lam64); dfree(m->gadj); dfree(m->dsig); dfree(m->pn_d); dfree(m->lsbuf);

@@ -120,6 +120,148 @@ k_coarse_block(Grid gr, Groups gp, const double* __restrict__ Emod, const uint8_
   }
 }
 
+// The same blocks from the cut-element records of each group G (the shells
+// of the coarse right-hand side: k_build_cut_recs).  Every element that
+// couples G with a neighbour H, or on which W_G is not a rigid motion, is one
+// of G's records.  Blocks:
+//   blockIdx.y < nself: a share of E_GG, its 36 sums left in part[G][share];
+//     the group's last share adds the shares in order (deterministic);
+//   blockIdx.y = nself + s: E_GH for the neighbour slot 14 + s (the 13
+//     neighbours after G in group order), written with its transpose E_HG.
+// Element math in TC, per-thread sums in TC, block sums in FP64, as in
+// k_coarse_block.
+template <typename TC>
+__global__ void __launch_bounds__(COARSE_THREADS)
+k_coarse_cut(Grid gr, Groups gp, int nself, const uint4* __restrict__ cut, const long long* __restrict__ cut_off,
+             const double* __restrict__ Emod, ElemConsts<TC> K, double* __restrict__ Ec, double* __restrict__ part,
+             unsigned int* __restrict__ counter) {
+  __shared__ double red[32 * 36];
+  __shared__ bool s_last;
+  const int G = blockIdx.x, y = blockIdx.y;
+  const bool self = y < nself;
+  const int slot = self ? 13 : 14 + (y - nself);
+  const int Gx = G % gp.ngx, Gy = (G / gp.ngx) % gp.ngy, Gz = G / (gp.ngx * gp.ngy);
+  const int Hx = Gx + slot % 3 - 1, Hy = Gy + (slot / 3) % 3 - 1, Hz = Gz + slot / 9 - 1;
+  if (Hx < 0 || Hy < 0 || Hz < 0 || Hx >= gp.ngx || Hy >= gp.ngy || Hz >= gp.ngz) return;
+  const int H = Hx + gp.ngx * (Hy + gp.ngy * Hz);
+  auto lohi = [&](int X, int ng, int n, int& lo, int& hi) {
+    lo = gp.g * X;
+    hi = (X == ng - 1) ? n : gp.g * X + gp.g - 1;
+  };
+  int gxl, gxh, gyl, gyh, gzl, gzh, hxl, hxh, hyl, hyh, hzl, hzh;
+  lohi(Gx, gp.ngx, gr.nx, gxl, gxh); lohi(Gy, gp.ngy, gr.ny, gyl, gyh); lohi(Gz, gp.ngz, gr.nz, gzl, gzh);
+  lohi(Hx, gp.ngx, gr.nx, hxl, hxh); lohi(Hy, gp.ngy, gr.ny, hyl, hyh); lohi(Hz, gp.ngz, gr.nz, hzl, hzh);
+  const TC cgx = (TC)(0.5 * gp.h * (gxl + gxh)), cgy = (TC)(0.5 * gp.h * (gyl + gyh)), cgz = (TC)(0.5 * gp.h * (gzl + gzh));
+  const TC chx = (TC)(0.5 * gp.h * (hxl + hxh)), chy = (TC)(0.5 * gp.h * (hyl + hyh)), chz = (TC)(0.5 * gp.h * (hzl + hzh));
+  const TC hh = (TC)gp.h;
+  const long long base = cut_off[G];
+  const int cnt = (int)(cut_off[G + 1] - base);
+  int tb = 0, te = cnt;
+  if (self) {
+    const int per = (cnt + nself - 1) / nself;
+    tb = y * per;
+    te = min(tb + per, cnt);
+  }
+  TC acc[36];
+#pragma unroll
+  for (int q = 0; q < 36; ++q) acc[q] = TC(0);
+  for (int t = tb + threadIdx.x; t < te; t += blockDim.x) {
+    const uint4 rec = cut[base + t];
+    const int ei = gxl - 1 + (int)(rec.z & 1023u), ej = gyl - 1 + (int)((rec.z >> 10) & 1023u),
+              ek = gzl - 1 + (int)((rec.z >> 20) & 1023u);
+    const unsigned ing = rec.w >> 24, fbits = rec.w & 0xFFFFFFu;
+    unsigned inh = ing;
+    if (!self) {
+      inh = 0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int i = ei + (a & 1), j = ej + ((a >> 1) & 1), k = ek + ((a >> 2) & 1);
+        if (i >= hxl && i <= hxh && j >= hyl && j <= hyh && k >= hzl && k <= hzh) inh |= 1u << a;
+      }
+      if (!inh) continue;
+    }
+    const TC Ee = (TC)Emod[rec.y];
+#pragma unroll 1
+    for (int col = 0; col < 6; ++col) {
+      TC v[3][8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const TC rx = hh * (TC)(ei + (a & 1)) - chx;
+        const TC ry = hh * (TC)(ej + ((a >> 1) & 1)) - chy;
+        const TC rz = hh * (TC)(ek + ((a >> 2) & 1)) - chz;
+        TC w0 = 0, w1 = 0, w2 = 0;
+        if (col == 0) w0 = 1;
+        else if (col == 1) w1 = 1;
+        else if (col == 2) w2 = 1;
+        else if (col == 3) { w1 = -rz; w2 = ry; }    // e_x x r
+        else if (col == 4) { w0 = rz; w2 = -rx; }    // e_y x r
+        else { w0 = -ry; w1 = rx; }                  // e_z x r
+        const unsigned fb = (fbits >> (3 * a)) & 7u;
+        const bool h_a = (inh >> a) & 1u;
+        v[0][a] = (h_a && !(fb & 1)) ? w0 : TC(0);
+        v[1][a] = (h_a && !(fb & 2)) ? w1 : TC(0);
+        v[2][a] = (h_a && !(fb & 4)) ? w2 : TC(0);
+      }
+      hex8_apply(v, Ee, K);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        if (!((ing >> a) & 1u)) continue;
+        const unsigned fb = (fbits >> (3 * a)) & 7u;
+        const TC fx = (fb & 1) ? TC(0) : v[0][a];
+        const TC fy = (fb & 2) ? TC(0) : v[1][a];
+        const TC fz = (fb & 4) ? TC(0) : v[2][a];
+        const TC rx = hh * (TC)(ei + (a & 1)) - cgx;
+        const TC ry = hh * (TC)(ej + ((a >> 1) & 1)) - cgy;
+        const TC rz = hh * (TC)(ek + ((a >> 2) & 1)) - cgz;
+        TC* o = acc;  // o[r * 6 + col]
+        switch (col) {
+#define AFD_ACC(C)                                   \
+  case C:                                            \
+    o[0 * 6 + C] += fx;                              \
+    o[1 * 6 + C] += fy;                              \
+    o[2 * 6 + C] += fz;                              \
+    o[3 * 6 + C] += ry * fz - rz * fy;               \
+    o[4 * 6 + C] += rz * fx - rx * fz;               \
+    o[5 * 6 + C] += rx * fy - ry * fx;               \
+    break;
+          AFD_ACC(0) AFD_ACC(1) AFD_ACC(2) AFD_ACC(3) AFD_ACC(4) AFD_ACC(5)
+#undef AFD_ACC
+        }
+      }
+    }
+  }
+  double o[36];
+  block_sum_to_f64<36>(acc, red, o);
+  const int nc = 6 * gp.ng;
+  if (!self) {
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < 36; ++q) {
+        Ec[(size_t)(6 * G + q / 6) * nc + 6 * H + q % 6] = o[q];
+        Ec[(size_t)(6 * H + q % 6) * nc + 6 * G + q / 6] = o[q];
+      }
+    }
+    return;
+  }
+  double* mine = part + ((size_t)G * nself + y) * 36;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 36; ++q) mine[q] = o[q];
+    __threadfence();
+    s_last = atomicAdd(&counter[G], 1u) == (unsigned)nself - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 36) {
+    const double* pp = part + (size_t)G * nself * 36;
+    double v = 0.0;
+    for (int s2 = 0; s2 < nself; ++s2) v += pp[s2 * 36 + threadIdx.x];
+    Ec[(size_t)(6 * G + threadIdx.x / 6) * nc + 6 * G + threadIdx.x % 6] = v;
+  }
+  if (threadIdx.x == 0) counter[G] = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // Dense inverse of the SPD coarse matrix by blocked Gauss-Jordan sweeps:
 // sweeping block K replaces A_KK by -A_KK^{-1}, A_iK by A_iK A_KK^{-1},
