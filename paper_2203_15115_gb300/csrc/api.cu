@@ -985,11 +985,12 @@ static int launch_persistent(afd_mesh* m, Work<float>& w, float* x, int nrhs, in
 }
 
 // ---------------------------------------------------------------------------
-// deflated PCG (Sec. 3.5) in type T on K x = b; x holds the initial guess.
+// deflated PCG (Sec. 3.5) in type T on K x = b; x holds the initial guess
+// (x_zero: the caller zeroed it, so the first residual is b itself).
 // Per-RHS stop: r.r <= target2[r]; RHS with active[r] == 0 are skipped.
 // ---------------------------------------------------------------------------
 template <typename T, typename TB>
-static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std::vector<double>& target2,
+static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, bool x_zero, int nrhs, const std::vector<double>& target2,
                 const std::vector<int>& active, int max_iters, std::vector<CGState>& out) {
   constexpr bool F64 = sizeof(T) == 8;
   const Grid& gr = m->gr;
@@ -1017,9 +1018,16 @@ static int dpcg(afd_mesh* m, Work<T>& w, const TB* b, T* x, int nrhs, const std:
   unsigned int* cnt_co = m->counters + MAX_RHS;  // coarse step
   T* P[2] = {w.p, w.t};
   const dim3 vg(RED_BLOCKS, nrhs);
-  // r = b - K x ; x += W Einv W^T r ; r = b - K x  (deflated start)
-  TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, w.r, w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
-  k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, w.r, nullptr, m->fixed, m->v, nullptr, m->st); m->launches++;
+  // r = b - K x ; x += W Einv W^T r ; r = b - K x  (deflated start); for x = 0 the first r is b itself
+  if constexpr (std::is_same<T, TB>::value) {
+    if (x_zero) {
+      k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, b, nullptr, m->fixed, m->v, nullptr, m->st); m->launches++;
+    }
+  }
+  if (!x_zero || !std::is_same<T, TB>::value) {
+    TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, w.r, w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
+    k_restrict<T><<<gg, 256, 0, m->s>>>(gr, m->gp, w.r, nullptr, m->fixed, m->v, nullptr, m->st); m->launches++;
+  }
   k_coarse_solve<T><<<(m->nc * 32 + 255) / 256, 256, 0, m->s>>>(m->nc, nrhs, Einv, m->v, m->mu, m->st); m->launches++;
   k_prolong<T><<<pg, 256, 0, m->s>>>(2, gr, m->gp, x, nullptr, m->mu, m->fixed, m->st); m->launches++;
   TRY((launch_stencil<T, ST_RESIDUAL, TB>(m, x, w.r, w.E, b, nullptr, m->partials, m->done, nrhs, w.K)));
@@ -1473,7 +1481,7 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
       // the recursive residual drifts from the true one: aim 10% below the tolerance
     for (int r = 0; r < R; ++r) t2[r] = (0.9 * rel_tol * m->fnorm[r]) * (0.9 * rel_tol * m->fnorm[r]);
     std::vector<CGState> st;
-    TRY((dpcg<double, double>(m, m->w64, m->f64, m->u64, R, t2, act, m->opt.max_iter, st)));
+    TRY((dpcg<double, double>(m, m->w64, m->f64, m->u64, cold, R, t2, act, m->opt.max_iter, st)));
     for (int r = 0; r < R; ++r) {
       iters[r] = st[r].iters;
       status[r] = st[r].status;
@@ -1519,7 +1527,7 @@ int afd_solve(afd_mesh* m, double rel_tol, int warm_start, afd_stats* per_rhs, d
       std::vector<CGState> st;
       int budget = m->opt.max_iter;
       for (int r = 0; r < R; ++r) if (act[r]) budget = std::min(budget, std::max(1, m->opt.max_iter - iters[r]));
-      TRY((dpcg<float, float>(m, m->w32, b32, m->w32.x, R, t2, act, budget, st)));
+      TRY((dpcg<float, float>(m, m->w32, b32, m->w32.x, true, R, t2, act, budget, st)));
       std::vector<int> skip(R);
       for (int r = 0; r < R; ++r) {
         skip[r] = !act[r];
