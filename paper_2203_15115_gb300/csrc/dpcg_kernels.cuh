@@ -12,7 +12,7 @@ namespace afd {
 
 constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs: grid of the vector kernels
 constexpr int RED_THREADS = 256;
-constexpr int CSTEP_THREADS = 128;  // threads of a coarse-step block: one warp per row of the inverse
+constexpr int CSTEP_THREADS = 256;  // threads of a coarse-step block: one warp per row of the inverse (measured against 64 and 128)
 
 // Per-RHS scalar state of the (inner) deflated PCG.
 struct CGState {
