@@ -1795,8 +1795,14 @@ static int lobpcg(afd_mesh* m, EigKind kind, int n_modes, int kp, double tol, in
   std::vector<double> V;
   auto images = [&](const double* Xs, double* AXs, double* BXs) -> int {   // A and B of kp rows
     double* KXs = kind == EIG_MODAL ? AXs : BXs;
-    TRY((launch_stencil<double, ST_APPLY, double>(m, Xs, KXs, m->w64.E, nullptr, nullptr, nullptr, nullptr, kp,
-                                                    m->w64.K)));
+    // K X from the FP64 block: in double-float arithmetic on mixed meshes (a few 2^-44 of the element forces,
+    // on the FP32 pipes), in FP64 on FP64 meshes
+    if (m->opt.precision == AFD_MIXED)
+      TRY((launch_stencil<double, ST_APPLY, double, dfloat>(m, Xs, KXs, m->w64.E, nullptr, nullptr, nullptr, nullptr,
+                                                              kp, m->w64.K)));
+    else
+      TRY((launch_stencil<double, ST_APPLY, double>(m, Xs, KXs, m->w64.E, nullptr, nullptr, nullptr, nullptr, kp,
+                                                      m->w64.K)));
     if (kind == EIG_MODAL) {
       k_mass_apply<<<vgrid, 256, 0, m->s>>>(g.ndof, g.vs, m->mmass, Xs, BXs); m->launches++;
     } else {
